@@ -1,0 +1,316 @@
+/*
+ * pt_oracle.c -- plain CPU oracle for Metropolis-Hastings with Parallel Tempering on the
+ * periodic two-dimensional Ising model (arXiv 2512.03825: Sec. 2.1 Eq. 1, Sec. 2.2 Eqs. 2-3,
+ * Sec. 3 replica scheduling and swap rule).
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the slow, obviously-correct definition that the
+ * CUDA library is compared against bit for bit. Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it. It shares no code, header or table generator with
+ * the CUDA library: Philox, the quantiser and both threshold formulas are written here again.
+ *
+ * State: one int8 spin (+1 / -1) per site and per temperature index, spin[k][y][x].
+ * Replica k always runs at temperature index k (inverse temperature beta[k]); an accepted
+ * exchange swaps the two configurations, as Sec. 2.1 describes ("swapping the state").
+ * chain[k] records which initial chain currently sits at temperature k (diagnostic only).
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key = the 64-bit seed.
+ *   initial spin  (site i, temperature k): ctr = {i, 0, k>>2, TAG_INIT}        word k&3, bit 31
+ *   spin update   (site i, temp k, sweep t): ctr = {i, lo32(t), k>>2, TAG_SPIN|hi32(t)<<8} word k&3
+ *   exchange      (pair k, exchange e):      ctr = {k, lo32(e), 0, TAG_EXCH|hi32(e)<<8}   word 0
+ * The paper fixes no generator; the counter layout is this framework's choice and the CUDA
+ * library uses the same one. Nothing here is blocked, fused or reordered for speed.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_OK 0
+#define ORACLE_EINVAL (-1)
+#define ORACLE_ENOMEM (-2)
+
+#define TAG_SPIN 0u
+#define TAG_EXCH 1u
+#define TAG_INIT 2u
+
+/* ---------------------------------------------------------------------------------------
+ * Philox4x32-10, written from the definition in Salmon et al., "Parallel Random Numbers: As
+ * Easy as 1, 2, 3" (SC'11): ten rounds of two 32x32->64 multiplications whose halves are
+ * xored with the other counter words and the round key; the key is bumped by the Weyl
+ * constants between rounds.
+ * ------------------------------------------------------------------------------------- */
+static const uint32_t PHILOX_M0 = 0xD2511F53u, PHILOX_M1 = 0xCD9E8D57u;
+static const uint32_t PHILOX_W0 = 0x9E3779B9u, PHILOX_W1 = 0xBB67AE85u;
+
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        if (round < 9) { k0 += PHILOX_W0; k1 += PHILOX_W1; }
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static uint32_t philox_word(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                            int word) {
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    oracle_philox4x32_10(ctr, key, out);
+    return out[word];
+}
+
+/* ---------------------------------------------------------------------------------------
+ * Energy quantisation. Eq. 3 is evaluated in integers: s is the smallest integer in
+ * 1..1000 for which s*J and s*h are both within 1e-9 of integers; J_int = round(s*J),
+ * h_int = round(s*h), and s*E(sigma) = E_int(sigma) exactly. (The paper works in floating
+ * point and says nothing about this; the integer form makes every decision exact.)
+ * ------------------------------------------------------------------------------------- */
+int oracle_quantise(double J, double h, int64_t* s_out, int64_t* J_int, int64_t* h_int) {
+    if (!isfinite(J) || !isfinite(h)) return ORACLE_EINVAL;
+    for (int64_t s = 1; s <= 1000; ++s) {
+        double sj = (double)s * J, sh = (double)s * h;
+        double rj = nearbyint(sj), rh = nearbyint(sh);
+        if (fabs(sj - rj) <= 1e-9 && fabs(sh - rh) <= 1e-9) {
+            if (fabs(rj) > 1048576.0 || fabs(rh) > 1048576.0) return ORACLE_EINVAL;
+            *s_out = s;
+            *J_int = (int64_t)rj;
+            *h_int = (int64_t)rh;
+            return ORACLE_OK;
+        }
+    }
+    return ORACLE_EINVAL;
+}
+
+/* Metropolis acceptance threshold (Eq. 1 with the Boltzmann target of Eq. 2, k_B = 1):
+ * a trial that raises the energy by dE (= dE_int / s) is accepted with probability
+ * exp(-beta * dE). With a 32-bit uniform integer u the test is u < T where
+ * T = floor(2^32 * exp(-(beta * dE_int) / s)). dE_int <= 0 is always accepted: T = 2^32.
+ * Returned in [0, 2^32]. */
+uint64_t oracle_spin_threshold(double beta, int64_t dE_int, int64_t s) {
+    if (dE_int <= 0) return 4294967296ull;
+    double x = (beta * (double)dE_int) / (double)s;
+    return (uint64_t)floor(4294967296.0 * exp(-x));
+}
+
+/* Replica-exchange threshold (Sec. 3, the Barker-form swap probability
+ * e^{x} / (1 + e^{x}) with x = (beta_lo - beta_hi)(E_lo - E_hi), which equals
+ * 1 / (1 + e^{y}) with y = (beta_hi - beta_lo) * n / s, n = E_int(lo) - E_int(hi)).
+ * Accept iff u < S. Products y above 44 are always rejected (S = 0) and below -44 always
+ * accepted (S = 2^32); in between S = floor(2^32 / (1 + exp(y))). Returned in [0, 2^32]. */
+uint64_t oracle_swap_threshold(double beta_lo, double beta_hi, int64_t n, int64_t s) {
+    double y = ((beta_hi - beta_lo) * (double)n) / (double)s;
+    if (y > 44.0) return 0;
+    if (y < -44.0) return 4294967296ull;
+    return (uint64_t)floor(4294967296.0 / (1.0 + exp(y)));
+}
+
+/* --------------------------------------------------------------------------------------- */
+
+typedef struct oracle_pt {
+    int L, R;
+    double* beta;     /* [R], by temperature index */
+    int64_t s, J_int, h_int;
+    uint64_t seed;
+    int8_t* spin;     /* [R][L][L] */
+    int32_t* chain;   /* [R] */
+    uint64_t t, e;    /* sweeps done, exchanges done */
+    uint64_t* attempted; /* [R-1] */
+    uint64_t* accepted;  /* [R-1] */
+} oracle_pt;
+
+static int threads_wanted = 1;
+void oracle_set_threads(int n) { threads_wanted = n < 1 ? 1 : n; }
+int oracle_get_threads(void) { return threads_wanted; }
+
+static int8_t* lattice(const oracle_pt* p, int k) { return p->spin + (size_t)k * p->L * p->L; }
+
+void oracle_destroy(oracle_pt* p) {
+    if (!p) return;
+    free(p->beta); free(p->spin); free(p->chain); free(p->attempted); free(p->accepted);
+    free(p);
+}
+
+/* Initialisation phase (Sec. 3: build the data structures): every spin of every replica is
+ * drawn uniformly from {-1, +1} with the TAG_INIT stream; chains start in temperature order. */
+int oracle_create(int L, const double* betas, int R, double J, double h, uint64_t seed,
+                  oracle_pt** out) {
+    *out = NULL;
+    if (L < 4 || L > 16384 || (L & 1) || R < 1 || R > 2048 || !betas) return ORACLE_EINVAL;
+    for (int k = 0; k < R; ++k)
+        if (!isfinite(betas[k]) || betas[k] < 0.0) return ORACLE_EINVAL;
+    oracle_pt* p = (oracle_pt*)calloc(1, sizeof(oracle_pt));
+    if (!p) return ORACLE_ENOMEM;
+    if (oracle_quantise(J, h, &p->s, &p->J_int, &p->h_int) != ORACLE_OK) { free(p); return ORACLE_EINVAL; }
+    p->L = L; p->R = R; p->seed = seed;
+    p->beta = (double*)malloc(sizeof(double) * R);
+    p->spin = (int8_t*)malloc((size_t)R * L * L);
+    p->chain = (int32_t*)malloc(sizeof(int32_t) * R);
+    p->attempted = (uint64_t*)calloc(R, sizeof(uint64_t));
+    p->accepted = (uint64_t*)calloc(R, sizeof(uint64_t));
+    if (!p->beta || !p->spin || !p->chain || !p->attempted || !p->accepted) {
+        oracle_destroy(p); return ORACLE_ENOMEM;
+    }
+    memcpy(p->beta, betas, sizeof(double) * R);
+    for (int k = 0; k < R; ++k) {
+        p->chain[k] = k;
+        int8_t* sp = lattice(p, k);
+        for (int y = 0; y < L; ++y)
+            for (int x = 0; x < L; ++x) {
+                uint32_t i = (uint32_t)(y * L + x);
+                uint32_t u = philox_word(seed, i, 0u, (uint32_t)(k >> 2), TAG_INIT, k & 3);
+                sp[y * L + x] = (u >> 31) ? (int8_t)1 : (int8_t)-1;
+            }
+    }
+    *out = p;
+    return ORACLE_OK;
+}
+
+/* Eq. 3 in integers: E_int = h_int * sum_i sigma_i - J_int * sum_<ij> sigma_i sigma_j, each of
+ * the 2 L^2 nearest-neighbour bonds of the periodic lattice counted once (right and down). */
+int64_t oracle_energy_int(const oracle_pt* p, int k) {
+    const int L = p->L;
+    const int8_t* sp = lattice(p, k);
+    int64_t field = 0, bonds = 0;
+    for (int y = 0; y < L; ++y)
+        for (int x = 0; x < L; ++x) {
+            int s = sp[y * L + x];
+            int right = sp[y * L + (x + 1) % L];
+            int down = sp[((y + 1) % L) * L + x];
+            field += s;
+            bonds += s * right + s * down;
+        }
+    return p->h_int * field - p->J_int * bonds;
+}
+
+int64_t oracle_magnetisation(const oracle_pt* p, int k) {
+    const int8_t* sp = lattice(p, k);
+    int64_t m = 0;
+    for (size_t i = 0; i < (size_t)p->L * p->L; ++i) m += sp[i];
+    return m;
+}
+
+/* One single-spin Metropolis trial at site (x, y) of replica k in sweep t (Sec. 2.1, Eq. 1):
+ * the trial state flips sigma; Delta E from Eq. 3 is 2 sigma (J * sum_nb sigma_nb - h); the
+ * trial is accepted when u < T(beta_k, Delta E). */
+static void metropolis_site(oracle_pt* p, int k, int x, int y) {
+    const int L = p->L;
+    int8_t* sp = lattice(p, k);
+    int s = sp[y * L + x];
+    int nb = sp[y * L + (x + 1) % L] + sp[y * L + (x + L - 1) % L] +
+             sp[((y + 1) % L) * L + x] + sp[((y + L - 1) % L) * L + x];
+    int64_t dE_int = 2 * (int64_t)s * (p->J_int * nb - p->h_int);
+    if (dE_int <= 0) { sp[y * L + x] = (int8_t)-s; return; }
+    uint32_t i = (uint32_t)(y * L + x);
+    uint32_t u = philox_word(p->seed, i, (uint32_t)p->t, (uint32_t)(k >> 2),
+                             TAG_SPIN | ((uint32_t)(p->t >> 32) << 8), k & 3);
+    if ((uint64_t)u < oracle_spin_threshold(p->beta[k], dE_int, p->s)) sp[y * L + x] = (int8_t)-s;
+}
+
+/* One sweep: every site gets one trial. Sites are visited colour by colour on the
+ * checkerboard (colour 0 = (x + y) even, then colour 1); sites of one colour have no common
+ * bond, so their trials are independent and their order does not matter. */
+static void sweep_once(oracle_pt* p) {
+    const int L = p->L, R = p->R;
+    for (int colour = 0; colour < 2; ++colour) {
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(threads_wanted) schedule(static) collapse(2)
+#endif
+        for (int k = 0; k < R; ++k)
+            for (int y = 0; y < L; ++y)
+                for (int x = (y + colour) & 1; x < L; x += 2) metropolis_site(p, k, x, y);
+    }
+    p->t += 1;
+}
+
+static void swap_replicas(oracle_pt* p, int a, int b) {
+    size_t n = (size_t)p->L * p->L;
+    int8_t* sa = lattice(p, a);
+    int8_t* sb = lattice(p, b);
+    for (size_t i = 0; i < n; ++i) { int8_t t = sa[i]; sa[i] = sb[i]; sb[i] = t; }
+    int32_t c = p->chain[a]; p->chain[a] = p->chain[b]; p->chain[b] = c;
+}
+
+/* Swap iteration (Sec. 3): neighbours only, each replica at most once; the first swap
+ * iteration pairs (0,1),(2,3),..., the next (1,2),(3,4),..., alternating. */
+static void exchange_once(oracle_pt* p) {
+    const int R = p->R;
+    int parity = (int)(p->e & 1);
+    for (int k = parity; k + 1 < R; k += 2) {
+        int64_t n = oracle_energy_int(p, k) - oracle_energy_int(p, k + 1);
+        uint64_t S = oracle_swap_threshold(p->beta[k], p->beta[k + 1], n, p->s);
+        uint32_t u = philox_word(p->seed, (uint32_t)k, (uint32_t)p->e, 0u,
+                                 TAG_EXCH | ((uint32_t)(p->e >> 32) << 8), 0);
+        p->attempted[k] += 1;
+        if ((uint64_t)u < S) {
+            p->accepted[k] += 1;
+            swap_replicas(p, k, k + 1);
+        }
+    }
+    p->e += 1;
+}
+
+/* Execution phase (Sec. 3, interval scheduling): n sweeps; with m > 0 a swap iteration follows
+ * every sweep after which the total number of sweeps done since creation is a multiple of m.
+ * m = 0 runs without swaps. */
+int oracle_sweep(oracle_pt* p, int64_t n, int m) {
+    if (!p || n < 0 || m < 0) return ORACLE_EINVAL;
+    for (int64_t j = 0; j < n; ++j) {
+        sweep_once(p);
+        if (m > 0 && p->t % (uint64_t)m == 0) exchange_once(p);
+    }
+    return ORACLE_OK;
+}
+
+/* Same as oracle_sweep, recording E_int and M of every temperature after each sweep (after
+ * that sweep's swap iteration, if any): E_out and M_out are [n][R]. */
+int oracle_trace(oracle_pt* p, int64_t n, int m, int64_t* E_out, int64_t* M_out) {
+    if (!p || n < 0 || m < 0) return ORACLE_EINVAL;
+    for (int64_t j = 0; j < n; ++j) {
+        sweep_once(p);
+        if (m > 0 && p->t % (uint64_t)m == 0) exchange_once(p);
+        for (int k = 0; k < p->R; ++k) {
+            if (E_out) E_out[j * p->R + k] = oracle_energy_int(p, k);
+            if (M_out) M_out[j * p->R + k] = oracle_magnetisation(p, k);
+        }
+    }
+    return ORACLE_OK;
+}
+
+int64_t oracle_scale(const oracle_pt* p) { return p->s; }
+
+int oracle_get_spins(const oracle_pt* p, int k, int8_t* out) {
+    if (!p || k < 0 || k >= p->R || !out) return ORACLE_EINVAL;
+    memcpy(out, lattice(p, k), (size_t)p->L * p->L);
+    return ORACLE_OK;
+}
+
+int oracle_set_spins(oracle_pt* p, int k, const int8_t* in) {
+    if (!p || k < 0 || k >= p->R || !in) return ORACLE_EINVAL;
+    for (size_t i = 0; i < (size_t)p->L * p->L; ++i)
+        if (in[i] != 1 && in[i] != -1) return ORACLE_EINVAL;
+    memcpy(lattice(p, k), in, (size_t)p->L * p->L);
+    return ORACLE_OK;
+}
+
+void oracle_chain_map(const oracle_pt* p, int32_t* out) { memcpy(out, p->chain, sizeof(int32_t) * p->R); }
+
+void oracle_swap_stats(const oracle_pt* p, uint64_t* attempted, uint64_t* accepted) {
+    if (p->R < 2) return;
+    if (attempted) memcpy(attempted, p->attempted, sizeof(uint64_t) * (p->R - 1));
+    if (accepted) memcpy(accepted, p->accepted, sizeof(uint64_t) * (p->R - 1));
+}
+
+void oracle_counters(const oracle_pt* p, uint64_t* t, uint64_t* e) { *t = p->t; *e = p->e; }
