@@ -8,15 +8,16 @@
  * benchmark's CPU-baseline leg may load it. It shares no code, header or table generator with
  * the CUDA library: Philox, the quantiser and both threshold formulas are written here again.
  *
- * State: one int8 spin (+1 / -1) per site and per temperature index, spin[k][y][x].
- * Replica k always runs at temperature index k (inverse temperature beta[k]); an accepted
- * exchange swaps the two configurations, as Sec. 2.1 describes ("swapping the state").
- * chain[k] records which initial chain currently sits at temperature k (diagnostic only).
+ * State: one int8 spin (+1 / -1) per site and per replica slot, spin[r][y][x]. Replica r
+ * keeps its configuration in slot r for the whole run and samples at temperature index
+ * temp_of_slot[r] (inverse temperature beta[temp_of_slot[r]]); slot_of_temp[] is the inverse
+ * permutation. An accepted exchange between temperatures k and k+1 swaps their slots in these
+ * two maps, which is the same Markov chain as swapping the two configurations (Sec. 2.1).
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key = the 64-bit seed.
- *   initial spin  (site i, temperature k): ctr = {i, 0, k>>2, TAG_INIT}        word k&3, bit 31
- *   spin update   (site i, temp k, sweep t): ctr = {i, lo32(t), k>>2, TAG_SPIN|hi32(t)<<8} word k&3
- *   exchange      (pair k, exchange e):      ctr = {k, lo32(e), 0, TAG_EXCH|hi32(e)<<8}   word 0
+ *   initial spin  (site i, slot r):           ctr = {i, 0, r>>2, TAG_INIT}                word r&3, bit 31
+ *   spin update   (site i, slot r, sweep t):  ctr = {i, lo32(t), r>>2, TAG_SPIN|hi32(t)<<8} word r&3
+ *   exchange      (pair k, exchange e):       ctr = {k, lo32(e), 0, TAG_EXCH|hi32(e)<<8}   word 0
  * The paper fixes no generator; the counter layout is this framework's choice and the CUDA
  * library uses the same one. Nothing here is blocked, fused or reordered for speed.
  */
@@ -124,8 +125,9 @@ typedef struct oracle_pt {
     double* beta;     /* [R], by temperature index */
     int64_t s, J_int, h_int;
     uint64_t seed;
-    int8_t* spin;     /* [R][L][L] */
-    int32_t* chain;   /* [R] */
+    int8_t* spin;     /* [R][L][L], by replica slot */
+    int32_t* temp_of_slot;  /* [R] */
+    int32_t* slot_of_temp;  /* [R] */
     uint64_t t, e;    /* sweeps done, exchanges done */
     uint64_t* attempted; /* [R-1] */
     uint64_t* accepted;  /* [R-1] */
@@ -135,16 +137,17 @@ static int threads_wanted = 1;
 void oracle_set_threads(int n) { threads_wanted = n < 1 ? 1 : n; }
 int oracle_get_threads(void) { return threads_wanted; }
 
-static int8_t* lattice(const oracle_pt* p, int k) { return p->spin + (size_t)k * p->L * p->L; }
+static int8_t* lattice(const oracle_pt* p, int r) { return p->spin + (size_t)r * p->L * p->L; }
 
 void oracle_destroy(oracle_pt* p) {
     if (!p) return;
-    free(p->beta); free(p->spin); free(p->chain); free(p->attempted); free(p->accepted);
+    free(p->beta); free(p->spin); free(p->temp_of_slot); free(p->slot_of_temp);
+    free(p->attempted); free(p->accepted);
     free(p);
 }
 
 /* Initialisation phase (Sec. 3: build the data structures): every spin of every replica is
- * drawn uniformly from {-1, +1} with the TAG_INIT stream; chains start in temperature order. */
+ * drawn uniformly from {-1, +1} with the TAG_INIT stream; slot r starts at temperature r. */
 int oracle_create(int L, const double* betas, int R, double J, double h, uint64_t seed,
                   oracle_pt** out) {
     *out = NULL;
@@ -157,20 +160,23 @@ int oracle_create(int L, const double* betas, int R, double J, double h, uint64_
     p->L = L; p->R = R; p->seed = seed;
     p->beta = (double*)malloc(sizeof(double) * R);
     p->spin = (int8_t*)malloc((size_t)R * L * L);
-    p->chain = (int32_t*)malloc(sizeof(int32_t) * R);
+    p->temp_of_slot = (int32_t*)malloc(sizeof(int32_t) * R);
+    p->slot_of_temp = (int32_t*)malloc(sizeof(int32_t) * R);
     p->attempted = (uint64_t*)calloc(R, sizeof(uint64_t));
     p->accepted = (uint64_t*)calloc(R, sizeof(uint64_t));
-    if (!p->beta || !p->spin || !p->chain || !p->attempted || !p->accepted) {
+    if (!p->beta || !p->spin || !p->temp_of_slot || !p->slot_of_temp || !p->attempted ||
+        !p->accepted) {
         oracle_destroy(p); return ORACLE_ENOMEM;
     }
     memcpy(p->beta, betas, sizeof(double) * R);
-    for (int k = 0; k < R; ++k) {
-        p->chain[k] = k;
-        int8_t* sp = lattice(p, k);
+    for (int r = 0; r < R; ++r) {
+        p->temp_of_slot[r] = r;
+        p->slot_of_temp[r] = r;
+        int8_t* sp = lattice(p, r);
         for (int y = 0; y < L; ++y)
             for (int x = 0; x < L; ++x) {
                 uint32_t i = (uint32_t)(y * L + x);
-                uint32_t u = philox_word(seed, i, 0u, (uint32_t)(k >> 2), TAG_INIT, k & 3);
+                uint32_t u = philox_word(seed, i, 0u, (uint32_t)(r >> 2), TAG_INIT, r & 3);
                 sp[y * L + x] = (u >> 31) ? (int8_t)1 : (int8_t)-1;
             }
     }
@@ -179,10 +185,11 @@ int oracle_create(int L, const double* betas, int R, double J, double h, uint64_
 }
 
 /* Eq. 3 in integers: E_int = h_int * sum_i sigma_i - J_int * sum_<ij> sigma_i sigma_j, each of
- * the 2 L^2 nearest-neighbour bonds of the periodic lattice counted once (right and down). */
-int64_t oracle_energy_int(const oracle_pt* p, int k) {
+ * the 2 L^2 nearest-neighbour bonds of the periodic lattice counted once (right and down).
+ * Of the configuration held in slot r. */
+static int64_t slot_energy_int(const oracle_pt* p, int r) {
     const int L = p->L;
-    const int8_t* sp = lattice(p, k);
+    const int8_t* sp = lattice(p, r);
     int64_t field = 0, bonds = 0;
     for (int y = 0; y < L; ++y)
         for (int x = 0; x < L; ++x) {
@@ -195,28 +202,36 @@ int64_t oracle_energy_int(const oracle_pt* p, int k) {
     return p->h_int * field - p->J_int * bonds;
 }
 
-int64_t oracle_magnetisation(const oracle_pt* p, int k) {
-    const int8_t* sp = lattice(p, k);
+static int64_t slot_magnetisation(const oracle_pt* p, int r) {
+    const int8_t* sp = lattice(p, r);
     int64_t m = 0;
     for (size_t i = 0; i < (size_t)p->L * p->L; ++i) m += sp[i];
     return m;
 }
 
-/* One single-spin Metropolis trial at site (x, y) of replica k in sweep t (Sec. 2.1, Eq. 1):
- * the trial state flips sigma; Delta E from Eq. 3 is 2 sigma (J * sum_nb sigma_nb - h); the
- * trial is accepted when u < T(beta_k, Delta E). */
-static void metropolis_site(oracle_pt* p, int k, int x, int y) {
+/* Energy and magnetisation of the configuration currently at temperature index k. */
+int64_t oracle_energy_int(const oracle_pt* p, int k) { return slot_energy_int(p, p->slot_of_temp[k]); }
+int64_t oracle_magnetisation(const oracle_pt* p, int k) {
+    return slot_magnetisation(p, p->slot_of_temp[k]);
+}
+
+/* One single-spin Metropolis trial at site (x, y) of the replica in slot r in sweep t
+ * (Sec. 2.1, Eq. 1): the trial state flips sigma; Delta E from Eq. 3 is
+ * 2 sigma (J * sum_nb sigma_nb - h); the trial is accepted when u < T(beta, Delta E) with beta
+ * the inverse temperature the slot currently runs at. */
+static void metropolis_site(oracle_pt* p, int r, int x, int y) {
     const int L = p->L;
-    int8_t* sp = lattice(p, k);
+    int8_t* sp = lattice(p, r);
     int s = sp[y * L + x];
     int nb = sp[y * L + (x + 1) % L] + sp[y * L + (x + L - 1) % L] +
              sp[((y + 1) % L) * L + x] + sp[((y + L - 1) % L) * L + x];
     int64_t dE_int = 2 * (int64_t)s * (p->J_int * nb - p->h_int);
     if (dE_int <= 0) { sp[y * L + x] = (int8_t)-s; return; }
     uint32_t i = (uint32_t)(y * L + x);
-    uint32_t u = philox_word(p->seed, i, (uint32_t)p->t, (uint32_t)(k >> 2),
-                             TAG_SPIN | ((uint32_t)(p->t >> 32) << 8), k & 3);
-    if ((uint64_t)u < oracle_spin_threshold(p->beta[k], dE_int, p->s)) sp[y * L + x] = (int8_t)-s;
+    uint32_t u = philox_word(p->seed, i, (uint32_t)p->t, (uint32_t)(r >> 2),
+                             TAG_SPIN | ((uint32_t)(p->t >> 32) << 8), r & 3);
+    double beta = p->beta[p->temp_of_slot[r]];
+    if ((uint64_t)u < oracle_spin_threshold(beta, dE_int, p->s)) sp[y * L + x] = (int8_t)-s;
 }
 
 /* One sweep: every site gets one trial. Sites are visited colour by colour on the
@@ -228,23 +243,24 @@ static void sweep_once(oracle_pt* p) {
 #ifdef _OPENMP
 #pragma omp parallel for num_threads(threads_wanted) schedule(static) collapse(2)
 #endif
-        for (int k = 0; k < R; ++k)
+        for (int r = 0; r < R; ++r)
             for (int y = 0; y < L; ++y)
-                for (int x = (y + colour) & 1; x < L; x += 2) metropolis_site(p, k, x, y);
+                for (int x = (y + colour) & 1; x < L; x += 2) metropolis_site(p, r, x, y);
     }
     p->t += 1;
 }
 
-static void swap_replicas(oracle_pt* p, int a, int b) {
-    size_t n = (size_t)p->L * p->L;
-    int8_t* sa = lattice(p, a);
-    int8_t* sb = lattice(p, b);
-    for (size_t i = 0; i < n; ++i) { int8_t t = sa[i]; sa[i] = sb[i]; sb[i] = t; }
-    int32_t c = p->chain[a]; p->chain[a] = p->chain[b]; p->chain[b] = c;
+/* Exchange the configurations at temperatures k and k+1 by swapping their slots. */
+static void swap_temperatures(oracle_pt* p, int k) {
+    int a = p->slot_of_temp[k], b = p->slot_of_temp[k + 1];
+    p->slot_of_temp[k] = b;
+    p->slot_of_temp[k + 1] = a;
+    p->temp_of_slot[a] = k + 1;
+    p->temp_of_slot[b] = k;
 }
 
 /* Swap iteration (Sec. 3): neighbours only, each replica at most once; the first swap
- * iteration pairs (0,1),(2,3),..., the next (1,2),(3,4),..., alternating. */
+ * iteration pairs temperatures (0,1),(2,3),..., the next (1,2),(3,4),..., alternating. */
 static void exchange_once(oracle_pt* p) {
     const int R = p->R;
     int parity = (int)(p->e & 1);
@@ -256,7 +272,7 @@ static void exchange_once(oracle_pt* p) {
         p->attempted[k] += 1;
         if ((uint64_t)u < S) {
             p->accepted[k] += 1;
-            swap_replicas(p, k, k + 1);
+            swap_temperatures(p, k);
         }
     }
     p->e += 1;
@@ -291,9 +307,10 @@ int oracle_trace(oracle_pt* p, int64_t n, int m, int64_t* E_out, int64_t* M_out)
 
 int64_t oracle_scale(const oracle_pt* p) { return p->s; }
 
+/* Spins of the configuration currently at temperature k. */
 int oracle_get_spins(const oracle_pt* p, int k, int8_t* out) {
     if (!p || k < 0 || k >= p->R || !out) return ORACLE_EINVAL;
-    memcpy(out, lattice(p, k), (size_t)p->L * p->L);
+    memcpy(out, lattice(p, p->slot_of_temp[k]), (size_t)p->L * p->L);
     return ORACLE_OK;
 }
 
@@ -301,11 +318,14 @@ int oracle_set_spins(oracle_pt* p, int k, const int8_t* in) {
     if (!p || k < 0 || k >= p->R || !in) return ORACLE_EINVAL;
     for (size_t i = 0; i < (size_t)p->L * p->L; ++i)
         if (in[i] != 1 && in[i] != -1) return ORACLE_EINVAL;
-    memcpy(lattice(p, k), in, (size_t)p->L * p->L);
+    memcpy(lattice(p, p->slot_of_temp[k]), in, (size_t)p->L * p->L);
     return ORACLE_OK;
 }
 
-void oracle_chain_map(const oracle_pt* p, int32_t* out) { memcpy(out, p->chain, sizeof(int32_t) * p->R); }
+/* slot_of_temp: the replica slot (chain) currently at each temperature index. */
+void oracle_chain_map(const oracle_pt* p, int32_t* out) {
+    memcpy(out, p->slot_of_temp, sizeof(int32_t) * p->R);
+}
 
 void oracle_swap_stats(const oracle_pt* p, uint64_t* attempted, uint64_t* accepted) {
     if (p->R < 2) return;

@@ -305,6 +305,26 @@ def test_first_exchange_pairs_even_neighbours():
     assert p.swap_stats()[0].tolist() == [1, 1, 1, 1, 1]
 
 
+def test_replica_streams_are_independent():
+    """Every slot draws its own random numbers: slots started from one configuration at one
+    temperature part ways, and so does a rerun with another seed."""
+    L, R = 16, 12
+    p = oracle.OracleProblem(L, np.full(R, 0.42), seed=4)
+    q = oracle.OracleProblem(L, np.full(R, 0.42), seed=5)
+    start = np.ones((L, L), np.int8)
+    start[::3, ::5] = -1
+    for k in range(R):
+        p.set_spins(k, start)
+        q.set_spins(k, start)
+    p.sweep(6)
+    q.sweep(6)
+    s = p.spins().reshape(R, -1)
+    for a in range(R):
+        assert (s[a] != q.spins(a).reshape(-1)).mean() > 0.02
+        for b in range(a + 1, R):
+            assert (s[a] != s[b]).mean() > 0.02, (a, b)
+
+
 def test_initial_state_uniform():
     L, R = 128, 8
     p = oracle.OracleProblem(L, np.full(R, 0.4), seed=0x5EED0002)
