@@ -1,0 +1,184 @@
+/*
+ * pt.h -- C ABI of libpt: Metropolis-Hastings with Parallel Tempering for the periodic
+ * two-dimensional Ising model on one NVIDIA B300 (sm_103a).
+ *
+ * Method (arXiv 2512.03825):
+ *   - Sec. 2.2, Eq. 3: E(sigma) = h * sum_i sigma_i - J * sum_<ij> sigma_i sigma_j on an L x L
+ *     periodic square lattice, every nearest-neighbour bond counted once. The field enters
+ *     with the paper's + sign, so h > 0 favours negative magnetisation.
+ *   - Sec. 2.2, Eq. 2: Boltzmann target P(E) ~ exp(-beta E), k_B = 1, beta = 1/T.
+ *   - Sec. 2.1, Eq. 1: Metropolis acceptance min(1, exp(-beta dE)) for single-spin flips.
+ *   - Sec. 3: R replicas at R temperatures run in intervals; between intervals neighbouring
+ *     temperatures exchange states, pairs (0,1),(2,3),... on the first swap iteration and
+ *     (1,2),(3,4),... on the next, alternating, with probability
+ *     e^x / (1 + e^x), x = (beta_k - beta_k+1)(E_k - E_k+1).
+ *
+ * Exact integer form (all decisions are bit-reproducible):
+ *   - J and h are quantised: s = smallest integer in 1..1000 with s*J and s*h within 1e-9
+ *     of integers; J_int = round(s*J), h_int = round(s*h), |J_int|, |h_int| <= 2^20.
+ *     E_int = s * E is an exact int64.
+ *   - Sweep t (t = 0, 1, ... counted since pt_create) visits colour 0 of the checkerboard
+ *     ((x + y) even) and then colour 1. The replica in slot r at site i = y*L + x draws
+ *     u = Philox4x32-10(key = seed, ctr = {i, lo32(t), r >> 2, 0 | hi32(t) << 8}) word r & 3
+ *     and flips when dE_int <= 0 or u < floor(2^32 * exp(-(beta * dE_int) / s)), where
+ *     dE_int = 2 sigma (J_int * sum_nb sigma_nb - h_int) and beta is the inverse temperature
+ *     the slot currently runs at (all in IEEE double, libm exp, no fused operations).
+ *   - Replica slot r starts at temperature index r with spins sigma = +1 iff bit 31 of
+ *     Philox(ctr = {i, 0, r >> 2, 2}) word r & 3 is set.
+ *   - After every sweep that leaves the total sweep count a multiple of exchange_every (> 0),
+ *     swap iteration e (e = 0, 1, ... since pt_create) tries the pairs (k, k+1), k = e & 1,
+ *     e & 1 + 2, ...: with n = E_int(at k) - E_int(at k+1), y = ((beta_k+1 - beta_k) * n) / s
+ *     and u = Philox(ctr = {k, lo32(e), 0, 1 | hi32(e) << 8}) word 0, the pair swaps when
+ *     u < S with S = 0 for y > 44, S = 2^32 for y < -44 and floor(2^32 / (1 + exp(y)))
+ *     otherwise. A swap exchanges the two slots' temperature indices; configurations never
+ *     move in memory.
+ *
+ * Conventions for every call:
+ *   - Return value 0 (PT_OK) on success, a negative PT_E* code otherwise; pt_strerror() turns
+ *     a code into text and pt_last_error() gives the detail of the last failure on the
+ *     calling thread.
+ *   - A problem whose device work failed is poisoned: later calls on it return PT_ESTATE
+ *     until it is destroyed.
+ *   - Output arrays are owned by the caller and must hold the stated number of elements;
+ *     every array argument is host memory unless stated otherwise.
+ *   - One pt_problem must not be used from two host threads at once.
+ *   - pt_sweep and pt_sweep_batch are asynchronous on the problem's CUDA stream; every
+ *     getter synchronises that stream before it returns.
+ *   - The library needs a CUDA device of compute capability 10.3 (B300). Without one every
+ *     call that touches the device returns PT_ENODEV; nothing falls back to the CPU.
+ */
+#ifndef PT_H_
+#define PT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PT_OK 0
+#define PT_EINVAL (-1)   /* malformed argument */
+#define PT_ENOMEM (-2)   /* device or host allocation failed */
+#define PT_ECUDA (-3)    /* a CUDA call failed */
+#define PT_ETIMEOUT (-4) /* a device-side wait gave up */
+#define PT_ESTATE (-5)   /* the problem was poisoned by an earlier failure */
+#define PT_ENODEV (-6)   /* no usable sm_103 device */
+#define PT_EINTERNAL (-7)
+
+#define PT_MAX_L 16384
+#define PT_MAX_R 2048
+
+typedef struct pt_problem pt_problem; /* opaque; owned by the library until pt_destroy */
+
+/* Create one PT problem (Sec. 3, initialisation phase): L x L periodic lattice (L even,
+ * 4 <= L <= PT_MAX_L), R temperatures with inverse temperatures betas[0..R-1] (finite,
+ * >= 0; copied; their order defines the temperature index; 1 <= R <= PT_MAX_R), coupling J,
+ * field h, 64-bit seed. Allocates the device state (about L*L*ceil(R/32)*4 bytes of spins
+ * plus the threshold tables) through the allocator of pt_set_allocator (cudaMalloc by
+ * default), draws the initial spins on the device, and stores the handle in *out. The
+ * problem runs on the legacy default stream until pt_set_stream. Errors: PT_EINVAL,
+ * PT_ENOMEM, PT_ECUDA, PT_ENODEV. */
+int pt_create(int L, const double* betas, int R, double J, double h, uint64_t seed,
+              pt_problem** out);
+
+/* Release the problem and its device memory (synchronises its stream first). NULL is a
+ * no-op. */
+void pt_destroy(pt_problem* p);
+
+/* Run the problem's future work on `cuda_stream` (a cudaStream_t, e.g. a torch stream
+ * handle). Synchronises the previous stream first. */
+int pt_set_stream(pt_problem* p, void* cuda_stream);
+
+/* Sec. 3, execution phase: n >= 0 sweeps, with a swap iteration after every sweep that
+ * leaves the total sweep count a multiple of exchange_every (0 = no swaps; < 0 is
+ * PT_EINVAL). pt_sweep(a, m) followed by pt_sweep(b, m) equals pt_sweep(a + b, m).
+ * Launches the per-problem kernels (the plain path) and returns without waiting. */
+int pt_sweep(pt_problem* p, int64_t n, int exchange_every);
+
+/* Advance `count` problems together in one persistent kernel: problem j runs n[j] >= 0
+ * sweeps with exchange_every[j] (same meaning as pt_sweep). All problems must be on the
+ * same stream. Results are bit-identical to calling pt_sweep on each problem alone. */
+int pt_sweep_batch(pt_problem* const* problems, int count, const int64_t* n,
+                   const int* exchange_every);
+
+/* Launch shape of pt_sweep_batch (chosen by the autotuner; results never depend on it):
+ * cluster = CTAs per thread-block cluster (1, 2, 4, 8 or 16); problems with
+ * L >= joint_min_L are spread over a whole cluster, smaller ones run on a single CTA. Applies
+ * to later batches of every problem. PT_EINVAL for other cluster sizes or joint_min_L < 4. */
+int pt_set_batch_tuning(int cluster, int joint_min_L);
+int pt_get_batch_tuning(int* cluster, int* joint_min_L);
+
+/* Energies E = E_int / s of the configurations at each temperature index, out[R]. */
+int pt_energies(pt_problem* p, double* out);
+
+/* Magnetisations M = sum_i sigma_i at each temperature index, out[R]. */
+int pt_magnetisations(pt_problem* p, double* out);
+
+/* Swap statistics per temperature pair (k, k+1): attempts and acceptances, each [R-1]
+ * (either pointer may be NULL; nothing is written when R == 1). */
+int pt_swap_stats(pt_problem* p, uint64_t* attempted, uint64_t* accepted);
+
+/* Exact integer observables per temperature index: E_int[R], M[R] (either may be NULL) and
+ * the quantisation scale s (may be NULL). */
+int pt_energies_int(pt_problem* p, int64_t* E_int, int64_t* M, int64_t* scale);
+
+/* Spins (+1 / -1, row-major [L][L], site (x, y) at y*L + x) of the configuration at
+ * temperature index k. */
+int pt_get_spins(pt_problem* p, int k, int8_t* out);
+
+/* Overwrite the configuration at temperature index k with in[L*L] (values +1 / -1 only,
+ * else PT_EINVAL). */
+int pt_set_spins(pt_problem* p, int k, const int8_t* in);
+
+/* slot_of_temp[R]: the replica slot (chain) currently at each temperature index. */
+int pt_chain_map(pt_problem* p, int32_t* slot_of_temp);
+
+/* Sweeps and swap iterations done since pt_create (either pointer may be NULL). */
+int pt_counters(pt_problem* p, uint64_t* sweeps_done, uint64_t* exchanges_done);
+
+/* Wait for the problem's queued work; reports device-side failures. */
+int pt_synchronize(pt_problem* p);
+
+/* Device bytes held by the problem (spins, tables and bookkeeping). */
+size_t pt_device_bytes(const pt_problem* p);
+
+/* Device bytes pt_create would allocate for these arguments (0 if they are invalid). Used
+ * for admission against a memory budget before creating. */
+size_t pt_estimate_device_bytes(int L, const double* betas, int R, double J, double h);
+
+/* Route device allocations of later pt_create calls through alloc/free (e.g. the PyTorch
+ * caching allocator). alloc(bytes, stream, ctx) returns a device pointer aligned to 256
+ * bytes or NULL; free(ptr, stream, ctx) releases it. Pass NULLs to restore cudaMalloc. */
+typedef void* (*pt_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*pt_free_fn)(void* ptr, void* stream, void* ctx);
+int pt_set_allocator(pt_alloc_fn alloc, pt_free_fn free, void* ctx);
+
+/* Text for a PT_E* code (static storage). */
+const char* pt_strerror(int code);
+
+/* Detail of the last failure on the calling thread (static thread-local storage). */
+const char* pt_last_error(void);
+
+/* ---- host-side tables, exposed so they can be checked without a GPU ------------------ */
+
+/* The quantisation above: *s, *J_int, *h_int. PT_EINVAL if J or h cannot be quantised. */
+int pt_quantise(double J, double h, int64_t* s, int64_t* J_int, int64_t* h_int);
+
+/* Metropolis threshold floor(2^32 * exp(-(beta * dE_int) / s)) for dE_int > 0, 2^32 for
+ * dE_int <= 0 (Eq. 1 with Eq. 2). */
+uint64_t pt_spin_threshold(double beta, int64_t dE_int, int64_t s);
+
+/* Exchange threshold S of the swap rule above, in [0, 2^32], for the pair with inverse
+ * temperatures beta_lo (index k) and beta_hi (index k+1) and energy difference n. Computed
+ * from the table the device uses. */
+uint64_t pt_swap_threshold(double beta_lo, double beta_hi, int64_t n, int64_t s);
+
+/* Library version string. */
+const char* pt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PT_H_ */

@@ -1,0 +1,96 @@
+"""ctypes binding of libpt.so (declarations in include/pt.h). Argument marshalling only:
+every step of the sampler runs in the library's CUDA kernels.
+
+The library is loaded from this package's directory. If it is missing the import of this
+module raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpt.so")
+
+PT_OK = 0
+PT_EINVAL = -1
+PT_ENOMEM = -2
+PT_ECUDA = -3
+PT_ETIMEOUT = -4
+PT_ESTATE = -5
+PT_ENODEV = -6
+PT_EINTERNAL = -7
+PT_MAX_L = 16384
+PT_MAX_R = 2048
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+# (name, restype, argtypes) of every function include/pt.h declares
+P = C.c_void_p
+SIGNATURES = [
+    ("pt_create", C.c_int, [C.c_int, C.POINTER(C.c_double), C.c_int, C.c_double, C.c_double,
+                            C.c_uint64, C.POINTER(P)]),
+    ("pt_destroy", None, [P]),
+    ("pt_set_stream", C.c_int, [P, P]),
+    ("pt_sweep", C.c_int, [P, C.c_int64, C.c_int]),
+    ("pt_sweep_batch", C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.c_int64),
+                                 C.POINTER(C.c_int)]),
+    ("pt_set_batch_tuning", C.c_int, [C.c_int, C.c_int]),
+    ("pt_get_batch_tuning", C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    ("pt_energies", C.c_int, [P, C.POINTER(C.c_double)]),
+    ("pt_magnetisations", C.c_int, [P, C.POINTER(C.c_double)]),
+    ("pt_swap_stats", C.c_int, [P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
+    ("pt_energies_int", C.c_int, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                  C.POINTER(C.c_int64)]),
+    ("pt_get_spins", C.c_int, [P, C.c_int, C.POINTER(C.c_int8)]),
+    ("pt_set_spins", C.c_int, [P, C.c_int, C.POINTER(C.c_int8)]),
+    ("pt_chain_map", C.c_int, [P, C.POINTER(C.c_int32)]),
+    ("pt_counters", C.c_int, [P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
+    ("pt_synchronize", C.c_int, [P]),
+    ("pt_device_bytes", C.c_size_t, [P]),
+    ("pt_estimate_device_bytes", C.c_size_t, [C.c_int, C.POINTER(C.c_double), C.c_int,
+                                              C.c_double, C.c_double]),
+    ("pt_set_allocator", C.c_int, [ALLOC_FN, FREE_FN, P]),
+    ("pt_strerror", C.c_char_p, [C.c_int]),
+    ("pt_last_error", C.c_char_p, []),
+    ("pt_quantise", C.c_int, [C.c_double, C.c_double, C.POINTER(C.c_int64),
+                              C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    ("pt_spin_threshold", C.c_uint64, [C.c_double, C.c_int64, C.c_int64]),
+    ("pt_swap_threshold", C.c_uint64, [C.c_double, C.c_double, C.c_int64, C.c_int64]),
+    ("pt_version", C.c_char_p, []),
+]
+
+
+class PTError(RuntimeError):
+    """A libpt call returned a PT_E* code."""
+
+    def __init__(self, code, where, detail):
+        self.code = code
+        super().__init__("%s failed: %s (%d): %s" % (where, _strerror(code), code, detail))
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libpt.so is not built (%s); run "
+                          "`python -m paper_2512_03825_b300.build` or __graft_entry__.build()"
+                          % LIB_PATH)
+    lib = C.CDLL(LIB_PATH)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _strerror(code):
+    return lib.pt_strerror(int(code)).decode()
+
+
+def check(rc, where):
+    if rc != PT_OK:
+        raise PTError(rc, where, lib.pt_last_error().decode())
+    return rc

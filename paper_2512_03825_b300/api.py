@@ -1,0 +1,187 @@
+"""Python face of libpt: one PT problem per `PTProblem`, `sweep_batch` for many at once.
+
+PyTorch provides the device memory (through `use_torch_allocator`) and the streams; all
+sampling work is done by the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+
+from ._lib import ALLOC_FN, FREE_FN, check, lib
+
+
+def _dptr(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+class PTProblem:
+    """Metropolis-Hastings with parallel tempering on an L x L periodic Ising lattice with R
+    temperatures (inverse temperatures `betas`), coupling J and field h."""
+
+    def __init__(self, L: int, betas: Sequence[float], J: float = 1.0, h: float = 0.0,
+                 seed: int = 0, stream=None):
+        b = np.ascontiguousarray(betas, dtype=np.float64)
+        h_ = C.c_void_p()
+        check(lib.pt_create(int(L), _dptr(b, C.c_double), int(b.size), float(J), float(h),
+                            int(seed) & 0xFFFFFFFFFFFFFFFF, C.byref(h_)), "pt_create")
+        self._h = h_
+        self.L, self.R = int(L), int(b.size)
+        self.betas = b.copy()
+        self.J, self.h, self.seed = float(J), float(h), int(seed)
+        if stream is not None:
+            self.set_stream(stream)
+
+    # -- lifetime ------------------------------------------------------------------------
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib.pt_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # interpreter shutdown
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None (default)."""
+        raw = getattr(stream, "cuda_stream", stream)
+        check(lib.pt_set_stream(self._h, C.c_void_p(int(raw or 0))), "pt_set_stream")
+
+    # -- work ----------------------------------------------------------------------------
+    def sweep(self, n: int, exchange_every: int = 0):
+        check(lib.pt_sweep(self._h, int(n), int(exchange_every)), "pt_sweep")
+
+    def synchronize(self):
+        check(lib.pt_synchronize(self._h), "pt_synchronize")
+
+    # -- observables ---------------------------------------------------------------------
+    def energies_int(self):
+        E = np.zeros(self.R, np.int64)
+        check(lib.pt_energies_int(self._h, _dptr(E, C.c_int64), None, None), "pt_energies_int")
+        return E
+
+    def magnetisations(self):
+        M = np.zeros(self.R, np.int64)
+        check(lib.pt_energies_int(self._h, None, _dptr(M, C.c_int64), None), "pt_energies_int")
+        return M
+
+    @property
+    def scale(self):
+        s = C.c_int64()
+        check(lib.pt_energies_int(self._h, None, None, C.byref(s)), "pt_energies_int")
+        return s.value
+
+    def energies(self):
+        out = np.zeros(self.R, np.float64)
+        check(lib.pt_energies(self._h, _dptr(out, C.c_double)), "pt_energies")
+        return out
+
+    def magnetisations_f(self):
+        out = np.zeros(self.R, np.float64)
+        check(lib.pt_magnetisations(self._h, _dptr(out, C.c_double)), "pt_magnetisations")
+        return out
+
+    def swap_stats(self):
+        n = max(self.R - 1, 0)
+        att = np.zeros(max(n, 1), np.uint64)
+        acc = np.zeros(max(n, 1), np.uint64)
+        check(lib.pt_swap_stats(self._h, _dptr(att, C.c_uint64), _dptr(acc, C.c_uint64)),
+              "pt_swap_stats")
+        return att[:n], acc[:n]
+
+    def chain_map(self):
+        out = np.zeros(self.R, np.int32)
+        check(lib.pt_chain_map(self._h, _dptr(out, C.c_int32)), "pt_chain_map")
+        return out
+
+    def counters(self):
+        t, e = C.c_uint64(), C.c_uint64()
+        check(lib.pt_counters(self._h, C.byref(t), C.byref(e)), "pt_counters")
+        return t.value, e.value
+
+    def spins(self, k: Optional[int] = None):
+        if k is None:
+            return np.stack([self.spins(j) for j in range(self.R)])
+        out = np.zeros((self.L, self.L), np.int8)
+        check(lib.pt_get_spins(self._h, int(k), _dptr(out, C.c_int8)), "pt_get_spins")
+        return out
+
+    def set_spins(self, k: int, arr):
+        a = np.ascontiguousarray(arr, dtype=np.int8).reshape(self.L, self.L)
+        check(lib.pt_set_spins(self._h, int(k), _dptr(a, C.c_int8)), "pt_set_spins")
+
+    @property
+    def device_bytes(self):
+        return int(lib.pt_device_bytes(self._h))
+
+
+def sweep_batch(problems: Sequence[PTProblem], n, exchange_every):
+    """Advance all problems together in one persistent kernel (n, exchange_every: an int
+    or one value per problem)."""
+    k = len(problems)
+    if k == 0:
+        return
+    ns = np.ascontiguousarray(np.broadcast_to(np.asarray(n, np.int64), (k,)))
+    ms = np.ascontiguousarray(np.broadcast_to(np.asarray(exchange_every, np.int32), (k,)))
+    hs = (C.c_void_p * k)(*[p.handle.value for p in problems])
+    check(lib.pt_sweep_batch(hs, k, _dptr(ns, C.c_int64), _dptr(ms, C.c_int32)),
+          "pt_sweep_batch")
+
+
+def estimate_device_bytes(L, betas, J=1.0, h=0.0):
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    return int(lib.pt_estimate_device_bytes(int(L), _dptr(b, C.c_double), int(b.size),
+                                            float(J), float(h)))
+
+
+def quantise(J, h):
+    s, ji, hi = C.c_int64(), C.c_int64(), C.c_int64()
+    check(lib.pt_quantise(float(J), float(h), C.byref(s), C.byref(ji), C.byref(hi)),
+          "pt_quantise")
+    return s.value, ji.value, hi.value
+
+
+def spin_threshold(beta, dE_int, s):
+    return int(lib.pt_spin_threshold(float(beta), int(dE_int), int(s)))
+
+
+def swap_threshold(beta_lo, beta_hi, n, s):
+    return int(lib.pt_swap_threshold(float(beta_lo), float(beta_hi), int(n), int(s)))
+
+
+# -- PyTorch as the device-memory provider -------------------------------------------------
+_torch_hooks = None
+
+
+def use_torch_allocator(enable: bool = True):
+    """Route the library's device allocations through torch's caching allocator."""
+    global _torch_hooks
+    if not enable:
+        check(lib.pt_set_allocator(ALLOC_FN(), FREE_FN(), None), "pt_set_allocator")
+        _torch_hooks = None
+        return
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            dev = torch.cuda.current_device()
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream or None))
+        except Exception:
+            return None
+
+    def _free(ptr, stream, ctx):
+        if ptr:
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+    hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
+    check(lib.pt_set_allocator(hooks[0], hooks[1], None), "pt_set_allocator")
+    _torch_hooks = hooks

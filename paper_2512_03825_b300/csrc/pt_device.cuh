@@ -1,0 +1,224 @@
+// pt_device.cuh -- device building blocks of the parallel-tempering sweep (sm_103a).
+//
+// Everything here is integer arithmetic on CUDA cores: nothing in the method is a dense
+// contraction, so the tensor cores have no role.
+#pragma once
+#include <stdint.h>
+
+#include "pt_types.h"
+
+namespace ptb {
+
+// ---------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32 -> 64-bit
+// products whose halves are xored with the other counter words and the round key; the key
+// advances by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------------------
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+struct Philox4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                  uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c0);
+    const uint32_t lo0 = kPhiloxM0 * c0;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c2);
+    const uint32_t lo1 = kPhiloxM1 * c2;
+    const uint32_t rk0 = k0 + (uint32_t)r * kPhiloxW0;
+    const uint32_t rk1 = k1 + (uint32_t)r * kPhiloxW1;
+    c0 = hi1 ^ c1 ^ rk0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ rk1;
+    c3 = lo0;
+  }
+  return Philox4{c0, c1, c2, c3};
+}
+
+// Counter words shared by every spin-update draw of one sweep.
+struct SweepCtr {
+  uint32_t t_lo;  // lo32(t)
+  uint32_t c3;    // kTagSpin | hi32(t) << 8
+  uint32_t k0, k1;
+};
+
+__device__ __forceinline__ SweepCtr make_sweep_ctr(uint64_t t, uint32_t k0, uint32_t k1) {
+  return SweepCtr{(uint32_t)t, kTagSpin | ((uint32_t)(t >> 32) << 8), k0, k1};
+}
+
+// ---------------------------------------------------------------------------------------
+// Anti-aligned neighbour count, bit-sliced over the 32 slots of a word.
+// a_j = s ^ n_j marks the slots whose neighbour j points the other way; k = sum_j a_j.
+// ---------------------------------------------------------------------------------------
+struct NbCount {
+  uint32_t b0, b1, b2;  // binary digits of k (0..4)
+};
+
+__device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) {
+  return (a & b) | (a & c) | (b & c);
+}
+
+__device__ __forceinline__ NbCount count4(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3) {
+  const uint32_t x01 = a0 ^ a1, c01 = a0 & a1;
+  const uint32_t x23 = a2 ^ a3, c23 = a2 & a3;
+  const uint32_t c0 = x01 & x23;
+  NbCount k;
+  k.b0 = x01 ^ x23;
+  k.b1 = c01 ^ c23 ^ c0;
+  k.b2 = maj3(c01, c23, c0);
+  return k;
+}
+
+// ---------------------------------------------------------------------------------------
+// Metropolis update of one word = 32 slots at one site (Eq. 1 with the Boltzmann target of
+// Eq. 2 on the local energy change of Eq. 3). Returns the new word.
+//   s        centre word; n0..n3 its four neighbour words (other colour)
+//   site     y * L + x;  blk0 = 8 * plane (Philox counter word 2 of the first block)
+//   nblk     Philox blocks needed (4 slots each; ceil(used slots / 4))
+// ---------------------------------------------------------------------------------------
+
+// h = 0, J > 0: dE = 4 J (2 - k); classes k = 0 and k = 1 need a random number, k >= 2
+// always flips. Because T0 <= T1 bit by bit, "u < T0 or (k == 1 and u < T1)" is the exact
+// rule for both random classes.
+__device__ __forceinline__ uint32_t update_word_ferro(uint32_t s, uint32_t n0, uint32_t n1,
+                                                      uint32_t n2, uint32_t n3, uint32_t site,
+                                                      uint32_t blk0, int nblk,
+                                                      const uint32_t (&T0)[32],
+                                                      const uint32_t (&T1)[32], uint32_t alw0,
+                                                      uint32_t alw1, uint32_t used,
+                                                      const SweepCtr& cx) {
+  const uint32_t a0 = s ^ n0, a1 = s ^ n1, a2 = s ^ n2, a3 = s ^ n3;
+  const uint32_t x01 = a0 ^ a1, x23 = a2 ^ a3;
+  const uint32_t ge2 = (a0 & a1) | (a2 & a3) | (x01 & x23);
+  const uint32_t eq1 = (x01 ^ x23) & ~ge2;
+  uint32_t acc = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    if (j < nblk) {
+      const Philox4 r = philox4x32_10(site, cx.t_lo, blk0 + (uint32_t)j, cx.c3, cx.k0, cx.k1);
+      const uint32_t u[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int b = 4 * j + q;
+        const bool f = (u[q] < T0[b]) || (((eq1 >> b) & 1u) && (u[q] < T1[b]));
+        acc |= (uint32_t)f << b;
+      }
+    }
+  }
+  const uint32_t flip = (ge2 | alw0 | (eq1 & alw1) | acc) & used;
+  return s ^ flip;
+}
+
+// Any J, h: class c = 2 k + (sigma == +1) per bit; thresholds from the plane table.
+__device__ __forceinline__ uint32_t update_word_generic(uint32_t s, uint32_t n0, uint32_t n1,
+                                                        uint32_t n2, uint32_t n3,
+                                                        uint32_t site, uint32_t blk0, int nblk,
+                                                        const PlaneGeneric& pl,
+                                                        const SweepCtr& cx) {
+  const NbCount k = count4(s ^ n0, s ^ n1, s ^ n2, s ^ n3);
+  const uint32_t z[5] = {~(k.b0 | k.b1 | k.b2), k.b0 & ~k.b1 & ~k.b2, ~k.b0 & k.b1 & ~k.b2,
+                         k.b0 & k.b1, k.b2};
+  uint32_t always = 0;
+#pragma unroll
+  for (int kk = 0; kk < 5; ++kk)
+    always |= z[kk] & ((s & pl.alw[2 * kk + 1]) | (~s & pl.alw[2 * kk]));
+  uint32_t acc = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    if (j < nblk) {
+      const Philox4 r = philox4x32_10(site, cx.t_lo, blk0 + (uint32_t)j, cx.c3, cx.k0, cx.k1);
+      const uint32_t u[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int b = 4 * j + q;
+        const uint32_t kb = ((k.b0 >> b) & 1u) | (((k.b1 >> b) & 1u) << 1) |
+                            (((k.b2 >> b) & 1u) << 2);
+        const uint32_t cls = 2u * kb + ((s >> b) & 1u);
+        acc |= (uint32_t)(u[q] < pl.T[cls][b]) << b;
+      }
+    }
+  }
+  const uint32_t flip = (always | acc) & pl.used;
+  return s ^ flip;
+}
+
+// ---------------------------------------------------------------------------------------
+// Bit-sliced per-slot counters: level l holds bit l of 32 independent counts. Additions by
+// one thread ripple through the low NT levels only (its counts must stay below 2^NT); the
+// warp sum uses all NB levels (the warp's counts must stay below 2^NB).
+// ---------------------------------------------------------------------------------------
+template <int NB, int NT>
+struct BitCounter {
+  static_assert(NT >= 3 && NT <= NB, "counter depth");
+  uint32_t c[NB];
+
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int l = 0; l < NB; ++l) c[l] = 0;
+  }
+  // add a per-slot number given by its binary digits d0 (+ 2 d1 + 4 d2)
+  __device__ __forceinline__ void add3(uint32_t d0, uint32_t d1, uint32_t d2) {
+    uint32_t carry = c[0] & d0;
+    c[0] ^= d0;
+    uint32_t nc = maj3(c[1], d1, carry);
+    c[1] ^= d1 ^ carry;
+    carry = nc;
+    nc = maj3(c[2], d2, carry);
+    c[2] ^= d2 ^ carry;
+    carry = nc;
+#pragma unroll
+    for (int l = 3; l < NT; ++l) {
+      nc = c[l] & carry;
+      c[l] ^= carry;
+      carry = nc;
+    }
+  }
+  __device__ __forceinline__ void add2(uint32_t d0, uint32_t d1) {
+    uint32_t carry = c[0] & d0;
+    c[0] ^= d0;
+    uint32_t nc = maj3(c[1], d1, carry);
+    c[1] ^= d1 ^ carry;
+    carry = nc;
+#pragma unroll
+    for (int l = 2; l < NT; ++l) {
+      nc = c[l] & carry;
+      c[l] ^= carry;
+      carry = nc;
+    }
+  }
+  // sum over the warp (every lane ends with the total), then lane b returns the count of
+  // slot bit b. Counts must fit NB bits after the sum.
+  __device__ __forceinline__ uint32_t warp_total_for_lane() {
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      uint32_t carry = 0;
+#pragma unroll
+      for (int l = 0; l < NB; ++l) {
+        const uint32_t o = __shfl_xor_sync(0xffffffffu, c[l], off);
+        const uint32_t sum = c[l] ^ o ^ carry;
+        carry = maj3(c[l], o, carry);
+        c[l] = sum;
+      }
+    }
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t v = 0;
+#pragma unroll
+    for (int l = 0; l < NB; ++l) v |= ((c[l] >> lane) & 1u) << l;
+    return v;
+  }
+};
+
+// ---------------------------------------------------------------------------------------
+// Word addressing
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ size_t word_index(int L, int w, int c, int y, int i) {
+  return (((size_t)w * 2 + c) * L + y) * (size_t)(L >> 1) + i;
+}
+
+}  // namespace ptb

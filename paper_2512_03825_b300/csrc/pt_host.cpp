@@ -1,0 +1,769 @@
+// pt_host.cpp -- host side of libpt: argument checks, the integer energy scale, the FP64
+// threshold tables (built once per problem on the host), device allocation and the C ABI of
+// include/pt.h. All compute happens in the kernels; nothing here falls back to the CPU.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "pt.h"
+#include "pt_batch.h"
+#include "pt_internal.h"
+#include "pt_launch.h"
+
+using namespace ptb;
+
+namespace {
+thread_local std::string g_last_error;
+}  // namespace
+
+int ptb::fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+namespace {
+
+struct Allocator {
+  pt_alloc_fn alloc = nullptr;
+  pt_free_fn free = nullptr;
+  void* ctx = nullptr;
+};
+std::mutex g_mu;
+Allocator g_alloc;
+
+constexpr uint64_t kTwo32 = 1ull << 32;
+
+// ---------------------------------------------------------------------------------------
+// Exact integer energies (the quantisation of include/pt.h)
+// ---------------------------------------------------------------------------------------
+int quantise(double J, double h, int64_t* s_out, int64_t* Ji, int64_t* hi) {
+  if (!std::isfinite(J) || !std::isfinite(h)) return PT_EINVAL;
+  for (int64_t s = 1; s <= 1000; ++s) {
+    const double a = (double)s * J, b = (double)s * h;
+    const double ra = std::nearbyint(a), rb = std::nearbyint(b);
+    if (std::fabs(a - ra) <= 1e-9 && std::fabs(b - rb) <= 1e-9) {
+      if (std::fabs(ra) > 1048576.0 || std::fabs(rb) > 1048576.0) return PT_EINVAL;
+      *s_out = s;
+      *Ji = (int64_t)ra;
+      *hi = (int64_t)rb;
+      return PT_OK;
+    }
+  }
+  return PT_EINVAL;
+}
+
+// Metropolis threshold of Eq. 1 (Boltzmann ratio of Eq. 2) as a 33-bit integer.
+uint64_t spin_threshold(double beta, int64_t dE_int, int64_t s) {
+  if (dE_int <= 0) return kTwo32;
+  const double x = (beta * (double)dE_int) / (double)s;
+  return (uint64_t)std::floor(4294967296.0 * std::exp(-x));
+}
+
+// Barker swap threshold of Sec. 3 with the +-44 cut-offs.
+uint64_t swap_rule(double beta_lo, double beta_hi, int64_t n, int64_t s) {
+  const double y = ((beta_hi - beta_lo) * (double)n) / (double)s;
+  if (y > 44.0) return 0;
+  if (y < -44.0) return kTwo32;
+  return (uint64_t)std::floor(4294967296.0 / (1.0 + std::exp(y)));
+}
+
+// The exchange threshold of one temperature pair as a function of n: constant below n_lo
+// and above n_hi, tabulated in between. S(n) is monotone in n (y is linear in n and the
+// Barker form is monotone in y), so the saturated ranges are found by bisection and then
+// checked at their edges.
+struct PairTable {
+  int64_t n_lo = 1, n_hi = 0;
+  uint64_t S_below = 0, S_above = 0;
+  std::vector<uint32_t> vals;
+};
+
+int build_pair_table(double blo, double bhi, int64_t s, PairTable* out) {
+  PairTable t;
+  const double d = bhi - blo;
+  if (d == 0.0) {  // y = 0 for every n
+    t.S_below = t.S_above = swap_rule(blo, bhi, 0, s);
+    *out = std::move(t);
+    return PT_OK;
+  }
+  // beyond +-N the cut-offs decide (|y| > 44)
+  const double nmax = std::ceil(45.0 * (double)s / std::fabs(d)) + 2.0;
+  if (nmax > 4.0e9) return fail(PT_EINVAL, "temperature pair too close: |dbeta| = %g", d);
+  const int64_t N = (int64_t)nmax;
+  t.S_below = swap_rule(blo, bhi, -N, s);
+  t.S_above = swap_rule(blo, bhi, N, s);
+  // n_lo = smallest n with S(n) != S_below
+  int64_t lo = -N, hi = N;  // S(lo) == S_below, search in (lo, hi]
+  while (hi - lo > 1) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    if (swap_rule(blo, bhi, mid, s) != t.S_below) hi = mid; else lo = mid;
+  }
+  t.n_lo = hi;
+  lo = -N;
+  hi = N;  // largest n with S(n) != S_above: S(hi) == S_above, search in [lo, hi)
+  while (hi - lo > 1) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    if (swap_rule(blo, bhi, mid, s) != t.S_above) lo = mid; else hi = mid;
+  }
+  t.n_hi = lo;
+  if (t.n_hi < t.n_lo) return fail(PT_EINTERNAL, "empty exchange table");
+  const int64_t len = t.n_hi - t.n_lo + 1;
+  t.vals.resize((size_t)len);
+  uint64_t prev = t.S_below;
+  for (int64_t j = 0; j < len; ++j) {
+    const uint64_t v = swap_rule(blo, bhi, t.n_lo + j, s);
+    if (v >= kTwo32) return fail(PT_EINTERNAL, "exchange table entry saturates inside");
+    if ((d > 0 && v > prev) || (d < 0 && v < prev))
+      return fail(PT_EINTERNAL, "exchange threshold not monotone at n = %lld",
+                  (long long)(t.n_lo + j));
+    prev = v;
+    t.vals[(size_t)j] = (uint32_t)v;
+  }
+  if (swap_rule(blo, bhi, t.n_lo - 1, s) != t.S_below ||
+      swap_rule(blo, bhi, t.n_hi + 1, s) != t.S_above)
+    return fail(PT_EINTERNAL, "exchange table edges inconsistent");
+  *out = std::move(t);
+  return PT_OK;
+}
+
+// Tables depend only on (beta_lo, beta_hi, s); requests with the same ladder share them.
+struct PairKey {
+  uint64_t blo, bhi;
+  int64_t s;
+  bool operator<(const PairKey& o) const {
+    return std::tie(blo, bhi, s) < std::tie(o.blo, o.bhi, o.s);
+  }
+};
+std::mutex g_table_mu;
+std::map<PairKey, std::shared_ptr<const PairTable>> g_tables;
+size_t g_table_bytes = 0;
+constexpr size_t kTableCacheCap = size_t(2) << 30;
+
+int get_pair_table(double blo, double bhi, int64_t s, std::shared_ptr<const PairTable>* out) {
+  PairKey key;
+  memcpy(&key.blo, &blo, 8);
+  memcpy(&key.bhi, &bhi, 8);
+  key.s = s;
+  {
+    std::lock_guard<std::mutex> lk(g_table_mu);
+    auto it = g_tables.find(key);
+    if (it != g_tables.end()) {
+      *out = it->second;
+      return PT_OK;
+    }
+  }
+  auto t = std::make_shared<PairTable>();
+  const int rc = build_pair_table(blo, bhi, s, t.get());
+  if (rc != PT_OK) return rc;
+  std::lock_guard<std::mutex> lk(g_table_mu);
+  if (g_table_bytes > kTableCacheCap) {
+    g_tables.clear();
+    g_table_bytes = 0;
+  }
+  g_table_bytes += t->vals.size() * 4;
+  g_tables[key] = t;
+  *out = t;
+  return PT_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Device
+// ---------------------------------------------------------------------------------------
+int current_device(DeviceInfo* info) {
+  static std::mutex mu;
+  static std::map<int, DeviceInfo> cache;
+  int dev = -1;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PT_ENODEV, "no CUDA device: %s", cudaGetErrorString(err));
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(dev);
+  if (it == cache.end()) {
+    cudaDeviceProp prop;
+    err = cudaGetDeviceProperties(&prop, dev);
+    if (err != cudaSuccess) return fail(PT_ENODEV, "%s", cudaGetErrorString(err));
+    if (!(prop.major == 10 && prop.minor == 3))
+      return fail(PT_ENODEV, "device %d is sm_%d%d; libpt is built for sm_103a only", dev,
+                  prop.major, prop.minor);
+    DeviceInfo d;
+    d.device = dev;
+    d.sms = prop.multiProcessorCount;
+    d.cc_major = prop.major;
+    d.cc_minor = prop.minor;
+    d.smem_optin = prop.sharedMemPerBlockOptin;
+    it = cache.emplace(dev, d).first;
+  }
+  *info = it->second;
+  return PT_OK;
+}
+
+// Sub-buffer layout of the single device allocation of a problem.
+struct Layout {
+  size_t spins, T_temp, planes, temp_of_slot, slot_of_temp, cnt, E_slot, M_slot, attempted,
+      accepted, pairs, table, status, total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+Layout make_layout(int L, int R, int W, int mode, size_t table_entries) {
+  Layout l;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align256(off + bytes);
+    return at;
+  };
+  const size_t npairs = (size_t)std::max(R - 1, 1);
+  l.spins = take((size_t)W * L * L * 4);
+  l.T_temp = take((size_t)R * kClasses * 8);
+  l.planes = take((size_t)W * (mode == kModeFerro ? sizeof(PlaneFerro) : sizeof(PlaneGeneric)));
+  l.temp_of_slot = take((size_t)R * 4);
+  l.slot_of_temp = take((size_t)R * 4);
+  l.cnt = take((size_t)2 * W * 32 * 4);
+  l.E_slot = take((size_t)R * 8);
+  l.M_slot = take((size_t)R * 8);
+  l.attempted = take(npairs * 8);
+  l.accepted = take(npairs * 8);
+  l.pairs = take(npairs * sizeof(SwapPair));
+  l.table = take(std::max<size_t>(table_entries, 1) * 4);
+  l.status = take(64);
+  l.total = off;
+  return l;
+}
+
+int check_args(int L, const double* betas, int R, double J, double h, int64_t* s, int64_t* Ji,
+               int64_t* hi) {
+  if (L < 4 || L > PT_MAX_L || (L & 1))
+    return fail(PT_EINVAL, "L = %d must be even and within [4, %d]", L, PT_MAX_L);
+  if (R < 1 || R > PT_MAX_R) return fail(PT_EINVAL, "R = %d outside [1, %d]", R, PT_MAX_R);
+  if (!betas) return fail(PT_EINVAL, "betas is NULL");
+  for (int k = 0; k < R; ++k)
+    if (!std::isfinite(betas[k]) || betas[k] < 0.0)
+      return fail(PT_EINVAL, "betas[%d] = %g must be finite and >= 0", k, betas[k]);
+  if (quantise(J, h, s, Ji, hi) != PT_OK)
+    return fail(PT_EINVAL, "J = %g, h = %g have no common integer scale s <= 1000 (or exceed "
+                "2^20 after scaling)", J, h);
+  return PT_OK;
+}
+
+int mode_for(int64_t J_int, int64_t h_int) {
+  return (h_int == 0 && J_int > 0) ? kModeFerro : kModeGeneric;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Problem object
+// ---------------------------------------------------------------------------------------
+namespace ptb {
+
+int problem_fail(pt_problem* p, int code, const char* what, cudaError_t err) {
+  p->poisoned = code;
+  return fail(code, "%s: %s", what, cudaGetErrorString(err));
+}
+
+int problem_check(pt_problem* p) {
+  if (!p) return fail(PT_EINVAL, "problem is NULL");
+  if (p->poisoned) return fail(PT_ESTATE, "problem poisoned by an earlier failure (%s)",
+                                pt_strerror(p->poisoned));
+  return PT_OK;
+}
+
+int problem_device_guard(pt_problem* p) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return fail(PT_ENODEV, "cudaGetDevice failed");
+  if (cur != p->dev_info.device) {
+    const cudaError_t err = cudaSetDevice(p->dev_info.device);
+    if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "cudaSetDevice", err);
+  }
+  return PT_OK;
+}
+
+}  // namespace ptb
+
+namespace {
+
+void* dev_alloc(size_t bytes, cudaStream_t st, Allocator* used) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  *used = g_alloc;
+  if (g_alloc.alloc) return g_alloc.alloc(bytes, (void*)st, g_alloc.ctx);
+  void* ptr = nullptr;
+  if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return ptr;
+}
+
+void dev_free(void* ptr, cudaStream_t st, const Allocator& a) {
+  if (!ptr) return;
+  if (a.free)
+    a.free(ptr, (void*)st, a.ctx);
+  else
+    cudaFree(ptr);
+}
+
+// Host copy of one plane (both colours) of the problem.
+int read_plane(pt_problem* p, int w, std::vector<uint32_t>* buf) {
+  buf->resize((size_t)p->L * p->L);
+  cudaError_t err = cudaMemcpyAsync(buf->data(), p->dev.spins + (size_t)w * p->L * p->L,
+                                    buf->size() * 4, cudaMemcpyDeviceToHost, p->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(p->stream);
+  if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "reading spins", err);
+  return PT_OK;
+}
+
+int slot_at_temperature(pt_problem* p, int k, int* slot) {
+  int32_t r = -1;
+  cudaError_t err = cudaMemcpyAsync(&r, p->dev.slot_of_temp + k, 4, cudaMemcpyDeviceToHost,
+                                    p->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(p->stream);
+  if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "reading slot map", err);
+  if (r < 0 || r >= p->R) return fail(PT_EINTERNAL, "slot map corrupt");
+  *slot = r;
+  return PT_OK;
+}
+
+// Energy pass + finalize so that E_slot / M_slot describe the current state.
+int refresh_observables(pt_problem* p) {
+  cudaError_t err = launch_energy(p->dev, p->dev_info, p->stream);
+  if (err == cudaSuccess) err = launch_exchange(p->dev, p->e, kStepEnergy, p->stream);
+  if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "energy launch", err);
+  return PT_OK;
+}
+
+int read_observables(pt_problem* p, std::vector<int64_t>* E, std::vector<int64_t>* M,
+                     std::vector<int32_t>* slot_of_temp) {
+  int rc = refresh_observables(p);
+  if (rc) return rc;
+  E->resize(p->R);
+  M->resize(p->R);
+  slot_of_temp->resize(p->R);
+  cudaError_t err = cudaMemcpyAsync(E->data(), p->dev.E_slot, p->R * 8, cudaMemcpyDeviceToHost,
+                                    p->stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(M->data(), p->dev.M_slot, p->R * 8, cudaMemcpyDeviceToHost, p->stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(slot_of_temp->data(), p->dev.slot_of_temp, p->R * 4,
+                          cudaMemcpyDeviceToHost, p->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(p->stream);
+  if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "reading observables", err);
+  return PT_OK;
+}
+
+}  // namespace
+
+// =======================================================================================
+// C ABI
+// =======================================================================================
+extern "C" {
+
+const char* pt_version(void) { return "libpt 0.1 (sm_103a)"; }
+
+const char* pt_strerror(int code) {
+  switch (code) {
+    case PT_OK: return "ok";
+    case PT_EINVAL: return "invalid argument";
+    case PT_ENOMEM: return "out of memory";
+    case PT_ECUDA: return "CUDA error";
+    case PT_ETIMEOUT: return "device wait timed out";
+    case PT_ESTATE: return "problem poisoned by an earlier failure";
+    case PT_ENODEV: return "no usable sm_103 device";
+    case PT_EINTERNAL: return "internal error";
+    default: return "unknown error";
+  }
+}
+
+const char* pt_last_error(void) { return g_last_error.c_str(); }
+
+int pt_quantise(double J, double h, int64_t* s, int64_t* J_int, int64_t* h_int) {
+  if (!s || !J_int || !h_int) return fail(PT_EINVAL, "NULL output");
+  const int rc = quantise(J, h, s, J_int, h_int);
+  if (rc) return fail(rc, "J = %g, h = %g cannot be quantised", J, h);
+  return PT_OK;
+}
+
+uint64_t pt_spin_threshold(double beta, int64_t dE_int, int64_t s) {
+  return spin_threshold(beta, dE_int, s);
+}
+
+uint64_t pt_swap_threshold(double beta_lo, double beta_hi, int64_t n, int64_t s) {
+  std::shared_ptr<const PairTable> t;
+  if (get_pair_table(beta_lo, beta_hi, s, &t) != PT_OK) return ~uint64_t(0);
+  if (n < t->n_lo) return t->S_below;
+  if (n > t->n_hi) return t->S_above;
+  return t->vals[(size_t)(n - t->n_lo)];
+}
+
+int pt_set_allocator(pt_alloc_fn alloc, pt_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(PT_EINVAL, "alloc and free must both be set or both be NULL");
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_alloc.alloc = alloc;
+  g_alloc.free = free_fn;
+  g_alloc.ctx = ctx;
+  return PT_OK;
+}
+
+size_t pt_estimate_device_bytes(int L, const double* betas, int R, double J, double h) {
+  int64_t s, Ji, hi;
+  if (check_args(L, betas, R, J, h, &s, &Ji, &hi) != PT_OK) return 0;
+  size_t entries = 0;
+  for (int k = 0; k + 1 < R; ++k) {
+    std::shared_ptr<const PairTable> t;
+    if (get_pair_table(betas[k], betas[k + 1], s, &t) != PT_OK) return 0;
+    entries += t->vals.size();
+  }
+  const int W = (R + 31) / 32;
+  return make_layout(L, R, W, mode_for(Ji, hi), entries).total;
+}
+
+int pt_create(int L, const double* betas, int R, double J, double h, uint64_t seed,
+              pt_problem** out) {
+  if (!out) return fail(PT_EINVAL, "out is NULL");
+  *out = nullptr;
+  int64_t s, Ji, hi;
+  int rc = check_args(L, betas, R, J, h, &s, &Ji, &hi);
+  if (rc) return rc;
+  DeviceInfo dev;
+  rc = current_device(&dev);
+  if (rc) return rc;
+
+  std::unique_ptr<pt_problem> p(new pt_problem());
+  p->L = L;
+  p->R = R;
+  p->W = (R + 31) / 32;
+  p->mode = mode_for(Ji, hi);
+  p->betas.assign(betas, betas + R);
+  p->J = J;
+  p->h = h;
+  p->s = s;
+  p->J_int = Ji;
+  p->h_int = hi;
+  p->seed = seed;
+  p->dev_info = dev;
+  p->stream = 0;
+
+  // thresholds by temperature, class c = 2 k + (sigma == +1)
+  std::vector<uint64_t> T_temp((size_t)R * kClasses);
+  for (int k = 0; k < R; ++k)
+    for (int kk = 0; kk <= 4; ++kk)
+      for (int up = 0; up <= 1; ++up) {
+        const int64_t sigma = up ? 1 : -1;
+        const int64_t nb = 4 - 2 * kk;  // sigma * sum of neighbour spins
+        const int64_t dE = 2 * (Ji * nb - hi * sigma);
+        T_temp[(size_t)k * kClasses + 2 * kk + up] = spin_threshold(betas[k], dE, s);
+      }
+  if (p->mode == kModeFerro)
+    for (int k = 0; k < R; ++k)
+      if (T_temp[(size_t)k * kClasses + 1] > T_temp[(size_t)k * kClasses + 3])
+        return fail(PT_EINTERNAL, "threshold order violated at temperature %d", k);
+
+  // exchange tables
+  const int npairs = std::max(R - 1, 1);
+  std::vector<std::shared_ptr<const PairTable>> tabs;
+  std::vector<SwapPair> pairs((size_t)npairs);
+  size_t entries = 0;
+  for (int k = 0; k + 1 < R; ++k) {
+    std::shared_ptr<const PairTable> t;
+    rc = get_pair_table(betas[k], betas[k + 1], s, &t);
+    if (rc) return rc;
+    pairs[k].n_lo = t->n_lo;
+    pairs[k].n_hi = t->n_hi;
+    pairs[k].S_below = t->S_below;
+    pairs[k].S_above = t->S_above;
+    pairs[k].offset = (int64_t)entries;
+    entries += t->vals.size();
+    tabs.push_back(t);
+  }
+
+  // device memory: one allocation
+  const Layout lay = make_layout(L, R, p->W, p->mode, entries);
+  Allocator used;
+  void* mem = dev_alloc(lay.total, p->stream, &used);
+  if (!mem) return fail(PT_ENOMEM, "device allocation of %zu bytes failed", lay.total);
+  p->dmem = mem;
+  p->dbytes = lay.total;
+  p->allocator_free = used.free;
+  p->allocator_ctx = used.ctx;
+  uint8_t* base = (uint8_t*)mem;
+  DevProblem& d = p->dev;
+  d.spins = (uint32_t*)(base + lay.spins);
+  d.L = L;
+  d.R = R;
+  d.W = p->W;
+  d.mode = p->mode;
+  d.key0 = (uint32_t)seed;
+  d.key1 = (uint32_t)(seed >> 32);
+  d.J_int = Ji;
+  d.h_int = hi;
+  d.s = s;
+  d.T_temp = (const uint64_t*)(base + lay.T_temp);
+  d.planes = base + lay.planes;
+  d.temp_of_slot = (int32_t*)(base + lay.temp_of_slot);
+  d.slot_of_temp = (int32_t*)(base + lay.slot_of_temp);
+  d.cnt = (uint32_t*)(base + lay.cnt);
+  d.E_slot = (int64_t*)(base + lay.E_slot);
+  d.M_slot = (int64_t*)(base + lay.M_slot);
+  d.attempted = (uint64_t*)(base + lay.attempted);
+  d.accepted = (uint64_t*)(base + lay.accepted);
+  d.pairs = (const SwapPair*)(base + lay.pairs);
+  d.swap_table = (const uint32_t*)(base + lay.table);
+  d.status = (int32_t*)(base + lay.status);
+
+  // one staging image of everything from T_temp to the end, copied in one transfer
+  const size_t img_off = lay.T_temp, img_len = lay.total - lay.T_temp;
+  std::vector<uint8_t> img(img_len, 0);
+  auto put = [&](size_t off, const void* src, size_t bytes) {
+    memcpy(img.data() + (off - img_off), src, bytes);
+  };
+  put(lay.T_temp, T_temp.data(), T_temp.size() * 8);
+  std::vector<int32_t> ident(R);
+  for (int r = 0; r < R; ++r) ident[r] = r;
+  put(lay.temp_of_slot, ident.data(), R * 4);
+  put(lay.slot_of_temp, ident.data(), R * 4);
+  put(lay.pairs, pairs.data(), pairs.size() * sizeof(SwapPair));
+  for (int k = 0; k + 1 < R; ++k)
+    if (!tabs[k]->vals.empty())
+      put(lay.table + (size_t)pairs[k].offset * 4, tabs[k]->vals.data(), tabs[k]->vals.size() * 4);
+  cudaError_t err = cudaMemcpyAsync(base + img_off, img.data(), img_len, cudaMemcpyHostToDevice,
+                                    p->stream);
+  if (err == cudaSuccess) err = launch_init(d, dev, p->stream);
+  if (err == cudaSuccess) err = launch_exchange(d, 0, kStepRebuild, p->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(p->stream);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    dev_free(mem, p->stream, used);
+    return fail(PT_ECUDA, "initialising problem: %s", cudaGetErrorString(err));
+  }
+  *out = p.release();
+  return PT_OK;
+}
+
+void pt_destroy(pt_problem* p) {
+  if (!p) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != p->dev_info.device) cudaSetDevice(p->dev_info.device);
+  cudaStreamSynchronize(p->stream);
+  cudaGetLastError();
+  Allocator a;
+  a.free = p->allocator_free;
+  a.ctx = p->allocator_ctx;
+  dev_free(p->dmem, p->stream, a);
+  if (cur >= 0 && cur != p->dev_info.device) cudaSetDevice(cur);
+  delete p;
+}
+
+int pt_set_stream(pt_problem* p, void* cuda_stream) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  if ((rc = problem_device_guard(p))) return rc;
+  const cudaError_t err = cudaStreamSynchronize(p->stream);
+  if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "synchronising old stream", err);
+  p->stream = (cudaStream_t)cuda_stream;
+  return PT_OK;
+}
+
+int pt_sweep(pt_problem* p, int64_t n, int exchange_every) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  if (n < 0 || exchange_every < 0)
+    return fail(PT_EINVAL, "n = %lld and exchange_every = %d must be >= 0", (long long)n,
+                exchange_every);
+  if ((rc = problem_device_guard(p))) return rc;
+  for (int64_t j = 0; j < n; ++j) {
+    cudaError_t err = launch_half_sweep(p->dev, p->dev_info, 0, p->t, p->stream);
+    if (err == cudaSuccess) err = launch_half_sweep(p->dev, p->dev_info, 1, p->t, p->stream);
+    if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "sweep launch", err);
+    p->t += 1;
+    if (exchange_every > 0 && p->t % (uint64_t)exchange_every == 0) {
+      err = launch_energy(p->dev, p->dev_info, p->stream);
+      if (err == cudaSuccess)
+        err = launch_exchange(p->dev, p->e, kStepEnergy | kStepExchange | kStepRebuild,
+                              p->stream);
+      if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "exchange launch", err);
+      p->e += 1;
+    }
+  }
+  return PT_OK;
+}
+
+int pt_synchronize(pt_problem* p) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  if ((rc = problem_device_guard(p))) return rc;
+  cudaError_t err = cudaStreamSynchronize(p->stream);
+  if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "synchronise", err);
+  int32_t status = 0;
+  err = cudaMemcpy(&status, p->dev.status, 4, cudaMemcpyDeviceToHost);
+  if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "reading status", err);
+  if (status != 0) {
+    p->poisoned = status == PT_ETIMEOUT ? PT_ETIMEOUT : PT_EINTERNAL;
+    return fail(p->poisoned, "device reported status %d", status);
+  }
+  return PT_OK;
+}
+
+int pt_energies_int(pt_problem* p, int64_t* E_int, int64_t* M, int64_t* scale) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  if ((rc = problem_device_guard(p))) return rc;
+  std::vector<int64_t> E, Ms;
+  std::vector<int32_t> sot;
+  if ((rc = read_observables(p, &E, &Ms, &sot))) return rc;
+  for (int k = 0; k < p->R; ++k) {
+    if (E_int) E_int[k] = E[sot[k]];
+    if (M) M[k] = Ms[sot[k]];
+  }
+  if (scale) *scale = p->s;
+  return pt_synchronize(p);
+}
+
+int pt_energies(pt_problem* p, double* out) {
+  if (!out) return fail(PT_EINVAL, "out is NULL");
+  std::vector<int64_t> E(p ? p->R : 0);
+  int64_t s = 1;
+  const int rc = pt_energies_int(p, E.data(), nullptr, &s);
+  if (rc) return rc;
+  for (int k = 0; k < p->R; ++k) out[k] = (double)E[k] / (double)s;
+  return PT_OK;
+}
+
+int pt_magnetisations(pt_problem* p, double* out) {
+  if (!out) return fail(PT_EINVAL, "out is NULL");
+  std::vector<int64_t> M(p ? p->R : 0);
+  const int rc = pt_energies_int(p, nullptr, M.data(), nullptr);
+  if (rc) return rc;
+  for (int k = 0; k < p->R; ++k) out[k] = (double)M[k];
+  return PT_OK;
+}
+
+int pt_swap_stats(pt_problem* p, uint64_t* attempted, uint64_t* accepted) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  if ((rc = problem_device_guard(p))) return rc;
+  if (p->R < 2) return pt_synchronize(p);
+  cudaError_t err = cudaSuccess;
+  if (attempted)
+    err = cudaMemcpyAsync(attempted, p->dev.attempted, (p->R - 1) * 8, cudaMemcpyDeviceToHost,
+                          p->stream);
+  if (err == cudaSuccess && accepted)
+    err = cudaMemcpyAsync(accepted, p->dev.accepted, (p->R - 1) * 8, cudaMemcpyDeviceToHost,
+                          p->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(p->stream);
+  if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "reading swap stats", err);
+  return pt_synchronize(p);
+}
+
+int pt_chain_map(pt_problem* p, int32_t* slot_of_temp) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  if (!slot_of_temp) return fail(PT_EINVAL, "out is NULL");
+  if ((rc = problem_device_guard(p))) return rc;
+  cudaError_t err = cudaMemcpyAsync(slot_of_temp, p->dev.slot_of_temp, p->R * 4,
+                                    cudaMemcpyDeviceToHost, p->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(p->stream);
+  if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "reading chain map", err);
+  return pt_synchronize(p);
+}
+
+int pt_counters(pt_problem* p, uint64_t* sweeps_done, uint64_t* exchanges_done) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  if (sweeps_done) *sweeps_done = p->t;
+  if (exchanges_done) *exchanges_done = p->e;
+  return PT_OK;
+}
+
+size_t pt_device_bytes(const pt_problem* p) { return p ? p->dbytes : 0; }
+
+int pt_get_spins(pt_problem* p, int k, int8_t* out) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  if (!out || k < 0 || k >= p->R) return fail(PT_EINVAL, "bad temperature index %d", k);
+  if ((rc = problem_device_guard(p))) return rc;
+  int r;
+  if ((rc = slot_at_temperature(p, k, &r))) return rc;
+  std::vector<uint32_t> plane;
+  if ((rc = read_plane(p, r >> 5, &plane))) return rc;
+  const int L = p->L, half = L / 2, b = r & 31;
+  for (int c = 0; c < 2; ++c)
+    for (int y = 0; y < L; ++y)
+      for (int i = 0; i < half; ++i) {
+        const int x = 2 * i + ((y + c) & 1);
+        const uint32_t w = plane[((size_t)c * L + y) * half + i];
+        out[(size_t)y * L + x] = ((w >> b) & 1u) ? (int8_t)1 : (int8_t)-1;
+      }
+  return pt_synchronize(p);
+}
+
+int pt_set_spins(pt_problem* p, int k, const int8_t* in) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  if (!in || k < 0 || k >= p->R) return fail(PT_EINVAL, "bad temperature index %d", k);
+  const int L = p->L, half = L / 2;
+  for (size_t q = 0; q < (size_t)L * L; ++q)
+    if (in[q] != 1 && in[q] != -1) return fail(PT_EINVAL, "spin %zu is %d, not +-1", q, in[q]);
+  if ((rc = problem_device_guard(p))) return rc;
+  int r;
+  if ((rc = slot_at_temperature(p, k, &r))) return rc;
+  std::vector<uint32_t> plane;
+  if ((rc = read_plane(p, r >> 5, &plane))) return rc;
+  const int b = r & 31;
+  for (int c = 0; c < 2; ++c)
+    for (int y = 0; y < L; ++y)
+      for (int i = 0; i < half; ++i) {
+        const int x = 2 * i + ((y + c) & 1);
+        uint32_t& w = plane[((size_t)c * L + y) * half + i];
+        w = (w & ~(1u << b)) | ((in[(size_t)y * L + x] > 0 ? 1u : 0u) << b);
+      }
+  cudaError_t err = cudaMemcpyAsync(p->dev.spins + (size_t)(r >> 5) * L * L, plane.data(),
+                                    plane.size() * 4, cudaMemcpyHostToDevice, p->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(p->stream);
+  if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "writing spins", err);
+  return PT_OK;
+}
+
+int pt_set_batch_tuning(int cluster, int joint_min_L) {
+  if (!(cluster == 1 || cluster == 2 || cluster == 4 || cluster == 8 || cluster == 16) ||
+      joint_min_L < 4)
+    return fail(PT_EINVAL, "cluster = %d, joint_min_L = %d", cluster, joint_min_L);
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_batch_tuning.cluster = cluster;
+  g_batch_tuning.joint_min_L = joint_min_L;
+  return PT_OK;
+}
+
+int pt_get_batch_tuning(int* cluster, int* joint_min_L) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (cluster) *cluster = g_batch_tuning.cluster;
+  if (joint_min_L) *joint_min_L = g_batch_tuning.joint_min_L;
+  return PT_OK;
+}
+
+int pt_sweep_batch(pt_problem* const* problems, int count, const int64_t* n,
+                   const int* exchange_every) {
+  if (count < 0 || (count > 0 && (!problems || !n || !exchange_every)))
+    return fail(PT_EINVAL, "bad batch arguments");
+  if (count == 0) return PT_OK;
+  return ptb::sweep_batch(problems, count, n, exchange_every);
+}
+
+}  // extern "C"

@@ -1,0 +1,34 @@
+// pt_internal.h -- the host-side problem object shared by the host translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "pt.h"
+#include "pt_launch.h"
+
+struct pt_problem {
+  int L = 0, R = 0, W = 0, mode = 0;
+  std::vector<double> betas;
+  double J = 0, h = 0;
+  int64_t s = 1, J_int = 0, h_int = 0;
+  uint64_t seed = 0;
+  uint64_t t = 0, e = 0;  // sweeps and swap iterations enqueued so far
+  cudaStream_t stream = 0;
+  void* dmem = nullptr;   // the problem's single device allocation
+  size_t dbytes = 0;
+  pt_free_fn allocator_free = nullptr;
+  void* allocator_ctx = nullptr;
+  ptb::DevProblem dev{};
+  ptb::DeviceInfo dev_info{};
+  int poisoned = 0;       // sticky PT_E* code once device work failed
+};
+
+namespace ptb {
+// Records the message for pt_last_error() and returns code.
+int fail(int code, const char* fmt, ...);
+int problem_fail(pt_problem* p, int code, const char* what, cudaError_t err);
+int problem_check(pt_problem* p);
+int problem_device_guard(pt_problem* p);
+}  // namespace ptb

@@ -1,0 +1,329 @@
+// pt_kernels.cu -- the per-problem ("plain") kernels: initial spins, one checkerboard half
+// sweep per launch, bit-sliced energy/magnetisation count, and the exchange step.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pt_device.cuh"
+#include "pt_launch.h"
+
+namespace ptb {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// Walks the words (y, i) of one colour of one plane with a grid-stride loop, keeping y and i
+// up to date without a division per step.
+struct RowWalker {
+  int y, i, dy, di, half;
+  __device__ __forceinline__ RowWalker(int start, int stride, int half_) : half(half_) {
+    y = start / half_;
+    i = start - y * half_;
+    dy = stride / half_;
+    di = stride - dy * half_;
+  }
+  __device__ __forceinline__ void step() {
+    i += di;
+    y += dy;
+    if (i >= half) {
+      i -= half;
+      y += 1;
+    }
+  }
+};
+
+__device__ __forceinline__ int nslots_of_plane(int R, int w) { return min(32, R - 32 * w); }
+
+__device__ __forceinline__ uint32_t used_mask(int nslots) {
+  return nslots >= 32 ? 0xffffffffu : ((1u << nslots) - 1u);
+}
+
+// ---------------------------------------------------------------------------------------
+// Initial state (Sec. 3 initialisation phase): sigma = +1 iff bit 31 of the TAG_INIT draw.
+// grid = (X, W, 2 colours)
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_init(DevProblem p) {
+  const int w = blockIdx.y, c = blockIdx.z;
+  const int L = p.L, half = L >> 1;
+  const int nslots = nslots_of_plane(p.R, w);
+  const int nblk = (nslots + 3) >> 2;
+  const uint32_t used = used_mask(nslots);
+  uint32_t* out = p.spins + word_index(L, w, c, 0, 0);
+  const int nwords = L * half;
+  const int start = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
+  if (start >= nwords) return;
+  RowWalker rw(start, stride, half);
+  for (int idx = start; idx < nwords; idx += stride, rw.step()) {
+    const int x = 2 * rw.i + ((rw.y + c) & 1);
+    const uint32_t site = (uint32_t)(rw.y * L + x);
+    uint32_t word = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (j < nblk) {
+        const Philox4 r = philox4x32_10(site, 0u, (uint32_t)(8 * w + j), kTagInit, p.key0, p.key1);
+        word |= ((r.x >> 31) << (4 * j)) | ((r.y >> 31) << (4 * j + 1)) |
+                ((r.z >> 31) << (4 * j + 2)) | ((r.w >> 31) << (4 * j + 3));
+      }
+    }
+    out[idx] = word & used;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// One half sweep: every word of colour `colour` of plane blockIdx.y gets its Metropolis
+// update. grid = (X, W)
+// ---------------------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_half_sweep(DevProblem p, int colour, uint64_t t) {
+  const int w = blockIdx.y;
+  const int L = p.L, half = L >> 1;
+  const int nslots = nslots_of_plane(p.R, w);
+  const int nblk = (nslots + 3) >> 2;
+  const SweepCtr cx = make_sweep_ctr(t, p.key0, p.key1);
+  uint32_t* own = p.spins + word_index(L, w, colour, 0, 0);
+  const uint32_t* oth = p.spins + word_index(L, w, colour ^ 1, 0, 0);
+  const int nwords = L * half;
+  const int start = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
+
+  if (MODE == kModeFerro) {
+    const PlaneFerro* pl = reinterpret_cast<const PlaneFerro*>(p.planes) + w;
+    uint32_t T0[32], T1[32];
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+      T0[b] = pl->T0[b];
+      T1[b] = pl->T1[b];
+    }
+    const uint32_t alw0 = pl->alw0, alw1 = pl->alw1, used = pl->used;
+    if (start >= nwords) return;
+    RowWalker rw(start, stride, half);
+    for (int idx = start; idx < nwords; idx += stride, rw.step()) {
+      const int y = rw.y, i = rw.i;
+      const int par = (y + colour) & 1;
+      const int ym = (y == 0) ? L - 1 : y - 1;
+      const int yp = (y == L - 1) ? 0 : y + 1;
+      const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
+      const uint32_t s = own[idx];
+      const uint32_t n0 = oth[ym * half + i];
+      const uint32_t n1 = oth[yp * half + i];
+      const uint32_t n2 = oth[y * half + i];
+      const uint32_t n3 = oth[y * half + ih];
+      const uint32_t site = (uint32_t)(y * L + 2 * i + par);
+      own[idx] = update_word_ferro(s, n0, n1, n2, n3, site, (uint32_t)(8 * w), nblk, T0, T1,
+                                   alw0, alw1, used, cx);
+    }
+  } else {
+    __shared__ PlaneGeneric pl;
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(
+        reinterpret_cast<const PlaneGeneric*>(p.planes) + w);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&pl);
+    for (int q = threadIdx.x; q < (int)(sizeof(PlaneGeneric) / 4); q += blockDim.x) dst[q] = src[q];
+    __syncthreads();
+    if (start >= nwords) return;
+    RowWalker rw(start, stride, half);
+    for (int idx = start; idx < nwords; idx += stride, rw.step()) {
+      const int y = rw.y, i = rw.i;
+      const int par = (y + colour) & 1;
+      const int ym = (y == 0) ? L - 1 : y - 1;
+      const int yp = (y == L - 1) ? 0 : y + 1;
+      const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
+      const uint32_t s = own[idx];
+      const uint32_t n0 = oth[ym * half + i];
+      const uint32_t n1 = oth[yp * half + i];
+      const uint32_t n2 = oth[y * half + i];
+      const uint32_t n3 = oth[y * half + ih];
+      const uint32_t site = (uint32_t)(y * L + 2 * i + par);
+      own[idx] = update_word_generic(s, n0, n1, n2, n3, site, (uint32_t)(8 * w), nblk, pl, cx);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Energy / magnetisation count (per slot): every bond joins a colour-0 and a colour-1 site,
+// so the unsatisfied bonds are the anti-aligned neighbours of the colour-0 sites; the up
+// spins are counted on both colours. Accumulated into p.cnt (which must start at zero).
+// grid = (X, W); each thread handles at most kMaxWordsPerThread colour-0 words.
+// ---------------------------------------------------------------------------------------
+constexpr int kMaxWordsPerThread = 4000;  // 4 * 4000 < 2^14 (per-thread counter depth)
+
+__global__ void __launch_bounds__(kThreads) k_energy(DevProblem p) {
+  const int w = blockIdx.y;
+  const int L = p.L, half = L >> 1;
+  const uint32_t* c0 = p.spins + word_index(L, w, 0, 0, 0);
+  const uint32_t* c1 = p.spins + word_index(L, w, 1, 0, 0);
+  const int nwords = L * half;
+  const int start = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
+  BitCounter<20, 14> U, N;
+  U.zero();
+  N.zero();
+  if (start < nwords) {
+    RowWalker rw(start, stride, half);
+    for (int idx = start; idx < nwords; idx += stride, rw.step()) {
+      const int y = rw.y, i = rw.i;
+      const int par = y & 1;
+      const int ym = (y == 0) ? L - 1 : y - 1;
+      const int yp = (y == L - 1) ? 0 : y + 1;
+      const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
+      const uint32_t s = c0[idx];
+      const uint32_t o = c1[idx];
+      const NbCount k = count4(s ^ c1[ym * half + i], s ^ c1[yp * half + i], s ^ o,
+                               s ^ c1[y * half + ih]);
+      U.add3(k.b0, k.b1, k.b2);
+      N.add2(s ^ o, s & o);
+    }
+  }
+  const uint32_t u = U.warp_total_for_lane();
+  const uint32_t n = N.warp_total_for_lane();
+  __shared__ uint32_t acc[2][32];
+  if (threadIdx.x < 64) (&acc[0][0])[threadIdx.x] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  atomicAdd(&acc[0][lane], u);
+  atomicAdd(&acc[1][lane], n);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    if (acc[0][threadIdx.x]) atomicAdd(&p.cnt[w * 32 + threadIdx.x], acc[0][threadIdx.x]);
+    if (acc[1][threadIdx.x])
+      atomicAdd(&p.cnt[p.W * 32 + w * 32 + threadIdx.x], acc[1][threadIdx.x]);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Exchange step (Sec. 3), one block:
+//   kEnergy:   E_slot / M_slot from the counts (then clears the counts)
+//   kExchange: swap iteration e on pairs (k, k+1), k = e & 1 (mod 2); swaps temperature
+//              indices of accepted pairs and counts attempts / acceptances
+//   kRebuild:  rewrites the per-plane thresholds for the current slot -> temperature map
+// ---------------------------------------------------------------------------------------
+__device__ void rebuild_planes(const DevProblem& p) {
+  const int R = p.R, W = p.W;
+  constexpr uint64_t kTwo32 = 1ull << 32;
+  for (int r = threadIdx.x; r < W * 32; r += blockDim.x) {  // whole warps: W * 32 % 32 == 0
+    const int w = r >> 5, b = r & 31;
+    const bool in_use = r < R;
+    const int temp = in_use ? p.temp_of_slot[r] : 0;
+    const uint32_t used = __ballot_sync(0xffffffffu, in_use);
+    if (p.mode == kModeFerro) {
+      PlaneFerro* pl = reinterpret_cast<PlaneFerro*>(p.planes) + w;
+      // class index 2 k + 1 (sigma = +1; with h = 0 both signs share the threshold)
+      const uint64_t t0 = in_use ? p.T_temp[(size_t)temp * kClasses + 1] : 0;
+      const uint64_t t1 = in_use ? p.T_temp[(size_t)temp * kClasses + 3] : 0;
+      pl->T0[b] = (uint32_t)min(t0, kTwo32 - 1);
+      pl->T1[b] = (uint32_t)min(t1, kTwo32 - 1);
+      const uint32_t a0 = __ballot_sync(0xffffffffu, in_use && t0 >= kTwo32);
+      const uint32_t a1 = __ballot_sync(0xffffffffu, in_use && t1 >= kTwo32);
+      if (b == 0) {
+        pl->alw0 = a0;
+        pl->alw1 = a1;
+        pl->used = used;
+        pl->pad = 0;
+      }
+    } else {
+      PlaneGeneric* pl = reinterpret_cast<PlaneGeneric*>(p.planes) + w;
+#pragma unroll
+      for (int c = 0; c < kClasses; ++c) {
+        const uint64_t tc = in_use ? p.T_temp[(size_t)temp * kClasses + c] : 0;
+        pl->T[c][b] = (uint32_t)min(tc, kTwo32 - 1);
+        const uint32_t a = __ballot_sync(0xffffffffu, in_use && tc >= kTwo32);
+        if (b == 0) pl->alw[c] = a;
+      }
+      if (b == 0) {
+        pl->used = used;
+        pl->pad = 0;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_exchange(DevProblem p, uint64_t e, int flags) {
+  const int R = p.R, W = p.W;
+  const int64_t L2 = (int64_t)p.L * p.L;
+  if (flags & kStepEnergy) {
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+      const int64_t U = p.cnt[r];
+      const int64_t ones = p.cnt[W * 32 + r];
+      const int64_t bonds = 2 * L2 - 2 * U;  // sum over bonds of sigma_i sigma_j
+      const int64_t M = 2 * ones - L2;
+      p.E_slot[r] = -p.J_int * bonds + p.h_int * M;
+      p.M_slot[r] = M;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 2 * W * 32; q += blockDim.x) p.cnt[q] = 0;
+  }
+  if (flags & kStepExchange) {
+    __syncthreads();
+    const int parity = (int)(e & 1);
+    const uint32_t c3 = kTagExch | ((uint32_t)(e >> 32) << 8);
+    for (int k = parity + 2 * threadIdx.x; k + 1 < R; k += 2 * blockDim.x) {
+      const int a = p.slot_of_temp[k], b = p.slot_of_temp[k + 1];
+      const int64_t n = p.E_slot[a] - p.E_slot[b];
+      const SwapPair sp = p.pairs[k];
+      uint64_t S;
+      if (n < sp.n_lo)
+        S = sp.S_below;
+      else if (n > sp.n_hi)
+        S = sp.S_above;
+      else
+        S = p.swap_table[sp.offset + (n - sp.n_lo)];
+      const Philox4 rnd = philox4x32_10((uint32_t)k, (uint32_t)e, 0u, c3, p.key0, p.key1);
+      p.attempted[k] += 1;
+      if ((uint64_t)rnd.x < S) {
+        p.accepted[k] += 1;
+        p.slot_of_temp[k] = b;
+        p.slot_of_temp[k + 1] = a;
+        p.temp_of_slot[a] = k + 1;
+        p.temp_of_slot[b] = k;
+      }
+    }
+  }
+  if (flags & kStepRebuild) {
+    __syncthreads();
+    rebuild_planes(p);
+  }
+}
+
+int grid_x_for(int nwords, int W, int sms, int per_sm) {
+  int want = (nwords + kThreads - 1) / kThreads;
+  int cap = (sms * per_sm + W - 1) / W;
+  if (cap < 1) cap = 1;
+  return want < cap ? (want > 0 ? want : 1) : cap;
+}
+
+}  // namespace
+
+cudaError_t launch_init(const DevProblem& p, const DeviceInfo& dev, cudaStream_t st) {
+  const int nwords = p.L * (p.L >> 1);
+  dim3 grid(grid_x_for(nwords, p.W, dev.sms, 8), p.W, 2);
+  k_init<<<grid, kThreads, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_half_sweep(const DevProblem& p, const DeviceInfo& dev, int colour,
+                              uint64_t t, cudaStream_t st) {
+  const int nwords = p.L * (p.L >> 1);
+  dim3 grid(grid_x_for(nwords, p.W, dev.sms, 4), p.W);
+  if (p.mode == kModeFerro)
+    k_half_sweep<kModeFerro><<<grid, kThreads, 0, st>>>(p, colour, t);
+  else
+    k_half_sweep<kModeGeneric><<<grid, kThreads, 0, st>>>(p, colour, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy(const DevProblem& p, const DeviceInfo& dev, cudaStream_t st) {
+  const int nwords = p.L * (p.L >> 1);
+  int gx = grid_x_for(nwords, p.W, dev.sms, 8);
+  const int min_gx = (nwords + kThreads * kMaxWordsPerThread - 1) / (kThreads * kMaxWordsPerThread);
+  if (gx < min_gx) gx = min_gx;
+  dim3 grid(gx, p.W);
+  k_energy<<<grid, kThreads, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exchange(const DevProblem& p, uint64_t e, int flags, cudaStream_t st) {
+  k_exchange<<<1, kThreads, 0, st>>>(p, e, flags);
+  return cudaGetLastError();
+}
+
+}  // namespace ptb

@@ -1,0 +1,29 @@
+// pt_launch.h -- host-side entry points of the kernels (implemented in the .cu files).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pt_types.h"
+
+namespace ptb {
+
+struct DeviceInfo {
+  int device;
+  int sms;
+  int cc_major, cc_minor;
+  size_t smem_optin;  // max dynamic shared memory per block (opt-in)
+};
+
+enum StepFlags : int {
+  kStepEnergy = 1,    // turn the accumulated counts into E_slot / M_slot and clear them
+  kStepExchange = 2,  // one swap iteration
+  kStepRebuild = 4,   // refresh the per-plane thresholds
+};
+
+cudaError_t launch_init(const DevProblem& p, const DeviceInfo& dev, cudaStream_t st);
+cudaError_t launch_half_sweep(const DevProblem& p, const DeviceInfo& dev, int colour,
+                              uint64_t t, cudaStream_t st);
+cudaError_t launch_energy(const DevProblem& p, const DeviceInfo& dev, cudaStream_t st);
+cudaError_t launch_exchange(const DevProblem& p, uint64_t e, int flags, cudaStream_t st);
+
+}  // namespace ptb

@@ -1,0 +1,111 @@
+"""The C-ABI library without a GPU: it loads, exports every function include/pt.h declares,
+its host-built tables equal the oracle's value for value, and device calls fail loudly
+(PT_ENODEV) instead of falling back to the CPU."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from tests.conftest import ROOT
+
+TWO32 = 1 << 32
+
+
+@pytest.fixture(scope="module")
+def pt():
+    from paper_2512_03825_b300 import build as B
+    B.build()
+    from paper_2512_03825_b300 import _lib
+    return _lib
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "pt.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(pt_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(n for n in names if not n.endswith("_fn")))
+
+
+def test_exports_every_declared_function(pt):
+    declared = _declared_functions()
+    assert len(declared) >= 20
+    raw = C.CDLL(pt.LIB_PATH)
+    for name in declared:
+        assert hasattr(raw, name), name
+    bound = {n for n, _, _ in pt.SIGNATURES}
+    assert set(declared) == bound
+
+
+def test_only_pt_symbols_exported(pt):
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", pt.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    syms = [line.split()[-1] for line in out.splitlines() if " T " in line]
+    assert syms and all(s.startswith("pt_") for s in syms), syms
+
+
+def test_quantise_matches_oracle(pt):
+    from paper_2512_03825_b300 import api
+    for J, h in [(1, 0), (1, 0.1), (0.5, 0), (1 / 3, 0), (-1, 0.25), (2, -0.3), (0, 1)]:
+        assert api.quantise(J, h) == oracle.quantise(J, h)
+    with pytest.raises(Exception):
+        api.quantise(np.pi, 0)
+
+
+def test_spin_thresholds_equal_oracle(pt):
+    from paper_2512_03825_b300 import api
+    rng = np.random.Generator(np.random.PCG64(1))
+    for _ in range(20000):
+        beta = float(rng.uniform(0, 2.0)) if rng.random() > 0.05 else 0.0
+        dE = int(rng.integers(-100, 100))
+        s = int(rng.choice([1, 2, 10, 1000]))
+        assert api.spin_threshold(beta, dE, s) == oracle.spin_threshold(beta, dE, s)
+
+
+@pytest.mark.parametrize("blo,bhi,s", [
+    (0.30, 0.30 + 0.25 / 31, 1), (0.35, 0.35 + 0.15 / 63, 1), (0.3, 0.3 + 0.3 / 63, 10),
+    (0.5, 0.4, 1), (0.4, 0.4, 1), (0.2, 0.6, 1), (0.0, 1e-3, 2), (1.0, 0.2, 10)])
+def test_swap_table_equals_oracle(pt, blo, bhi, s):
+    """Every n where the table or its saturated ends decide: equal to the oracle's direct
+    evaluation of the rule (checked on the whole interior, its edges and far outside)."""
+    from paper_2512_03825_b300 import api
+    d = bhi - blo
+    if d == 0:
+        ns = list(range(-50, 51)) + [10 ** 9, -10 ** 9]
+    else:
+        N = int(np.ceil(46.0 * s / abs(d)))
+        ns = list(range(-N, N + 1, max(1, N // 20000))) + [N + 5, -N - 5, 10 ** 12, -10 ** 12]
+        # dense around both saturation edges
+        lo_edge = int(np.floor(-36.8 * s / d)) if d > 0 else int(np.floor(36.8 * s / -d))
+        hi_edge = int(np.floor(22.2 * s / d)) if d > 0 else int(np.floor(-22.2 * s / -d))
+        for e in (lo_edge, hi_edge):
+            ns += list(range(e - 300, e + 300))
+    for n in ns:
+        assert api.swap_threshold(blo, bhi, n, s) == oracle.swap_threshold(blo, bhi, n, s), n
+
+
+def test_no_gpu_fails_loudly(pt):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2512_03825_b300 import api
+    with pytest.raises(pt.PTError) as ei:
+        api.PTProblem(16, [0.3, 0.4])
+    assert ei.value.code == pt.PT_ENODEV
+
+
+def test_bad_arguments_rejected_before_device(pt):
+    from paper_2512_03825_b300 import api
+    for L, betas, J, h in [(5, [0.1], 1, 0), (2, [0.1], 1, 0), (8, [], 1, 0), (8, [-0.1], 1, 0),
+                           (8, [float("nan")], 1, 0), (8, [0.1], np.pi, 0),
+                           (32768, [0.1], 1, 0)]:
+        with pytest.raises(pt.PTError) as ei:
+            api.PTProblem(L, betas, J=J, h=h)
+        assert ei.value.code == pt.PT_EINVAL
+    assert api.estimate_device_bytes(5, [0.1]) == 0
+    assert api.estimate_device_bytes(1024, np.linspace(0.35, 0.5, 64)) > 8 * 2 ** 20

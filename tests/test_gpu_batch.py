@@ -1,0 +1,117 @@
+"""The batched persistent kernel: each problem advanced inside a batch is bit-identical to
+the same problem advanced alone (plain path) and to the CPU oracle, for every launch shape
+the autotuner may pick, and batches compose with plain sweeps and with each other."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_03825_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2512_03825_b300 import build as B
+    B.build()
+    from paper_2512_03825_b300 import api as A
+    return A
+
+
+@pytest.fixture
+def tuning(api):
+    from paper_2512_03825_b300._lib import lib
+    import ctypes as C
+    c, j = C.c_int(), C.c_int()
+    lib.pt_get_batch_tuning(C.byref(c), C.byref(j))
+    yield lambda cl, jm: lib.pt_set_batch_tuning(cl, jm)
+    lib.pt_set_batch_tuning(c.value, j.value)
+
+
+def state(g):
+    return (g.spins(), g.energies_int(), g.magnetisations(), g.chain_map(),
+            *g.swap_stats(), g.counters())
+
+
+def assert_state_equal(a, b, where=""):
+    for x, y in zip(state(a) if not isinstance(a, tuple) else a,
+                    state(b) if not isinstance(b, tuple) else b):
+        np.testing.assert_array_equal(np.asarray(x), np.asarray(y), err_msg=where)
+
+
+def mixed_problems(n=24, seed=5):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for j in range(n):
+        L = int(rng.choice([4, 6, 8, 12, 16, 24, 32, 48, 64]))
+        R = int(rng.integers(1, 70))
+        J, h = [(1.0, 0.0), (1.0, 0.1), (-1.0, 0.25), (1.0, 0.0)][j % 4]
+        out.append(W.Problem(L=L, betas=W.linear_ladder(0.2, 0.8, R), J=J, h=h,
+                             seed=1000 + j, sweeps=int(rng.integers(0, 30)),
+                             every=int(rng.integers(0, 4))))
+    return out
+
+
+def test_batch_equals_plain_and_oracle(api, tuning):
+    probs = mixed_problems()
+    plain = []
+    for pr in probs:
+        g = api.PTProblem(pr.L, pr.betas, J=pr.J, h=pr.h, seed=pr.seed)
+        g.sweep(pr.sweeps, pr.every)
+        plain.append(state(g))
+    for cl, jm in [(4, 16), (1, 4), (2, 8), (8, 16), (4, 1 << 20)]:
+        tuning(cl, jm)
+        batch = [api.PTProblem(pr.L, pr.betas, J=pr.J, h=pr.h, seed=pr.seed) for pr in probs]
+        api.sweep_batch(batch, [pr.sweeps for pr in probs], [pr.every for pr in probs])
+        for j, (b, ref) in enumerate(zip(batch, plain)):
+            assert_state_equal(state(b), ref, "cluster %d joint>=%d problem %d" % (cl, jm, j))
+    oracle.set_threads(8)
+    for pr in probs[:6]:
+        o = oracle.OracleProblem(pr.L, pr.betas, J=pr.J, h=pr.h, seed=pr.seed)
+        o.sweep(pr.sweeps, pr.every)
+        g = api.PTProblem(pr.L, pr.betas, J=pr.J, h=pr.h, seed=pr.seed)
+        api.sweep_batch([g], [pr.sweeps], [pr.every])
+        np.testing.assert_array_equal(g.spins(), o.spins())
+        np.testing.assert_array_equal(g.chain_map(), o.chain_map())
+        np.testing.assert_array_equal(g.energies_int(), o.energies_int())
+
+
+def test_batch_composes_with_plain(api, tuning):
+    tuning(4, 16)
+    pr = W.Problem(L=64, betas=W.linear_ladder(0.3, 0.6, 40), seed=77)
+    a = api.PTProblem(pr.L, pr.betas, seed=pr.seed)
+    b = api.PTProblem(pr.L, pr.betas, seed=pr.seed)
+    a.sweep(23, 3)
+    api.sweep_batch([b], [5], [3])
+    b.sweep(7, 3)
+    api.sweep_batch([b], [11], [3])
+    assert_state_equal(a, b)
+
+
+def test_batched_workload_sample_vs_oracle(api, tuning):
+    """A sample of the 256-problem batched workload, short runs, against the oracle."""
+    tuning(4, 128)
+    probs = W.batched_problems()[:12]
+    gs = [api.PTProblem(p.L, p.betas, seed=p.seed) for p in probs]
+    api.sweep_batch(gs, 6, 1)
+    oracle.set_threads(8)
+    for p, g in zip(probs, gs):
+        o = oracle.OracleProblem(p.L, p.betas, seed=p.seed)
+        o.sweep(6, 1)
+        np.testing.assert_array_equal(g.spins(), o.spins())
+        np.testing.assert_array_equal(g.chain_map(), o.chain_map())
+        for x, y in zip(g.swap_stats(), o.swap_stats()):
+            np.testing.assert_array_equal(x, y)
+
+
+def test_batch_rejects_bad_input(api):
+    from paper_2512_03825_b300._lib import PTError
+    g = api.PTProblem(8, [0.3, 0.4], seed=1)
+    with pytest.raises(PTError):
+        api.sweep_batch([g, g], 1, 1)
+    with pytest.raises(PTError):
+        api.sweep_batch([g], -1, 1)
+    api.sweep_batch([g], 0, 0)
+    assert g.counters() == (0, 0)
