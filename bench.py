@@ -1,0 +1,429 @@
+#!/usr/bin/env python
+"""Benchmark: spin-flip attempts per second of parallel-tempering Metropolis on the 2D
+Ising model, batched persistent kernel vs the plain one-problem-per-launch path, on B300.
+
+Default workload (one step): 256 independent PT problems, L uniform over
+{32, 48, 64, 96, 128, 256}, R uniform in 8..48, betas linear 0.30 -> 0.60, J = 1, h = 0,
+2000 sweeps each with an exchange after every sweep, advanced by one pt_sweep_batch call.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload batched|single|serve]
+
+Prints one JSON line (rank 0). With N > 1 (torchrun) every rank runs its own copy of the
+workload on its own GPU (independent problems, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "spin-flip attempts/sec (all replicas, 1 B300) batched vs plain; serve p50/p99"
+UNIT = "attempts/s"
+MUL_PER_ATTEMPT = 5.0  # Philox4x32-10: 20 32x32->64 products per block of 4 draws
+IMUL_WIDE_PER_CLK_SM = 32.0  # 32x32->64 integer products per clock per SM (4 SMSPs x 8)
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["batched", "single", "serve"], default="batched")
+    ap.add_argument("--sweeps", type=int, default=2000, help="sweeps per problem per step")
+    ap.add_argument("--problems", type=int, default=256)
+    ap.add_argument("--quick", action="store_true",
+                    help="skip the side measurements (plain path, L1024, e2e, CPU baseline)")
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; weak scaling over independent problems)
+# ---------------------------------------------------------------------------------------
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+def _attempts(probs, sweeps):
+    return float(sum(p.L * p.L * p.R for p in probs)) * sweeps
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_2512_03825_b300 import api
+    from paper_2512_03825_b300 import workloads as W
+    from paper_2512_03825_b300 import autotune
+
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    api.use_torch_allocator(True)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    tuning = autotune.apply_cached_or_default()
+
+    if args.workload == "single":
+        return run_single(args, rank, world, stream, sms)
+    if args.workload == "serve":
+        from paper_2512_03825_b300 import serve
+        return serve.bench_serve(args, rank, world, stream)
+
+    probs = W.batched_problems(n=args.problems, sweeps=args.sweeps, every=1)
+    handles = [api.PTProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed, stream=stream)
+               for p in probs]
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    per_step = _attempts(probs, args.sweeps)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            api.sweep_batch(handles, args.sweeps, 1)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        clocks = ClockSampler(dev)
+        barrier(world)
+        torch.cuda.synchronize()
+        clocks.start()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()                     # evict the lattices from L2 between steps
+            ev[k][0].record(stream)
+            api.sweep_batch(handles, args.sweeps, 1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        wall = time.perf_counter() - t0
+        clk = clocks.stop()
+    kernel_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(kernel_ms) / 1e3
+    total_s = max_over_ranks(total_s, world)
+    value = per_step * args.steps * world / total_s
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded problem mix; random +-1 initial spins)",
+        "config": {
+            "workload": "batched-256: %d PT problems, L in {32,48,64,96,128,256}, R 8-48, "
+                        "betas 0.30-0.60, J=1, h=0, %d sweeps, exchange every sweep"
+                        % (args.problems, args.sweeps),
+            "problems": args.problems, "sweeps_per_step": args.sweeps, "exchange_every": 1,
+            "attempts_per_step": per_step, "parallelism": "independent problems per GPU",
+            "l2": "flushed (256 MiB write) between timed steps",
+            "batch_tuning": tuning,
+        },
+        "clocks": clk,
+        "gpu_launches": args.steps,  # one persistent k_batch launch per step
+        "wall_s": wall,
+    }
+    peaks = measured_peaks()
+    clock_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    peak_mul = sms * IMUL_WIDE_PER_CLK_SM * clock_mhz * 1e6
+    achieved_mul = MUL_PER_ATTEMPT * per_step / (statistics.mean(kernel_ms) / 1e3)
+    out["roofline"] = {
+        "bound": "alu", "kernel": "k_batch",
+        "achieved": achieved_mul / 1e12, "peak": peak_mul / 1e12, "unit": "T int-mul/s",
+        "frac": achieved_mul / peak_mul,
+        "traffic": None,
+        "note": "32x32->64 integer multiplies (Philox4x32-10, 5 per attempt) against %d SMs x "
+                "%d per clock x %.0f MHz" % (sms, IMUL_WIDE_PER_CLK_SM, clock_mhz),
+    }
+    if not args.quick and rank == 0:
+        out["plain"] = bench_plain_sample(probs, stream)
+        out["batched_vs_plain"] = value / world / out["plain"]["value"]
+        out["single_L1024_R64"] = bench_single(stream, sms, clock_mhz)
+        out["e2e"] = bench_e2e(probs, args.sweeps, stream, world)
+        out["cpu_baseline"] = cpu_baseline_sample(probs)
+    elif not args.quick:
+        bench_e2e(probs, args.sweeps, stream, world)
+    for h in handles:
+        h.close()
+    return out
+
+
+def bench_plain_sample(probs, stream, n_problems=32, sweeps=200):
+    """The plain one-problem-per-launch path on a sample of the same problem mix."""
+    import torch
+    from paper_2512_03825_b300 import api
+    sample = probs[:: max(1, len(probs) // n_problems)][:n_problems]
+    hs = [api.PTProblem(p.L, p.betas, seed=p.seed, stream=stream) for p in sample]
+    for h in hs:
+        h.sweep(5, 1)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for h in hs:
+        h.sweep(sweeps, 1)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    for h in hs:
+        h.close()
+    att = _attempts(sample, sweeps)
+    return {"value": att / (ms / 1e3), "unit": UNIT, "problems": len(sample),
+            "sweeps": sweeps, "launches": len(sample) * sweeps * 4}
+
+
+def bench_single(stream, sms, clock_mhz, sweeps=200):
+    """The roofline config: L = 1024, R = 64, exchange every 5 sweeps, plain path."""
+    import torch
+    from paper_2512_03825_b300 import api
+    from paper_2512_03825_b300 import workloads as W
+    p = W.SINGLE["L1024_R64"]
+    h = api.PTProblem(p.L, p.betas, seed=p.seed, stream=stream)
+    h.sweep(10, p.every)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    h.sweep(sweeps, p.every)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    h.close()
+    att = float(p.L * p.L * p.R * sweeps)
+    v = att / (ms / 1e3)
+    peak_att = sms * IMUL_WIDE_PER_CLK_SM * clock_mhz * 1e6 / MUL_PER_ATTEMPT
+    return {"value": v, "unit": UNIT, "sweeps": sweeps, "every": p.every,
+            "frac_of_mul_roofline": v / peak_att, "us_per_sweep": 1e3 * ms / sweeps}
+
+
+def bench_e2e(probs, sweeps, stream, world):
+    """The same step through the C ABI from host buffers: create every problem from host
+    betas (tables copied to the device), run the batch, read energies, magnetisations,
+    temperature maps and swap counters back, destroy."""
+    import torch
+    from paper_2512_03825_b300 import api
+
+    def step():
+        hs = [api.PTProblem(p.L, p.betas, seed=p.seed, stream=stream) for p in probs]
+        h2d = sum(h.device_bytes - h.L * h.L * ((h.R + 31) // 32) * 4 for h in hs)
+        api.sweep_batch(hs, sweeps, 1)
+        d2h = 0
+        for h in hs:
+            E = h.energies_int()
+            M = h.magnetisations()
+            c = h.chain_map()
+            att, acc = h.swap_stats()
+            d2h += E.nbytes + M.nbytes + c.nbytes + att.nbytes + acc.nbytes
+        for h in hs:
+            h.close()
+        return h2d, d2h
+
+    step()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    h2d, d2h = step()
+    torch.cuda.synchronize()
+    barrier(world)
+    dt = max_over_ranks(time.perf_counter() - t0, world)
+    return {"value": _attempts(probs, sweeps) * world / dt, "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "s_per_step": dt}
+
+
+def cpu_baseline_sample(probs, n_problems=16, sweeps=40):
+    """The oracle, as it stands, on a bounded sample of the same workload."""
+    import oracle
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    sample = probs[:: max(1, len(probs) // n_problems)][:n_problems]
+    t0 = time.perf_counter()
+    for p in sample:
+        o = oracle.OracleProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed)
+        o.sweep(sweeps, 1)
+    dt = time.perf_counter() - t0
+    return {"value": _attempts(sample, sweeps) / dt, "unit": UNIT, "cores": threads,
+            "kind": "oracle",
+            "sample": "%d of the batched problems (every %d-th), %d sweeps each, exchange every "
+                      "sweep, %.1f s" % (len(sample), max(1, len(probs) // n_problems), sweeps,
+                                         dt)}
+
+
+def run_single(args, rank, world, stream, sms):
+    import torch
+    from paper_2512_03825_b300 import api
+    from paper_2512_03825_b300 import workloads as W
+    p = W.SINGLE["L1024_R64"]
+    h = api.PTProblem(p.L, p.betas, seed=p.seed, stream=stream)
+    for _ in range(args.warmup):
+        h.sweep(p.sweeps // 10, p.every)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    barrier(world)
+    clocks.start()
+    a.record(stream)
+    for _ in range(args.steps):
+        h.sweep(p.sweeps, p.every)
+    b.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    s = max_over_ranks(a.elapsed_time(b) / 1e3, world)
+    per_step = float(p.L * p.L * p.R * p.sweeps)
+    return {"metric": METRIC, "value": per_step * args.steps * world / s, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * s / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "single L=1024 R=64 betas 0.35-0.50, 1000 sweeps, "
+                                   "exchange every 5, plain path"},
+            "clocks": clk, "gpu_launches": args.steps * (2 * p.sweeps + 2 * p.sweeps // p.every)}
+
+
+# ---------------------------------------------------------------------------------------
+# reference arm: the CPU oracle on the host cores
+# ---------------------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+    from paper_2512_03825_b300 import workloads as W
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    probs = W.batched_problems(n=args.problems, sweeps=args.sweeps, every=1)
+    sample = probs[::16][:16]
+    sweeps = 20
+    for _ in range(max(0, min(args.warmup, 1))):
+        o = oracle.OracleProblem(sample[0].L, sample[0].betas, seed=sample[0].seed)
+        o.sweep(2, 1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for p in sample:
+            o = oracle.OracleProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed)
+            o.sweep(sweeps, 1)
+        times.append(time.perf_counter() - t0)
+    att = _attempts(sample, sweeps)
+    v = att * len(times) / sum(times)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int8",
+            "data": "synthetic (same seeded problem mix)",
+            "config": {"workload": "batched-256 (bounded sample: 16 problems x %d sweeps per "
+                                   "step)" % sweeps},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "16 of the 256 batched problems, %d sweeps each" % sweeps},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local = dist_setup(args)
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -102,12 +102,19 @@ int pt_sweep(pt_problem* p, int64_t n, int exchange_every);
 int pt_sweep_batch(pt_problem* const* problems, int count, const int64_t* n,
                    const int* exchange_every);
 
-/* Launch shape of pt_sweep_batch (chosen by the autotuner; results never depend on it):
- * cluster = CTAs per thread-block cluster (1, 2, 4, 8 or 16); problems with
- * L >= joint_min_L are spread over a whole cluster, smaller ones run on a single CTA. Applies
- * to later batches of every problem. PT_EINVAL for other cluster sizes or joint_min_L < 4. */
-int pt_set_batch_tuning(int cluster, int joint_min_L);
-int pt_get_batch_tuning(int* cluster, int* joint_min_L);
+/* How pt_sweep_batch runs (chosen by the autotuner; results never depend on it):
+ *   PT_BATCH_FLAT    -- all problems advance sweep by sweep together; every half sweep is
+ *                       one launch over equal-sized word tiles of all problems, followed by
+ *                       an energy-count and an exchange launch when any problem is due;
+ *   PT_BATCH_CLUSTER -- one persistent kernel; a problem with L >= joint_min_L runs on a
+ *                       whole thread-block cluster of `cluster` CTAs (1 to 16) for all of its
+ *                       sweeps, smaller ones on a single CTA.
+ * Applies to later batches of every problem. PT_EINVAL for an unknown strategy, cluster
+ * outside 1..16 or joint_min_L < 4. */
+#define PT_BATCH_FLAT 0
+#define PT_BATCH_CLUSTER 1
+int pt_set_batch_tuning(int strategy, int cluster, int joint_min_L);
+int pt_get_batch_tuning(int* strategy, int* cluster, int* joint_min_L);
 
 /* Energies E = E_int / s of the configurations at each temperature index, out[R]. */
 int pt_energies(pt_problem* p, double* out);

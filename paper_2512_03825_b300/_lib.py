@@ -20,6 +20,8 @@ PT_ETIMEOUT = -4
 PT_ESTATE = -5
 PT_ENODEV = -6
 PT_EINTERNAL = -7
+PT_BATCH_FLAT = 0
+PT_BATCH_CLUSTER = 1
 PT_MAX_L = 16384
 PT_MAX_R = 2048
 
@@ -36,8 +38,9 @@ SIGNATURES = [
     ("pt_sweep", C.c_int, [P, C.c_int64, C.c_int]),
     ("pt_sweep_batch", C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.c_int64),
                                  C.POINTER(C.c_int)]),
-    ("pt_set_batch_tuning", C.c_int, [C.c_int, C.c_int]),
-    ("pt_get_batch_tuning", C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    ("pt_set_batch_tuning", C.c_int, [C.c_int, C.c_int, C.c_int]),
+    ("pt_get_batch_tuning", C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                      C.POINTER(C.c_int)]),
     ("pt_energies", C.c_int, [P, C.POINTER(C.c_double)]),
     ("pt_magnetisations", C.c_int, [P, C.POINTER(C.c_double)]),
     ("pt_swap_stats", C.c_int, [P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),

@@ -17,6 +17,8 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "pt_batch.h"
@@ -30,7 +32,7 @@ namespace ptb {
 
 namespace {
 
-constexpr int kBatchThreads = 512;
+constexpr int kBatchThreads = 384;
 
 struct BatchItem {
   DevProblem p;
@@ -101,59 +103,103 @@ struct PlaneDeal {
   }
 };
 
+// Walks this warp's words of rows [y0, y1) of one colour: q = rank * 32 + lane, stepping by
+// nranks * 32, with (row, i) kept up to date by additions only.
+struct WordWalk {
+  int q, step, yy, i, dyy, di, half;
+  __device__ __forceinline__ WordWalk(int q0, int step_, int half_)
+      : q(q0), step(step_), half(half_) {
+    yy = q0 / half_;
+    i = q0 - yy * half_;
+    dyy = step_ / half_;
+    di = step_ - dyy * half_;
+  }
+  __device__ __forceinline__ void next() {
+    q += step;
+    i += di;
+    yy += dyy;
+    if (i >= half) {
+      i -= half;
+      yy += 1;
+    }
+  }
+};
+
+// The five words one update reads: the centre and its four neighbours (other colour).
+struct Nb5 {
+  uint32_t s, n0, n1, n2, n3;
+};
+
+// Rows inside [y0, y1) were last written by this CTA, so L1 may serve them; the two halo
+// rows just outside belong to another CTA of the cluster and are read from L2 (.cg), never
+// from a possibly stale L1 line. A single-CTA gang owns every row.
+__device__ __forceinline__ uint32_t ld_row(const uint32_t* p, bool own) {
+  return own ? *p : __ldcg(p);
+}
+
+__device__ __forceinline__ Nb5 load_nb(const uint32_t* own, const uint32_t* oth, int L, int half,
+                                       int y, int i, int colour, int y0, int y1) {
+  const int par = (y + colour) & 1;
+  const int ym = (y == 0) ? L - 1 : y - 1;
+  const int yp = (y == L - 1) ? 0 : y + 1;
+  const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
+  const size_t idx = (size_t)y * half + i;
+  Nb5 v;
+  v.s = own[idx];
+  v.n0 = ld_row(oth + (size_t)ym * half + i, ym >= y0 && ym < y1);
+  v.n1 = ld_row(oth + (size_t)yp * half + i, yp >= y0 && yp < y1);
+  v.n2 = oth[idx];
+  v.n3 = oth[(size_t)y * half + ih];
+  return v;
+}
+
+template <int MODE>
+__device__ __forceinline__ void half_sweep_plane(const DevProblem& p, int w, int colour,
+                                                 const SweepCtr& cx, int y0, int y1, int nwords,
+                                                 const PlaneDeal& deal, const FerroRegs& th,
+                                                 const PlaneGeneric* gen_smem) {
+  const int L = p.L, half = L >> 1;
+  const int lane = threadIdx.x & 31;
+  const int nblk = (plane_slots(p.R, w) + 3) >> 2;
+  uint32_t* own = p.spins + word_index(L, w, colour, 0, 0);
+  const uint32_t* oth = p.spins + word_index(L, w, colour ^ 1, 0, 0);
+  WordWalk ww(deal.rank * 32 + lane, deal.nranks * 32, half);
+  if (ww.q >= nwords) return;
+  // software pipeline: the next word's loads are in flight while this word is updated
+  Nb5 cur = load_nb(own, oth, L, half, y0 + ww.yy, ww.i, colour, y0, y1);
+  for (;;) {
+    const int y = y0 + ww.yy, i = ww.i;
+    WordWalk nx = ww;
+    nx.next();
+    Nb5 nxt = cur;
+    if (nx.q < nwords) nxt = load_nb(own, oth, L, half, y0 + nx.yy, nx.i, colour, y0, y1);
+    const int par = (y + colour) & 1;
+    const uint32_t site = (uint32_t)(y * L + 2 * i + par);
+    const size_t idx = (size_t)y * half + i;
+    if (MODE == kModeFerro)
+      own[idx] = update_word_ferro(cur.s, cur.n0, cur.n1, cur.n2, cur.n3, site,
+                                   (uint32_t)(8 * w), nblk, th.T0, th.T1, th.alw0, th.alw1,
+                                   th.used, cx);
+    else
+      own[idx] = update_word_generic(cur.s, cur.n0, cur.n1, cur.n2, cur.n3, site,
+                                     (uint32_t)(8 * w), nblk, gen_smem[w], cx);
+    if (nx.q >= nwords) break;
+    ww = nx;
+    cur = nxt;
+  }
+}
+
+// One half sweep of rows [y0, y1). `th` holds the thresholds of this warp's plane when the
+// warp owns a single plane (W <= warps per CTA); otherwise they are loaded plane by plane.
 template <int MODE>
 __device__ void half_sweep_rows(const DevProblem& p, int colour, uint64_t t, int y0, int y1,
-                                const PlaneGeneric* gen_smem) {
-  const int L = p.L, half = L >> 1;
+                                FerroRegs& th, bool th_loaded, const PlaneGeneric* gen_smem) {
   const SweepCtr cx = make_sweep_ctr(t, p.key0, p.key1);
   const PlaneDeal deal(p.W);
-  const int lane = threadIdx.x & 31;
-  const int nwords = (y1 - y0) * half;
+  const int nwords = (y1 - y0) * (p.L >> 1);
   for (int w = deal.w_first; w < p.W; w += deal.w_step) {
-    const int nblk = (plane_slots(p.R, w) + 3) >> 2;
-    uint32_t* own = p.spins + word_index(L, w, colour, 0, 0);
-    const uint32_t* oth = p.spins + word_index(L, w, colour ^ 1, 0, 0);
-    if (MODE == kModeFerro) {
-      FerroRegs th;
-      th.load(reinterpret_cast<const PlaneFerro*>(p.planes) + w);
-      for (int q = deal.rank * 32 + lane; q < nwords; q += deal.nranks * 32) {
-        const int yy = q / half;
-        const int i = q - yy * half;
-        const int y = y0 + yy;
-        const int par = (y + colour) & 1;
-        const int ym = (y == 0) ? L - 1 : y - 1;
-        const int yp = (y == L - 1) ? 0 : y + 1;
-        const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
-        const size_t idx = (size_t)y * half + i;
-        const uint32_t s = ldcg(own + idx);
-        const uint32_t n0 = ldcg(oth + (size_t)ym * half + i);
-        const uint32_t n1 = ldcg(oth + (size_t)yp * half + i);
-        const uint32_t n2 = ldcg(oth + idx);
-        const uint32_t n3 = ldcg(oth + (size_t)y * half + ih);
-        const uint32_t site = (uint32_t)(y * L + 2 * i + par);
-        own[idx] = update_word_ferro(s, n0, n1, n2, n3, site, (uint32_t)(8 * w), nblk, th.T0,
-                                     th.T1, th.alw0, th.alw1, th.used, cx);
-      }
-    } else {
-      const PlaneGeneric& pl = gen_smem[w];
-      for (int q = deal.rank * 32 + lane; q < nwords; q += deal.nranks * 32) {
-        const int yy = q / half;
-        const int i = q - yy * half;
-        const int y = y0 + yy;
-        const int par = (y + colour) & 1;
-        const int ym = (y == 0) ? L - 1 : y - 1;
-        const int yp = (y == L - 1) ? 0 : y + 1;
-        const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
-        const size_t idx = (size_t)y * half + i;
-        const uint32_t s = ldcg(own + idx);
-        const uint32_t n0 = ldcg(oth + (size_t)ym * half + i);
-        const uint32_t n1 = ldcg(oth + (size_t)yp * half + i);
-        const uint32_t n2 = ldcg(oth + idx);
-        const uint32_t n3 = ldcg(oth + (size_t)y * half + ih);
-        const uint32_t site = (uint32_t)(y * L + 2 * i + par);
-        own[idx] = update_word_generic(s, n0, n1, n2, n3, site, (uint32_t)(8 * w), nblk, pl, cx);
-      }
-    }
+    if (MODE == kModeFerro && !th_loaded) th.load(reinterpret_cast<const PlaneFerro*>(p.planes) + w);
+    half_sweep_plane<MODE>(p, w, colour, cx, y0, y1, nwords, deal, th, gen_smem);
   }
 }
 
@@ -169,20 +215,18 @@ __device__ void count_rows(const DevProblem& p, int y0, int y1, uint32_t* acc_sm
     BitCounter<20, 14> U, N;
     U.zero();
     N.zero();
-    for (int q = deal.rank * 32 + lane; q < nwords; q += deal.nranks * 32) {
-      const int yy = q / half;
-      const int i = q - yy * half;
-      const int y = y0 + yy;
+    for (WordWalk ww(deal.rank * 32 + lane, deal.nranks * 32, half); ww.q < nwords; ww.next()) {
+      const int y = y0 + ww.yy, i = ww.i;
       const int par = y & 1;
       const int ym = (y == 0) ? L - 1 : y - 1;
       const int yp = (y == L - 1) ? 0 : y + 1;
       const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
       const size_t idx = (size_t)y * half + i;
-      const uint32_t s = ldcg(c0 + idx);
-      const uint32_t o = ldcg(c1 + idx);
-      const NbCount k = count4(s ^ ldcg(c1 + (size_t)ym * half + i),
-                               s ^ ldcg(c1 + (size_t)yp * half + i), s ^ o,
-                               s ^ ldcg(c1 + (size_t)y * half + ih));
+      const uint32_t s = c0[idx];
+      const uint32_t o = c1[idx];
+      const NbCount k = count4(s ^ ld_row(c1 + (size_t)ym * half + i, ym >= y0 && ym < y1),
+                               s ^ ld_row(c1 + (size_t)yp * half + i, yp >= y0 && yp < y1),
+                               s ^ o, s ^ c1[(size_t)y * half + ih]);
       U.add3(k.b0, k.b1, k.b2);
       N.add2(s ^ o, s & o);
     }
@@ -277,7 +321,11 @@ __device__ void run_item(const BatchItem& it, const Gang<JOINT>& gang, uint32_t*
   const int y1 = (int)((int64_t)L * (gang.rank + 1) / gang.size);
   PlaneGeneric* gen = reinterpret_cast<PlaneGeneric*>(smem_words);
   uint32_t* acc = smem_words;  // [2][W*32] counters (generic tables are reloaded after use)
-  if (p.mode != kModeFerro) {
+  const bool one_plane = p.W <= (int)(blockDim.x >> 5);
+  FerroRegs th;
+  if (p.mode == kModeFerro) {
+    if (one_plane) th.load(reinterpret_cast<const PlaneFerro*>(p.planes) + PlaneDeal(p.W).w_first);
+  } else {
     load_generic_planes(p, gen);
     __syncthreads();
   }
@@ -285,18 +333,17 @@ __device__ void run_item(const BatchItem& it, const Gang<JOINT>& gang, uint32_t*
   for (int64_t j = 0; j < it.n; ++j) {
     const uint64_t t = it.t0 + (uint64_t)j;
     if (p.mode == kModeFerro) {
-      half_sweep_rows<kModeFerro>(p, 0, t, y0, y1, gen);
+      half_sweep_rows<kModeFerro>(p, 0, t, y0, y1, th, one_plane, gen);
       gang.sync();
-      half_sweep_rows<kModeFerro>(p, 1, t, y0, y1, gen);
+      half_sweep_rows<kModeFerro>(p, 1, t, y0, y1, th, one_plane, gen);
     } else {
-      half_sweep_rows<kModeGeneric>(p, 0, t, y0, y1, gen);
+      half_sweep_rows<kModeGeneric>(p, 0, t, y0, y1, th, false, gen);
       gang.sync();
-      half_sweep_rows<kModeGeneric>(p, 1, t, y0, y1, gen);
+      half_sweep_rows<kModeGeneric>(p, 1, t, y0, y1, th, false, gen);
     }
     gang.sync();
     if (it.m > 0 && (t + 1) % (uint64_t)it.m == 0) {
       // count this CTA's rows into shared counters, then into the problem's counters
-      __syncthreads();
       for (int q = threadIdx.x; q < 2 * p.W * 32; q += blockDim.x) acc[q] = 0;
       __syncthreads();
       count_rows(p, y0, y1, acc);
@@ -307,7 +354,10 @@ __device__ void run_item(const BatchItem& it, const Gang<JOINT>& gang, uint32_t*
       if (gang.rank == 0) exchange_step(p, e);
       e += 1;
       gang.sync();
-      if (p.mode != kModeFerro) {
+      if (p.mode == kModeFerro) {
+        if (one_plane)
+          th.load(reinterpret_cast<const PlaneFerro*>(p.planes) + PlaneDeal(p.W).w_first);
+      } else {
         load_generic_planes(p, gen);
         __syncthreads();
       }
@@ -323,7 +373,7 @@ __device__ __forceinline__ void stage_item(const BatchItem* src, BatchItem* dst)
 }
 
 __global__ void __launch_bounds__(kBatchThreads, 1)
-    k_batch(const BatchItem* __restrict__ items, BatchQueues* queues) {
+    k_batch(const BatchItem* __restrict__ items, BatchQueues* queues, int single_only) {
   extern __shared__ uint32_t smem_words[];
   __shared__ int item_s;
   __shared__ __align__(16) BatchItem cur;
@@ -332,7 +382,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
   const int G = (int)cluster.num_blocks();
   const int n_joint = queues->n_joint;
   // joint items: one problem per cluster
-  if (G > 1 && n_joint > 0) {
+  if (!single_only && G > 1 && n_joint > 0) {
     for (;;) {
       if (rank == 0 && threadIdx.x == 0) item_s = atomicAdd(&queues->next_joint, 1);
       cluster.sync();
@@ -348,8 +398,9 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
   }
   // single items: one problem per CTA (with G == 1 the joint items are single ones too)
   const int n_single = queues->n_single;
-  const int base = G > 1 ? n_joint : 0;
-  const int total = G > 1 ? n_single : n_joint + n_single;
+  const bool split = single_only || G > 1;
+  const int base = split ? n_joint : 0;
+  const int total = split ? n_single : n_joint + n_single;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) item_s = atomicAdd(&queues->next_single, 1);
@@ -362,10 +413,26 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
   }
 }
 
-struct Scratch {
-  void* ptr = nullptr;
-  size_t bytes = 0;
+// A second stream per device for the helper launch (fork / join through events, so the
+// pair also records into a CUDA graph when the caller's stream is being captured).
+struct HelperStream {
+  bool ok = false;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
+
+HelperStream& helper_stream(int device) {
+  static std::mutex mu;
+  static std::map<int, HelperStream> streams;
+  std::lock_guard<std::mutex> lk(mu);
+  HelperStream& hs = streams[device];
+  if (!hs.ok) {
+    hs.ok = cudaStreamCreateWithFlags(&hs.stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&hs.fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&hs.join, cudaEventDisableTiming) == cudaSuccess;
+  }
+  return hs;
+}
 
 }  // namespace
 
@@ -373,6 +440,17 @@ struct Scratch {
 // Host side
 // ---------------------------------------------------------------------------------------
 BatchTuning g_batch_tuning;  // set through pt_set_batch_tuning (the autotuner)
+
+// Host mirrors of the sweep and swap-iteration counters after a batch.
+static void advance_counters(pt_problem* const* ps, int count, const int64_t* n,
+                             const int* every) {
+  for (int j = 0; j < count; ++j) {
+    pt_problem* p = ps[j];
+    const int m = every[j];
+    if (m > 0) p->e += (p->t + (uint64_t)n[j]) / (uint64_t)m - p->t / (uint64_t)m;
+    p->t += (uint64_t)n[j];
+  }
+}
 
 int sweep_batch(pt_problem* const* ps, int count, const int64_t* n, const int* every) {
   // checks
@@ -399,6 +477,12 @@ int sweep_batch(pt_problem* const* ps, int count, const int64_t* n, const int* e
   if (rc) return rc;
   const DeviceInfo& di = ps[0]->dev_info;
   const BatchTuning tune = g_batch_tuning;
+  if (tune.strategy == PT_BATCH_FLAT) {
+    rc = sweep_batch_flat(ps, count, n, every, st, di);
+    if (rc) return rc;
+    advance_counters(ps, count, n, every);
+    return PT_OK;
+  }
 
   // items, heaviest first; joint = large enough to share a cluster
   struct Order {
@@ -446,7 +530,8 @@ int sweep_batch(pt_problem* const* ps, int count, const int64_t* n, const int* e
   err = cudaMemcpyAsync(d_items, all.data(), items_bytes, cudaMemcpyHostToDevice, st);
   if (err == cudaSuccess) err = cudaMemcpyAsync(d_q, &q, sizeof q, cudaMemcpyHostToDevice, st);
 
-  // one persistent launch: as many clusters as fit
+  // one persistent launch: as many clusters as fit; with clusters, a second launch of
+  // plain CTAs on a forked stream drains the single queue on the SMs the clusters leave idle
   const int G = std::max(1, tune.cluster);
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -470,10 +555,21 @@ int sweep_batch(pt_problem* const* ps, int count, const int64_t* n, const int* e
   }
   if (err == cudaSuccess) {
     if (clusters < 1) clusters = 1;
-    const int want = (int)all.size();
-    (void)want;
     cfg.gridDim = dim3(G * clusters);
-    err = cudaLaunchKernelEx(&cfg, k_batch, (const BatchItem*)d_items, d_q);
+    err = cudaLaunchKernelEx(&cfg, k_batch, (const BatchItem*)d_items, d_q, 0);
+  }
+  const int helpers = G > 1 && !single.empty() ? di.sms - G * clusters : 0;
+  if (err == cudaSuccess && helpers > 0) {
+    HelperStream& hs = helper_stream(di.device);
+    if (!hs.ok) err = cudaErrorNotReady;
+    if (err == cudaSuccess) err = cudaEventRecord(hs.fork, st);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(hs.stream, hs.fork, 0);
+    if (err == cudaSuccess) {
+      k_batch<<<helpers, kBatchThreads, smem, hs.stream>>>(d_items, d_q, 1);
+      err = cudaGetLastError();
+    }
+    if (err == cudaSuccess) err = cudaEventRecord(hs.join, hs.stream);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(st, hs.join, 0);
   }
   cudaError_t err2 = cudaFreeAsync(scratch, st);
   if (err == cudaSuccess) err = err2;
@@ -481,12 +577,7 @@ int sweep_batch(pt_problem* const* ps, int count, const int64_t* n, const int* e
     for (int j = 0; j < count; ++j) ps[j]->poisoned = PT_ECUDA;
     return fail(PT_ECUDA, "batch launch: %s", cudaGetErrorString(err));
   }
-  for (int j = 0; j < count; ++j) {
-    pt_problem* p = ps[j];
-    const int m = every[j];
-    if (m > 0) p->e += (p->t + (uint64_t)n[j]) / (uint64_t)m - p->t / (uint64_t)m;
-    p->t += (uint64_t)n[j];
-  }
+  advance_counters(ps, count, n, every);
   return PT_OK;
 }
 

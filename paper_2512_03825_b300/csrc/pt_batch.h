@@ -2,16 +2,26 @@
 #pragma once
 #include <stdint.h>
 
+#include <cuda_runtime.h>
+
 #include "pt.h"
 
 namespace ptb {
-// Launch shape of the batched kernel: cluster = CTAs per cluster (1 = no clusters);
-// problems with L >= joint_min_L are spread over a whole cluster, smaller ones run on one CTA.
+// Batched path: strategy PT_BATCH_FLAT (lock-step tiles, pt_flat.cu) or PT_BATCH_CLUSTER (one
+// persistent kernel, pt_batch.cu). For the latter, cluster = CTAs per cluster (1 = no
+// clusters); problems with L >= joint_min_L are spread over a whole cluster, smaller ones run
+// on one CTA.
 struct BatchTuning {
+  int strategy = PT_BATCH_FLAT;
   int cluster = 4;
   int joint_min_L = 128;
 };
 extern BatchTuning g_batch_tuning;
+
+struct DeviceInfo;
+// The lock-step path (pt_flat.cu); problems are already checked.
+int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const int* every,
+                     cudaStream_t st, const DeviceInfo& di);
 
 int sweep_batch(pt_problem* const* problems, int count, const int64_t* n,
                 const int* exchange_every);

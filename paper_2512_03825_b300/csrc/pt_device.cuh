@@ -83,8 +83,20 @@ __device__ __forceinline__ NbCount count4(uint32_t a0, uint32_t a1, uint32_t a2,
 //   nblk     Philox blocks needed (4 slots each; ceil(used slots / 4))
 // ---------------------------------------------------------------------------------------
 
+// acc * 2 + [u >= T]: the carry out of u - T shifted into the low end of acc. Fed from
+// bit 31 down to bit 0, a word of 32 such calls is the mask of rejected trials. Two integer
+// instructions per trial on the ALU pipe; no predicate or select.
+__device__ __forceinline__ uint32_t shift_in_reject(uint32_t acc, uint32_t u, uint32_t T) {
+  uint32_t r;
+  asm("{\n\t.reg .u32 d;\n\tsub.cc.u32 d, %1, %2;\n\taddc.u32 %0, %3, %3;\n\t}"
+      : "=r"(r)
+      : "r"(u), "r"(T), "r"(acc));
+  return r;
+}
+
 // h = 0, J > 0: dE = 4 J (2 - k); classes k = 0 and k = 1 need a random number, k >= 2
-// always flips. Because T0 <= T1 bit by bit, "u < T0 or (k == 1 and u < T1)" is the exact
+// always flips. Each trial is compared with both thresholds: rej0 / rej1 collect u >= T0 and
+// u >= T1, and because T0 <= T1 bit by bit, "not rej0, or k == 1 and not rej1" is the exact
 // rule for both random classes.
 __device__ __forceinline__ uint32_t update_word_ferro(uint32_t s, uint32_t n0, uint32_t n1,
                                                       uint32_t n2, uint32_t n3, uint32_t site,
@@ -97,20 +109,24 @@ __device__ __forceinline__ uint32_t update_word_ferro(uint32_t s, uint32_t n0, u
   const uint32_t x01 = a0 ^ a1, x23 = a2 ^ a3;
   const uint32_t ge2 = (a0 & a1) | (a2 & a3) | (x01 & x23);
   const uint32_t eq1 = (x01 ^ x23) & ~ge2;
-  uint32_t acc = 0;
+  // slots of blocks j >= nblk are unused: their bits start out as "rejected" and no
+  // compare is spent on them
+  uint32_t rej0 = nblk >= 8 ? 0u : (0xffffffffu >> (4 * nblk));
+  uint32_t rej1 = rej0;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
+  for (int j = 7; j >= 0; --j) {
     if (j < nblk) {
       const Philox4 r = philox4x32_10(site, cx.t_lo, blk0 + (uint32_t)j, cx.c3, cx.k0, cx.k1);
       const uint32_t u[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 3; q >= 0; --q) {
         const int b = 4 * j + q;
-        const bool f = (u[q] < T0[b]) || (((eq1 >> b) & 1u) && (u[q] < T1[b]));
-        acc |= (uint32_t)f << b;
+        rej0 = shift_in_reject(rej0, u[q], T0[b]);
+        rej1 = shift_in_reject(rej1, u[q], T1[b]);
       }
     }
   }
+  const uint32_t acc = ~rej0 | (eq1 & ~rej1);
   const uint32_t flip = (ge2 | alw0 | (eq1 & alw1) | acc) & used;
   return s ^ flip;
 }
@@ -128,23 +144,23 @@ __device__ __forceinline__ uint32_t update_word_generic(uint32_t s, uint32_t n0,
 #pragma unroll
   for (int kk = 0; kk < 5; ++kk)
     always |= z[kk] & ((s & pl.alw[2 * kk + 1]) | (~s & pl.alw[2 * kk]));
-  uint32_t acc = 0;
+  uint32_t rej = nblk >= 8 ? 0u : (0xffffffffu >> (4 * nblk));
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
+  for (int j = 7; j >= 0; --j) {
     if (j < nblk) {
       const Philox4 r = philox4x32_10(site, cx.t_lo, blk0 + (uint32_t)j, cx.c3, cx.k0, cx.k1);
       const uint32_t u[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 3; q >= 0; --q) {
         const int b = 4 * j + q;
         const uint32_t kb = ((k.b0 >> b) & 1u) | (((k.b1 >> b) & 1u) << 1) |
                             (((k.b2 >> b) & 1u) << 2);
         const uint32_t cls = 2u * kb + ((s >> b) & 1u);
-        acc |= (uint32_t)(u[q] < pl.T[cls][b]) << b;
+        rej = shift_in_reject(rej, u[q], pl.T[cls][b]);
       }
     }
   }
-  const uint32_t flip = (always | acc) & pl.used;
+  const uint32_t flip = (always | ~rej) & pl.used;
   return s ^ flip;
 }
 

@@ -1,0 +1,409 @@
+// pt_flat.cu -- the lock-step batched path: all problems of a batch advance sweep by sweep
+// together. Each half sweep is one launch over a list of equal-sized word tiles drawn from
+// every problem and plane, so the work is balanced across the SMs however uneven L and R
+// are; the energy count and the exchange step of every problem due for one are one launch
+// each. Kernel boundaries order the steps: nothing waits on a flag.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <queue>
+#include <utility>
+#include <vector>
+
+#include "pt_batch.h"
+#include "pt_device.cuh"
+#include "pt_internal.h"
+#include "pt_launch.h"
+
+namespace ptb {
+
+namespace {
+
+constexpr int kFlatThreads = 256;
+constexpr int kTileWords = 512;  // target words per warp tile (16 per lane)
+
+struct FlatProblem {
+  DevProblem p;
+  uint64_t t0, e0;  // counters when the batch starts
+  int64_t n;        // sweeps in this batch
+  int m;            // exchange every m sweeps (0 = never)
+  int pad;
+};
+
+// A warp's unit of work: words [q0, q1) of one colour of plane w of one problem
+// (q = y * L/2 + i). Tiles never straddle planes, so a warp's thresholds are uniform.
+struct Tile {
+  int prob;
+  int w;
+  int q0, q1;
+};
+
+// Does problem fp run sweep j of this batch, and does an exchange follow it?
+__device__ __forceinline__ bool runs(const FlatProblem& fp, int64_t j) { return j < fp.n; }
+__device__ __forceinline__ bool exchanges_after(const FlatProblem& fp, int64_t j) {
+  return j < fp.n && fp.m > 0 && (fp.t0 + (uint64_t)j + 1) % (uint64_t)fp.m == 0;
+}
+// swap iteration index used after sweep j (valid when exchanges_after)
+__device__ __forceinline__ uint64_t exchange_index(const FlatProblem& fp, int64_t j) {
+  const uint64_t m = (uint64_t)fp.m;
+  return fp.e0 + (fp.t0 + (uint64_t)j + 1) / m - fp.t0 / m - 1;
+}
+
+// ---------------------------------------------------------------------------------------
+// half sweep over all warp tiles. With COUNT (colour 1 only), a warp whose problem is due
+// for an exchange after this sweep also counts, from the words it already holds, the
+// unsatisfied bonds of its updated sites (all four bonds of a colour-1 site; every bond has
+// exactly one colour-1 end) and the up spins of its sites and of their colour-0 neighbours
+// one row up (a one-to-one map between the colours), into the problem's counters.
+// ---------------------------------------------------------------------------------------
+// Tiles are dealt to warps by the host (longest-processing-time first on their Philox
+// work), warp g taking tiles [first[g], first[g + 1]) of the list.
+template <int MODE, bool COUNT>
+__global__ void __launch_bounds__(kFlatThreads, 2) k_flat_half(const FlatProblem* __restrict__ probs,
+                                                             const Tile* __restrict__ tiles,
+                                                             const int* __restrict__ first,
+                                                             int colour, int64_t j) {
+  __shared__ PlaneGeneric gen[kFlatThreads / 32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int tend = first[g + 1];
+  for (int tix = first[g]; tix < tend; ++tix) {
+    const Tile tl = tiles[tix];
+    const FlatProblem& fp = probs[tl.prob];
+    const int64_t n = fp.n;
+    if (j >= n) continue;  // warp-uniform
+    const uint64_t t = fp.t0 + (uint64_t)j;
+    const DevProblem& p = fp.p;
+    const int w = tl.w;
+    const int L = p.L, half = L >> 1;
+    const int nblk = (min(32, p.R - 32 * w) + 3) >> 2;
+    const SweepCtr cx = make_sweep_ctr(t, p.key0, p.key1);
+    uint32_t* own = p.spins + word_index(L, w, colour, 0, 0);
+    const uint32_t* oth = p.spins + word_index(L, w, colour ^ 1, 0, 0);
+    const bool count = COUNT && fp.m > 0 && (t + 1) % (uint64_t)fp.m == 0;
+    const int q_start = tl.q0 + lane;
+    int y = q_start / half, i = q_start - y * half;
+    const int dy = 32 / half, di = 32 - dy * half;
+    if (MODE == kModeFerro) {
+      const PlaneFerro* pl = reinterpret_cast<const PlaneFerro*>(p.planes) + w;
+      uint32_t T0[32], T1[32];
+#pragma unroll
+      for (int b = 0; b < 32; ++b) {
+        T0[b] = pl->T0[b];
+        T1[b] = pl->T1[b];
+      }
+      const uint32_t alw0 = pl->alw0, alw1 = pl->alw1, used = pl->used;
+      for (int q = q_start; q < tl.q1; q += 32) {
+        const int par = (y + colour) & 1;
+        const int ym = (y == 0) ? L - 1 : y - 1;
+        const int yp = (y == L - 1) ? 0 : y + 1;
+        const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
+        const uint32_t s = own[q];
+        const uint32_t n0 = oth[ym * half + i];
+        const uint32_t n1 = oth[yp * half + i];
+        const uint32_t n2 = oth[q];
+        const uint32_t n3 = oth[y * half + ih];
+        const uint32_t site = (uint32_t)(y * L + 2 * i + par);
+        own[q] = update_word_ferro(s, n0, n1, n2, n3, site, (uint32_t)(8 * w), nblk, T0, T1,
+                                   alw0, alw1, used, cx);
+        i += di;
+        y += dy;
+        if (i >= half) {
+          i -= half;
+          y += 1;
+        }
+      }
+    } else {
+      // the warp's generic thresholds live in its own shared slot
+      {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(
+            reinterpret_cast<const PlaneGeneric*>(p.planes) + w);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&gen[wib]);
+        for (int q = lane; q < (int)(sizeof(PlaneGeneric) / 4); q += 32) dst[q] = src[q];
+        __syncwarp();
+      }
+      const PlaneGeneric& pl = gen[wib];
+      for (int q = q_start; q < tl.q1; q += 32) {
+        const int par = (y + colour) & 1;
+        const int ym = (y == 0) ? L - 1 : y - 1;
+        const int yp = (y == L - 1) ? 0 : y + 1;
+        const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
+        const uint32_t s = own[q];
+        const uint32_t n0 = oth[ym * half + i];
+        const uint32_t n1 = oth[yp * half + i];
+        const uint32_t n2 = oth[q];
+        const uint32_t n3 = oth[y * half + ih];
+        const uint32_t site = (uint32_t)(y * L + 2 * i + par);
+        own[q] = update_word_generic(s, n0, n1, n2, n3, site, (uint32_t)(8 * w), nblk, pl,
+                                     cx);
+        i += di;
+        y += dy;
+        if (i >= half) {
+          i -= half;
+          y += 1;
+        }
+      }
+      __syncwarp();
+    }
+    if (COUNT && count) {
+      // second pass over the words this lane just wrote (and their colour-0 neighbours,
+      // unchanged in this launch), mostly from L1
+      BitCounter<13, 8> U, N;
+      U.zero();
+      N.zero();
+      int yc = q_start / half, ic = q_start - yc * half;
+      for (int q = q_start; q < tl.q1; q += 32) {
+        const int par = (yc + colour) & 1;
+        const int ym = (yc == 0) ? L - 1 : yc - 1;
+        const int yp = (yc == L - 1) ? 0 : yc + 1;
+        const int ih = par ? ((ic + 1 == half) ? 0 : ic + 1) : ((ic == 0) ? half - 1 : ic - 1);
+        const uint32_t ns = own[q];
+        const uint32_t n0 = oth[ym * half + ic];
+        const NbCount k = count4(ns ^ n0, ns ^ oth[yp * half + ic], ns ^ oth[q],
+                                 ns ^ oth[yc * half + ih]);
+        U.add3(k.b0, k.b1, k.b2);
+        N.add2(ns ^ n0, ns & n0);
+        ic += di;
+        yc += dy;
+        if (ic >= half) {
+          ic -= half;
+          yc += 1;
+        }
+      }
+      const uint32_t u = U.warp_total_for_lane();
+      const uint32_t nn = N.warp_total_for_lane();
+      if (u) atomicAdd(&p.cnt[w * 32 + lane], u);
+      if (nn) atomicAdd(&p.cnt[p.W * 32 + w * 32 + lane], nn);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// exchange step: one block per problem due for one (same three parts as k_exchange)
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kFlatThreads) k_flat_exchange(const FlatProblem* __restrict__ probs,
+                                                                 int nprobs, int64_t j) {
+  for (int pi = blockIdx.x; pi < nprobs; pi += gridDim.x) {
+    const FlatProblem& fp = probs[pi];
+    if (!exchanges_after(fp, j)) continue;
+    const DevProblem& p = fp.p;
+    const uint64_t e = exchange_index(fp, j);
+    const int R = p.R, W = p.W;
+    const int64_t L2 = (int64_t)p.L * p.L;
+    __syncthreads();
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+      const int64_t U = p.cnt[r];
+      const int64_t ones = p.cnt[W * 32 + r];
+      const int64_t bonds = 2 * L2 - 2 * U;
+      const int64_t M = 2 * ones - L2;
+      p.E_slot[r] = -p.J_int * bonds + p.h_int * M;
+      p.M_slot[r] = M;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 2 * W * 32; q += blockDim.x) p.cnt[q] = 0;
+    const int parity = (int)(e & 1);
+    const uint32_t c3 = kTagExch | ((uint32_t)(e >> 32) << 8);
+    for (int k = parity + 2 * threadIdx.x; k + 1 < R; k += 2 * blockDim.x) {
+      const int a = p.slot_of_temp[k], b = p.slot_of_temp[k + 1];
+      const int64_t n = p.E_slot[a] - p.E_slot[b];
+      const SwapPair sp = p.pairs[k];
+      uint64_t S;
+      if (n < sp.n_lo)
+        S = sp.S_below;
+      else if (n > sp.n_hi)
+        S = sp.S_above;
+      else
+        S = p.swap_table[sp.offset + (n - sp.n_lo)];
+      const Philox4 rnd = philox4x32_10((uint32_t)k, (uint32_t)e, 0u, c3, p.key0, p.key1);
+      p.attempted[k] += 1;
+      if ((uint64_t)rnd.x < S) {
+        p.accepted[k] += 1;
+        p.slot_of_temp[k] = b;
+        p.slot_of_temp[k + 1] = a;
+        p.temp_of_slot[a] = k + 1;
+        p.temp_of_slot[b] = k;
+      }
+    }
+    __syncthreads();
+    constexpr uint64_t kTwo32 = 1ull << 32;
+    for (int r = threadIdx.x; r < W * 32; r += blockDim.x) {
+      const int w = r >> 5, b = r & 31;
+      const bool in_use = r < R;
+      const int temp = in_use ? p.temp_of_slot[r] : 0;
+      if (p.mode == kModeFerro) {
+        PlaneFerro* pl = reinterpret_cast<PlaneFerro*>(p.planes) + w;
+        const uint64_t t0 = in_use ? p.T_temp[(size_t)temp * kClasses + 1] : 0;
+        const uint64_t t1 = in_use ? p.T_temp[(size_t)temp * kClasses + 3] : 0;
+        pl->T0[b] = (uint32_t)min(t0, kTwo32 - 1);
+        pl->T1[b] = (uint32_t)min(t1, kTwo32 - 1);
+        const uint32_t a0 = __ballot_sync(0xffffffffu, in_use && t0 >= kTwo32);
+        const uint32_t a1 = __ballot_sync(0xffffffffu, in_use && t1 >= kTwo32);
+        if (b == 0) {
+          pl->alw0 = a0;
+          pl->alw1 = a1;
+        }
+      } else {
+        PlaneGeneric* pl = reinterpret_cast<PlaneGeneric*>(p.planes) + w;
+#pragma unroll
+        for (int c = 0; c < kClasses; ++c) {
+          const uint64_t tc = in_use ? p.T_temp[(size_t)temp * kClasses + c] : 0;
+          pl->T[c][b] = (uint32_t)min(tc, kTwo32 - 1);
+          const uint32_t a = __ballot_sync(0xffffffffu, in_use && tc >= kTwo32);
+          if (b == 0) pl->alw[c] = a;
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// host: one batch = per sweep j, half sweep 0 and 1 over all tiles of both modes, then the
+// count and exchange launches when any problem is due for an exchange after sweep j
+// ---------------------------------------------------------------------------------------
+// Work of a tile in Philox blocks (the dominant cost of a word).
+static int64_t tile_cost(const Tile& t, int R) {
+  const int slots = std::min(32, R - 32 * t.w);
+  return (int64_t)((slots + 3) / 4 + 1) * (t.q1 - t.q0);
+}
+
+// Longest-processing-time-first assignment of tiles to `nwarps` warps: returns the tiles
+// reordered warp by warp and the CSR offsets first[0..nwarps].
+static void deal_tiles(const std::vector<Tile>& in, const std::vector<FlatProblem>& probs,
+                       int nwarps, std::vector<Tile>* out, std::vector<int>* first) {
+  std::vector<int> order(in.size());
+  for (size_t k = 0; k < in.size(); ++k) order[k] = (int)k;
+  std::vector<int64_t> cost(in.size());
+  for (size_t k = 0; k < in.size(); ++k) cost[k] = tile_cost(in[k], probs[in[k].prob].p.R);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  typedef std::pair<int64_t, int> Load;  // (work so far, warp)
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+  for (int w = 0; w < nwarps; ++w) heap.push(Load(0, w));
+  std::vector<std::vector<int>> per(nwarps);
+  for (int k : order) {
+    Load l = heap.top();
+    heap.pop();
+    per[l.second].push_back(k);
+    l.first += cost[k];
+    heap.push(l);
+  }
+  out->clear();
+  first->assign((size_t)nwarps + 1, 0);
+  for (int w = 0; w < nwarps; ++w) {
+    (*first)[w] = (int)out->size();
+    for (int k : per[w]) out->push_back(in[k]);
+  }
+  (*first)[nwarps] = (int)out->size();
+}
+
+int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const int* every,
+                     cudaStream_t st, const DeviceInfo& di) {
+  std::vector<FlatProblem> probs;
+  std::vector<Tile> tiles[2];  // by mode
+  int64_t n_max = 0;
+  for (int j = 0; j < count; ++j) {
+    if (n[j] <= 0) continue;
+    pt_problem* p = ps[j];
+    FlatProblem fp{};
+    fp.p = p->dev;
+    fp.t0 = p->t;
+    fp.e0 = p->e;
+    fp.n = n[j];
+    fp.m = every[j];
+    const int pi = (int)probs.size();
+    probs.push_back(fp);
+    n_max = std::max(n_max, n[j]);
+    const int words = p->L * (p->L / 2);
+    const int ntile = std::max(1, (words + kTileWords / 2) / kTileWords);
+    for (int w = 0; w < p->W; ++w)
+      for (int k = 0; k < ntile; ++k) {
+        Tile t;
+        t.prob = pi;
+        t.w = w;
+        t.q0 = (int)((int64_t)words * k / ntile);
+        t.q1 = (int)((int64_t)words * (k + 1) / ntile);
+        tiles[p->mode == kModeFerro ? 0 : 1].push_back(t);
+      }
+  }
+  if (probs.empty()) return PT_OK;
+  // one persistent wave per launch: as many CTAs as are resident at once, each warp with
+  // its own share of the tiles
+  int per_sm[2] = {1, 1};
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm[0], k_flat_half<kModeFerro, true>, kFlatThreads, 0);
+  if (err == cudaSuccess)
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm[1], k_flat_half<kModeGeneric, true>, kFlatThreads, 0);
+  if (err != cudaSuccess) return fail(PT_ECUDA, "occupancy: %s", cudaGetErrorString(err));
+  const int wpb = kFlatThreads / 32;
+  std::vector<Tile> dealt[2];
+  std::vector<int> first[2];
+  int grid[2] = {0, 0};
+  for (int md = 0; md < 2; ++md) {
+    if (tiles[md].empty()) continue;
+    const int blocks = std::max(1, per_sm[md]) * di.sms;
+    const int needed = (int)((tiles[md].size() + wpb - 1) / wpb);
+    grid[md] = std::max(1, std::min(blocks, needed));
+    deal_tiles(tiles[md], probs, grid[md] * wpb, &dealt[md], &first[md]);
+  }
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t pb = probs.size() * sizeof(FlatProblem);
+  const size_t tb[2] = {dealt[0].size() * sizeof(Tile), dealt[1].size() * sizeof(Tile)};
+  const size_t fb[2] = {first[0].size() * sizeof(int), first[1].size() * sizeof(int)};
+  const size_t total = al(pb) + al(tb[0]) + al(tb[1]) + al(fb[0]) + al(fb[1]) + 256;
+  void* scratch = nullptr;
+  err = cudaMallocAsync(&scratch, total, st);
+  if (err != cudaSuccess) return fail(PT_ENOMEM, "batch scratch: %s", cudaGetErrorString(err));
+  char* cur = (char*)scratch;
+  FlatProblem* d_probs = (FlatProblem*)cur;
+  cur += al(pb);
+  Tile* d_tiles[2];
+  int* d_first[2];
+  for (int md = 0; md < 2; ++md) {
+    d_tiles[md] = (Tile*)cur;
+    cur += al(tb[md]);
+  }
+  for (int md = 0; md < 2; ++md) {
+    d_first[md] = (int*)cur;
+    cur += al(fb[md]);
+  }
+  err = cudaMemcpyAsync(d_probs, probs.data(), pb, cudaMemcpyHostToDevice, st);
+  for (int md = 0; md < 2 && err == cudaSuccess; ++md) {
+    if (!tb[md]) continue;
+    err = cudaMemcpyAsync(d_tiles[md], dealt[md].data(), tb[md], cudaMemcpyHostToDevice, st);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(d_first[md], first[md].data(), fb[md], cudaMemcpyHostToDevice, st);
+  }
+  // which sweeps are followed by at least one exchange
+  std::vector<char> any_exchange((size_t)n_max, 0);
+  for (const FlatProblem& fp : probs)
+    if (fp.m > 0)
+      for (int64_t j = 0; j < fp.n; ++j)
+        if ((fp.t0 + (uint64_t)j + 1) % (uint64_t)fp.m == 0) any_exchange[(size_t)j] = 1;
+  const int np = (int)probs.size();
+  for (int64_t j = 0; j < n_max && err == cudaSuccess; ++j) {
+    const bool ex = any_exchange[(size_t)j] != 0;
+    if (grid[0]) k_flat_half<kModeFerro, false><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles[0], d_first[0], 0, j);
+    if (grid[1]) k_flat_half<kModeGeneric, false><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles[1], d_first[1], 0, j);
+    if (ex) {
+      if (grid[0]) k_flat_half<kModeFerro, true><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles[0], d_first[0], 1, j);
+      if (grid[1]) k_flat_half<kModeGeneric, true><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles[1], d_first[1], 1, j);
+      k_flat_exchange<<<std::min(np, di.sms * 8), kFlatThreads, 0, st>>>(d_probs, np, j);
+    } else {
+      if (grid[0]) k_flat_half<kModeFerro, false><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles[0], d_first[0], 1, j);
+      if (grid[1]) k_flat_half<kModeGeneric, false><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles[1], d_first[1], 1, j);
+    }
+    err = cudaGetLastError();
+  }
+  const cudaError_t err2 = cudaFreeAsync(scratch, st);
+  if (err == cudaSuccess) err = err2;
+  if (err != cudaSuccess) {
+    for (int j = 0; j < count; ++j) ps[j]->poisoned = PT_ECUDA;
+    return fail(PT_ECUDA, "flat batch launch: %s", cudaGetErrorString(err));
+  }
+  return PT_OK;
+}
+
+}  // namespace ptb

@@ -741,18 +741,21 @@ int pt_set_spins(pt_problem* p, int k, const int8_t* in) {
   return PT_OK;
 }
 
-int pt_set_batch_tuning(int cluster, int joint_min_L) {
-  if (!(cluster == 1 || cluster == 2 || cluster == 4 || cluster == 8 || cluster == 16) ||
-      joint_min_L < 4)
-    return fail(PT_EINVAL, "cluster = %d, joint_min_L = %d", cluster, joint_min_L);
+int pt_set_batch_tuning(int strategy, int cluster, int joint_min_L) {
+  if ((strategy != PT_BATCH_FLAT && strategy != PT_BATCH_CLUSTER) || cluster < 1 ||
+      cluster > 16 || joint_min_L < 4)
+    return fail(PT_EINVAL, "strategy = %d, cluster = %d, joint_min_L = %d", strategy, cluster,
+                joint_min_L);
   std::lock_guard<std::mutex> lk(g_mu);
+  g_batch_tuning.strategy = strategy;
   g_batch_tuning.cluster = cluster;
   g_batch_tuning.joint_min_L = joint_min_L;
   return PT_OK;
 }
 
-int pt_get_batch_tuning(int* cluster, int* joint_min_L) {
+int pt_get_batch_tuning(int* strategy, int* cluster, int* joint_min_L) {
   std::lock_guard<std::mutex> lk(g_mu);
+  if (strategy) *strategy = g_batch_tuning.strategy;
   if (cluster) *cluster = g_batch_tuning.cluster;
   if (joint_min_L) *joint_min_L = g_batch_tuning.joint_min_L;
   return PT_OK;

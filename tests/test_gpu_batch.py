@@ -24,10 +24,13 @@ def api():
 def tuning(api):
     from paper_2512_03825_b300._lib import lib
     import ctypes as C
-    c, j = C.c_int(), C.c_int()
-    lib.pt_get_batch_tuning(C.byref(c), C.byref(j))
-    yield lambda cl, jm: lib.pt_set_batch_tuning(cl, jm)
-    lib.pt_set_batch_tuning(c.value, j.value)
+    s, c, j = C.c_int(), C.c_int(), C.c_int()
+    lib.pt_get_batch_tuning(C.byref(s), C.byref(c), C.byref(j))
+
+    def setter(cl, jm, strategy=1):
+        assert lib.pt_set_batch_tuning(strategy, cl, jm) == 0
+    yield setter
+    lib.pt_set_batch_tuning(s.value, c.value, j.value)
 
 
 def state(g):
@@ -61,12 +64,14 @@ def test_batch_equals_plain_and_oracle(api, tuning):
         g = api.PTProblem(pr.L, pr.betas, J=pr.J, h=pr.h, seed=pr.seed)
         g.sweep(pr.sweeps, pr.every)
         plain.append(state(g))
-    for cl, jm in [(4, 16), (1, 4), (2, 8), (8, 16), (4, 1 << 20)]:
-        tuning(cl, jm)
+    for st, cl, jm in [(0, 1, 4), (1, 4, 16), (1, 1, 4), (1, 2, 8), (1, 8, 16), (1, 3, 8),
+                       (1, 6, 12), (1, 4, 1 << 20)]:
+        tuning(cl, jm, st)
         batch = [api.PTProblem(pr.L, pr.betas, J=pr.J, h=pr.h, seed=pr.seed) for pr in probs]
         api.sweep_batch(batch, [pr.sweeps for pr in probs], [pr.every for pr in probs])
         for j, (b, ref) in enumerate(zip(batch, plain)):
-            assert_state_equal(state(b), ref, "cluster %d joint>=%d problem %d" % (cl, jm, j))
+            assert_state_equal(state(b), ref,
+                               "strategy %d cluster %d joint>=%d problem %d" % (st, cl, jm, j))
     oracle.set_threads(8)
     for pr in probs[:6]:
         o = oracle.OracleProblem(pr.L, pr.betas, J=pr.J, h=pr.h, seed=pr.seed)
@@ -78,8 +83,9 @@ def test_batch_equals_plain_and_oracle(api, tuning):
         np.testing.assert_array_equal(g.energies_int(), o.energies_int())
 
 
-def test_batch_composes_with_plain(api, tuning):
-    tuning(4, 16)
+@pytest.mark.parametrize("strategy", [0, 1])
+def test_batch_composes_with_plain(api, tuning, strategy):
+    tuning(4, 16, strategy)
     pr = W.Problem(L=64, betas=W.linear_ladder(0.3, 0.6, 40), seed=77)
     a = api.PTProblem(pr.L, pr.betas, seed=pr.seed)
     b = api.PTProblem(pr.L, pr.betas, seed=pr.seed)
@@ -90,9 +96,10 @@ def test_batch_composes_with_plain(api, tuning):
     assert_state_equal(a, b)
 
 
-def test_batched_workload_sample_vs_oracle(api, tuning):
+@pytest.mark.parametrize("strategy", [0, 1])
+def test_batched_workload_sample_vs_oracle(api, tuning, strategy):
     """A sample of the 256-problem batched workload, short runs, against the oracle."""
-    tuning(4, 128)
+    tuning(4, 128, strategy)
     probs = W.batched_problems()[:12]
     gs = [api.PTProblem(p.L, p.betas, seed=p.seed) for p in probs]
     api.sweep_batch(gs, 6, 1)
