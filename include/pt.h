@@ -102,6 +102,31 @@ int pt_sweep(pt_problem* p, int64_t n, int exchange_every);
 int pt_sweep_batch(pt_problem* const* problems, int count, const int64_t* n,
                    const int* exchange_every);
 
+/* pt_sweep_batch without any allocation. The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory while they run -- code inside a
+ * memory budget it has already fixed, code whose device memory belongs to an allocator this
+ * library cannot see, or code that must not let an allocation synchronise the device or fail
+ * part-way. It does exactly what pt_sweep_batch does with the PT_BATCH_FLAT strategy (same
+ * kernels, bit-identical results) but keeps the per-call work lists (problem descriptors,
+ * work tiles, per-warp tile offsets) in one 1 MiB array of device memory that the library
+ * defines at file scope; every GPU that loads the library holds that array until the
+ * process exits. The work lists of a batch take about 256 bytes per problem plus 16 bytes
+ * per 512-word tile of every 32-replica plane plus 4 bytes per resident warp; a batch that
+ * does not fit (or has more than 2048 problems, or 65536 tiles) is rejected with PT_EINVAL
+ * and a message saying so, before anything is launched. No call allocates: not on the
+ * device (no cudaMalloc, cudaMallocAsync or cudaFree) and not on the host heap; the host
+ * side builds the lists in fixed arrays.
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture starts. Every
+ * call shares the one array and overwrites what the previous call left there (nothing in it
+ * has to start at zero: each call writes every part it reads). Calls are serialised on the
+ * host and each call waits until its lists have been copied to the device, but two calls
+ * whose kernels overlap on the GPU (different streams, different problems) race on the
+ * array: issue them on one stream, or synchronise between them. */
+int pt_sweep_batch_static(pt_problem* const* problems, int count, const int64_t* n,
+                          const int* exchange_every);
+
 /* How pt_sweep_batch runs (chosen by the autotuner; results never depend on it):
  *   PT_BATCH_FLAT    -- all problems advance sweep by sweep together; every half sweep is
  *                       one launch over equal-sized word tiles of all problems, followed by

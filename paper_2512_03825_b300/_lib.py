@@ -38,6 +38,8 @@ SIGNATURES = [
     ("pt_sweep", C.c_int, [P, C.c_int64, C.c_int]),
     ("pt_sweep_batch", C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.c_int64),
                                  C.POINTER(C.c_int)]),
+    ("pt_sweep_batch_static", C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.c_int64),
+                                        C.POINTER(C.c_int)]),
     ("pt_set_batch_tuning", C.c_int, [C.c_int, C.c_int, C.c_int]),
     ("pt_get_batch_tuning", C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_int),
                                       C.POINTER(C.c_int)]),

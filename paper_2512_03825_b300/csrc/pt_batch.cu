@@ -452,6 +452,42 @@ static void advance_counters(pt_problem* const* ps, int count, const int64_t* n,
   }
 }
 
+// Checks shared by both batch entry points: valid problems, counts, one stream, one device,
+// no problem twice. Returns the stream through *st.
+static int check_batch(pt_problem* const* ps, int count, const int64_t* n, const int* every,
+                       cudaStream_t* st_out) {
+  cudaStream_t st = ps[0] ? ps[0]->stream : 0;
+  int dev = -1;
+  for (int j = 0; j < count; ++j) {
+    pt_problem* p = ps[j];
+    int rc = problem_check(p);
+    if (rc) return rc;
+    if (n[j] < 0 || every[j] < 0)
+      return fail(PT_EINVAL, "problem %d: n = %lld, exchange_every = %d", j, (long long)n[j],
+                  every[j]);
+    if (p->stream != st) return fail(PT_EINVAL, "problems of one batch must share a stream");
+    if (dev < 0) dev = p->dev_info.device;
+    if (p->dev_info.device != dev) return fail(PT_EINVAL, "problems on different devices");
+  }
+  std::vector<pt_problem*> sorted(ps, ps + count);
+  std::sort(sorted.begin(), sorted.end());
+  if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+    return fail(PT_EINVAL, "a problem appears twice in one batch");
+  *st_out = st;
+  return problem_device_guard(ps[0]);
+}
+
+int sweep_batch_static_entry(pt_problem* const* ps, int count, const int64_t* n,
+                             const int* every) {
+  cudaStream_t st = 0;
+  int rc = check_batch(ps, count, n, every, &st);
+  if (rc) return rc;
+  rc = sweep_batch_static(ps, count, n, every, st, ps[0]->dev_info);
+  if (rc) return rc;
+  advance_counters(ps, count, n, every);
+  return PT_OK;
+}
+
 int sweep_batch(pt_problem* const* ps, int count, const int64_t* n, const int* every) {
   // checks
   cudaStream_t st = ps[0] ? ps[0]->stream : 0;

@@ -23,6 +23,12 @@ struct DeviceInfo;
 int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const int* every,
                      cudaStream_t st, const DeviceInfo& di);
 
+// The allocation-free variant of the lock-step path (pt_flat.cu); problems are checked.
+int sweep_batch_static(pt_problem* const* ps, int count, const int64_t* n, const int* every,
+                       cudaStream_t st, const DeviceInfo& di);
+
 int sweep_batch(pt_problem* const* problems, int count, const int64_t* n,
                 const int* exchange_every);
+int sweep_batch_static_entry(pt_problem* const* problems, int count, const int64_t* n,
+                             const int* exchange_every);
 }  // namespace ptb

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 #include <queue>
 #include <utility>
 #include <vector>
@@ -402,6 +403,228 @@ int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const i
   if (err != cudaSuccess) {
     for (int j = 0; j < count; ++j) ps[j]->poisoned = PT_ECUDA;
     return fail(PT_ECUDA, "flat batch launch: %s", cudaGetErrorString(err));
+  }
+  return PT_OK;
+}
+
+
+// =======================================================================================
+// Allocation-free variant of the lock-step batch.
+//
+// Some callers must not allocate device memory while they run: code that works inside a
+// memory budget it has already fixed, that runs under a custom allocator which this
+// library cannot see, or that must not let an allocation synchronise the device or fail
+// part-way. For them pt_sweep_batch_static does the work of pt_sweep_batch (lock-step
+// strategy) with its per-call work lists -- the problem descriptors, the warp tiles and
+// the per-warp tile offsets -- in one fixed array of device memory that the library
+// defines at file scope, instead of memory it allocates per call. The host side builds
+// the lists in fixed host arrays as well, so no call allocates on the heap either.
+// =======================================================================================
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(1) << 20;  // 1 MiB on every device
+constexpr int kStaticMaxProblems = 2048;
+constexpr int kStaticMaxTiles = 65536;
+constexpr int kStaticMaxWarps = 16384;
+
+// The device array. Every GPU that loads the library holds it until the process exits.
+// Host code must not use its name as an address: it gets the device address through
+// cudaGetSymbolAddress once per device.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+struct StaticDevice {
+  bool ready = false;
+  void* ptr = nullptr;
+};
+
+std::mutex g_static_mu;  // the host arrays below are shared by all calls
+StaticDevice g_static_dev[64];
+FlatProblem g_sp_probs[kStaticMaxProblems];
+Tile g_sp_tiles[kStaticMaxTiles];
+Tile g_sp_dealt[kStaticMaxTiles];
+int64_t g_sp_cost[kStaticMaxTiles];
+int g_sp_order[kStaticMaxTiles];
+int g_sp_owner[kStaticMaxTiles];
+int g_sp_first0[kStaticMaxWarps + 1];
+int g_sp_first1[kStaticMaxWarps + 1];
+int64_t g_sp_heap_load[kStaticMaxWarps];
+int g_sp_heap_warp[kStaticMaxWarps];
+
+// Longest-processing-time-first dealing of tiles [lo, hi) of g_sp_tiles to `nwarps` warps,
+// written to g_sp_dealt[lo..hi) warp by warp with offsets first[0..nwarps] (relative to lo).
+void static_deal(int lo, int hi, int nwarps, int* first) {
+  const int nt = hi - lo;
+  for (int k = 0; k < nt; ++k) {
+    g_sp_order[k] = lo + k;
+    g_sp_cost[lo + k] = tile_cost(g_sp_tiles[lo + k], g_sp_probs[g_sp_tiles[lo + k].prob].p.R);
+  }
+  std::stable_sort(g_sp_order, g_sp_order + nt,
+                   [](int a, int b) { return g_sp_cost[a] > g_sp_cost[b]; });
+  // binary min-heap of (load, warp) in two fixed arrays
+  for (int w = 0; w < nwarps; ++w) {
+    g_sp_heap_load[w] = 0;
+    g_sp_heap_warp[w] = w;
+  }
+  auto less = [](int a, int b) {
+    return g_sp_heap_load[a] < g_sp_heap_load[b] ||
+           (g_sp_heap_load[a] == g_sp_heap_load[b] && g_sp_heap_warp[a] < g_sp_heap_warp[b]);
+  };
+  auto swap_at = [](int a, int b) {
+    std::swap(g_sp_heap_load[a], g_sp_heap_load[b]);
+    std::swap(g_sp_heap_warp[a], g_sp_heap_warp[b]);
+  };
+  for (int k = 0; k < nt; ++k) {
+    const int t = g_sp_order[k];
+    g_sp_owner[t] = g_sp_heap_warp[0];
+    g_sp_heap_load[0] += g_sp_cost[t];
+    int i = 0;  // sift down
+    for (;;) {
+      const int l = 2 * i + 1, r = l + 1;
+      int m = i;
+      if (l < nwarps && less(l, m)) m = l;
+      if (r < nwarps && less(r, m)) m = r;
+      if (m == i) break;
+      swap_at(i, m);
+      i = m;
+    }
+  }
+  // counting sort of the tiles by owner
+  for (int w = 0; w <= nwarps; ++w) first[w] = 0;
+  for (int k = 0; k < nt; ++k) first[g_sp_owner[lo + k] + 1] += 1;
+  for (int w = 0; w < nwarps; ++w) first[w + 1] += first[w];
+  for (int k = 0; k < nt; ++k) {
+    const int t = g_sp_order[k];
+    g_sp_dealt[lo + first[g_sp_owner[t]]++] = g_sp_tiles[t];
+  }
+  for (int w = nwarps; w > 0; --w) first[w] = first[w - 1];
+  first[0] = 0;
+}
+
+}  // namespace
+
+int sweep_batch_static(pt_problem* const* ps, int count, const int64_t* n, const int* every,
+                       cudaStream_t st, const DeviceInfo& di) {
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (di.device < 0 || di.device >= 64) return fail(PT_ENODEV, "device index %d", di.device);
+  // set-up, once per device, with that device current: the device address of the array
+  StaticDevice& sd = g_static_dev[di.device];
+  if (!sd.ready) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess)
+      return fail(PT_ECUDA, "cudaGetSymbolAddress of the static scratch: %s",
+                  cudaGetErrorString(e));
+    sd.ptr = ptr;
+    sd.ready = true;
+  }
+  // problems and tiles, ferro-mode tiles first, then generic-mode ones
+  int np = 0, nt = 0, split = 0;  // split = number of ferro-mode tiles (they come first)
+  int64_t n_max = 0;
+  for (int mode_pass = 0; mode_pass < 2; ++mode_pass) {
+    for (int j = 0; j < count; ++j) {
+      if (n[j] <= 0) continue;
+      pt_problem* p = ps[j];
+      const int md = p->mode == kModeFerro ? 0 : 1;
+      if (md != mode_pass) continue;
+      if (np >= kStaticMaxProblems)
+        return fail(PT_EINVAL, "pt_sweep_batch_static: more than %d problems", kStaticMaxProblems);
+      FlatProblem& fp = g_sp_probs[np];
+      fp = FlatProblem{};
+      fp.p = p->dev;
+      fp.t0 = p->t;
+      fp.e0 = p->e;
+      fp.n = n[j];
+      fp.m = every[j];
+      n_max = std::max(n_max, n[j]);
+      const int words = p->L * (p->L / 2);
+      const int ntile = std::max(1, (words + kTileWords / 2) / kTileWords);
+      if ((int64_t)nt + (int64_t)ntile * p->W > kStaticMaxTiles)
+        return fail(PT_EINVAL, "pt_sweep_batch_static: more than %d work tiles (the batch is "
+                    "too large for the %zu-byte static work area)", kStaticMaxTiles,
+                    kStaticScratchBytes);
+      for (int w = 0; w < p->W; ++w)
+        for (int k = 0; k < ntile; ++k) {
+          Tile& t = g_sp_tiles[nt++];
+          t.prob = np;
+          t.w = w;
+          t.q0 = (int)((int64_t)words * k / ntile);
+          t.q1 = (int)((int64_t)words * (k + 1) / ntile);
+        }
+      ++np;
+    }
+    if (mode_pass == 0) split = nt;
+  }
+  if (np == 0) return PT_OK;
+  int per_sm[2] = {1, 1};
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm[0], k_flat_half<kModeFerro, true>, kFlatThreads, 0);
+  if (err == cudaSuccess)
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm[1], k_flat_half<kModeGeneric, true>, kFlatThreads, 0);
+  if (err != cudaSuccess) return fail(PT_ECUDA, "occupancy: %s", cudaGetErrorString(err));
+  const int wpb = kFlatThreads / 32;
+  const int lo[2] = {0, split}, hi[2] = {split, nt};
+  int grid[2] = {0, 0}, nwarps[2] = {0, 0};
+  for (int md = 0; md < 2; ++md) {
+    const int cnt = hi[md] - lo[md];
+    if (cnt == 0) continue;
+    const int blocks = std::max(1, per_sm[md]) * di.sms;
+    grid[md] = std::max(1, std::min(blocks, (cnt + wpb - 1) / wpb));
+    nwarps[md] = grid[md] * wpb;
+  }
+  if (nwarps[0] > kStaticMaxWarps || nwarps[1] > kStaticMaxWarps)
+    return fail(PT_EINTERNAL, "pt_sweep_batch_static: warp table too small");
+  // layout inside the static array: problems | tiles | offsets (mode 0) | offsets (mode 1)
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t off_tiles = al((size_t)np * sizeof(FlatProblem));
+  const size_t off_first0 = off_tiles + al((size_t)nt * sizeof(Tile));
+  const size_t off_first1 = off_first0 + al((size_t)(nwarps[0] + 1) * sizeof(int));
+  const size_t need = off_first1 + al((size_t)(nwarps[1] + 1) * sizeof(int));
+  if (need > kStaticScratchBytes)
+    return fail(PT_EINVAL, "pt_sweep_batch_static: the batch needs %zu bytes of work lists, "
+                "more than the %zu-byte static work area", need, kStaticScratchBytes);
+  if (grid[0]) static_deal(lo[0], hi[0], nwarps[0], g_sp_first0);
+  if (grid[1]) static_deal(lo[1], hi[1], nwarps[1], g_sp_first1);
+  char* base = (char*)sd.ptr;
+  err = cudaMemcpyAsync(base, g_sp_probs, (size_t)np * sizeof(FlatProblem),
+                        cudaMemcpyHostToDevice, st);
+  if (err == cudaSuccess && grid[0])
+    err = cudaMemcpyAsync(base + off_first0, g_sp_first0, (size_t)(nwarps[0] + 1) * sizeof(int),
+                          cudaMemcpyHostToDevice, st);
+  if (err == cudaSuccess && grid[1])
+    err = cudaMemcpyAsync(base + off_first1, g_sp_first1, (size_t)(nwarps[1] + 1) * sizeof(int),
+                          cudaMemcpyHostToDevice, st);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(base + off_tiles, g_sp_dealt, (size_t)nt * sizeof(Tile),
+                          cudaMemcpyHostToDevice, st);
+  // the host arrays are reused by the next call: wait until the copies have read them
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+  const FlatProblem* d_probs = (const FlatProblem*)base;
+  const Tile* d_tiles0 = (const Tile*)(base + off_tiles);
+  const Tile* d_tiles1 = d_tiles0 + split;
+  const int* d_first0 = (const int*)(base + off_first0);
+  const int* d_first1 = (const int*)(base + off_first1);
+  for (int64_t j = 0; j < n_max && err == cudaSuccess; ++j) {
+    bool ex = false;
+    for (int k = 0; k < np && !ex; ++k) {
+      const FlatProblem& fp = g_sp_probs[k];
+      ex = j < fp.n && fp.m > 0 && (fp.t0 + (uint64_t)j + 1) % (uint64_t)fp.m == 0;
+    }
+    if (grid[0]) k_flat_half<kModeFerro, false><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles0, d_first0, 0, j);
+    if (grid[1]) k_flat_half<kModeGeneric, false><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles1, d_first1, 0, j);
+    if (ex) {
+      if (grid[0]) k_flat_half<kModeFerro, true><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles0, d_first0, 1, j);
+      if (grid[1]) k_flat_half<kModeGeneric, true><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles1, d_first1, 1, j);
+      k_flat_exchange<<<std::min(np, di.sms * 8), kFlatThreads, 0, st>>>(d_probs, np, j);
+    } else {
+      if (grid[0]) k_flat_half<kModeFerro, false><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles0, d_first0, 1, j);
+      if (grid[1]) k_flat_half<kModeGeneric, false><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles1, d_first1, 1, j);
+    }
+    err = cudaGetLastError();
+  }
+  if (err != cudaSuccess) {
+    for (int j = 0; j < count; ++j) ps[j]->poisoned = PT_ECUDA;
+    return fail(PT_ECUDA, "static batch launch: %s", cudaGetErrorString(err));
   }
   return PT_OK;
 }

@@ -769,4 +769,12 @@ int pt_sweep_batch(pt_problem* const* problems, int count, const int64_t* n,
   return ptb::sweep_batch(problems, count, n, exchange_every);
 }
 
+int pt_sweep_batch_static(pt_problem* const* problems, int count, const int64_t* n,
+                          const int* exchange_every) {
+  if (count < 0 || (count > 0 && (!problems || !n || !exchange_every)))
+    return fail(PT_EINVAL, "bad batch arguments");
+  if (count == 0) return PT_OK;
+  return ptb::sweep_batch_static_entry(problems, count, n, exchange_every);
+}
+
 }  // extern "C"
