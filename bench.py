@@ -1,6 +1,7 @@
 #!/usr/bin/env python
 """Benchmark: spin-flip attempts per second of parallel-tempering Metropolis on the 2D
-Ising model, batched persistent kernel vs the plain one-problem-per-launch path, on B300.
+Ising model, batched path vs the plain one-problem-per-launch path, on B300, plus the
+continuous-batching server's p50/p99 latency.
 
 Default workload (one step): 256 independent PT problems, L uniform over
 {32, 48, 64, 96, 128, 256}, R uniform in 8..48, betas linear 0.30 -> 0.60, J = 1, h = 0,
@@ -42,6 +43,10 @@ def parse_args(argv=None):
     ap.add_argument("--workload", choices=["batched", "single", "serve"], default="batched")
     ap.add_argument("--sweeps", type=int, default=2000, help="sweeps per problem per step")
     ap.add_argument("--problems", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=300,
+                    help="requests in the short serving run of the default line")
+    ap.add_argument("--requests", type=int, default=2000,
+                    help="requests of --workload serve")
     ap.add_argument("--quick", action="store_true",
                     help="skip the side measurements (plain path, L1024, e2e, CPU baseline)")
     return ap.parse_args(argv)
@@ -169,7 +174,15 @@ def run_ours(args, rank, world, local):
         return run_single(args, rank, world, stream, sms)
     if args.workload == "serve":
         from paper_2512_03825_b300 import serve
-        return serve.bench_serve(args, rank, world, stream)
+        res = serve.bench_serve(args, rank, world, stream)
+        return {"metric": METRIC, "value": res["attempts_per_s"], "unit": UNIT,
+                "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * res["wall_s"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "u32", "data": "synthetic Poisson request stream",
+                "config": {"workload": "serving: %d Poisson PT requests, L 32-512, R 8-64, "
+                                       "sweeps 1e2-1e4, h in {0, 0.1}, 80 GB budget"
+                                       % args.requests},
+                "serve": res}
 
     probs = W.batched_problems(n=args.problems, sweeps=args.sweeps, every=1)
     handles = [api.PTProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed, stream=stream)
@@ -217,7 +230,7 @@ def run_ours(args, rank, world, local):
             "batch_tuning": tuning,
         },
         "clocks": clk,
-        "gpu_launches": args.steps,  # one persistent k_batch launch per step
+        "gpu_launches": args.steps * launches_per_batch(probs, args.sweeps, tuning),
         "wall_s": wall,
     }
     peaks = measured_peaks()
@@ -225,7 +238,8 @@ def run_ours(args, rank, world, local):
     peak_mul = sms * IMUL_WIDE_PER_CLK_SM * clock_mhz * 1e6
     achieved_mul = MUL_PER_ATTEMPT * per_step / (statistics.mean(kernel_ms) / 1e3)
     out["roofline"] = {
-        "bound": "alu", "kernel": "k_batch",
+        "bound": "alu",
+        "kernel": "k_flat_half" if tuning.get("strategy", 0) == 0 else "k_batch",
         "achieved": achieved_mul / 1e12, "peak": peak_mul / 1e12, "unit": "T int-mul/s",
         "frac": achieved_mul / peak_mul,
         "traffic": None,
@@ -233,6 +247,7 @@ def run_ours(args, rank, world, local):
                 "%d per clock x %.0f MHz" % (sms, IMUL_WIDE_PER_CLK_SM, clock_mhz),
     }
     if not args.quick and rank == 0:
+        out["serve"] = bench_serve_short(stream, args.serve_requests)
         out["plain"] = bench_plain_sample(probs, stream)
         out["batched_vs_plain"] = value / world / out["plain"]["value"]
         out["single_L1024_R64"] = bench_single(stream, sms, clock_mhz)
@@ -242,6 +257,26 @@ def run_ours(args, rank, world, local):
         bench_e2e(probs, args.sweeps, stream, world)
     for h in handles:
         h.close()
+    return out
+
+
+def launches_per_batch(probs, sweeps, tuning):
+    """Kernel launches of one pt_sweep_batch call: the lock-step strategy launches two
+    half sweeps per sweep plus one exchange launch after every sweep with an exchange (one
+    mode here: h = 0); the cluster strategy is one persistent launch plus a helper."""
+    if tuning.get("strategy", 0) == 0:
+        return sweeps * 3
+    return 2
+
+
+def bench_serve_short(stream, nreq):
+    """A shorter run of the serving workload (the full one is --workload serve)."""
+    from paper_2512_03825_b300 import serve
+
+    class A:
+        requests = nreq
+    out = serve.bench_serve(A, 0, 1, stream)
+    out["note"] = "%d Poisson requests at 80%% of the measured batched rate" % nreq
     return out
 
 

@@ -125,7 +125,7 @@ class PTProblem:
 
 
 def sweep_batch(problems: Sequence[PTProblem], n, exchange_every):
-    """Advance all problems together in one persistent kernel (n, exchange_every: an int
+    """Advance all problems together with the batched strategy (n, exchange_every: an int
     or one value per problem)."""
     k = len(problems)
     if k == 0:
@@ -159,15 +159,23 @@ def swap_threshold(beta_lo, beta_hi, n, s):
 
 
 # -- PyTorch as the device-memory provider -------------------------------------------------
+# Every problem remembers the free function it was allocated with, so the ctypes callbacks
+# handed to the library must outlive every problem: they are kept for the whole process and
+# installed at most once.
 _torch_hooks = None
+_all_hooks = []
 
 
 def use_torch_allocator(enable: bool = True):
-    """Route the library's device allocations through torch's caching allocator."""
+    """Route the library's device allocations through torch's caching allocator (idempotent).
+    With enable=False, later problems go back to cudaMalloc; problems created through torch
+    keep releasing their memory through it."""
     global _torch_hooks
     if not enable:
         check(lib.pt_set_allocator(ALLOC_FN(), FREE_FN(), None), "pt_set_allocator")
         _torch_hooks = None
+        return
+    if _torch_hooks is not None:
         return
     import torch
 
@@ -180,8 +188,12 @@ def use_torch_allocator(enable: bool = True):
 
     def _free(ptr, stream, ctx):
         if ptr:
-            torch.cuda.caching_allocator_delete(int(ptr))
+            try:
+                torch.cuda.caching_allocator_delete(int(ptr))
+            except Exception:  # interpreter shutdown
+                pass
 
     hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _all_hooks.append(hooks)
     check(lib.pt_set_allocator(hooks[0], hooks[1], None), "pt_set_allocator")
     _torch_hooks = hooks

@@ -109,3 +109,17 @@ def test_bad_arguments_rejected_before_device(pt):
         assert ei.value.code == pt.PT_EINVAL
     assert api.estimate_device_bytes(5, [0.1]) == 0
     assert api.estimate_device_bytes(1024, np.linspace(0.35, 0.5, 64)) > 8 * 2 ** 20
+
+
+def test_allocator_hooks_are_kept_alive(pt):
+    """Re-enabling the torch allocator must not free the callbacks that existing problems
+    will call when they are destroyed."""
+    from paper_2512_03825_b300 import api
+    api.use_torch_allocator(True)
+    first = api._torch_hooks
+    api.use_torch_allocator(True)
+    assert api._torch_hooks is first
+    api.use_torch_allocator(False)
+    api.use_torch_allocator(True)
+    assert first in api._all_hooks
+    api.use_torch_allocator(False)
