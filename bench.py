@@ -33,6 +33,23 @@ UNIT = "attempts/s"
 MUL_PER_ATTEMPT = 5.0  # Philox4x32-10: 20 32x32->64 products per block of 4 draws
 IMUL_WIDE_PER_CLK_SM = 32.0  # 32x32->64 integer products per clock per SM (4 SMSPs x 8)
 
+# DRAM traffic of one k_flat_half launch (colour 0) on the batched-256 workload from the ncu
+# capture summarised in profiles/k_flat_half_batched-256.md (cold caches: one read of the
+# whole state). Valid only for the kernel source it was taken on.
+FLAT_TRAFFIC_BYTES = 25.937152e6 + 41.728e3
+FLAT_TRAFFIC_SOURCES = ("paper_2512_03825_b300/csrc/pt_device.cuh",
+                        "paper_2512_03825_b300/csrc/pt_flat.cu")
+FLAT_TRAFFIC_SOURCE_HASH = "6335ed12aa33494a"
+
+
+def _flat_traffic():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in FLAT_TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return FLAT_TRAFFIC_BYTES if h.hexdigest()[:16] == FLAT_TRAFFIC_SOURCE_HASH else None
+
 
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
@@ -236,15 +253,38 @@ def run_ours(args, rank, world, local):
     peaks = measured_peaks()
     clock_mhz = float(peaks.get("sm_max_mhz", 2032.0))
     peak_mul = sms * IMUL_WIDE_PER_CLK_SM * clock_mhz * 1e6
-    achieved_mul = MUL_PER_ATTEMPT * per_step / (statistics.mean(kernel_ms) / 1e3)
+    flat = tuning.get("strategy", 0) == 0
+    if flat:
+        # the dominant kernel on its own: a batch without exchanges is nothing but
+        # k_flat_half launches (two per sweep), timed on the problems' stream
+        nsw = 50
+        with torch.cuda.stream(stream):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            api.sweep_batch(handles, nsw, 0)
+            b.record(stream)
+            torch.cuda.synchronize()
+        launch_s = a.elapsed_time(b) / 1e3 / (2 * nsw)
+        per_launch_mul = MUL_PER_ATTEMPT * per_step / args.sweeps / 2
+        achieved_mul = per_launch_mul / launch_s
+        how = ("k_flat_half: algorithmic products of one half sweep of all 256 problems (5 per "
+               "attempt) / its average launch duration over %d launches (CUDA events)"
+               % (2 * nsw))
+        traffic = _flat_traffic()
+    else:
+        achieved_mul = MUL_PER_ATTEMPT * per_step / (statistics.mean(kernel_ms) / 1e3)
+        how = "k_batch: products of one batch / its duration"
+        traffic = None
     out["roofline"] = {
         "bound": "alu",
-        "kernel": "k_flat_half" if tuning.get("strategy", 0) == 0 else "k_batch",
+        "kernel": "k_flat_half" if flat else "k_batch",
         "achieved": achieved_mul / 1e12, "peak": peak_mul / 1e12, "unit": "T int-mul/s",
         "frac": achieved_mul / peak_mul,
-        "traffic": None,
+        "traffic": traffic,
         "note": "32x32->64 integer multiplies (Philox4x32-10, 5 per attempt) against %d SMs x "
-                "%d per clock x %.0f MHz" % (sms, IMUL_WIDE_PER_CLK_SM, clock_mhz),
+                "%d per clock x %.0f MHz (max clock; of measured SM count); %s; traffic = DRAM "
+                "bytes per launch from ncu (cold caches)" % (sms, IMUL_WIDE_PER_CLK_SM,
+                                                              clock_mhz, how),
     }
     if not args.quick and rank == 0:
         out["serve"] = bench_serve_short(stream, args.serve_requests)
