@@ -60,6 +60,10 @@ def lib():
         L.oracle_swap_stats.restype = None
         L.oracle_counters.argtypes = [P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
         L.oracle_counters.restype = None
+        L.oracle_load_state.argtypes = [P, C.POINTER(C.c_int8), C.POINTER(C.c_int32),
+                                        C.c_uint64, C.c_uint64, C.POINTER(C.c_uint64),
+                                        C.POINTER(C.c_uint64)]
+        L.oracle_load_state.restype = C.c_int
         L.oracle_set_threads.argtypes = [C.c_int]
         L.oracle_set_threads.restype = None
         L.oracle_get_threads.argtypes = []
@@ -191,3 +195,18 @@ class OracleProblem:
         t, e = C.c_uint64(), C.c_uint64()
         lib().oracle_counters(self._h, C.byref(t), C.byref(e))
         return t.value, e.value
+
+    def load_state(self, spins_by_slot, slot_of_temp, t, e, attempted, accepted):
+        """Continue the chain from a given state: spins [R][L][L] by slot, the temperature
+        map, the counters and the swap statistics."""
+        sp = np.ascontiguousarray(spins_by_slot, dtype=np.int8).reshape(self.R, self.L, self.L)
+        so = np.ascontiguousarray(slot_of_temp, dtype=np.int32)
+        att = np.ascontiguousarray(attempted, dtype=np.uint64)
+        acc = np.ascontiguousarray(accepted, dtype=np.uint64)
+        if att.size == 0:
+            att = np.zeros(1, np.uint64)
+            acc = np.zeros(1, np.uint64)
+        rc = lib().oracle_load_state(self._h, _ptr(sp, C.c_int8), _ptr(so, C.c_int32), int(t),
+                                     int(e), _ptr(att, C.c_uint64), _ptr(acc, C.c_uint64))
+        if rc != 0:
+            raise ValueError("oracle_load_state failed (%d)" % rc)

@@ -334,3 +334,33 @@ void oracle_swap_stats(const oracle_pt* p, uint64_t* attempted, uint64_t* accept
 }
 
 void oracle_counters(const oracle_pt* p, uint64_t* t, uint64_t* e) { *t = p->t; *e = p->e; }
+
+/* Replace the whole state (test support: lets a test continue the chain from a state taken
+ * elsewhere). spins_by_slot is [R][L][L] (+1 / -1), slot_of_temp a permutation of 0..R-1,
+ * t and e the sweep and swap-iteration counters, attempted / accepted [R-1] (may be NULL
+ * when R == 1). */
+int oracle_load_state(oracle_pt* p, const int8_t* spins_by_slot, const int32_t* slot_of_temp,
+                      uint64_t t, uint64_t e, const uint64_t* attempted,
+                      const uint64_t* accepted) {
+    const int R = p->R;
+    const size_t n = (size_t)p->L * p->L;
+    for (size_t i = 0; i < (size_t)R * n; ++i)
+        if (spins_by_slot[i] != 1 && spins_by_slot[i] != -1) return ORACLE_EINVAL;
+    for (int k = 0; k < R; ++k) {
+        if (slot_of_temp[k] < 0 || slot_of_temp[k] >= R) return ORACLE_EINVAL;
+        for (int j = 0; j < k; ++j)
+            if (slot_of_temp[j] == slot_of_temp[k]) return ORACLE_EINVAL;
+    }
+    memcpy(p->spin, spins_by_slot, (size_t)R * n);
+    for (int k = 0; k < R; ++k) {
+        p->slot_of_temp[k] = slot_of_temp[k];
+        p->temp_of_slot[slot_of_temp[k]] = k;
+    }
+    p->t = t;
+    p->e = e;
+    if (R > 1) {
+        memcpy(p->attempted, attempted, sizeof(uint64_t) * (R - 1));
+        memcpy(p->accepted, accepted, sizeof(uint64_t) * (R - 1));
+    }
+    return ORACLE_OK;
+}
