@@ -15,6 +15,7 @@ struct BatchTuning {
   int strategy = PT_BATCH_FLAT;
   int cluster = 4;
   int joint_min_L = 128;
+  int fuse_exchange = 0;  // lock-step: exchange in the colour-1 launch (1) or its own (0)
 };
 extern BatchTuning g_batch_tuning;
 
