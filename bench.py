@@ -72,13 +72,12 @@ def parse_args(argv=None):
 # ---------------------------------------------------------------------------------------
 # distributed plumbing (one process per GPU; weak scaling over independent problems)
 # ---------------------------------------------------------------------------------------
-def dist_setup(args):
+def dist_setup(args, backend="nccl"):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        backend = "nccl"
         dist.init_process_group(backend=backend)
     return rank, world, local
 
@@ -89,14 +88,45 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def _reduce(x, world, op):
     if world == 1:
-        return x
+        return float(x)
     import torch
     import torch.distributed as dist
-    t = torch.tensor([float(x)], device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(x, world):
+    """The slowest rank's value (timing): the job is done when every rank is."""
+    import torch.distributed as dist
+    return _reduce(x, world, dist.ReduceOp.MAX if world > 1 else None)
+
+
+def sum_over_ranks(x, world):
+    import torch.distributed as dist
+    return _reduce(x, world, dist.ReduceOp.SUM if world > 1 else None)
+
+
+RANK_SEED_STRIDE = 0x10000
+
+
+def rank_problems(rank, n, sweeps, every=1):
+    """This rank's share of the work: its own copy of the batched workload with seeds offset
+    by rank, so every rank advances different (independent) problems of the same shape."""
+    from paper_2512_03825_b300 import workloads as W
+    import dataclasses
+    probs = W.batched_problems(n=n, sweeps=sweeps, every=every)
+    return [dataclasses.replace(p, seed=p.seed + rank * RANK_SEED_STRIDE) for p in probs]
+
+
+def job_throughput(attempts_this_rank, seconds_this_rank, world):
+    """Whole-job attempts per second: all ranks' attempts over the slowest rank's time."""
+    total = sum_over_ranks(attempts_this_rank, world)
+    slowest = max_over_ranks(seconds_this_rank, world)
+    return total / slowest, total, slowest
 
 
 # ---------------------------------------------------------------------------------------
@@ -201,7 +231,7 @@ def run_ours(args, rank, world, local):
                                        % args.requests},
                 "serve": res}
 
-    probs = W.batched_problems(n=args.problems, sweeps=args.sweeps, every=1)
+    probs = rank_problems(rank, args.problems, args.sweeps, 1)
     handles = [api.PTProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed, stream=stream)
                for p in probs]
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
@@ -228,9 +258,7 @@ def run_ours(args, rank, world, local):
         wall = time.perf_counter() - t0
         clk = clocks.stop()
     kernel_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(kernel_ms) / 1e3
-    total_s = max_over_ranks(total_s, world)
-    value = per_step * args.steps * world / total_s
+    value, _, total_s = job_throughput(per_step * args.steps, sum(kernel_ms) / 1e3, world)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
