@@ -93,8 +93,43 @@ int pt_set_stream(pt_problem* p, void* cuda_stream);
 /* Sec. 3, execution phase: n >= 0 sweeps, with a swap iteration after every sweep that
  * leaves the total sweep count a multiple of exchange_every (0 = no swaps; < 0 is
  * PT_EINVAL). pt_sweep(a, m) followed by pt_sweep(b, m) equals pt_sweep(a + b, m).
- * Launches the per-problem kernels (the plain path) and returns without waiting. */
+ * Launches the problem's kernels (the plain path: see pt_set_sweep_tuning) and returns
+ * without waiting. */
 int pt_sweep(pt_problem* p, int64_t n, int exchange_every);
+
+/* How pt_sweep runs this problem (results never depend on it):
+ *   PT_SWEEP_AUTO       -- persistent when the problem fits, else launches (the default);
+ *   PT_SWEEP_LAUNCHES   -- one launch per half sweep, plus an energy-count and an exchange
+ *                          launch after each sweep that ends with a swap iteration;
+ *   PT_SWEEP_PERSISTENT -- one cooperative launch per call (up to 65536 sweeps each) whose
+ *                          CTAs meet at grid barriers between half sweeps and all compute
+ *                          the swap iterations themselves. It fits when every 32-replica
+ *                          plane gets at least one CTA of one resident wave and no thread
+ *                          owns more than 255 words of a colour; pt_sweep returns PT_EINVAL
+ *                          otherwise.
+ * words_per_thread (1..255, 0 = the default 1) sets how many words of each colour a thread
+ * of the persistent kernel aims to own: the CTA count is the one that gives that many,
+ * capped at one resident wave. PT_EINVAL for an unknown strategy or a count out of range. */
+#define PT_SWEEP_AUTO 0
+#define PT_SWEEP_LAUNCHES 1
+#define PT_SWEEP_PERSISTENT 2
+int pt_set_sweep_tuning(pt_problem* p, int strategy, int words_per_thread);
+
+/* The problem's sweep strategy, words-per-thread setting and the CTA count the persistent
+ * kernel would use (0 when the problem does not fit it). Any pointer may be NULL. */
+int pt_get_sweep_tuning(pt_problem* p, int* strategy, int* words_per_thread, int* grid);
+
+/* Time limit of each wait of the persistent kernel at a grid barrier, in seconds
+ * (0 < seconds <= 60; default 1). A wait that runs out stores PT_ETIMEOUT in the problem's
+ * device status, every CTA leaves the kernel, and the next pt_synchronize (or getter)
+ * returns PT_ETIMEOUT and poisons the problem; the CUDA context stays usable. */
+int pt_set_wait_limit(pt_problem* p, double seconds);
+
+/* Test support for the bounded wait; the paper has no counterpart. The next persistent launch
+ * of this problem waits at its first grid barrier for `arrivals` (>= 0) more CTAs than it
+ * has, so that every wait runs out after the wait limit and the launch ends with
+ * PT_ETIMEOUT as described above. Applies to one launch. */
+int pt_debug_stall_barrier(pt_problem* p, int arrivals);
 
 /* Advance `count` problems together in one persistent kernel: problem j runs n[j] >= 0
  * sweeps with exchange_every[j] (same meaning as pt_sweep). All problems must be on the

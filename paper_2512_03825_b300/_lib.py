@@ -22,6 +22,9 @@ PT_ENODEV = -6
 PT_EINTERNAL = -7
 PT_BATCH_FLAT = 0
 PT_BATCH_CLUSTER = 1
+PT_SWEEP_AUTO = 0
+PT_SWEEP_LAUNCHES = 1
+PT_SWEEP_PERSISTENT = 2
 PT_MAX_L = 16384
 PT_MAX_R = 2048
 
@@ -36,6 +39,11 @@ SIGNATURES = [
     ("pt_destroy", None, [P]),
     ("pt_set_stream", C.c_int, [P, P]),
     ("pt_sweep", C.c_int, [P, C.c_int64, C.c_int]),
+    ("pt_set_sweep_tuning", C.c_int, [P, C.c_int, C.c_int]),
+    ("pt_get_sweep_tuning", C.c_int, [P, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                      C.POINTER(C.c_int)]),
+    ("pt_set_wait_limit", C.c_int, [P, C.c_double]),
+    ("pt_debug_stall_barrier", C.c_int, [P, C.c_int]),
     ("pt_sweep_batch", C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.c_int64),
                                  C.POINTER(C.c_int)]),
     ("pt_sweep_batch_static", C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.c_int64),

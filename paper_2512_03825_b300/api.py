@@ -63,6 +63,24 @@ class PTProblem:
     def synchronize(self):
         check(lib.pt_synchronize(self._h), "pt_synchronize")
 
+    def set_sweep_tuning(self, strategy: int = 0, words_per_thread: int = 0):
+        """strategy: PT_SWEEP_AUTO (0), PT_SWEEP_LAUNCHES (1) or PT_SWEEP_PERSISTENT (2)."""
+        check(lib.pt_set_sweep_tuning(self._h, int(strategy), int(words_per_thread)),
+              "pt_set_sweep_tuning")
+
+    def sweep_tuning(self):
+        """(strategy, words_per_thread, persistent grid or 0)."""
+        s, w, g = C.c_int(), C.c_int(), C.c_int()
+        check(lib.pt_get_sweep_tuning(self._h, C.byref(s), C.byref(w), C.byref(g)),
+              "pt_get_sweep_tuning")
+        return s.value, w.value, g.value
+
+    def set_wait_limit(self, seconds: float):
+        check(lib.pt_set_wait_limit(self._h, float(seconds)), "pt_set_wait_limit")
+
+    def debug_stall_barrier(self, arrivals: int):
+        check(lib.pt_debug_stall_barrier(self._h, int(arrivals)), "pt_debug_stall_barrier")
+
     # -- observables ---------------------------------------------------------------------
     def energies_int(self):
         E = np.zeros(self.R, np.int64)

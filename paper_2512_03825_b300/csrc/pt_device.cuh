@@ -41,6 +41,29 @@ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint3
   return Philox4{c0, c1, c2, c3};
 }
 
+// The ten round keys (k + r * W, mod 2^32) of one seed, computed on the host. Held in a
+// __grid_constant__ kernel parameter and indexed with constants, each key is an operand
+// straight from the constant bank: no register and no instruction per round.
+struct RoundKeys {
+  uint32_t k0[10], k1[10];
+};
+
+__device__ __forceinline__ Philox4 philox4x32_10_rk(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                     uint32_t c3, const RoundKeys& rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c0);
+    const uint32_t lo0 = kPhiloxM0 * c0;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c2);
+    const uint32_t lo1 = kPhiloxM1 * c2;
+    c0 = hi1 ^ c1 ^ rk.k0[r];
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ rk.k1[r];
+    c3 = lo0;
+  }
+  return Philox4{c0, c1, c2, c3};
+}
+
 // Counter words shared by every spin-update draw of one sweep.
 struct SweepCtr {
   uint32_t t_lo;  // lo32(t)
@@ -131,12 +154,50 @@ __device__ __forceinline__ uint32_t update_word_ferro(uint32_t s, uint32_t n0, u
   return s ^ flip;
 }
 
+// update_word_ferro with the thresholds in shared memory, interleaved so that one 16-byte
+// broadcast load serves two slots: thr[m] = {T0[2m], T1[2m], T0[2m+1], T1[2m+1]}, and the
+// round keys from the parameter bank. Same decisions, bit for bit.
+__device__ __forceinline__ uint32_t update_word_ferro_smem(uint32_t s, uint32_t n0, uint32_t n1,
+                                                           uint32_t n2, uint32_t n3,
+                                                           uint32_t site, uint32_t blk0,
+                                                           int nblk, const uint4* thr,
+                                                           uint32_t alw0, uint32_t alw1,
+                                                           uint32_t used, uint32_t t_lo,
+                                                           uint32_t c3, const RoundKeys& rk) {
+  const uint32_t a0 = s ^ n0, a1 = s ^ n1, a2 = s ^ n2, a3 = s ^ n3;
+  const uint32_t x01 = a0 ^ a1, x23 = a2 ^ a3;
+  const uint32_t ge2 = (a0 & a1) | (a2 & a3) | (x01 & x23);
+  const uint32_t eq1 = (x01 ^ x23) & ~ge2;
+  uint32_t rej0 = nblk >= 8 ? 0u : (0xffffffffu >> (4 * nblk));
+  uint32_t rej1 = rej0;
+#pragma unroll
+  for (int j = 7; j >= 0; --j) {
+    if (j < nblk) {
+      const Philox4 r = philox4x32_10_rk(site, t_lo, blk0 + (uint32_t)j, c3, rk);
+      const uint4 lo = thr[2 * j], hi = thr[2 * j + 1];  // slots 4j, 4j+1 | 4j+2, 4j+3
+      rej0 = shift_in_reject(rej0, r.w, hi.z);
+      rej1 = shift_in_reject(rej1, r.w, hi.w);
+      rej0 = shift_in_reject(rej0, r.z, hi.x);
+      rej1 = shift_in_reject(rej1, r.z, hi.y);
+      rej0 = shift_in_reject(rej0, r.y, lo.z);
+      rej1 = shift_in_reject(rej1, r.y, lo.w);
+      rej0 = shift_in_reject(rej0, r.x, lo.x);
+      rej1 = shift_in_reject(rej1, r.x, lo.y);
+    }
+  }
+  const uint32_t acc = ~rej0 | (eq1 & ~rej1);
+  const uint32_t flip = (ge2 | alw0 | (eq1 & alw1) | acc) & used;
+  return s ^ flip;
+}
+
 // Any J, h: class c = 2 k + (sigma == +1) per bit; thresholds from the plane table.
-__device__ __forceinline__ uint32_t update_word_generic(uint32_t s, uint32_t n0, uint32_t n1,
-                                                        uint32_t n2, uint32_t n3,
-                                                        uint32_t site, uint32_t blk0, int nblk,
-                                                        const PlaneGeneric& pl,
-                                                        const SweepCtr& cx) {
+// `draw(j)` returns Philox block j of this site (slots 4j .. 4j+3).
+template <class Draw>
+__device__ __forceinline__ uint32_t update_word_generic_with(uint32_t s, uint32_t n0,
+                                                             uint32_t n1, uint32_t n2,
+                                                             uint32_t n3, int nblk,
+                                                             const PlaneGeneric& pl,
+                                                             const Draw& draw) {
   const NbCount k = count4(s ^ n0, s ^ n1, s ^ n2, s ^ n3);
   const uint32_t z[5] = {~(k.b0 | k.b1 | k.b2), k.b0 & ~k.b1 & ~k.b2, ~k.b0 & k.b1 & ~k.b2,
                          k.b0 & k.b1, k.b2};
@@ -148,7 +209,7 @@ __device__ __forceinline__ uint32_t update_word_generic(uint32_t s, uint32_t n0,
 #pragma unroll
   for (int j = 7; j >= 0; --j) {
     if (j < nblk) {
-      const Philox4 r = philox4x32_10(site, cx.t_lo, blk0 + (uint32_t)j, cx.c3, cx.k0, cx.k1);
+      const Philox4 r = draw(j);
       const uint32_t u[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
       for (int q = 3; q >= 0; --q) {
@@ -162,6 +223,16 @@ __device__ __forceinline__ uint32_t update_word_generic(uint32_t s, uint32_t n0,
   }
   const uint32_t flip = (always | ~rej) & pl.used;
   return s ^ flip;
+}
+
+__device__ __forceinline__ uint32_t update_word_generic(uint32_t s, uint32_t n0, uint32_t n1,
+                                                        uint32_t n2, uint32_t n3,
+                                                        uint32_t site, uint32_t blk0, int nblk,
+                                                        const PlaneGeneric& pl,
+                                                        const SweepCtr& cx) {
+  return update_word_generic_with(s, n0, n1, n2, n3, nblk, pl, [&](int j) {
+    return philox4x32_10(site, cx.t_lo, blk0 + (uint32_t)j, cx.c3, cx.k0, cx.k1);
+  });
 }
 
 // ---------------------------------------------------------------------------------------

@@ -19,6 +19,7 @@
 #include "pt_batch.h"
 #include "pt_internal.h"
 #include "pt_launch.h"
+#include "pt_persist.h"
 
 using namespace ptb;
 
@@ -235,7 +236,7 @@ Layout make_layout(int L, int R, int W, int mode, size_t table_entries) {
   l.planes = take((size_t)W * (mode == kModeFerro ? sizeof(PlaneFerro) : sizeof(PlaneGeneric)));
   l.temp_of_slot = take((size_t)R * 4);
   l.slot_of_temp = take((size_t)R * 4);
-  l.cnt = take((size_t)2 * W * 32 * 4);
+  l.cnt = take(count_words(W) * 4);
   l.E_slot = take((size_t)R * 8);
   l.M_slot = take((size_t)R * 8);
   l.attempted = take(npairs * 8);
@@ -581,6 +582,26 @@ int pt_set_stream(pt_problem* p, void* cuda_stream) {
   return PT_OK;
 }
 
+namespace {
+
+// pt_sweep as cooperative launches of at most kPersistChunk sweeps each.
+int sweep_persistent(pt_problem* p, int64_t n, int m) {
+  while (n > 0) {
+    const int c = (int)std::min<int64_t>(n, kPersistChunk);
+    const cudaError_t err = launch_persist(p->dev, p->plan, p->t, p->e, c, m, p->stall,
+                                           p->wait_limit_ns, p->stream);
+    p->stall = 0;
+    if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "persistent sweep launch", err);
+    const uint64_t t1 = p->t + (uint64_t)c;
+    if (m > 0) p->e += t1 / (uint64_t)m - p->t / (uint64_t)m;  // sweeps t with (t+1) % m == 0
+    p->t = t1;
+    n -= c;
+  }
+  return PT_OK;
+}
+
+}  // namespace
+
 int pt_sweep(pt_problem* p, int64_t n, int exchange_every) {
   int rc = problem_check(p);
   if (rc) return rc;
@@ -588,6 +609,18 @@ int pt_sweep(pt_problem* p, int64_t n, int exchange_every) {
     return fail(PT_EINVAL, "n = %lld and exchange_every = %d must be >= 0", (long long)n,
                 exchange_every);
   if ((rc = problem_device_guard(p))) return rc;
+  if (n == 0) return PT_OK;
+  if (p->sweep_strategy != PT_SWEEP_LAUNCHES) {
+    if (!p->plan_valid) {
+      const cudaError_t err = persist_plan(p->dev, p->dev_info, p->words_per_thread, &p->plan);
+      if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "persistent occupancy", err);
+      p->plan_valid = true;
+    }
+    if (p->plan.grid > 0) return sweep_persistent(p, n, exchange_every);
+    if (p->sweep_strategy == PT_SWEEP_PERSISTENT)
+      return fail(PT_EINVAL, "L = %d, R = %d does not fit one resident wave of the persistent "
+                  "kernel with <= %d words per thread", p->L, p->R, kPersistMaxWordsPerThread);
+  }
   for (int64_t j = 0; j < n; ++j) {
     cudaError_t err = launch_half_sweep(p->dev, p->dev_info, 0, p->t, p->stream);
     if (err == cudaSuccess) err = launch_half_sweep(p->dev, p->dev_info, 1, p->t, p->stream);
@@ -602,6 +635,52 @@ int pt_sweep(pt_problem* p, int64_t n, int exchange_every) {
       p->e += 1;
     }
   }
+  return PT_OK;
+}
+
+int pt_set_sweep_tuning(pt_problem* p, int strategy, int words_per_thread) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  if (strategy < PT_SWEEP_AUTO || strategy > PT_SWEEP_PERSISTENT)
+    return fail(PT_EINVAL, "unknown sweep strategy %d", strategy);
+  if (words_per_thread < 0 || words_per_thread > kPersistMaxWordsPerThread)
+    return fail(PT_EINVAL, "words_per_thread = %d outside 0..%d", words_per_thread,
+                kPersistMaxWordsPerThread);
+  p->sweep_strategy = strategy;
+  p->words_per_thread = words_per_thread ? words_per_thread : kPersistDefaultWords;
+  p->plan_valid = false;
+  return PT_OK;
+}
+
+int pt_get_sweep_tuning(pt_problem* p, int* strategy, int* words_per_thread, int* grid) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  if ((rc = problem_device_guard(p))) return rc;
+  if (!p->plan_valid) {
+    const cudaError_t err = persist_plan(p->dev, p->dev_info, p->words_per_thread, &p->plan);
+    if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "persistent occupancy", err);
+    p->plan_valid = true;
+  }
+  if (strategy) *strategy = p->sweep_strategy;
+  if (words_per_thread) *words_per_thread = p->words_per_thread;
+  if (grid) *grid = p->plan.grid;
+  return PT_OK;
+}
+
+int pt_set_wait_limit(pt_problem* p, double seconds) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  if (!(seconds > 0.0 && seconds <= 60.0))
+    return fail(PT_EINVAL, "wait limit %g s outside (0, 60]", seconds);
+  p->wait_limit_ns = (uint64_t)(seconds * 1e9);
+  return PT_OK;
+}
+
+int pt_debug_stall_barrier(pt_problem* p, int arrivals) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  if (arrivals < 0) return fail(PT_EINVAL, "arrivals = %d must be >= 0", arrivals);
+  p->stall = arrivals;
   return PT_OK;
 }
 

@@ -7,6 +7,7 @@
 
 #include "pt.h"
 #include "pt_launch.h"
+#include "pt_persist.h"
 
 struct pt_problem {
   int L = 0, R = 0, W = 0, mode = 0;
@@ -23,6 +24,12 @@ struct pt_problem {
   ptb::DevProblem dev{};
   ptb::DeviceInfo dev_info{};
   int poisoned = 0;       // sticky PT_E* code once device work failed
+  int sweep_strategy = PT_SWEEP_AUTO;
+  int words_per_thread = ptb::kPersistDefaultWords;
+  bool plan_valid = false;  // plan is computed on first use
+  ptb::PersistPlan plan{};
+  uint64_t wait_limit_ns = 1000000000ull;
+  int stall = 0;            // pt_debug_stall_barrier, one launch
 };
 
 namespace ptb {

@@ -1,0 +1,394 @@
+// pt_persist.cu -- the single-problem path as one persistent launch per pt_sweep call.
+//
+// A cooperative launch keeps every CTA resident, so the CTAs can meet at a grid barrier
+// between the two half sweeps of a sweep instead of ending the kernel (Sec. 3: all sites of
+// one colour are independent given the other colour; the two colours alternate). Each CTA
+// owns a fixed share of the words of one plane for the whole launch:
+//   plane w = blockIdx.x % W, words q = q0, q0 + step, ... of each colour,
+//   q0 = (blockIdx.x / W) * 256 + threadIdx.x, step = (gridDim.x / W) * 256,
+// so the plane's thresholds stay in shared memory (read as 16-byte broadcasts) and the
+// words the thread itself wrote come back through L1; the other colour, written by other
+// CTAs, is read through L2 (ld.global.cg).
+//
+// Replica exchange (Sec. 3, Eq. 5): after the colour-1 half sweep of an exchange sweep each
+// CTA adds its plane's bond (and up-spin) counts of the new state into a count buffer; after
+// the barrier EVERY CTA computes the same swap iteration from the complete counts, on its own
+// shared-memory copy of the temperature map, and rebuilds its plane's thresholds. Only block 0
+// writes the swap statistics; the maps and the plane tables go back to global memory at the
+// end of the launch. Two count buffers alternate by swap index: block 0 clears the one of the
+// next exchange while the current one is being read.
+//
+// The barrier counter and both count buffers are cleared by the host before each launch.
+// A barrier wait that exceeds its time limit stores PT_ETIMEOUT in the status word; every
+// waiting CTA that sees a non-zero status (or runs out of time itself) leaves the kernel.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pt.h"
+#include "pt_device.cuh"
+#include "pt_persist.h"
+
+namespace ptb {
+
+namespace {
+
+constexpr uint64_t kTwo32 = 1ull << 32;
+
+struct PersistArgs {
+  DevProblem p;
+  uint64_t t0, e0;
+  int n;         // sweeps in this launch
+  int m;         // exchange after every m-th sweep (0: never)
+  int stall;     // extra arrivals the first barrier waits for (test of the bounded wait)
+  uint64_t limit_ns;
+  RoundKeys rk;  // Philox round keys of the seed (constant-bank operands)
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Every CTA arrives once; returns false when the wait gave up (time limit or a status set
+// by another CTA): the caller leaves the kernel.
+__device__ bool grid_barrier(unsigned* bar, unsigned target, int* status, uint64_t limit_ns,
+                             int* ok_s) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();  // the CTA's writes (ordered before by the block barrier) go first
+    atomicAdd(bar, 1u);
+    const uint64_t t0 = global_ns();
+    while ((int)(ld_acquire(bar) - target) < 0) {
+      if (*(volatile int*)status != 0) {
+        ok = 0;
+        break;
+      }
+      if (global_ns() - t0 > limit_ns) {
+        atomicCAS(status, 0, PT_ETIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(20);
+    }
+    __threadfence();
+    *ok_s = ok;
+  }
+  __syncthreads();
+  return *ok_s != 0;
+}
+
+// The plane's thresholds under the temperature map tos, staged in shared memory by warp 0
+// (same rule as the plane rebuild of the exchange kernel).
+template <int MODE>
+__device__ void stage_plane(const DevProblem& p, const int32_t* tos, int w, PlaneFerro& fer,
+                            PlaneGeneric& gen) {
+  if (threadIdx.x < 32) {
+    const int b = threadIdx.x, r = 32 * w + b;
+    const bool in_use = r < p.R;
+    const int temp = in_use ? tos[r] : 0;
+    const uint32_t used = __ballot_sync(0xffffffffu, in_use);
+    if (MODE == kModeFerro) {
+      const uint64_t t0 = in_use ? p.T_temp[(size_t)temp * kClasses + 1] : 0;
+      const uint64_t t1 = in_use ? p.T_temp[(size_t)temp * kClasses + 3] : 0;
+      fer.T0[b] = (uint32_t)min(t0, kTwo32 - 1);
+      fer.T1[b] = (uint32_t)min(t1, kTwo32 - 1);
+      const uint32_t a0 = __ballot_sync(0xffffffffu, in_use && t0 >= kTwo32);
+      const uint32_t a1 = __ballot_sync(0xffffffffu, in_use && t1 >= kTwo32);
+      if (b == 0) {
+        fer.alw0 = a0;
+        fer.alw1 = a1;
+        fer.used = used;
+        fer.pad = 0;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < kClasses; ++c) {
+        const uint64_t tc = in_use ? p.T_temp[(size_t)temp * kClasses + c] : 0;
+        gen.T[c][b] = (uint32_t)min(tc, kTwo32 - 1);
+        const uint32_t a = __ballot_sync(0xffffffffu, in_use && tc >= kTwo32);
+        if (b == 0) gen.alw[c] = a;
+      }
+      if (b == 0) {
+        gen.used = used;
+        gen.pad = 0;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// E_int of a slot from its counts: U unsatisfied bonds, `ones` up spins (zero in the
+// ferromagnetic zero-field case, where h_int = 0 and they are not counted).
+__device__ __forceinline__ int64_t slot_energy(const DevProblem& p, int64_t L2, int64_t U,
+                                               int64_t ones) {
+  return -p.J_int * (2 * L2 - 2 * U) + p.h_int * (2 * ones - L2);
+}
+
+// Swap iteration e on this CTA's copy of the maps (every CTA draws the same numbers and so
+// reaches the same maps); `owner` also counts attempts and acceptances.
+__device__ void exchange_local(const DevProblem& p, uint64_t e, const uint32_t* cb,
+                               int32_t* sot, int32_t* tos, bool owner) {
+  const int R = p.R, W = p.W;
+  const int64_t L2 = (int64_t)p.L * p.L;
+  const int parity = (int)(e & 1);
+  const uint32_t c3 = kTagExch | ((uint32_t)(e >> 32) << 8);
+  for (int k = parity + 2 * (int)threadIdx.x; k + 1 < R; k += 2 * (int)blockDim.x) {
+    const int a = sot[k], b = sot[k + 1];
+    const int64_t Ea = slot_energy(p, L2, __ldcg(cb + a), __ldcg(cb + W * 32 + a));
+    const int64_t Eb = slot_energy(p, L2, __ldcg(cb + b), __ldcg(cb + W * 32 + b));
+    const int64_t n = Ea - Eb;
+    const SwapPair sp = p.pairs[k];
+    uint64_t S;
+    if (n < sp.n_lo)
+      S = sp.S_below;
+    else if (n > sp.n_hi)
+      S = sp.S_above;
+    else
+      S = p.swap_table[sp.offset + (n - sp.n_lo)];
+    const Philox4 rnd = philox4x32_10((uint32_t)k, (uint32_t)e, 0u, c3, p.key0, p.key1);
+    const bool accept = (uint64_t)rnd.x < S;
+    if (owner) {
+      p.attempted[k] += 1;
+      if (accept) p.accepted[k] += 1;
+    }
+    if (accept) {
+      sot[k] = b;
+      sot[k + 1] = a;
+      tos[a] = k + 1;
+      tos[b] = k;
+    }
+  }
+  __syncthreads();
+}
+
+// One half sweep over this thread's words of colour `colour` of plane w. With COUNT, the
+// new colour-1 words' anti-aligned neighbours (every bond has exactly one colour-1 end) and,
+// in the generic case, the up spins of the colour-1 word and of the colour-0 word one row up
+// (a one-to-one pairing of the colours) are added to U / N.
+template <int MODE, bool COUNT>
+__device__ __forceinline__ void half_pass(const DevProblem& p, int w, int colour, uint64_t t,
+                                          const RoundKeys& rk, int q0, int step, int y0,
+                                          int i0, int dy, int di, const uint4* thr,
+                                          uint32_t alw0, uint32_t alw1, uint32_t used,
+                                          const PlaneGeneric& gen, BitCounter<15, 10>& U,
+                                          BitCounter<15, 10>& N) {
+  const uint32_t t_lo = (uint32_t)t, c3 = kTagSpin | ((uint32_t)(t >> 32) << 8);
+  const uint32_t blk0 = (uint32_t)(8 * w);
+  const int L = p.L, half = L >> 1;
+  const int nwords = L * half;
+  const int nblk = (min(32, p.R - 32 * w) + 3) >> 2;
+  uint32_t* own = p.spins + word_index(L, w, colour, 0, 0);
+  const uint32_t* oth = p.spins + word_index(L, w, colour ^ 1, 0, 0);
+  int y = y0, i = i0;
+  for (int q = q0; q < nwords; q += step) {
+    const int par = (y + colour) & 1;
+    const int ym = (y == 0) ? L - 1 : y - 1;
+    const int yp = (y == L - 1) ? 0 : y + 1;
+    const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
+    const uint32_t s = own[q];
+    const uint32_t n0 = __ldcg(oth + ym * half + i);
+    const uint32_t n1 = __ldcg(oth + yp * half + i);
+    const uint32_t n2 = __ldcg(oth + q);
+    const uint32_t n3 = __ldcg(oth + y * half + ih);
+    const uint32_t site = (uint32_t)(y * L + 2 * i + par);
+    uint32_t ns;
+    if (MODE == kModeFerro)
+      ns = update_word_ferro_smem(s, n0, n1, n2, n3, site, blk0, nblk, thr, alw0, alw1, used,
+                                  t_lo, c3, rk);
+    else
+      ns = update_word_generic_with(s, n0, n1, n2, n3, nblk, gen, [&](int j) {
+        return philox4x32_10_rk(site, t_lo, blk0 + (uint32_t)j, c3, rk);
+      });
+    own[q] = ns;
+    if (COUNT) {
+      const NbCount k = count4(ns ^ n0, ns ^ n1, ns ^ n2, ns ^ n3);
+      U.add3(k.b0, k.b1, k.b2);
+      if (MODE != kModeFerro) N.add2(ns ^ n0, ns & n0);
+    }
+    i += di;
+    y += dy;
+    if (i >= half) {
+      i -= half;
+      y += 1;
+    }
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_constant__ PersistArgs a) {
+  extern __shared__ int32_t map_s[];  // [R] slot_of_temp, then [R] temp_of_slot
+  __shared__ PlaneFerro fer;
+  __shared__ uint4 thr[16];  // ferro thresholds, interleaved for 16-byte broadcast loads
+  __shared__ PlaneGeneric gen;
+  __shared__ uint32_t acc[2][32];
+  __shared__ int ok_s;
+  const DevProblem& p = a.p;
+  const int R = p.R, W = p.W;
+  int32_t* sot = map_s;
+  int32_t* tos = map_s + R;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    sot[r] = p.slot_of_temp[r];
+    tos[r] = p.temp_of_slot[r];
+  }
+  __syncthreads();
+
+  const int w = blockIdx.x % W;
+  const int q0 = (blockIdx.x / W) * kPersistThreads + threadIdx.x;
+  const int step = (gridDim.x / W) * kPersistThreads;
+  const int half = p.L >> 1;
+  const int y0 = q0 / half, i0 = q0 - y0 * half;
+  const int dy = step / half, di = step - dy * half;
+  uint32_t* const cnt_base = p.cnt + 2 * W * 32;  // two buffers of [2][W * 32]
+  unsigned* const bar = p.cnt + 6 * W * 32;
+
+  uint32_t alw0 = 0, alw1 = 0, used = 0;
+  auto load_plane = [&]() {
+    stage_plane<MODE>(p, tos, w, fer, gen);
+    if (MODE == kModeFerro) {
+      if (threadIdx.x < 16) {
+        const int b = 2 * threadIdx.x;
+        thr[threadIdx.x] = make_uint4(fer.T0[b], fer.T1[b], fer.T0[b + 1], fer.T1[b + 1]);
+      }
+      alw0 = fer.alw0;
+      alw1 = fer.alw1;
+      used = fer.used;
+      __syncthreads();
+    }
+  };
+  load_plane();
+
+  unsigned target = 0;
+  uint64_t e = a.e0;
+  bool exchanged = false;
+  for (int j = 0; j < a.n; ++j) {
+    const uint64_t t = a.t0 + (uint64_t)j;
+    BitCounter<15, 10> U, N;
+    half_pass<MODE, false>(p, w, 0, t, a.rk, q0, step, y0, i0, dy, di, thr, alw0, alw1,
+                           used, gen, U, N);
+    target += gridDim.x + (j == 0 ? (unsigned)a.stall : 0u);
+    if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s)) return;
+    const bool ex = a.m > 0 && (t + 1) % (uint64_t)a.m == 0;
+    if (!ex) {
+      half_pass<MODE, false>(p, w, 1, t, a.rk, q0, step, y0, i0, dy, di, thr, alw0, alw1,
+                             used, gen, U, N);
+      if (j + 1 == a.n) break;  // the kernel's end orders this half sweep before what follows
+      target += gridDim.x;
+      if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s)) return;
+      continue;
+    }
+    uint32_t* const cb = cnt_base + (e & 1) * 2 * W * 32;
+    U.zero();
+    N.zero();
+    half_pass<MODE, true>(p, w, 1, t, a.rk, q0, step, y0, i0, dy, di, thr, alw0, alw1,
+                          used, gen, U, N);
+    const uint32_t u = U.warp_total_for_lane();
+    const uint32_t nn = MODE == kModeFerro ? 0u : N.warp_total_for_lane();
+    if (threadIdx.x < 64) (&acc[0][0])[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    if (u) atomicAdd(&acc[0][lane], u);
+    if (nn) atomicAdd(&acc[1][lane], nn);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      if (acc[0][threadIdx.x]) atomicAdd(&cb[w * 32 + threadIdx.x], acc[0][threadIdx.x]);
+      if (acc[1][threadIdx.x]) atomicAdd(&cb[W * 32 + w * 32 + threadIdx.x], acc[1][threadIdx.x]);
+    }
+    target += gridDim.x;
+    if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s)) return;
+    exchange_local(p, e, cb, sot, tos, blockIdx.x == 0);
+    if (blockIdx.x == 0) {
+      // the other buffer was last read in the previous swap iteration, before this sweep's
+      // first barrier; it is next written after the next sweep's first barrier
+      uint32_t* const nb = cnt_base + ((e + 1) & 1) * 2 * W * 32;
+      for (int q = threadIdx.x; q < 2 * W * 32; q += blockDim.x) nb[q] = 0;
+    }
+    load_plane();
+    e += 1;
+    exchanged = true;
+  }
+
+  if (exchanged) {
+    if (blockIdx.x == 0)
+      for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        p.slot_of_temp[r] = sot[r];
+        p.temp_of_slot[r] = tos[r];
+      }
+    if (blockIdx.x < W) {  // one CTA per plane writes the plane's table back
+      if (MODE == kModeFerro) {
+        PlaneFerro* dst = reinterpret_cast<PlaneFerro*>(p.planes) + w;
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(&fer);
+        for (int q = threadIdx.x; q < (int)(sizeof(PlaneFerro) / 4); q += blockDim.x)
+          reinterpret_cast<uint32_t*>(dst)[q] = src[q];
+      } else {
+        PlaneGeneric* dst = reinterpret_cast<PlaneGeneric*>(p.planes) + w;
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(&gen);
+        for (int q = threadIdx.x; q < (int)(sizeof(PlaneGeneric) / 4); q += blockDim.x)
+          reinterpret_cast<uint32_t*>(dst)[q] = src[q];
+      }
+    }
+  }
+}
+
+const void* persist_fn(int mode) {
+  return mode == kModeFerro ? (const void*)k_persist<kModeFerro>
+                            : (const void*)k_persist<kModeGeneric>;
+}
+
+}  // namespace
+
+size_t persist_smem(int R) { return (size_t)2 * R * sizeof(int32_t); }
+
+cudaError_t persist_plan(const DevProblem& p, const DeviceInfo& dev, int words_per_thread,
+                         PersistPlan* plan) {
+  plan->grid = 0;
+  plan->words_per_thread = 0;
+  int per_sm = 0;
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, persist_fn(p.mode), kPersistThreads, persist_smem(p.R));
+  if (err != cudaSuccess) return err;
+  const int64_t planes_fit = (int64_t)per_sm * dev.sms / p.W;  // CTAs per plane at most
+  if (planes_fit < 1) return cudaSuccess;
+  const int64_t words = (int64_t)p.L * (p.L / 2);  // per colour and plane
+  const int64_t per_cta = (int64_t)words_per_thread * kPersistThreads;
+  int64_t g = (words + per_cta - 1) / per_cta;
+  if (g > planes_fit) g = planes_fit;
+  if (g < 1) g = 1;
+  const int64_t wpt = (words + g * kPersistThreads - 1) / (g * kPersistThreads);
+  if (wpt > kPersistMaxWordsPerThread) return cudaSuccess;
+  plan->grid = (int)(g * p.W);
+  plan->words_per_thread = (int)wpt;
+  return cudaSuccess;
+}
+
+cudaError_t launch_persist(const DevProblem& p, const PersistPlan& plan, uint64_t t0,
+                           uint64_t e0, int n, int m, int stall, uint64_t limit_ns,
+                           cudaStream_t st) {
+  // the two count buffers and the barrier counter follow the per-launch kernels' counts
+  cudaError_t err = cudaMemsetAsync(p.cnt + 2 * p.W * 32, 0, persist_clear_bytes(p.W), st);
+  if (err != cudaSuccess) return err;
+  PersistArgs a;
+  a.p = p;
+  a.t0 = t0;
+  a.e0 = e0;
+  a.n = n;
+  a.m = m;
+  a.stall = stall;
+  a.limit_ns = limit_ns;
+  for (int r = 0; r < 10; ++r) {
+    a.rk.k0[r] = p.key0 + (uint32_t)r * kPhiloxW0;
+    a.rk.k1[r] = p.key1 + (uint32_t)r * kPhiloxW1;
+  }
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel(persist_fn(p.mode), dim3(plan.grid), dim3(kPersistThreads),
+                                     args, persist_smem(p.R), st);
+}
+
+}  // namespace ptb

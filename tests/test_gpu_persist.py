@@ -1,0 +1,172 @@
+"""The two ways pt_sweep runs one problem -- one launch per half sweep, or one persistent
+cooperative launch whose CTAs meet at grid barriers -- against the CPU oracle, bit for bit,
+on grids of one CTA, several CTAs per plane, several planes with a ragged last plane, and
+ragged word shares; switching between them (and the batched path) mid-run; more sweeps than
+one persistent launch takes; and the bounded barrier wait, made to run out on purpose by
+waiting for CTAs that do not exist."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_03825_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+AUTO, LAUNCHES, PERSISTENT = 0, 1, 2
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2512_03825_b300 import build as B
+    B.build()
+    from paper_2512_03825_b300 import api as A
+    oracle.set_threads(8)
+    return A
+
+
+def assert_same(g, o, where=""):
+    np.testing.assert_array_equal(g.chain_map(), o.chain_map(), err_msg=where + " chain map")
+    np.testing.assert_array_equal(g.energies_int(), o.energies_int(), err_msg=where + " E")
+    np.testing.assert_array_equal(g.magnetisations(), o.magnetisations(), err_msg=where + " M")
+    for k in range(o.R):
+        np.testing.assert_array_equal(g.spins(k), o.spins(k), err_msg=where + " spins %d" % k)
+    for a, b in zip(g.swap_stats(), o.swap_stats()):
+        np.testing.assert_array_equal(a, b, err_msg=where + " swap stats")
+    assert g.counters() == o.counters(), where
+
+
+def make(api, prob, strategy, wpt=0):
+    g = api.PTProblem(prob.L, prob.betas, J=prob.J, h=prob.h, seed=prob.seed)
+    g.set_sweep_tuning(strategy, wpt)
+    o = oracle.OracleProblem(prob.L, prob.betas, J=prob.J, h=prob.h, seed=prob.seed)
+    return g, o
+
+
+CASES = [
+    # (L, R, J, h, words per thread, sweeps, exchange_every)
+    (4, 1, 1.0, 0.0, 0, 25, 1),        # smallest lattice, one replica, one CTA
+    (6, 3, 1.0, 0.0, 1, 30, 1),        # L/2 odd
+    (16, 8, 1.0, 0.0, 1, 40, 3),
+    (30, 5, -1.0, 0.25, 2, 30, 2),     # generic mode (antiferromagnet in a field)
+    (64, 33, 1.0, 0.0, 1, 24, 1),      # two planes, the second with one slot
+    (64, 70, 1.0, 0.1, 3, 20, 4),      # three planes, generic, ragged shares
+    (130, 40, 0.5, 0.0, 7, 12, 5),     # s = 2, ragged shares
+    (128, 32, 1.0, 0.0, 0, 15, 0),     # no exchanges
+]
+
+
+@pytest.mark.parametrize("strategy", [LAUNCHES, PERSISTENT])
+@pytest.mark.parametrize("L,R,J,h,wpt,n,m", CASES)
+def test_strategy_matches_oracle(api, strategy, L, R, J, h, wpt, n, m):
+    prob = W.Problem(L=L, betas=W.linear_ladder(0.2, 0.7, R), J=J, h=h,
+                     seed=0x9E00 + 7 * L + R)
+    g, o = make(api, prob, strategy, wpt)
+    s, w, grid = g.sweep_tuning()
+    assert s == strategy
+    if strategy == PERSISTENT:
+        W_planes = (R + 31) // 32
+        assert grid > 0 and grid % W_planes == 0
+    for k in (1, n - 1):                # two calls: the state carries over between launches
+        g.sweep(k, m)
+        o.sweep(k, m)
+    assert_same(g, o, "L%d R%d strategy %d" % (L, R, strategy))
+
+
+def test_grid_follows_words_per_thread(api):
+    prob = W.Problem(L=256, betas=W.linear_ladder(0.3, 0.6, 64), seed=5)
+    g = api.PTProblem(prob.L, prob.betas, seed=prob.seed)
+    grids = []
+    for wpt in (1, 4, 16, 64, 255):
+        g.set_sweep_tuning(PERSISTENT, wpt)
+        grids.append(g.sweep_tuning()[2])
+    words = 256 * 128
+    assert all(x % 2 == 0 for x in grids)
+    assert grids == sorted(grids, reverse=True)
+    assert grids[-1] == 2 and grids[3] == 2 * words // (64 * 256)
+
+
+def test_switching_strategies_mid_run(api):
+    """Launches, persistent, batched and persistent again, one after the other on one
+    problem, equal the oracle: each path leaves the maps, thresholds and counts as the next
+    one expects."""
+    prob = W.Problem(L=96, betas=W.linear_ladder(0.25, 0.65, 48), J=1.0, h=0.0, seed=77)
+    g, o = make(api, prob, LAUNCHES)
+    g.sweep(7, 2)
+    o.sweep(7, 2)
+    g.set_sweep_tuning(PERSISTENT, 1)
+    g.sweep(9, 2)
+    o.sweep(9, 2)
+    assert_same(g, o, "launches then persistent")
+    api.sweep_batch([g], 5, 2)
+    o.sweep(5, 2)
+    g.sweep(6, 3)
+    o.sweep(6, 3)
+    assert_same(g, o, "then batched, then persistent")
+    g.set_sweep_tuning(LAUNCHES)
+    g.sweep(4, 3)
+    o.sweep(4, 3)
+    assert_same(g, o, "then launches again")
+
+
+def test_more_sweeps_than_one_launch(api):
+    """70000 sweeps is two persistent launches (65536 + 4464)."""
+    prob = W.Problem(L=4, betas=(0.3, 0.45, 0.6), seed=123)
+    g, o = make(api, prob, PERSISTENT)
+    g.sweep(70000, 7)
+    o.sweep(70000, 7)
+    assert_same(g, o, "70000 sweeps")
+
+
+def test_persistent_equals_launches_at_L512(api):
+    prob = W.Problem(L=512, betas=W.linear_ladder(0.35, 0.5, 64), seed=0x5EED0042)
+    a = api.PTProblem(prob.L, prob.betas, seed=prob.seed)
+    b = api.PTProblem(prob.L, prob.betas, seed=prob.seed)
+    a.set_sweep_tuning(LAUNCHES)
+    b.set_sweep_tuning(PERSISTENT)
+    a.sweep(40, 5)
+    b.sweep(40, 5)
+    np.testing.assert_array_equal(a.chain_map(), b.chain_map())
+    np.testing.assert_array_equal(a.energies_int(), b.energies_int())
+    for x, y in zip(a.swap_stats(), b.swap_stats()):
+        np.testing.assert_array_equal(x, y)
+    for k in range(0, 64, 9):
+        np.testing.assert_array_equal(a.spins(k), b.spins(k))
+
+
+def test_tuning_arguments_checked(api):
+    from paper_2512_03825_b300 import _lib
+    g = api.PTProblem(8, [0.3])
+    for call in (lambda: g.set_sweep_tuning(3), lambda: g.set_sweep_tuning(PERSISTENT, 256),
+                 lambda: g.set_sweep_tuning(PERSISTENT, -1), lambda: g.set_wait_limit(0.0),
+                 lambda: g.set_wait_limit(61.0), lambda: g.debug_stall_barrier(-1)):
+        with pytest.raises(_lib.PTError) as ei:
+            call()
+        assert ei.value.code == _lib.PT_EINVAL
+    g.sweep(3, 1)                       # nothing above changed the problem
+    g.synchronize()
+
+
+def test_barrier_wait_runs_out_and_context_survives(api):
+    """The first grid barrier waits for one CTA more than the launch has: every wait gives
+    up after the 50 ms limit, the problem reports PT_ETIMEOUT and stays poisoned, and a new
+    problem on the same context still matches the oracle."""
+    from paper_2512_03825_b300 import _lib
+    prob = W.Problem(L=64, betas=W.linear_ladder(0.3, 0.5, 40), seed=9)
+    g = api.PTProblem(prob.L, prob.betas, seed=prob.seed)
+    g.set_sweep_tuning(PERSISTENT, 1)
+    g.set_wait_limit(0.05)
+    g.debug_stall_barrier(1)
+    g.sweep(3, 1)
+    with pytest.raises(_lib.PTError) as ei:
+        g.synchronize()
+    assert ei.value.code == _lib.PT_ETIMEOUT
+    with pytest.raises(_lib.PTError) as ei:
+        g.sweep(1, 1)
+    assert ei.value.code in (_lib.PT_ETIMEOUT, _lib.PT_ESTATE)
+    g.close()
+    h, o = make(api, prob, PERSISTENT, 1)
+    h.sweep(12, 1)
+    o.sweep(12, 1)
+    assert_same(h, o, "after a timed-out launch")
