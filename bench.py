@@ -36,10 +36,10 @@ IMUL_WIDE_PER_CLK_SM = 32.0  # 32x32->64 integer products per clock per SM (4 SM
 # DRAM traffic of one k_flat_half launch (colour 0) on the batched-256 workload from the ncu
 # capture summarised in profiles/k_flat_half_batched-256.md (cold caches: one read of the
 # whole state). Valid only for the kernel source it was taken on.
-FLAT_TRAFFIC_BYTES = 25.937152e6 + 41.728e3
+FLAT_TRAFFIC_BYTES = 25.933824e6 + 0.0
 FLAT_TRAFFIC_SOURCES = ("paper_2512_03825_b300/csrc/pt_device.cuh",
                         "paper_2512_03825_b300/csrc/pt_flat.cu")
-FLAT_TRAFFIC_SOURCE_HASH = "6335ed12aa33494a"
+FLAT_TRAFFIC_SOURCE_HASH = "78ea9616e87016b6"
 
 
 def _flat_traffic():
@@ -284,20 +284,26 @@ def run_ours(args, rank, world, local):
     flat = tuning.get("strategy", 0) == 0
     if flat:
         # the dominant kernel on its own: a batch without exchanges is nothing but
-        # k_flat_half launches (two per sweep), timed on the problems' stream
-        nsw = 50
+        # k_flat_half launches (two per sweep), timed on the problems' stream. Two batch
+        # lengths, so that the per-call host work (tile dealing, list upload) cancels in
+        # the difference.
+        lens = (100, 500)
+        took = []
         with torch.cuda.stream(stream):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            api.sweep_batch(handles, nsw, 0)
-            b.record(stream)
-            torch.cuda.synchronize()
-        launch_s = a.elapsed_time(b) / 1e3 / (2 * nsw)
+            for nsw in lens:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                api.sweep_batch(handles, nsw, 0)
+                b.record(stream)
+                torch.cuda.synchronize()
+                took.append(a.elapsed_time(b) / 1e3)
+        launch_s = (took[1] - took[0]) / (2 * (lens[1] - lens[0]))
         per_launch_mul = MUL_PER_ATTEMPT * per_step / args.sweeps / 2
         achieved_mul = per_launch_mul / launch_s
-        how = ("k_flat_half: algorithmic products of one half sweep of all 256 problems (5 per "
-               "attempt) / its average launch duration over %d launches (CUDA events)"
-               % (2 * nsw))
+        how = ("k_flat_half: algorithmic products of one half sweep of all %d problems (5 per "
+               "attempt) / its average launch duration, (t(%d sweeps) - t(%d sweeps)) / %d "
+               "launches (CUDA events)" % (len(probs), lens[1], lens[0],
+                                          2 * (lens[1] - lens[0])))
         traffic = _flat_traffic()
     else:
         achieved_mul = MUL_PER_ATTEMPT * per_step / (statistics.mean(kernel_ms) / 1e3)
