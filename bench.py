@@ -36,10 +36,11 @@ IMUL_WIDE_PER_CLK_SM = 32.0  # 32x32->64 integer products per clock per SM (4 SM
 # DRAM traffic of one k_flat_half launch (colour 0) on the batched-256 workload from the ncu
 # capture summarised in profiles/k_flat_half_batched-256.md (cold caches: one read of the
 # whole state). Valid only for the kernel source it was taken on.
-FLAT_TRAFFIC_BYTES = 25.933824e6 + 0.0
+FLAT_TRAFFIC_BYTES = 25.938176e6 + 7.680e3
 FLAT_TRAFFIC_SOURCES = ("paper_2512_03825_b300/csrc/pt_device.cuh",
+                        "paper_2512_03825_b300/csrc/pt_flat.cuh",
                         "paper_2512_03825_b300/csrc/pt_flat.cu")
-FLAT_TRAFFIC_SOURCE_HASH = "78ea9616e87016b6"
+FLAT_TRAFFIC_SOURCE_HASH = "544dd6d3ff97a650"
 
 
 def _flat_traffic():
@@ -337,9 +338,13 @@ def run_ours(args, rank, world, local):
 def launches_per_batch(probs, sweeps, tuning):
     """Kernel launches of one pt_sweep_batch call: the lock-step strategy launches two
     half sweeps per sweep plus one exchange launch after every sweep with an exchange (one
-    mode here: h = 0); the cluster strategy is one persistent launch plus a helper."""
-    if tuning.get("strategy", 0) == 0:
+    mode here: h = 0); the dataflow strategy is one cooperative launch per mode; the
+    cluster strategy is one persistent launch plus a helper."""
+    strategy = tuning.get("strategy", 0)
+    if strategy == 0:
         return sweeps * 3
+    if strategy == 2:
+        return len({p.h == 0.0 and p.J > 0 for p in probs})
     return 2
 
 
@@ -355,26 +360,34 @@ def bench_serve_short(stream, nreq):
 
 
 def bench_plain_sample(probs, stream, n_problems=32, sweeps=200):
-    """The plain one-problem-per-launch path on a sample of the same problem mix."""
+    """The plain path -- one problem at a time through pt_sweep -- on a sample of the same
+    problem mix, in both of its strategies: one persistent launch per call (the default)
+    and one launch per half sweep plus the exchange launches."""
     import torch
     from paper_2512_03825_b300 import api
     sample = probs[:: max(1, len(probs) // n_problems)][:n_problems]
-    hs = [api.PTProblem(p.L, p.betas, seed=p.seed, stream=stream) for p in sample]
-    for h in hs:
-        h.sweep(5, 1)
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for h in hs:
-        h.sweep(sweeps, 1)
-    b.record(stream)
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b)
-    for h in hs:
-        h.close()
     att = _attempts(sample, sweeps)
-    return {"value": att / (ms / 1e3), "unit": UNIT, "problems": len(sample),
-            "sweeps": sweeps, "launches": len(sample) * sweeps * 4}
+    out = {}
+    for name, strategy in (("persistent", 2), ("launches", 1)):
+        hs = [api.PTProblem(p.L, p.betas, seed=p.seed, stream=stream) for p in sample]
+        for h in hs:
+            h.set_sweep_tuning(strategy)
+            h.sweep(5, 1)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for h in hs:
+            h.sweep(sweeps, 1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        for h in hs:
+            h.close()
+        out[name] = {"value": att / (ms / 1e3),
+                     "launches": len(sample) * (1 if strategy == 2 else sweeps * 4)}
+    return {"value": out["persistent"]["value"], "unit": UNIT, "problems": len(sample),
+            "sweeps": sweeps, "launches": out["persistent"]["launches"],
+            "launches_strategy": out["launches"]}
 
 
 def bench_single(stream, sms, clock_mhz, sweeps=200):

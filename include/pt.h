@@ -127,8 +127,9 @@ int pt_set_wait_limit(pt_problem* p, double seconds);
 
 /* Test support for the bounded wait; the paper has no counterpart. The next persistent launch
  * of this problem waits at its first grid barrier for `arrivals` (>= 0) more CTAs than it
- * has, so that every wait runs out after the wait limit and the launch ends with
- * PT_ETIMEOUT as described above. Applies to one launch. */
+ * has (in a PT_BATCH_FLOW batch: its first colour-1 wait expects that many more tiles), so
+ * that the wait runs out after the wait limit and the launch ends with PT_ETIMEOUT as
+ * described above. Applies to one launch. */
 int pt_debug_stall_barrier(pt_problem* p, int arrivals);
 
 /* Advance `count` problems together in one persistent kernel: problem j runs n[j] >= 0
@@ -165,14 +166,22 @@ int pt_sweep_batch_static(pt_problem* const* problems, int count, const int64_t*
 /* How pt_sweep_batch runs (chosen by the autotuner; results never depend on it):
  *   PT_BATCH_FLAT    -- all problems advance sweep by sweep together; every half sweep is
  *                       one launch over equal-sized word tiles of all problems, followed by
- *                       an energy-count and an exchange launch when any problem is due;
+ *                       an exchange launch when any problem is due;
  *   PT_BATCH_CLUSTER -- one persistent kernel; a problem with L >= joint_min_L runs on a
  *                       whole thread-block cluster of `cluster` CTAs (1 to 16) for all of its
- *                       sweeps, smaller ones on a single CTA.
+ *                       sweeps, smaller ones on a single CTA;
+ *   PT_BATCH_FLOW    -- the tiles of PT_BATCH_FLAT in one cooperative launch per call (one
+ *                       per mode: J, h with h = 0 and J > 0, and the rest), whose warps run
+ *                       all sweeps and order each problem's half sweeps and swap iterations
+ *                       by per-problem counters instead of launches. Each wait is bounded by
+ *                       the problem's wait limit (pt_set_wait_limit); a wait that runs out
+ *                       marks every problem of the call PT_ETIMEOUT, reported by the next
+ *                       pt_synchronize or getter. pt_debug_stall_barrier applies to it too.
  * Applies to later batches of every problem. PT_EINVAL for an unknown strategy, cluster
  * outside 1..16 or joint_min_L < 4. */
 #define PT_BATCH_FLAT 0
 #define PT_BATCH_CLUSTER 1
+#define PT_BATCH_FLOW 2
 int pt_set_batch_tuning(int strategy, int cluster, int joint_min_L);
 int pt_get_batch_tuning(int* strategy, int* cluster, int* joint_min_L);
 

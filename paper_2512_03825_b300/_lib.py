@@ -22,6 +22,7 @@ PT_ENODEV = -6
 PT_EINTERNAL = -7
 PT_BATCH_FLAT = 0
 PT_BATCH_CLUSTER = 1
+PT_BATCH_FLOW = 2
 PT_SWEEP_AUTO = 0
 PT_SWEEP_LAUNCHES = 1
 PT_SWEEP_PERSISTENT = 2

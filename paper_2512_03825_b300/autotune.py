@@ -1,8 +1,9 @@
 """Autotuner for the batched kernel's launch shape.
 
-Knobs: the batched strategy (lock-step tiles, or one persistent cluster kernel), and for
-the cluster kernel the CTAs per thread-block cluster and the lattice size from which a
-problem is spread over a whole cluster instead of one CTA. They change only how work is
+Knobs: the batched strategy (lock-step tiles, the same tiles in one dataflow launch, or
+one persistent cluster kernel), and for the cluster kernel the CTAs per thread-block
+cluster and the lattice size from which a problem is spread over a whole cluster instead
+of one CTA. They change only how work is
 distributed, never a result: `tune` checks that every candidate leaves every problem in the
 same state (spins, temperature map, swap counters) before it compares times.
 
@@ -20,10 +21,10 @@ from ._lib import check, lib
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "autotune_cache.json")
-FLAT, CLUSTER = 0, 1
+FLAT, CLUSTER, FLOW = 0, 1, 2
 DEFAULT = {"strategy": FLAT, "cluster": 4, "joint_min_L": 128}
 CANDIDATES: Tuple[Tuple[int, int, int], ...] = (
-    (FLAT, 1, 128), (CLUSTER, 1, 1 << 20), (CLUSTER, 2, 128), (CLUSTER, 3, 128),
+    (FLAT, 1, 128), (FLOW, 1, 128), (CLUSTER, 1, 1 << 20), (CLUSTER, 2, 128), (CLUSTER, 3, 128),
     (CLUSTER, 4, 256), (CLUSTER, 4, 128), (CLUSTER, 4, 96), (CLUSTER, 6, 128),
     (CLUSTER, 8, 128))
 

@@ -513,8 +513,9 @@ int sweep_batch(pt_problem* const* ps, int count, const int64_t* n, const int* e
   if (rc) return rc;
   const DeviceInfo& di = ps[0]->dev_info;
   const BatchTuning tune = g_batch_tuning;
-  if (tune.strategy == PT_BATCH_FLAT) {
-    rc = sweep_batch_flat(ps, count, n, every, st, di);
+  if (tune.strategy == PT_BATCH_FLAT || tune.strategy == PT_BATCH_FLOW) {
+    rc = tune.strategy == PT_BATCH_FLAT ? sweep_batch_flat(ps, count, n, every, st, di)
+                                        : sweep_batch_flow(ps, count, n, every, st, di);
     if (rc) return rc;
     advance_counters(ps, count, n, every);
     return PT_OK;

@@ -7,21 +7,25 @@
 #include "pt.h"
 
 namespace ptb {
-// Batched path: strategy PT_BATCH_FLAT (lock-step tiles, pt_flat.cu) or PT_BATCH_CLUSTER (one
-// persistent kernel, pt_batch.cu). For the latter, cluster = CTAs per cluster (1 = no
+// Batched path: strategy PT_BATCH_FLAT (lock-step tiles, pt_flat.cu), PT_BATCH_FLOW (the same
+// tiles in one persistent dataflow launch, pt_flow.cu) or PT_BATCH_CLUSTER (one persistent
+// kernel of whole problems, pt_batch.cu). For the last, cluster = CTAs per cluster (1 = no
 // clusters); problems with L >= joint_min_L are spread over a whole cluster, smaller ones run
 // on one CTA.
 struct BatchTuning {
   int strategy = PT_BATCH_FLAT;
   int cluster = 4;
   int joint_min_L = 128;
-  int fuse_exchange = 0;  // lock-step: exchange in the colour-1 launch (1) or its own (0)
 };
 extern BatchTuning g_batch_tuning;
 
 struct DeviceInfo;
 // The lock-step path (pt_flat.cu); problems are already checked.
 int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const int* every,
+                     cudaStream_t st, const DeviceInfo& di);
+
+// The dataflow path (pt_flow.cu); problems are already checked.
+int sweep_batch_flow(pt_problem* const* ps, int count, const int64_t* n, const int* every,
                      cudaStream_t st, const DeviceInfo& di);
 
 // The allocation-free variant of the lock-step path (pt_flat.cu); problems are checked.

@@ -302,6 +302,49 @@ struct BitCounter {
 };
 
 // ---------------------------------------------------------------------------------------
+// Waiting inside persistent kernels: an acquire load of a counter and the global nanosecond
+// timer that bounds every wait.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Polling a counter with a relaxed load leaves the SM's L1 alone; the one acquire (load or
+// fence) after the wait is what orders the reads that follow it.
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+// Release-ordered add: every write of this thread (and, after a warp or block barrier, of
+// the threads it synchronised with) is visible to whoever acquires the new value.
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned atom_release_add_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.release.gpu.global.add.u32 %0, [%1], %2;"
+               : "=r"(old)
+               : "l"(p), "r"(v)
+               : "memory");
+  return old;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---------------------------------------------------------------------------------------
 // Word addressing
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ size_t word_index(int L, int w, int c, int y, int i) {

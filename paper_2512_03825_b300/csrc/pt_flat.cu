@@ -1,9 +1,8 @@
 // pt_flat.cu -- the lock-step batched path: all problems of a batch advance sweep by sweep
 // together. Each half sweep is one launch over a list of equal-sized word tiles drawn from
 // every problem and plane, so the work is balanced across the SMs however uneven L and R
-// are; the energy count and the exchange step of every problem due for one are one launch
-// each. Kernel boundaries order the steps: nothing waits on a flag.
-#include <cuda/atomic>
+// are; the exchange step of every problem due for one is one more launch. Kernel
+// boundaries order the steps: nothing waits on a flag.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -15,6 +14,7 @@
 
 #include "pt_batch.h"
 #include "pt_device.cuh"
+#include "pt_flat.cuh"
 #include "pt_internal.h"
 #include "pt_launch.h"
 
@@ -22,270 +22,28 @@ namespace ptb {
 
 namespace {
 
-constexpr int kFlatThreads = 256;
-constexpr int kTileWords = 512;  // target words per warp tile (16 per lane)
-
-struct FlatProblem {
-  DevProblem p;
-  uint64_t t0, e0;  // counters when the batch starts
-  int64_t n;        // sweeps in this batch
-  int m;            // exchange every m sweeps (0 = never)
-  int ntiles;       // work tiles of this problem (used by the fused exchange)
-};
-
-// A warp's unit of work: words [q0, q1) of one colour of plane w of one problem
-// (q = y * L/2 + i). Tiles never straddle planes, so a warp's thresholds are uniform.
-struct Tile {
-  int prob;
-  int w;
-  int q0, q1;
-};
-
-// Does problem fp run sweep j of this batch, and does an exchange follow it?
-__device__ __forceinline__ bool runs(const FlatProblem& fp, int64_t j) { return j < fp.n; }
-__device__ __forceinline__ bool exchanges_after(const FlatProblem& fp, int64_t j) {
-  return j < fp.n && fp.m > 0 && (fp.t0 + (uint64_t)j + 1) % (uint64_t)fp.m == 0;
-}
-// swap iteration index used after sweep j (valid when exchanges_after)
-__device__ __forceinline__ uint64_t exchange_index(const FlatProblem& fp, int64_t j) {
-  const uint64_t m = (uint64_t)fp.m;
-  return fp.e0 + (fp.t0 + (uint64_t)j + 1) / m - fp.t0 / m - 1;
-}
-
 // ---------------------------------------------------------------------------------------
-// Exchange step of one problem by one warp (the same three parts as k_exchange): energies
-// from the counts (then cleared), the swap iteration, and the plane thresholds for the new
-// slot -> temperature map.
+// Half sweep over all warp tiles; tiles are dealt to warps by the host (longest-processing-
+// time first on their Philox work), warp g taking tiles [first[g], first[g + 1]) of the
+// list. With COUNT (colour 1 only) warps whose problem is due for an exchange after this
+// sweep also count bonds (and up spins) for it.
 // ---------------------------------------------------------------------------------------
-__device__ void exchange_warp(const DevProblem& p, uint64_t e) {
-  const int lane = threadIdx.x & 31;
-  const int R = p.R, W = p.W;
-  const int64_t L2 = (int64_t)p.L * p.L;
-  for (int r = lane; r < R; r += 32) {
-    const int64_t U = __ldcg(p.cnt + r);
-    const int64_t ones = __ldcg(p.cnt + W * 32 + r);
-    const int64_t bonds = 2 * L2 - 2 * U;
-    const int64_t M = 2 * ones - L2;
-    p.E_slot[r] = -p.J_int * bonds + p.h_int * M;
-    p.M_slot[r] = M;
-  }
-  __syncwarp();
-  for (int q = lane; q < 2 * W * 32; q += 32) p.cnt[q] = 0;
-  const int parity = (int)(e & 1);
-  const uint32_t c3 = kTagExch | ((uint32_t)(e >> 32) << 8);
-  for (int k = parity + 2 * lane; k + 1 < R; k += 64) {
-    const int a = p.slot_of_temp[k], b = p.slot_of_temp[k + 1];
-    const int64_t n = p.E_slot[a] - p.E_slot[b];
-    const SwapPair sp = p.pairs[k];
-    uint64_t S;
-    if (n < sp.n_lo)
-      S = sp.S_below;
-    else if (n > sp.n_hi)
-      S = sp.S_above;
-    else
-      S = p.swap_table[sp.offset + (n - sp.n_lo)];
-    const Philox4 rnd = philox4x32_10((uint32_t)k, (uint32_t)e, 0u, c3, p.key0, p.key1);
-    p.attempted[k] += 1;
-    if ((uint64_t)rnd.x < S) {
-      p.accepted[k] += 1;
-      p.slot_of_temp[k] = b;
-      p.slot_of_temp[k + 1] = a;
-      p.temp_of_slot[a] = k + 1;
-      p.temp_of_slot[b] = k;
-    }
-  }
-  __syncwarp();
-  constexpr uint64_t kTwo32 = 1ull << 32;
-  for (int r = lane; r < W * 32; r += 32) {
-    const int w = r >> 5, b = r & 31;
-    const bool in_use = r < R;
-    const int temp = in_use ? p.temp_of_slot[r] : 0;
-    if (p.mode == kModeFerro) {
-      PlaneFerro* pl = reinterpret_cast<PlaneFerro*>(p.planes) + w;
-      const uint64_t t0 = in_use ? p.T_temp[(size_t)temp * kClasses + 1] : 0;
-      const uint64_t t1 = in_use ? p.T_temp[(size_t)temp * kClasses + 3] : 0;
-      pl->T0[b] = (uint32_t)min(t0, kTwo32 - 1);
-      pl->T1[b] = (uint32_t)min(t1, kTwo32 - 1);
-      const uint32_t a0 = __ballot_sync(0xffffffffu, in_use && t0 >= kTwo32);
-      const uint32_t a1 = __ballot_sync(0xffffffffu, in_use && t1 >= kTwo32);
-      if (b == 0) {
-        pl->alw0 = a0;
-        pl->alw1 = a1;
-      }
-    } else {
-      PlaneGeneric* pl = reinterpret_cast<PlaneGeneric*>(p.planes) + w;
-#pragma unroll
-      for (int c = 0; c < kClasses; ++c) {
-        const uint64_t tc = in_use ? p.T_temp[(size_t)temp * kClasses + c] : 0;
-        pl->T[c][b] = (uint32_t)min(tc, kTwo32 - 1);
-        const uint32_t a = __ballot_sync(0xffffffffu, in_use && tc >= kTwo32);
-        if (b == 0) pl->alw[c] = a;
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------------------
-// half sweep over all warp tiles. With COUNT (colour 1 only), a warp whose problem is due
-// for an exchange after this sweep also counts, from the words it already holds, the
-// unsatisfied bonds of its updated sites (all four bonds of a colour-1 site; every bond has
-// exactly one colour-1 end) and the up spins of its sites and of their colour-0 neighbours
-// one row up (a one-to-one map between the colours), into the problem's counters.
-// ---------------------------------------------------------------------------------------
-// Tiles are dealt to warps by the host (longest-processing-time first on their Philox
-// work), warp g taking tiles [first[g], first[g + 1]) of the list.
-//
-// With FUSE, the exchange step of a problem is done in the same launch by the warp that
-// finishes the problem's last tile: each warp, after adding its counts, fences and takes a
-// ticket on the problem's counter `done`; the warp holding the last ticket sees every count
-// and runs the exchange (no warp waits for another). It then clears the counter.
-template <int MODE, bool COUNT, bool FUSE>
+template <int MODE, bool COUNT>
 __global__ void __launch_bounds__(kFlatThreads, 2) k_flat_half(const FlatProblem* __restrict__ probs,
                                                              const Tile* __restrict__ tiles,
                                                              const int* __restrict__ first,
-                                                             int colour, int64_t j,
-                                                             int* __restrict__ done) {
+                                                             int colour, int64_t j) {
   __shared__ PlaneGeneric gen[kFlatThreads / 32];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  __shared__ uint4 thr_s[kFlatThreads / 32][16];  // ferro thresholds of each warp's tile
+  const int wib = threadIdx.x >> 5;
   const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int tend = first[g + 1];
   for (int tix = first[g]; tix < tend; ++tix) {
     const Tile tl = tiles[tix];
     const FlatProblem& fp = probs[tl.prob];
-    const int64_t n = fp.n;
-    if (j >= n) continue;  // warp-uniform
-    const uint64_t t = fp.t0 + (uint64_t)j;
-    const DevProblem& p = fp.p;
-    const int w = tl.w;
-    const int L = p.L, half = L >> 1;
-    const int nblk = (min(32, p.R - 32 * w) + 3) >> 2;
-    const SweepCtr cx = make_sweep_ctr(t, p.key0, p.key1);
-    uint32_t* own = p.spins + word_index(L, w, colour, 0, 0);
-    const uint32_t* oth = p.spins + word_index(L, w, colour ^ 1, 0, 0);
-    const bool count = COUNT && fp.m > 0 && (t + 1) % (uint64_t)fp.m == 0;
-    const int q_start = tl.q0 + lane;
-    int y = q_start / half, i = q_start - y * half;
-    const int dy = 32 / half, di = 32 - dy * half;
-    if (MODE == kModeFerro) {
-      const PlaneFerro* pl = reinterpret_cast<const PlaneFerro*>(p.planes) + w;
-      uint32_t T0[32], T1[32];
-#pragma unroll
-      for (int b = 0; b < 32; ++b) {
-        T0[b] = pl->T0[b];
-        T1[b] = pl->T1[b];
-      }
-      const uint32_t alw0 = pl->alw0, alw1 = pl->alw1, used = pl->used;
-      BitCounter<13, 8> Uf;
-      if (COUNT) Uf.zero();
-      for (int q = q_start; q < tl.q1; q += 32) {
-        const int par = (y + colour) & 1;
-        const int ym = (y == 0) ? L - 1 : y - 1;
-        const int yp = (y == L - 1) ? 0 : y + 1;
-        const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
-        const uint32_t s = own[q];
-        const uint32_t n0 = oth[ym * half + i];
-        const uint32_t n1 = oth[yp * half + i];
-        const uint32_t n2 = oth[q];
-        const uint32_t n3 = oth[y * half + ih];
-        const uint32_t site = (uint32_t)(y * L + 2 * i + par);
-        const uint32_t ns = update_word_ferro(s, n0, n1, n2, n3, site, (uint32_t)(8 * w), nblk,
-                                              T0, T1, alw0, alw1, used, cx);
-        own[q] = ns;
-        if (COUNT && count) {
-          // with h = 0 the exchange needs only the bonds: U of the new state, all four
-          // bonds of this colour-1 site (the colour-0 neighbours are this launch's inputs)
-          const NbCount k = count4(ns ^ n0, ns ^ n1, ns ^ n2, ns ^ n3);
-          Uf.add3(k.b0, k.b1, k.b2);
-        }
-        i += di;
-        y += dy;
-        if (i >= half) {
-          i -= half;
-          y += 1;
-        }
-      }
-      if (COUNT && count) {
-        const uint32_t u = Uf.warp_total_for_lane();
-        if (u) atomicAdd(&p.cnt[w * 32 + lane], u);
-      }
-    } else {
-      // the warp's generic thresholds live in its own shared slot
-      {
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(
-            reinterpret_cast<const PlaneGeneric*>(p.planes) + w);
-        uint32_t* dst = reinterpret_cast<uint32_t*>(&gen[wib]);
-        for (int q = lane; q < (int)(sizeof(PlaneGeneric) / 4); q += 32) dst[q] = src[q];
-        __syncwarp();
-      }
-      const PlaneGeneric& pl = gen[wib];
-      for (int q = q_start; q < tl.q1; q += 32) {
-        const int par = (y + colour) & 1;
-        const int ym = (y == 0) ? L - 1 : y - 1;
-        const int yp = (y == L - 1) ? 0 : y + 1;
-        const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
-        const uint32_t s = own[q];
-        const uint32_t n0 = oth[ym * half + i];
-        const uint32_t n1 = oth[yp * half + i];
-        const uint32_t n2 = oth[q];
-        const uint32_t n3 = oth[y * half + ih];
-        const uint32_t site = (uint32_t)(y * L + 2 * i + par);
-        own[q] = update_word_generic(s, n0, n1, n2, n3, site, (uint32_t)(8 * w), nblk, pl,
-                                     cx);
-        i += di;
-        y += dy;
-        if (i >= half) {
-          i -= half;
-          y += 1;
-        }
-      }
-      __syncwarp();
-    }
-    if (COUNT && count && MODE != kModeFerro) {
-      // second pass over the words this lane just wrote (and their colour-0 neighbours,
-      // unchanged in this launch), mostly from L1
-      BitCounter<13, 8> U, N;
-      U.zero();
-      N.zero();
-      int yc = q_start / half, ic = q_start - yc * half;
-      for (int q = q_start; q < tl.q1; q += 32) {
-        const int par = (yc + colour) & 1;
-        const int ym = (yc == 0) ? L - 1 : yc - 1;
-        const int yp = (yc == L - 1) ? 0 : yc + 1;
-        const int ih = par ? ((ic + 1 == half) ? 0 : ic + 1) : ((ic == 0) ? half - 1 : ic - 1);
-        const uint32_t ns = own[q];
-        const uint32_t n0 = oth[ym * half + ic];
-        const NbCount k = count4(ns ^ n0, ns ^ oth[yp * half + ic], ns ^ oth[q],
-                                 ns ^ oth[yc * half + ih]);
-        U.add3(k.b0, k.b1, k.b2);
-        N.add2(ns ^ n0, ns & n0);
-        ic += di;
-        yc += dy;
-        if (ic >= half) {
-          ic -= half;
-          yc += 1;
-        }
-      }
-      const uint32_t u = U.warp_total_for_lane();
-      const uint32_t nn = N.warp_total_for_lane();
-      if (u) atomicAdd(&p.cnt[w * 32 + lane], u);
-      if (nn) atomicAdd(&p.cnt[p.W * 32 + w * 32 + lane], nn);
-    }
-    if (FUSE && COUNT && count) {
-      // the ticket is a release by lane 0 after the warp barrier, so it publishes every
-      // lane's counts; the warp that draws the last ticket acquires them all
-      __syncwarp();
-      int ticket = 0;
-      if (lane == 0) {
-        cuda::atomic_ref<int, cuda::thread_scope_device> d(done[tl.prob]);
-        ticket = d.fetch_add(1, cuda::memory_order_acq_rel);
-      }
-      ticket = __shfl_sync(0xffffffffu, ticket, 0);
-      if (ticket == fp.ntiles - 1) {
-        exchange_warp(p, exchange_index(fp, j));
-        __syncwarp();
-        if (lane == 0) done[tl.prob] = 0;
-      }
-    }
+    if (j >= fp.n) continue;  // warp-uniform
+    const bool count = COUNT && exchanges_after(fp, j);
+    tile_half<MODE, COUNT, false>(fp, tl, colour, j, count, thr_s[wib], &gen[wib]);
   }
 }
 
@@ -371,18 +129,16 @@ __global__ void __launch_bounds__(kFlatThreads) k_flat_exchange(const FlatProble
 
 // ---------------------------------------------------------------------------------------
 // host: one batch = per sweep j, half sweep 0 and 1 over all tiles of both modes, then the
-// count and exchange launches when any problem is due for an exchange after sweep j
+// exchange launch when any problem is due for an exchange after sweep j
 // ---------------------------------------------------------------------------------------
 // Work of a tile in Philox blocks (the dominant cost of a word).
-static int64_t tile_cost(const Tile& t, int R) {
+int64_t tile_cost(const Tile& t, int R) {
   const int slots = std::min(32, R - 32 * t.w);
   return (int64_t)((slots + 3) / 4 + 1) * (t.q1 - t.q0);
 }
 
-// Longest-processing-time-first assignment of tiles to `nwarps` warps: returns the tiles
-// reordered warp by warp and the CSR offsets first[0..nwarps].
-static void deal_tiles(const std::vector<Tile>& in, const std::vector<FlatProblem>& probs,
-                       int nwarps, std::vector<Tile>* out, std::vector<int>* first) {
+void deal_tiles(const std::vector<Tile>& in, const std::vector<FlatProblem>& probs,
+                int nwarps, std::vector<Tile>* out, std::vector<int>* first) {
   std::vector<int> order(in.size());
   for (size_t k = 0; k < in.size(); ++k) order[k] = (int)k;
   std::vector<int64_t> cost(in.size());
@@ -408,10 +164,8 @@ static void deal_tiles(const std::vector<Tile>& in, const std::vector<FlatProble
   (*first)[nwarps] = (int)out->size();
 }
 
-int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const int* every,
-                     cudaStream_t st, const DeviceInfo& di) {
-  std::vector<FlatProblem> probs;
-  std::vector<Tile> tiles[2];  // by mode
+int64_t build_flat_lists(pt_problem* const* ps, int count, const int64_t* n, const int* every,
+                         std::vector<FlatProblem>* probs, std::vector<Tile> tiles[2]) {
   int64_t n_max = 0;
   for (int j = 0; j < count; ++j) {
     if (n[j] <= 0) continue;
@@ -422,11 +176,14 @@ int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const i
     fp.e0 = p->e;
     fp.n = n[j];
     fp.m = every[j];
-    const int pi = (int)probs.size();
-    probs.push_back(fp);
-    n_max = std::max(n_max, n[j]);
+    fp.wait_ns = p->wait_limit_ns;
+    fp.stall = p->stall;
+    const int pi = (int)probs->size();
     const int words = p->L * (p->L / 2);
     const int ntile = std::max(1, (words + kTileWords / 2) / kTileWords);
+    fp.ntiles = ntile * p->W;
+    probs->push_back(fp);
+    n_max = std::max(n_max, n[j]);
     for (int w = 0; w < p->W; ++w)
       for (int k = 0; k < ntile; ++k) {
         Tile t;
@@ -437,19 +194,25 @@ int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const i
         tiles[p->mode == kModeFerro ? 0 : 1].push_back(t);
       }
   }
+  return n_max;
+}
+
+int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const int* every,
+                     cudaStream_t st, const DeviceInfo& di) {
+  std::vector<FlatProblem> probs;
+  std::vector<Tile> tiles[2];  // by mode
+  const int64_t n_max = build_flat_lists(ps, count, n, every, &probs, tiles);
   if (probs.empty()) return PT_OK;
   // one persistent wave per launch: as many CTAs as are resident at once, each warp with
   // its own share of the tiles
   int per_sm[2] = {1, 1};
   cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm[0], k_flat_half<kModeFerro, true, true>, kFlatThreads, 0);
+      &per_sm[0], k_flat_half<kModeFerro, true>, kFlatThreads, 0);
   if (err == cudaSuccess)
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm[1], k_flat_half<kModeGeneric, true, true>, kFlatThreads, 0);
+        &per_sm[1], k_flat_half<kModeGeneric, true>, kFlatThreads, 0);
   if (err != cudaSuccess) return fail(PT_ECUDA, "occupancy: %s", cudaGetErrorString(err));
   const int wpb = kFlatThreads / 32;
-  for (const auto& tv : tiles)
-    for (const Tile& t : tv) probs[t.prob].ntiles += 1;
   std::vector<Tile> dealt[2];
   std::vector<int> first[2];
   int grid[2] = {0, 0};
@@ -464,8 +227,7 @@ int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const i
   const size_t pb = probs.size() * sizeof(FlatProblem);
   const size_t tb[2] = {dealt[0].size() * sizeof(Tile), dealt[1].size() * sizeof(Tile)};
   const size_t fb[2] = {first[0].size() * sizeof(int), first[1].size() * sizeof(int)};
-  const size_t db = probs.size() * sizeof(int);
-  const size_t total = al(pb) + al(tb[0]) + al(tb[1]) + al(fb[0]) + al(fb[1]) + al(db) + 256;
+  const size_t total = al(pb) + al(tb[0]) + al(tb[1]) + al(fb[0]) + al(fb[1]) + 256;
   void* scratch = nullptr;
   err = cudaMallocAsync(&scratch, total, st);
   if (err != cudaSuccess) return fail(PT_ENOMEM, "batch scratch: %s", cudaGetErrorString(err));
@@ -482,10 +244,7 @@ int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const i
     d_first[md] = (int*)cur;
     cur += al(fb[md]);
   }
-  int* d_done = (int*)cur;
-  err = cudaMemsetAsync(d_done, 0, db, st);
-  if (err == cudaSuccess)
-    err = cudaMemcpyAsync(d_probs, probs.data(), pb, cudaMemcpyHostToDevice, st);
+  err = cudaMemcpyAsync(d_probs, probs.data(), pb, cudaMemcpyHostToDevice, st);
   for (int md = 0; md < 2 && err == cudaSuccess; ++md) {
     if (!tb[md]) continue;
     err = cudaMemcpyAsync(d_tiles[md], dealt[md].data(), tb[md], cudaMemcpyHostToDevice, st);
@@ -498,22 +257,18 @@ int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const i
     if (fp.m > 0)
       for (int64_t j = 0; j < fp.n; ++j)
         if ((fp.t0 + (uint64_t)j + 1) % (uint64_t)fp.m == 0) any_exchange[(size_t)j] = 1;
-  const bool fuse = g_batch_tuning.fuse_exchange != 0;
   const int np = (int)probs.size();
   for (int64_t j = 0; j < n_max && err == cudaSuccess; ++j) {
     const bool ex = any_exchange[(size_t)j] != 0;
-    if (grid[0]) k_flat_half<kModeFerro, false, false><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles[0], d_first[0], 0, j, d_done);
-    if (grid[1]) k_flat_half<kModeGeneric, false, false><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles[1], d_first[1], 0, j, d_done);
-    if (ex && fuse) {
-      if (grid[0]) k_flat_half<kModeFerro, true, true><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles[0], d_first[0], 1, j, d_done);
-      if (grid[1]) k_flat_half<kModeGeneric, true, true><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles[1], d_first[1], 1, j, d_done);
-    } else if (ex) {
-      if (grid[0]) k_flat_half<kModeFerro, true, false><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles[0], d_first[0], 1, j, d_done);
-      if (grid[1]) k_flat_half<kModeGeneric, true, false><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles[1], d_first[1], 1, j, d_done);
+    if (grid[0]) k_flat_half<kModeFerro, false><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles[0], d_first[0], 0, j);
+    if (grid[1]) k_flat_half<kModeGeneric, false><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles[1], d_first[1], 0, j);
+    if (ex) {
+      if (grid[0]) k_flat_half<kModeFerro, true><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles[0], d_first[0], 1, j);
+      if (grid[1]) k_flat_half<kModeGeneric, true><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles[1], d_first[1], 1, j);
       k_flat_exchange<<<std::min(np, di.sms * 8), kFlatThreads, 0, st>>>(d_probs, np, j);
     } else {
-      if (grid[0]) k_flat_half<kModeFerro, false, false><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles[0], d_first[0], 1, j, d_done);
-      if (grid[1]) k_flat_half<kModeGeneric, false, false><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles[1], d_first[1], 1, j, d_done);
+      if (grid[0]) k_flat_half<kModeFerro, false><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles[0], d_first[0], 1, j);
+      if (grid[1]) k_flat_half<kModeGeneric, false><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles[1], d_first[1], 1, j);
     }
     err = cudaGetLastError();
   }
@@ -676,10 +431,10 @@ int sweep_batch_static(pt_problem* const* ps, int count, const int64_t* n, const
   if (np == 0) return PT_OK;
   int per_sm[2] = {1, 1};
   cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm[0], k_flat_half<kModeFerro, true, false>, kFlatThreads, 0);
+      &per_sm[0], k_flat_half<kModeFerro, true>, kFlatThreads, 0);
   if (err == cudaSuccess)
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm[1], k_flat_half<kModeGeneric, true, false>, kFlatThreads, 0);
+        &per_sm[1], k_flat_half<kModeGeneric, true>, kFlatThreads, 0);
   if (err != cudaSuccess) return fail(PT_ECUDA, "occupancy: %s", cudaGetErrorString(err));
   const int wpb = kFlatThreads / 32;
   const int lo[2] = {0, split}, hi[2] = {split, nt};
@@ -729,15 +484,15 @@ int sweep_batch_static(pt_problem* const* ps, int count, const int64_t* n, const
       const FlatProblem& fp = g_sp_probs[k];
       ex = j < fp.n && fp.m > 0 && (fp.t0 + (uint64_t)j + 1) % (uint64_t)fp.m == 0;
     }
-    if (grid[0]) k_flat_half<kModeFerro, false, false><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles0, d_first0, 0, j, nullptr);
-    if (grid[1]) k_flat_half<kModeGeneric, false, false><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles1, d_first1, 0, j, nullptr);
+    if (grid[0]) k_flat_half<kModeFerro, false><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles0, d_first0, 0, j);
+    if (grid[1]) k_flat_half<kModeGeneric, false><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles1, d_first1, 0, j);
     if (ex) {
-      if (grid[0]) k_flat_half<kModeFerro, true, false><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles0, d_first0, 1, j, nullptr);
-      if (grid[1]) k_flat_half<kModeGeneric, true, false><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles1, d_first1, 1, j, nullptr);
+      if (grid[0]) k_flat_half<kModeFerro, true><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles0, d_first0, 1, j);
+      if (grid[1]) k_flat_half<kModeGeneric, true><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles1, d_first1, 1, j);
       k_flat_exchange<<<std::min(np, di.sms * 8), kFlatThreads, 0, st>>>(d_probs, np, j);
     } else {
-      if (grid[0]) k_flat_half<kModeFerro, false, false><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles0, d_first0, 1, j, nullptr);
-      if (grid[1]) k_flat_half<kModeGeneric, false, false><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles1, d_first1, 1, j, nullptr);
+      if (grid[0]) k_flat_half<kModeFerro, false><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles0, d_first0, 1, j);
+      if (grid[1]) k_flat_half<kModeGeneric, false><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles1, d_first1, 1, j);
     }
     err = cudaGetLastError();
   }

@@ -821,7 +821,8 @@ int pt_set_spins(pt_problem* p, int k, const int8_t* in) {
 }
 
 int pt_set_batch_tuning(int strategy, int cluster, int joint_min_L) {
-  if ((strategy != PT_BATCH_FLAT && strategy != PT_BATCH_CLUSTER) || cluster < 1 ||
+  if ((strategy != PT_BATCH_FLAT && strategy != PT_BATCH_CLUSTER && strategy != PT_BATCH_FLOW) ||
+      cluster < 1 ||
       cluster > 16 || joint_min_L < 4)
     return fail(PT_EINVAL, "strategy = %d, cluster = %d, joint_min_L = %d", strategy, cluster,
                 joint_min_L);

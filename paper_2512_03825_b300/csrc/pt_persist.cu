@@ -44,18 +44,6 @@ struct PersistArgs {
   RoundKeys rk;  // Philox round keys of the seed (constant-bank operands)
 };
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
 // Every CTA arrives once; returns false when the wait gave up (time limit or a status set
 // by another CTA): the caller leaves the kernel.
 __device__ bool grid_barrier(unsigned* bar, unsigned target, int* status, uint64_t limit_ns,
@@ -66,7 +54,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned target, int* status, uint64
     __threadfence();  // the CTA's writes (ordered before by the block barrier) go first
     atomicAdd(bar, 1u);
     const uint64_t t0 = global_ns();
-    while ((int)(ld_acquire(bar) - target) < 0) {
+    while ((int)(ld_acquire_u32(bar) - target) < 0) {
       if (*(volatile int*)status != 0) {
         ok = 0;
         break;

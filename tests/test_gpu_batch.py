@@ -1,6 +1,8 @@
-"""The batched persistent kernel: each problem advanced inside a batch is bit-identical to
-the same problem advanced alone (plain path) and to the CPU oracle, for every launch shape
-the autotuner may pick, and batches compose with plain sweeps and with each other."""
+"""The batched paths (lock-step launches, cluster kernel, dataflow launch): each problem
+advanced inside a batch is bit-identical to the same problem advanced alone (plain path) and
+to the CPU oracle, for every launch shape the autotuner may pick, and batches compose with
+plain sweeps and with each other. The dataflow launch's bounded waits are made to run out
+once, on purpose, by a wait for tiles that do not exist."""
 from __future__ import annotations
 
 import numpy as np
@@ -64,8 +66,8 @@ def test_batch_equals_plain_and_oracle(api, tuning):
         g = api.PTProblem(pr.L, pr.betas, J=pr.J, h=pr.h, seed=pr.seed)
         g.sweep(pr.sweeps, pr.every)
         plain.append(state(g))
-    for st, cl, jm in [(0, 1, 4), (1, 4, 16), (1, 1, 4), (1, 2, 8), (1, 8, 16), (1, 3, 8),
-                       (1, 6, 12), (1, 4, 1 << 20)]:
+    for st, cl, jm in [(0, 1, 4), (2, 1, 4), (1, 4, 16), (1, 1, 4), (1, 2, 8), (1, 8, 16),
+                       (1, 3, 8), (1, 6, 12), (1, 4, 1 << 20)]:
         tuning(cl, jm, st)
         batch = [api.PTProblem(pr.L, pr.betas, J=pr.J, h=pr.h, seed=pr.seed) for pr in probs]
         api.sweep_batch(batch, [pr.sweeps for pr in probs], [pr.every for pr in probs])
@@ -83,7 +85,7 @@ def test_batch_equals_plain_and_oracle(api, tuning):
         np.testing.assert_array_equal(g.energies_int(), o.energies_int())
 
 
-@pytest.mark.parametrize("strategy", [0, 1])
+@pytest.mark.parametrize("strategy", [0, 1, 2])
 def test_batch_composes_with_plain(api, tuning, strategy):
     tuning(4, 16, strategy)
     pr = W.Problem(L=64, betas=W.linear_ladder(0.3, 0.6, 40), seed=77)
@@ -96,7 +98,7 @@ def test_batch_composes_with_plain(api, tuning, strategy):
     assert_state_equal(a, b)
 
 
-@pytest.mark.parametrize("strategy", [0, 1])
+@pytest.mark.parametrize("strategy", [0, 1, 2])
 def test_batched_workload_sample_vs_oracle(api, tuning, strategy):
     """A sample of the 256-problem batched workload, short runs, against the oracle."""
     tuning(4, 128, strategy)
@@ -122,3 +124,50 @@ def test_batch_rejects_bad_input(api):
         api.sweep_batch([g], -1, 1)
     api.sweep_batch([g], 0, 0)
     assert g.counters() == (0, 0)
+
+
+def test_flow_uneven_lengths_and_long_runs(api, tuning):
+    """Dataflow launch: problems with different sweep counts and exchange periods, many
+    tiles per problem (L = 256) next to one-tile problems, equal to the lock-step path."""
+    probs = [W.Problem(L=256, betas=W.linear_ladder(0.3, 0.6, 40), seed=11, sweeps=37, every=1),
+             W.Problem(L=8, betas=W.linear_ladder(0.3, 0.6, 5), seed=12, sweeps=120, every=3),
+             W.Problem(L=96, betas=W.linear_ladder(0.3, 0.6, 33), J=1.0, h=0.1, seed=13,
+                       sweeps=64, every=2),
+             W.Problem(L=32, betas=(0.4,), seed=14, sweeps=90, every=1)]
+    out = {}
+    for st in (0, 2):
+        tuning(1, 4, st)
+        gs = [api.PTProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed) for p in probs]
+        api.sweep_batch(gs, [p.sweeps for p in probs], [p.every for p in probs])
+        api.sweep_batch(gs, [5, 0, 9, 1], [1, 3, 2, 1])
+        out[st] = [state(g) for g in gs]
+    for j in range(len(probs)):
+        assert_state_equal(out[0][j], out[2][j], "problem %d" % j)
+
+
+def test_flow_wait_runs_out_and_context_survives(api, tuning):
+    """One problem's first colour-1 wait expects one tile more than exists: the wait gives
+    up after its 50 ms limit, every problem of the call reports PT_ETIMEOUT, and a new
+    batch on the same context still equals the oracle."""
+    from paper_2512_03825_b300 import _lib
+    tuning(1, 4, 2)
+    probs = [W.Problem(L=64, betas=W.linear_ladder(0.3, 0.5, 20), seed=21),
+             W.Problem(L=32, betas=W.linear_ladder(0.3, 0.5, 9), seed=22)]
+    gs = [api.PTProblem(p.L, p.betas, seed=p.seed) for p in probs]
+    for g in gs:
+        g.set_wait_limit(0.05)
+    gs[1].debug_stall_barrier(1)
+    api.sweep_batch(gs, 4, 1)
+    for g in gs:
+        with pytest.raises(_lib.PTError) as ei:
+            g.synchronize()
+        assert ei.value.code == _lib.PT_ETIMEOUT
+        g.close()
+    hs = [api.PTProblem(p.L, p.betas, seed=p.seed) for p in probs]
+    api.sweep_batch(hs, 6, 1)
+    oracle.set_threads(8)
+    for p, h in zip(probs, hs):
+        o = oracle.OracleProblem(p.L, p.betas, seed=p.seed)
+        o.sweep(6, 1)
+        np.testing.assert_array_equal(h.spins(), o.spins())
+        np.testing.assert_array_equal(h.chain_map(), o.chain_map())
