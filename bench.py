@@ -326,6 +326,8 @@ def run_ours(args, rank, world, local):
         out["plain"] = bench_plain_sample(probs, stream)
         out["batched_vs_plain"] = value / world / out["plain"]["value"]
         out["single_L1024_R64"] = bench_single(stream, sms, clock_mhz)
+        out["single_L128_R32"] = bench_single(stream, sms, clock_mhz, "L128_R32", 2000)
+        out["single_L16_R8"] = bench_single(stream, sms, clock_mhz, "L16_R8", 1000)
         out["e2e"] = bench_e2e(probs, args.sweeps, stream, world)
         out["cpu_baseline"] = cpu_baseline_sample(probs)
     elif not args.quick:
@@ -390,12 +392,12 @@ def bench_plain_sample(probs, stream, n_problems=32, sweeps=200):
             "launches_strategy": out["launches"]}
 
 
-def bench_single(stream, sms, clock_mhz, sweeps=200):
-    """The roofline config: L = 1024, R = 64, exchange every 5 sweeps, plain path."""
+def bench_single(stream, sms, clock_mhz, name="L1024_R64", sweeps=200):
+    """One single-problem config on the plain path (pt_sweep, default strategy)."""
     import torch
     from paper_2512_03825_b300 import api
     from paper_2512_03825_b300 import workloads as W
-    p = W.SINGLE["L1024_R64"]
+    p = W.SINGLE[name]
     h = api.PTProblem(p.L, p.betas, seed=p.seed, stream=stream)
     h.sweep(10, p.every)
     torch.cuda.synchronize()
@@ -405,12 +407,14 @@ def bench_single(stream, sms, clock_mhz, sweeps=200):
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
+    strategy, _, grid = h.sweep_tuning()
     h.close()
     att = float(p.L * p.L * p.R * sweeps)
     v = att / (ms / 1e3)
     peak_att = sms * IMUL_WIDE_PER_CLK_SM * clock_mhz * 1e6 / MUL_PER_ATTEMPT
     return {"value": v, "unit": UNIT, "sweeps": sweeps, "every": p.every,
-            "frac_of_mul_roofline": v / peak_att, "us_per_sweep": 1e3 * ms / sweeps}
+            "frac_of_mul_roofline": v / peak_att, "us_per_sweep": 1e3 * ms / sweeps,
+            "persistent_grid": grid}
 
 
 def bench_e2e(probs, sweeps, stream, world):
