@@ -64,6 +64,63 @@ __device__ __forceinline__ Philox4 philox4x32_10_rk(uint32_t c0, uint32_t c1, ui
   return Philox4{c0, c1, c2, c3};
 }
 
+// The eight blocks j of one site in one sweep have the counters {site, lo32(t), blk0 + j, c3}:
+// they differ in counter word 2 only. In round 1 the product of word 0 depends on the site
+// alone and that of word 2 on j alone; in round 2 the product of word 0 (which came from
+// word 2's product) depends on j and the sweep alone and that of word 2 on the site alone.
+// So a site needs two products for rounds 1-2 instead of 4 per block, and the j-dependent
+// round-1/2 terms are computed once per sweep and plane (BlockTerms). Same numbers, bit for
+// bit: only the order in which the products are formed changes.
+struct BlockTerms {
+  uint32_t X[8], Y[8], Z[8];  // per block: round-2 output terms that do not depend on the site
+};
+struct SiteTerms {
+  uint32_t H, Hlo, L0;  // round-1/2 products that do not depend on the block
+};
+
+__device__ __forceinline__ void block_terms(uint32_t blk0, uint32_t t_lo, const RoundKeys& rk,
+                                            BlockTerms& bt) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint32_t c2 = blk0 + (uint32_t)j;
+    const uint32_t h1 = __umulhi(kPhiloxM1, c2), l1 = kPhiloxM1 * c2;  // round 1, word 2
+    const uint32_t c0 = h1 ^ t_lo ^ rk.k0[0];                           // round-1 output 0
+    const uint32_t hA = __umulhi(kPhiloxM0, c0), lA = kPhiloxM0 * c0;   // round 2, word 0
+    bt.X[j] = l1 ^ rk.k0[1];
+    bt.Y[j] = hA ^ rk.k1[1];
+    bt.Z[j] = lA;
+  }
+}
+
+__device__ __forceinline__ SiteTerms site_terms(uint32_t site, uint32_t c3, const RoundKeys& rk) {
+  SiteTerms st;
+  const uint32_t h0 = __umulhi(kPhiloxM0, site);  // round 1, word 0
+  st.L0 = kPhiloxM0 * site;
+  const uint32_t c2 = h0 ^ c3 ^ rk.k1[0];         // round-1 output 2
+  st.H = __umulhi(kPhiloxM1, c2);                 // round 2, word 2
+  st.Hlo = kPhiloxM1 * c2;
+  return st;
+}
+
+// Philox4x32-10 block j of the site: the round-2 state from the shared terms, then rounds
+// 3-10.
+__device__ __forceinline__ Philox4 philox_site_block(const SiteTerms& st, const BlockTerms& bt,
+                                                     int j, const RoundKeys& rk) {
+  uint32_t c0 = st.H ^ bt.X[j], c1 = st.Hlo, c2 = bt.Y[j] ^ st.L0, c3 = bt.Z[j];
+#pragma unroll
+  for (int r = 2; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c0);
+    const uint32_t lo0 = kPhiloxM0 * c0;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c2);
+    const uint32_t lo1 = kPhiloxM1 * c2;
+    c0 = hi1 ^ c1 ^ rk.k0[r];
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ rk.k1[r];
+    c3 = lo0;
+  }
+  return Philox4{c0, c1, c2, c3};
+}
+
 // Counter words shared by every spin-update draw of one sweep.
 struct SweepCtr {
   uint32_t t_lo;  // lo32(t)
@@ -155,15 +212,15 @@ __device__ __forceinline__ uint32_t update_word_ferro(uint32_t s, uint32_t n0, u
 }
 
 // update_word_ferro with the thresholds in shared memory, interleaved so that one 16-byte
-// broadcast load serves two slots: thr[m] = {T0[2m], T1[2m], T0[2m+1], T1[2m+1]}, and the
-// round keys from the parameter bank. Same decisions, bit for bit.
+// broadcast load serves two slots: thr[m] = {T0[2m], T1[2m], T0[2m+1], T1[2m+1]}.
+// `draw(j)` returns Philox block j of this site (slots 4j .. 4j+3). Same decisions, bit for
+// bit.
+template <class Draw>
 __device__ __forceinline__ uint32_t update_word_ferro_smem(uint32_t s, uint32_t n0, uint32_t n1,
-                                                           uint32_t n2, uint32_t n3,
-                                                           uint32_t site, uint32_t blk0,
-                                                           int nblk, const uint4* thr,
-                                                           uint32_t alw0, uint32_t alw1,
-                                                           uint32_t used, uint32_t t_lo,
-                                                           uint32_t c3, const RoundKeys& rk) {
+                                                           uint32_t n2, uint32_t n3, int nblk,
+                                                           const uint4* thr, uint32_t alw0,
+                                                           uint32_t alw1, uint32_t used,
+                                                           const Draw& draw) {
   const uint32_t a0 = s ^ n0, a1 = s ^ n1, a2 = s ^ n2, a3 = s ^ n3;
   const uint32_t x01 = a0 ^ a1, x23 = a2 ^ a3;
   const uint32_t ge2 = (a0 & a1) | (a2 & a3) | (x01 & x23);
@@ -173,7 +230,7 @@ __device__ __forceinline__ uint32_t update_word_ferro_smem(uint32_t s, uint32_t 
 #pragma unroll
   for (int j = 7; j >= 0; --j) {
     if (j < nblk) {
-      const Philox4 r = philox4x32_10_rk(site, t_lo, blk0 + (uint32_t)j, c3, rk);
+      const Philox4 r = draw(j);
       const uint4 lo = thr[2 * j], hi = thr[2 * j + 1];  // slots 4j, 4j+1 | 4j+2, 4j+3
       rej0 = shift_in_reject(rej0, r.w, hi.z);
       rej1 = shift_in_reject(rej1, r.w, hi.w);

@@ -154,13 +154,15 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
   const int w = tl.w;
   const int L = p.L, half = L >> 1;
   const int nblk = (min(32, p.R - 32 * w) + 3) >> 2;
-  const uint32_t t_lo = (uint32_t)t, c3 = kTagSpin | ((uint32_t)(t >> 32) << 8);
+  const uint32_t c3 = kTagSpin | ((uint32_t)(t >> 32) << 8);
   RoundKeys rk;
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     rk.k0[r] = p.key0 + (uint32_t)r * kPhiloxW0;
     rk.k1[r] = p.key1 + (uint32_t)r * kPhiloxW1;
   }
+  BlockTerms bt;
+  block_terms((uint32_t)(8 * w), (uint32_t)t, rk, bt);
   uint32_t* own = p.spins + word_index(L, w, colour, 0, 0);
   const uint32_t* oth = p.spins + word_index(L, w, colour ^ 1, 0, 0);
   const int q_start = tl.q0 + lane;
@@ -190,8 +192,10 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
       const uint32_t n2 = ld_nb<NB_L2>(oth + q);
       const uint32_t n3 = ld_nb<NB_L2>(oth + y * half + ih);
       const uint32_t site = (uint32_t)(y * L + 2 * i + par);
-      const uint32_t ns = update_word_ferro_smem(s, n0, n1, n2, n3, site, (uint32_t)(8 * w),
-                                                 nblk, thr, alw0, alw1, used, t_lo, c3, rk);
+      const SiteTerms st = site_terms(site, c3, rk);
+      const uint32_t ns = update_word_ferro_smem(
+          s, n0, n1, n2, n3, nblk, thr, alw0, alw1, used,
+          [&](int jb) { return philox_site_block(st, bt, jb, rk); });
       own[q] = ns;
       if (COUNT && count) {
         // with h = 0 the exchange needs only the bonds: U of the new state, all four bonds
@@ -233,8 +237,9 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
       const uint32_t n2 = ld_nb<NB_L2>(oth + q);
       const uint32_t n3 = ld_nb<NB_L2>(oth + y * half + ih);
       const uint32_t site = (uint32_t)(y * L + 2 * i + par);
+      const SiteTerms st = site_terms(site, c3, rk);
       own[q] = update_word_generic_with(s, n0, n1, n2, n3, nblk, pl, [&](int jb) {
-        return philox4x32_10_rk(site, t_lo, (uint32_t)(8 * w + jb), c3, rk);
+        return philox_site_block(st, bt, jb, rk);
       });
       i += di;
       y += dy;

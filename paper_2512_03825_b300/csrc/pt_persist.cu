@@ -163,13 +163,12 @@ __device__ void exchange_local(const DevProblem& p, uint64_t e, const uint32_t* 
 // (a one-to-one pairing of the colours) are added to U / N.
 template <int MODE, bool COUNT>
 __device__ __forceinline__ void half_pass(const DevProblem& p, int w, int colour, uint64_t t,
-                                          const RoundKeys& rk, int q0, int step, int y0,
-                                          int i0, int dy, int di, const uint4* thr,
-                                          uint32_t alw0, uint32_t alw1, uint32_t used,
-                                          const PlaneGeneric& gen, BitCounter<15, 10>& U,
-                                          BitCounter<15, 10>& N) {
-  const uint32_t t_lo = (uint32_t)t, c3 = kTagSpin | ((uint32_t)(t >> 32) << 8);
-  const uint32_t blk0 = (uint32_t)(8 * w);
+                                          const RoundKeys& rk, const BlockTerms& bt, int q0,
+                                          int step, int y0, int i0, int dy, int di,
+                                          const uint4* thr, uint32_t alw0, uint32_t alw1,
+                                          uint32_t used, const PlaneGeneric& gen,
+                                          BitCounter<15, 10>& U, BitCounter<15, 10>& N) {
+  const uint32_t c3 = kTagSpin | ((uint32_t)(t >> 32) << 8);
   const int L = p.L, half = L >> 1;
   const int nwords = L * half;
   const int nblk = (min(32, p.R - 32 * w) + 3) >> 2;
@@ -187,14 +186,13 @@ __device__ __forceinline__ void half_pass(const DevProblem& p, int w, int colour
     const uint32_t n2 = __ldcg(oth + q);
     const uint32_t n3 = __ldcg(oth + y * half + ih);
     const uint32_t site = (uint32_t)(y * L + 2 * i + par);
+    const SiteTerms st = site_terms(site, c3, rk);
+    const auto draw = [&](int j) { return philox_site_block(st, bt, j, rk); };
     uint32_t ns;
     if (MODE == kModeFerro)
-      ns = update_word_ferro_smem(s, n0, n1, n2, n3, site, blk0, nblk, thr, alw0, alw1, used,
-                                  t_lo, c3, rk);
+      ns = update_word_ferro_smem(s, n0, n1, n2, n3, nblk, thr, alw0, alw1, used, draw);
     else
-      ns = update_word_generic_with(s, n0, n1, n2, n3, nblk, gen, [&](int j) {
-        return philox4x32_10_rk(site, t_lo, blk0 + (uint32_t)j, c3, rk);
-      });
+      ns = update_word_generic_with(s, n0, n1, n2, n3, nblk, gen, draw);
     own[q] = ns;
     if (COUNT) {
       const NbCount k = count4(ns ^ n0, ns ^ n1, ns ^ n2, ns ^ n3);
@@ -258,14 +256,16 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
   bool exchanged = false;
   for (int j = 0; j < a.n; ++j) {
     const uint64_t t = a.t0 + (uint64_t)j;
+    BlockTerms bt;
+    block_terms((uint32_t)(8 * w), (uint32_t)t, a.rk, bt);
     BitCounter<15, 10> U, N;
-    half_pass<MODE, false>(p, w, 0, t, a.rk, q0, step, y0, i0, dy, di, thr, alw0, alw1,
+    half_pass<MODE, false>(p, w, 0, t, a.rk, bt, q0, step, y0, i0, dy, di, thr, alw0, alw1,
                            used, gen, U, N);
     target += gridDim.x + (j == 0 ? (unsigned)a.stall : 0u);
     if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s)) return;
     const bool ex = a.m > 0 && (t + 1) % (uint64_t)a.m == 0;
     if (!ex) {
-      half_pass<MODE, false>(p, w, 1, t, a.rk, q0, step, y0, i0, dy, di, thr, alw0, alw1,
+      half_pass<MODE, false>(p, w, 1, t, a.rk, bt, q0, step, y0, i0, dy, di, thr, alw0, alw1,
                              used, gen, U, N);
       if (j + 1 == a.n) break;  // the kernel's end orders this half sweep before what follows
       target += gridDim.x;
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
     uint32_t* const cb = cnt_base + (e & 1) * 2 * W * 32;
     U.zero();
     N.zero();
-    half_pass<MODE, true>(p, w, 1, t, a.rk, q0, step, y0, i0, dy, di, thr, alw0, alw1,
+    half_pass<MODE, true>(p, w, 1, t, a.rk, bt, q0, step, y0, i0, dy, di, thr, alw0, alw1,
                           used, gen, U, N);
     const uint32_t u = U.warp_total_for_lane();
     const uint32_t nn = MODE == kModeFerro ? 0u : N.warp_total_for_lane();
