@@ -213,6 +213,26 @@ int pt_chain_map(pt_problem* p, int32_t* slot_of_temp);
 /* Sweeps and swap iterations done since pt_create (either pointer may be NULL). */
 int pt_counters(pt_problem* p, uint64_t* sweeps_done, uint64_t* exchanges_done);
 
+/* Observable traces: the per-sweep chain of energies and magnetisations at every
+ * temperature (the "stored chains" of the paper's CPU programs, Sec. 5), kept on the device in a ring
+ * of bounded size. After pt_trace_start(p, capacity) (1 <= capacity <= 2^32 rows), every sweep
+ * of pt_sweep or pt_sweep_batch appends one row E_int[R], M[R] by temperature index, taken
+ * after the sweep and its swap iteration (if any); the oldest rows are overwritten once
+ * `capacity` rows exist. The ring holds capacity * R * 16 bytes of device memory, allocated
+ * like the problem's own; restarting replaces the ring. Tracing makes every sweep count the
+ * bonds and up spins (a few per cent of a sweep); a batch with a traced problem runs the
+ * PT_BATCH_FLAT strategy. pt_trace_stop frees the ring (a no-op without one). Errors:
+ * PT_EINVAL, PT_ENOMEM, PT_ECUDA. */
+int pt_trace_start(pt_problem* p, int64_t capacity);
+int pt_trace_stop(pt_problem* p);
+
+/* Copy up to max_rows of the newest trace rows, oldest first, to E_int[rows][R] and
+ * M[rows][R] (either may be NULL); *rows = rows copied (min(max_rows, capacity, sweeps since
+ * pt_trace_start)) and *first_sweep = the sweeps done since pt_create when the first of them
+ * was taken (either may be NULL). Synchronises the stream. PT_ESTATE without a trace. */
+int pt_trace_read(pt_problem* p, int64_t max_rows, int64_t* E_int, int64_t* M,
+                  uint64_t* first_sweep, int64_t* rows);
+
 /* Wait for the problem's queued work; reports device-side failures. */
 int pt_synchronize(pt_problem* p);
 

@@ -61,6 +61,10 @@ SIGNATURES = [
     ("pt_set_spins", C.c_int, [P, C.c_int, C.POINTER(C.c_int8)]),
     ("pt_chain_map", C.c_int, [P, C.POINTER(C.c_int32)]),
     ("pt_counters", C.c_int, [P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
+    ("pt_trace_start", C.c_int, [P, C.c_int64]),
+    ("pt_trace_stop", C.c_int, [P]),
+    ("pt_trace_read", C.c_int, [P, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                C.POINTER(C.c_uint64), C.POINTER(C.c_int64)]),
     ("pt_synchronize", C.c_int, [P]),
     ("pt_device_bytes", C.c_size_t, [P]),
     ("pt_estimate_device_bytes", C.c_size_t, [C.c_int, C.POINTER(C.c_double), C.c_int,

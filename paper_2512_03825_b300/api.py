@@ -63,6 +63,28 @@ class PTProblem:
     def synchronize(self):
         check(lib.pt_synchronize(self._h), "pt_synchronize")
 
+    def trace_start(self, capacity: int):
+        """Record (E_int, M) of every temperature after each later sweep, in a device ring of
+        `capacity` rows."""
+        check(lib.pt_trace_start(self._h, int(capacity)), "pt_trace_start")
+
+    def trace_stop(self):
+        check(lib.pt_trace_stop(self._h), "pt_trace_stop")
+
+    def trace(self, max_rows: Optional[int] = None):
+        """(first_sweep, E_int[rows][R], M[rows][R]) of the newest trace rows, oldest first;
+        first_sweep = sweeps done when the first row was taken."""
+        if max_rows is None:
+            max_rows = self.counters()[0]
+        max_rows = int(max_rows)
+        E = np.zeros((max(max_rows, 1), self.R), np.int64)
+        M = np.zeros((max(max_rows, 1), self.R), np.int64)
+        first, rows = C.c_uint64(), C.c_int64()
+        check(lib.pt_trace_read(self._h, max_rows, _dptr(E, C.c_int64), _dptr(M, C.c_int64),
+                                C.byref(first), C.byref(rows)), "pt_trace_read")
+        n = rows.value
+        return first.value, E[:n].copy(), M[:n].copy()
+
     def set_sweep_tuning(self, strategy: int = 0, words_per_thread: int = 0):
         """strategy: PT_SWEEP_AUTO (0), PT_SWEEP_LAUNCHES (1) or PT_SWEEP_PERSISTENT (2)."""
         check(lib.pt_set_sweep_tuning(self._h, int(strategy), int(words_per_thread)),

@@ -512,7 +512,9 @@ int sweep_batch(pt_problem* const* ps, int count, const int64_t* n, const int* e
   int rc = problem_device_guard(ps[0]);
   if (rc) return rc;
   const DeviceInfo& di = ps[0]->dev_info;
-  const BatchTuning tune = g_batch_tuning;
+  BatchTuning tune = g_batch_tuning;
+  for (int j = 0; j < count; ++j)  // trace rows are written by the lock-step exchange launch
+    if (ps[j]->dev.trace_E != nullptr) tune.strategy = PT_BATCH_FLAT;
   if (tune.strategy == PT_BATCH_FLAT || tune.strategy == PT_BATCH_FLOW) {
     rc = tune.strategy == PT_BATCH_FLAT ? sweep_batch_flat(ps, count, n, every, st, di)
                                         : sweep_batch_flow(ps, count, n, every, st, di);

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(kFlatThreads, 2) k_flat_half(const FlatProblem
     const Tile tl = tiles[tix];
     const FlatProblem& fp = probs[tl.prob];
     if (j >= fp.n) continue;  // warp-uniform
-    const bool count = COUNT && exchanges_after(fp, j);
+    const bool count = COUNT && counts_after(fp, j);
     tile_half<MODE, COUNT, false>(fp, tl, colour, j, count, thr_s[wib], &gen[wib]);
   }
 }
@@ -54,9 +54,10 @@ __global__ void __launch_bounds__(kFlatThreads) k_flat_exchange(const FlatProble
                                                                  int nprobs, int64_t j) {
   for (int pi = blockIdx.x; pi < nprobs; pi += gridDim.x) {
     const FlatProblem& fp = probs[pi];
-    if (!exchanges_after(fp, j)) continue;
+    if (!counts_after(fp, j)) continue;
     const DevProblem& p = fp.p;
-    const uint64_t e = exchange_index(fp, j);
+    const bool ex = exchanges_after(fp, j);
+    const uint64_t e = ex ? exchange_index(fp, j) : 0;
     const int R = p.R, W = p.W;
     const int64_t L2 = (int64_t)p.L * p.L;
     __syncthreads();
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(kFlatThreads) k_flat_exchange(const FlatProble
     for (int q = threadIdx.x; q < 2 * W * 32; q += blockDim.x) p.cnt[q] = 0;
     const int parity = (int)(e & 1);
     const uint32_t c3 = kTagExch | ((uint32_t)(e >> 32) << 8);
-    for (int k = parity + 2 * threadIdx.x; k + 1 < R; k += 2 * blockDim.x) {
+    for (int k = parity + 2 * threadIdx.x; ex && k + 1 < R; k += 2 * blockDim.x) {
       const int a = p.slot_of_temp[k], b = p.slot_of_temp[k + 1];
       const int64_t n = p.E_slot[a] - p.E_slot[b];
       const SwapPair sp = p.pairs[k];
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(kFlatThreads) k_flat_exchange(const FlatProble
     }
     __syncthreads();
     constexpr uint64_t kTwo32 = 1ull << 32;
-    for (int r = threadIdx.x; r < W * 32; r += blockDim.x) {
+    for (int r = threadIdx.x; ex && r < W * 32; r += blockDim.x) {
       const int w = r >> 5, b = r & 31;
       const bool in_use = r < R;
       const int temp = in_use ? p.temp_of_slot[r] : 0;
@@ -120,6 +121,17 @@ __global__ void __launch_bounds__(kFlatThreads) k_flat_exchange(const FlatProble
           const uint32_t a = __ballot_sync(0xffffffffu, in_use && tc >= kTwo32);
           if (b == 0) pl->alw[c] = a;
         }
+      }
+    }
+    if (p.trace_E != nullptr) {
+      // the trace row of this sweep, by temperature index after its swap iteration
+      __syncthreads();
+      const uint64_t t = fp.t0 + (uint64_t)j;
+      const int64_t row = (int64_t)((t - p.trace_t0) % (uint64_t)p.trace_cap);
+      for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        const int k = p.temp_of_slot[r];
+        p.trace_E[row * R + k] = p.E_slot[r];
+        p.trace_M[row * R + k] = p.M_slot[r];
       }
     }
   }
@@ -251,12 +263,13 @@ int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const i
     if (err == cudaSuccess)
       err = cudaMemcpyAsync(d_first[md], first[md].data(), fb[md], cudaMemcpyHostToDevice, st);
   }
-  // which sweeps are followed by at least one exchange
+  // which sweeps are counted for at least one problem (a swap iteration or a trace row)
   std::vector<char> any_exchange((size_t)n_max, 0);
   for (const FlatProblem& fp : probs)
-    if (fp.m > 0)
-      for (int64_t j = 0; j < fp.n; ++j)
-        if ((fp.t0 + (uint64_t)j + 1) % (uint64_t)fp.m == 0) any_exchange[(size_t)j] = 1;
+    for (int64_t j = 0; j < fp.n; ++j)
+      if (fp.p.trace_E != nullptr ||
+          (fp.m > 0 && (fp.t0 + (uint64_t)j + 1) % (uint64_t)fp.m == 0))
+        any_exchange[(size_t)j] = 1;
   const int np = (int)probs.size();
   for (int64_t j = 0; j < n_max && err == cudaSuccess; ++j) {
     const bool ex = any_exchange[(size_t)j] != 0;
@@ -479,10 +492,11 @@ int sweep_batch_static(pt_problem* const* ps, int count, const int64_t* n, const
   const int* d_first0 = (const int*)(base + off_first0);
   const int* d_first1 = (const int*)(base + off_first1);
   for (int64_t j = 0; j < n_max && err == cudaSuccess; ++j) {
-    bool ex = false;
+    bool ex = false;  // counted for at least one problem (a swap iteration or a trace row)
     for (int k = 0; k < np && !ex; ++k) {
       const FlatProblem& fp = g_sp_probs[k];
-      ex = j < fp.n && fp.m > 0 && (fp.t0 + (uint64_t)j + 1) % (uint64_t)fp.m == 0;
+      ex = j < fp.n && (fp.p.trace_E != nullptr ||
+                        (fp.m > 0 && (fp.t0 + (uint64_t)j + 1) % (uint64_t)fp.m == 0));
     }
     if (grid[0]) k_flat_half<kModeFerro, false><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles0, d_first0, 0, j);
     if (grid[1]) k_flat_half<kModeGeneric, false><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles1, d_first1, 0, j);

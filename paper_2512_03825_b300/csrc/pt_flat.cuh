@@ -39,6 +39,10 @@ struct Tile {
 __device__ __forceinline__ bool exchanges_after(const FlatProblem& fp, int64_t j) {
   return j < fp.n && fp.m > 0 && (fp.t0 + (uint64_t)j + 1) % (uint64_t)fp.m == 0;
 }
+// Is sweep j of this batch counted for problem fp (a swap iteration or a trace row follows)?
+__device__ __forceinline__ bool counts_after(const FlatProblem& fp, int64_t j) {
+  return exchanges_after(fp, j) || (j < fp.n && fp.p.trace_E != nullptr);
+}
 // Swap iterations of this batch up to and including the one after sweep j.
 __device__ __forceinline__ uint64_t exchanges_through(const FlatProblem& fp, int64_t j) {
   const uint64_t m = (uint64_t)fp.m;
@@ -213,6 +217,27 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
     if (COUNT && count) {
       const uint32_t u = Uf.warp_total_for_lane();
       if (u) atomicAdd(&p.cnt[w * 32 + lane], u);
+      if (p.trace_E != nullptr) {
+        // a trace row needs M too: the up spins of this lane's colour-1 words and of the
+        // colour-0 words one row up, in a second pass
+        BitCounter<13, 8> N;
+        N.zero();
+        int yc = q_start / half, ic = q_start - yc * half;
+        for (int q = q_start; q < tl.q1; q += 32) {
+          const int ym = (yc == 0) ? L - 1 : yc - 1;
+          const uint32_t ns = own[q];
+          const uint32_t n0 = ld_nb<NB_L2>(oth + ym * half + ic);
+          N.add2(ns ^ n0, ns & n0);
+          ic += di;
+          yc += dy;
+          if (ic >= half) {
+            ic -= half;
+            yc += 1;
+          }
+        }
+        const uint32_t nn = N.warp_total_for_lane();
+        if (nn) atomicAdd(&p.cnt[p.W * 32 + w * 32 + lane], nn);
+      }
     }
   } else {
     // the warp's generic thresholds live in its own shared slot

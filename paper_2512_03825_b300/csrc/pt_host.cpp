@@ -568,6 +568,10 @@ void pt_destroy(pt_problem* p) {
   a.free = p->allocator_free;
   a.ctx = p->allocator_ctx;
   dev_free(p->dmem, p->stream, a);
+  Allocator ta;
+  ta.free = p->trace_free;
+  ta.ctx = p->trace_ctx;
+  dev_free(p->trace_mem, p->stream, ta);
   if (cur >= 0 && cur != p->dev_info.device) cudaSetDevice(cur);
   delete p;
 }
@@ -625,15 +629,17 @@ int pt_sweep(pt_problem* p, int64_t n, int exchange_every) {
     cudaError_t err = launch_half_sweep(p->dev, p->dev_info, 0, p->t, p->stream);
     if (err == cudaSuccess) err = launch_half_sweep(p->dev, p->dev_info, 1, p->t, p->stream);
     if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "sweep launch", err);
-    p->t += 1;
-    if (exchange_every > 0 && p->t % (uint64_t)exchange_every == 0) {
+    const bool ex = exchange_every > 0 && (p->t + 1) % (uint64_t)exchange_every == 0;
+    const bool trace = p->dev.trace_E != nullptr;
+    if (ex || trace) {
+      const int flags = kStepEnergy | (ex ? kStepExchange | kStepRebuild : 0) |
+                        (trace ? kStepTrace : 0);
       err = launch_energy(p->dev, p->dev_info, p->stream);
-      if (err == cudaSuccess)
-        err = launch_exchange(p->dev, p->e, kStepEnergy | kStepExchange | kStepRebuild,
-                              p->stream);
+      if (err == cudaSuccess) err = launch_exchange(p->dev, p->e, flags, p->stream, p->t);
       if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "exchange launch", err);
-      p->e += 1;
+      if (ex) p->e += 1;
     }
+    p->t += 1;
   }
   return PT_OK;
 }
@@ -771,7 +777,85 @@ int pt_counters(pt_problem* p, uint64_t* sweeps_done, uint64_t* exchanges_done) 
   return PT_OK;
 }
 
-size_t pt_device_bytes(const pt_problem* p) { return p ? p->dbytes : 0; }
+size_t pt_device_bytes(const pt_problem* p) { return p ? p->dbytes + p->trace_bytes : 0; }
+
+int pt_trace_start(pt_problem* p, int64_t capacity) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  if (capacity < 1 || capacity > ((int64_t)1 << 32))
+    return fail(PT_EINVAL, "trace capacity %lld outside [1, 2^32]", (long long)capacity);
+  if ((rc = problem_device_guard(p))) return rc;
+  if ((rc = pt_trace_stop(p))) return rc;
+  const size_t bytes = (size_t)capacity * p->R * 2 * sizeof(int64_t);
+  Allocator used;
+  void* mem = dev_alloc(bytes, p->stream, &used);
+  if (!mem) return fail(PT_ENOMEM, "trace ring of %zu bytes", bytes);
+  const cudaError_t err = cudaMemsetAsync(mem, 0, bytes, p->stream);
+  if (err != cudaSuccess) {
+    dev_free(mem, p->stream, used);
+    return problem_fail(p, PT_ECUDA, "clearing the trace ring", err);
+  }
+  p->trace_mem = mem;
+  p->trace_bytes = bytes;
+  p->trace_free = used.free;
+  p->trace_ctx = used.ctx;
+  p->dev.trace_E = (int64_t*)mem;
+  p->dev.trace_M = (int64_t*)mem + (size_t)capacity * p->R;
+  p->dev.trace_cap = capacity;
+  p->dev.trace_t0 = p->t;
+  return PT_OK;
+}
+
+int pt_trace_stop(pt_problem* p) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  if (!p->trace_mem) return PT_OK;
+  if ((rc = problem_device_guard(p))) return rc;
+  const cudaError_t err = cudaStreamSynchronize(p->stream);
+  if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "synchronise", err);
+  Allocator a;
+  a.free = p->trace_free;
+  a.ctx = p->trace_ctx;
+  dev_free(p->trace_mem, p->stream, a);
+  p->trace_mem = nullptr;
+  p->trace_bytes = 0;
+  p->dev.trace_E = p->dev.trace_M = nullptr;
+  p->dev.trace_cap = 0;
+  return PT_OK;
+}
+
+int pt_trace_read(pt_problem* p, int64_t max_rows, int64_t* E_int, int64_t* M,
+                  uint64_t* first_sweep, int64_t* rows) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  if (max_rows < 0) return fail(PT_EINVAL, "max_rows = %lld", (long long)max_rows);
+  if (!p->trace_mem) return fail(PT_ESTATE, "no trace: call pt_trace_start first");
+  if ((rc = problem_device_guard(p))) return rc;
+  const int64_t written = (int64_t)(p->t - p->dev.trace_t0);
+  const int64_t n = std::min<int64_t>(std::min<int64_t>(written, p->dev.trace_cap), max_rows);
+  const uint64_t first = p->t - (uint64_t)n;  // sweep index (0-based) of the first row
+  const int R = p->R;
+  cudaError_t err = cudaSuccess;
+  // rows first .. first + n - 1, in at most two pieces of the ring
+  int64_t done = 0;
+  while (done < n && err == cudaSuccess) {
+    const int64_t slot = (int64_t)((first + done - p->dev.trace_t0) % (uint64_t)p->dev.trace_cap);
+    const int64_t len = std::min<int64_t>(n - done, p->dev.trace_cap - slot);
+    const size_t off = (size_t)slot * R, cnt = (size_t)len * R * sizeof(int64_t);
+    if (E_int)
+      err = cudaMemcpyAsync(E_int + (size_t)done * R, p->dev.trace_E + off, cnt,
+                            cudaMemcpyDeviceToHost, p->stream);
+    if (err == cudaSuccess && M)
+      err = cudaMemcpyAsync(M + (size_t)done * R, p->dev.trace_M + off, cnt,
+                            cudaMemcpyDeviceToHost, p->stream);
+    done += len;
+  }
+  if (err == cudaSuccess) err = cudaStreamSynchronize(p->stream);
+  if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "reading the trace", err);
+  if (first_sweep) *first_sweep = first + 1;
+  if (rows) *rows = n;
+  return pt_synchronize(p);
+}
 
 int pt_get_spins(pt_problem* p, int k, int8_t* out) {
   int rc = problem_check(p);

@@ -30,6 +30,10 @@ struct pt_problem {
   ptb::PersistPlan plan{};
   uint64_t wait_limit_ns = 1000000000ull;
   int stall = 0;            // pt_debug_stall_barrier, one launch
+  void* trace_mem = nullptr;  // observable trace ring (dev.trace_E / trace_M), own allocation
+  size_t trace_bytes = 0;
+  pt_free_fn trace_free = nullptr;
+  void* trace_ctx = nullptr;
 };
 
 namespace ptb {

@@ -196,6 +196,8 @@ __global__ void __launch_bounds__(kThreads) k_energy(DevProblem p) {
 //   kExchange: swap iteration e on pairs (k, k+1), k = e & 1 (mod 2); swaps temperature
 //              indices of accepted pairs and counts attempts / acceptances
 //   kRebuild:  rewrites the per-plane thresholds for the current slot -> temperature map
+//   kTrace:    writes E_int / M of every slot at its (new) temperature index into the trace
+//              row of sweep t
 // ---------------------------------------------------------------------------------------
 __device__ void rebuild_planes(const DevProblem& p) {
   const int R = p.R, W = p.W;
@@ -237,7 +239,8 @@ __device__ void rebuild_planes(const DevProblem& p) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_exchange(DevProblem p, uint64_t e, int flags) {
+__global__ void __launch_bounds__(kThreads) k_exchange(DevProblem p, uint64_t e, int flags,
+                                                       uint64_t t) {
   const int R = p.R, W = p.W;
   const int64_t L2 = (int64_t)p.L * p.L;
   if (flags & kStepEnergy) {
@@ -282,6 +285,15 @@ __global__ void __launch_bounds__(kThreads) k_exchange(DevProblem p, uint64_t e,
     __syncthreads();
     rebuild_planes(p);
   }
+  if (flags & kStepTrace) {
+    __syncthreads();
+    const int64_t row = (int64_t)((t - p.trace_t0) % (uint64_t)p.trace_cap);
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+      const int k = p.temp_of_slot[r];
+      p.trace_E[row * R + k] = p.E_slot[r];
+      p.trace_M[row * R + k] = p.M_slot[r];
+    }
+  }
 }
 
 int grid_x_for(int nwords, int W, int sms, int per_sm) {
@@ -321,8 +333,9 @@ cudaError_t launch_energy(const DevProblem& p, const DeviceInfo& dev, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_exchange(const DevProblem& p, uint64_t e, int flags, cudaStream_t st) {
-  k_exchange<<<1, kThreads, 0, st>>>(p, e, flags);
+cudaError_t launch_exchange(const DevProblem& p, uint64_t e, int flags, cudaStream_t st,
+                            uint64_t t) {
+  k_exchange<<<1, kThreads, 0, st>>>(p, e, flags, t);
   return cudaGetLastError();
 }
 

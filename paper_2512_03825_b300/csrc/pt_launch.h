@@ -18,12 +18,14 @@ enum StepFlags : int {
   kStepEnergy = 1,    // turn the accumulated counts into E_slot / M_slot and clear them
   kStepExchange = 2,  // one swap iteration
   kStepRebuild = 4,   // refresh the per-plane thresholds
+  kStepTrace = 8,     // append the trace row of sweep t (after the other steps)
 };
 
 cudaError_t launch_init(const DevProblem& p, const DeviceInfo& dev, cudaStream_t st);
 cudaError_t launch_half_sweep(const DevProblem& p, const DeviceInfo& dev, int colour,
                               uint64_t t, cudaStream_t st);
 cudaError_t launch_energy(const DevProblem& p, const DeviceInfo& dev, cudaStream_t st);
-cudaError_t launch_exchange(const DevProblem& p, uint64_t e, int flags, cudaStream_t st);
+cudaError_t launch_exchange(const DevProblem& p, uint64_t e, int flags, cudaStream_t st,
+                            uint64_t t = 0);
 
 }  // namespace ptb

@@ -15,8 +15,9 @@
 // the barrier EVERY CTA computes the same swap iteration from the complete counts, on its own
 // shared-memory copy of the temperature map, and rebuilds its plane's thresholds. Only block 0
 // writes the swap statistics; the maps and the plane tables go back to global memory at the
-// end of the launch. Two count buffers alternate by swap index: block 0 clears the one of the
-// next exchange while the current one is being read.
+// end of the launch. When an observable trace is on, every sweep counts, and block 0 writes
+// the sweep's row. Two count buffers alternate between counted sweeps: block 0 clears the
+// other one while the current one is being read.
 //
 // The barrier counter and both count buffers are cleared by the host before each launch.
 // A barrier wait that exceeds its time limit stores PT_ETIMEOUT in the status word; every
@@ -159,14 +160,14 @@ __device__ void exchange_local(const DevProblem& p, uint64_t e, const uint32_t* 
 
 // One half sweep over this thread's words of colour `colour` of plane w. With COUNT, the
 // new colour-1 words' anti-aligned neighbours (every bond has exactly one colour-1 end) and,
-// in the generic case, the up spins of the colour-1 word and of the colour-0 word one row up
-// (a one-to-one pairing of the colours) are added to U / N.
+// with `ones` (always in the generic case), the up spins of the colour-1 word and of the
+// colour-0 word one row up (a one-to-one pairing of the colours) are added to U / N.
 template <int MODE, bool COUNT>
 __device__ __forceinline__ void half_pass(const DevProblem& p, int w, int colour, uint64_t t,
                                           const RoundKeys& rk, const BlockTerms& bt, int q0,
                                           int step, int y0, int i0, int dy, int di,
                                           const uint4* thr, uint32_t alw0, uint32_t alw1,
-                                          uint32_t used, const PlaneGeneric& gen,
+                                          uint32_t used, const PlaneGeneric& gen, bool ones,
                                           BitCounter<15, 10>& U, BitCounter<15, 10>& N) {
   const uint32_t c3 = kTagSpin | ((uint32_t)(t >> 32) << 8);
   const int L = p.L, half = L >> 1;
@@ -197,7 +198,7 @@ __device__ __forceinline__ void half_pass(const DevProblem& p, int w, int colour
     if (COUNT) {
       const NbCount k = count4(ns ^ n0, ns ^ n1, ns ^ n2, ns ^ n3);
       U.add3(k.b0, k.b1, k.b2);
-      if (MODE != kModeFerro) N.add2(ns ^ n0, ns & n0);
+      if (MODE != kModeFerro || ones) N.add2(ns ^ n0, ns & n0);
     }
     i += di;
     y += dy;
@@ -251,6 +252,8 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
   };
   load_plane();
 
+  const bool trace = p.trace_E != nullptr;
+  unsigned counted = 0;  // sweeps counted so far in this launch
   unsigned target = 0;
   uint64_t e = a.e0;
   bool exchanged = false;
@@ -260,25 +263,27 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
     block_terms((uint32_t)(8 * w), (uint32_t)t, a.rk, bt);
     BitCounter<15, 10> U, N;
     half_pass<MODE, false>(p, w, 0, t, a.rk, bt, q0, step, y0, i0, dy, di, thr, alw0, alw1,
-                           used, gen, U, N);
+                           used, gen, false, U, N);
     target += gridDim.x + (j == 0 ? (unsigned)a.stall : 0u);
     if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s)) return;
     const bool ex = a.m > 0 && (t + 1) % (uint64_t)a.m == 0;
-    if (!ex) {
+    if (!ex && !trace) {
       half_pass<MODE, false>(p, w, 1, t, a.rk, bt, q0, step, y0, i0, dy, di, thr, alw0, alw1,
-                             used, gen, U, N);
+                             used, gen, false, U, N);
       if (j + 1 == a.n) break;  // the kernel's end orders this half sweep before what follows
       target += gridDim.x;
       if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s)) return;
       continue;
     }
-    uint32_t* const cb = cnt_base + (e & 1) * 2 * W * 32;
+    // a swap iteration or a trace row follows: count this sweep into buffer `counted & 1`
+    // (the buffers alternate between counted sweeps)
+    uint32_t* const cb = cnt_base + (counted & 1) * 2 * W * 32;
     U.zero();
     N.zero();
     half_pass<MODE, true>(p, w, 1, t, a.rk, bt, q0, step, y0, i0, dy, di, thr, alw0, alw1,
-                          used, gen, U, N);
+                          used, gen, trace, U, N);
     const uint32_t u = U.warp_total_for_lane();
-    const uint32_t nn = MODE == kModeFerro ? 0u : N.warp_total_for_lane();
+    const uint32_t nn = (MODE == kModeFerro && !trace) ? 0u : N.warp_total_for_lane();
     if (threadIdx.x < 64) (&acc[0][0])[threadIdx.x] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -291,16 +296,29 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
     }
     target += gridDim.x;
     if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s)) return;
-    exchange_local(p, e, cb, sot, tos, blockIdx.x == 0);
+    if (ex) exchange_local(p, e, cb, sot, tos, blockIdx.x == 0);
     if (blockIdx.x == 0) {
-      // the other buffer was last read in the previous swap iteration, before this sweep's
-      // first barrier; it is next written after the next sweep's first barrier
-      uint32_t* const nb = cnt_base + ((e + 1) & 1) * 2 * W * 32;
+      if (trace) {
+        // the trace row of sweep t, by temperature index after its swap iteration
+        const int64_t L2 = (int64_t)p.L * p.L;
+        const int64_t row = (int64_t)((t - p.trace_t0) % (uint64_t)p.trace_cap);
+        for (int r = threadIdx.x; r < R; r += blockDim.x) {
+          const int64_t U_r = __ldcg(cb + r), ones = __ldcg(cb + W * 32 + r);
+          p.trace_E[row * R + tos[r]] = slot_energy(p, L2, U_r, ones);
+          p.trace_M[row * R + tos[r]] = 2 * ones - L2;
+        }
+      }
+      // the other buffer was last read after the previous counted sweep, before this
+      // sweep's first barrier; it is next written after the next sweep's first barrier
+      uint32_t* const nb = cnt_base + ((counted + 1) & 1) * 2 * W * 32;
       for (int q = threadIdx.x; q < 2 * W * 32; q += blockDim.x) nb[q] = 0;
     }
-    load_plane();
-    e += 1;
-    exchanged = true;
+    ++counted;
+    if (ex) {
+      load_plane();
+      e += 1;
+      exchanged = true;
+    }
   }
 
   if (exchanged) {

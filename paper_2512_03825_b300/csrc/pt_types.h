@@ -66,6 +66,13 @@ struct DevProblem {
   const SwapPair* pairs;   // [max(R-1, 1)]
   const uint32_t* swap_table;
   int32_t* status;         // device error word (0 = fine)
+  // observable trace (null when off): after sweep t (and its swap iteration), row
+  // (t - trace_t0) % trace_cap of trace_E / trace_M [trace_cap][R] holds E_int and M of
+  // every temperature index
+  int64_t* trace_E;
+  int64_t* trace_M;
+  int64_t trace_cap;
+  uint64_t trace_t0;
 };
 
 }  // namespace ptb
