@@ -328,6 +328,9 @@ def run_ours(args, rank, world, local):
         out["single_L1024_R64"] = bench_single(stream, sms, clock_mhz)
         out["single_L128_R32"] = bench_single(stream, sms, clock_mhz, "L128_R32", 2000)
         out["single_L16_R8"] = bench_single(stream, sms, clock_mhz, "L16_R8", 1000)
+        from paper_2512_03825_b300 import workloads as W
+        out["paper_L300_R1500"] = bench_single(stream, sms, clock_mhz, sweeps=300,
+                                               prob=W.paper_problem())
         out["e2e"] = bench_e2e(probs, args.sweeps, stream, world)
         out["cpu_baseline"] = cpu_baseline_sample(probs)
     elif not args.quick:
@@ -392,12 +395,12 @@ def bench_plain_sample(probs, stream, n_problems=32, sweeps=200):
             "launches_strategy": out["launches"]}
 
 
-def bench_single(stream, sms, clock_mhz, name="L1024_R64", sweeps=200):
+def bench_single(stream, sms, clock_mhz, name="L1024_R64", sweeps=200, prob=None):
     """One single-problem config on the plain path (pt_sweep, default strategy)."""
     import torch
     from paper_2512_03825_b300 import api
     from paper_2512_03825_b300 import workloads as W
-    p = W.SINGLE[name]
+    p = prob if prob is not None else W.SINGLE[name]
     h = api.PTProblem(p.L, p.betas, seed=p.seed, stream=stream)
     h.sweep(10, p.every)
     torch.cuda.synchronize()

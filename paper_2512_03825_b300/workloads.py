@@ -70,6 +70,16 @@ SINGLE = {
                          sweeps=1000, every=5),
 }
 
+
+def paper_problem(R: int = 1500, sweeps: int = 300_000, every: int = 100) -> Problem:
+    """The paper's own workload (Sec. 4): a 300 x 300 lattice, J = 1, B = 0, temperatures
+    T_i = 1 + 3 i / |R| for up to 1500 replicas, 300,000 iterations per replica, swaps every
+    0 / 100 / 1k / 10k iterations. Read with one iteration = one sweep of the lattice (our
+    update unit), the run is 300,000 sweeps with a swap iteration every 100 sweeps. Seed
+    0x5EED0006."""
+    return Problem(L=300, betas=paper_ladder(R), seed=0x5EED0006, sweeps=sweeps, every=every)
+
+
 BATCH_SIZES = (32, 48, 64, 96, 128, 256)
 
 
