@@ -37,6 +37,12 @@ def lib():
         L.oracle_create.argtypes = [C.c_int, C.POINTER(C.c_double), C.c_int, C.c_double,
                                     C.c_double, C.c_uint64, C.POINTER(P)]
         L.oracle_create.restype = C.c_int
+        L.oracle_create_ex.argtypes = [C.c_int, C.POINTER(C.c_double), C.c_int, C.c_double,
+                                       C.c_double, C.c_uint64, C.c_int, C.POINTER(P)]
+        L.oracle_create_ex.restype = C.c_int
+        L.oracle_swap_threshold_metropolis.argtypes = [C.c_double, C.c_double, C.c_int64,
+                                                       C.c_int64]
+        L.oracle_swap_threshold_metropolis.restype = C.c_uint64
         L.oracle_destroy.argtypes = [P]
         L.oracle_destroy.restype = None
         L.oracle_sweep.argtypes = [P, C.c_int64, C.c_int]
@@ -99,9 +105,14 @@ def spin_threshold(beta, dE_int, s):
     return int(lib().oracle_spin_threshold(float(beta), int(dE_int), int(s)))
 
 
-def swap_threshold(beta_lo, beta_hi, n, s):
-    """Replica-exchange threshold S in [0, 2^32] (accept iff u < S)."""
-    return int(lib().oracle_swap_threshold(float(beta_lo), float(beta_hi), int(n), int(s)))
+SWAP_BARKER, SWAP_METROPOLIS = 0, 1
+
+
+def swap_threshold(beta_lo, beta_hi, n, s, rule=SWAP_BARKER):
+    """Replica-exchange threshold S in [0, 2^32] (accept iff u < S), Barker or Metropolis."""
+    f = lib().oracle_swap_threshold_metropolis if rule == SWAP_METROPOLIS \
+        else lib().oracle_swap_threshold
+    return int(f(float(beta_lo), float(beta_hi), int(n), int(s)))
 
 
 def set_threads(n):
@@ -115,14 +126,15 @@ def get_threads():
 class OracleProblem:
     """One PT problem held by the oracle: int8 spins [R][L][L], temperature-indexed."""
 
-    def __init__(self, L, betas, J=1.0, h=0.0, seed=0):
+    def __init__(self, L, betas, J=1.0, h=0.0, seed=0, swap_rule=SWAP_BARKER):
         b = np.ascontiguousarray(betas, dtype=np.float64)
         h_ = C.c_void_p()
-        rc = lib().oracle_create(int(L), _ptr(b, C.c_double), int(b.size), float(J), float(h),
-                                 int(seed) & 0xFFFFFFFFFFFFFFFF, C.byref(h_))
+        rc = lib().oracle_create_ex(int(L), _ptr(b, C.c_double), int(b.size), float(J),
+                                    float(h), int(seed) & 0xFFFFFFFFFFFFFFFF, int(swap_rule),
+                                    C.byref(h_))
         if rc != 0:
-            raise ValueError("oracle_create failed (%d) for L=%r R=%r J=%r h=%r"
-                             % (rc, L, b.size, J, h))
+            raise ValueError("oracle_create failed (%d) for L=%r R=%r J=%r h=%r rule=%r"
+                             % (rc, L, b.size, J, h, swap_rule))
         self._h = h_
         self.L, self.R = int(L), int(b.size)
         self.betas = b.copy()

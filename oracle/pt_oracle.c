@@ -118,10 +118,26 @@ uint64_t oracle_swap_threshold(double beta_lo, double beta_hi, int64_t n, int64_
     return (uint64_t)floor(4294967296.0 / (1.0 + exp(y)));
 }
 
+/* The Metropolis-form swap probability min(1, e^{x}) = min(1, e^{-y}), the option next to the
+ * Barker form (the paper's rule is Barker; Metropolis is the usual alternative in the
+ * parallel-tempering literature). Accept iff u < S: S = 2^32 for y <= 0, 0 for y > 44, and
+ * floor(2^32 * exp(-y)) in between. Returned in [0, 2^32]. */
+uint64_t oracle_swap_threshold_metropolis(double beta_lo, double beta_hi, int64_t n,
+                                          int64_t s) {
+    double y = ((beta_hi - beta_lo) * (double)n) / (double)s;
+    if (y <= 0.0) return 4294967296ull;
+    if (y > 44.0) return 0;
+    return (uint64_t)floor(4294967296.0 * exp(-y));
+}
+
+#define ORACLE_SWAP_BARKER 0
+#define ORACLE_SWAP_METROPOLIS 1
+
 /* --------------------------------------------------------------------------------------- */
 
 typedef struct oracle_pt {
     int L, R;
+    int swap_rule;    /* ORACLE_SWAP_BARKER or ORACLE_SWAP_METROPOLIS */
     double* beta;     /* [R], by temperature index */
     int64_t s, J_int, h_int;
     uint64_t seed;
@@ -148,16 +164,18 @@ void oracle_destroy(oracle_pt* p) {
 
 /* Initialisation phase (Sec. 3: build the data structures): every spin of every replica is
  * drawn uniformly from {-1, +1} with the TAG_INIT stream; slot r starts at temperature r. */
-int oracle_create(int L, const double* betas, int R, double J, double h, uint64_t seed,
-                  oracle_pt** out) {
+int oracle_create_ex(int L, const double* betas, int R, double J, double h, uint64_t seed,
+                     int swap_rule, oracle_pt** out) {
     *out = NULL;
     if (L < 4 || L > 16384 || (L & 1) || R < 1 || R > 2048 || !betas) return ORACLE_EINVAL;
+    if (swap_rule != ORACLE_SWAP_BARKER && swap_rule != ORACLE_SWAP_METROPOLIS)
+        return ORACLE_EINVAL;
     for (int k = 0; k < R; ++k)
         if (!isfinite(betas[k]) || betas[k] < 0.0) return ORACLE_EINVAL;
     oracle_pt* p = (oracle_pt*)calloc(1, sizeof(oracle_pt));
     if (!p) return ORACLE_ENOMEM;
     if (oracle_quantise(J, h, &p->s, &p->J_int, &p->h_int) != ORACLE_OK) { free(p); return ORACLE_EINVAL; }
-    p->L = L; p->R = R; p->seed = seed;
+    p->L = L; p->R = R; p->seed = seed; p->swap_rule = swap_rule;
     p->beta = (double*)malloc(sizeof(double) * R);
     p->spin = (int8_t*)malloc((size_t)R * L * L);
     p->temp_of_slot = (int32_t*)malloc(sizeof(int32_t) * R);
@@ -182,6 +200,11 @@ int oracle_create(int L, const double* betas, int R, double J, double h, uint64_
     }
     *out = p;
     return ORACLE_OK;
+}
+
+int oracle_create(int L, const double* betas, int R, double J, double h, uint64_t seed,
+                  oracle_pt** out) {
+    return oracle_create_ex(L, betas, R, J, h, seed, ORACLE_SWAP_BARKER, out);
 }
 
 /* Eq. 3 in integers: E_int = h_int * sum_i sigma_i - J_int * sum_<ij> sigma_i sigma_j, each of
@@ -266,7 +289,9 @@ static void exchange_once(oracle_pt* p) {
     int parity = (int)(p->e & 1);
     for (int k = parity; k + 1 < R; k += 2) {
         int64_t n = oracle_energy_int(p, k) - oracle_energy_int(p, k + 1);
-        uint64_t S = oracle_swap_threshold(p->beta[k], p->beta[k + 1], n, p->s);
+        uint64_t S = p->swap_rule == ORACLE_SWAP_METROPOLIS
+                         ? oracle_swap_threshold_metropolis(p->beta[k], p->beta[k + 1], n, p->s)
+                         : oracle_swap_threshold(p->beta[k], p->beta[k + 1], n, p->s);
         uint32_t u = philox_word(p->seed, (uint32_t)k, (uint32_t)p->e, 0u,
                                  TAG_EXCH | ((uint32_t)(p->e >> 32) << 8), 0);
         p->attempted[k] += 1;

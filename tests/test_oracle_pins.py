@@ -18,6 +18,55 @@ from tests.conftest import ROOT
 TWO32 = 1 << 32
 
 
+def test_swap_threshold_metropolis_values():
+    """The Metropolis-form option min(1, e^{-y}): exact values (40-digit arithmetic), the
+    detailed-balance ratio p(y) / p(-y) = e^{-y} that every valid swap rule has -- checked
+    against the Barker form's own ratio, so each formula pins the other -- and p >= Barker
+    pointwise."""
+    import mpmath
+    mpmath.mp.dps = 40
+    M = oracle.SWAP_METROPOLIS
+    rng = np.random.Generator(np.random.PCG64(7))
+    for _ in range(2000):
+        b0 = float(rng.uniform(0.0, 1.0))
+        b1 = b0 + float(rng.uniform(-0.1, 0.1))
+        s = int(rng.choice([1, 10]))
+        n = int(rng.integers(-3000, 3000))
+        y = mpmath.mpf(b1 - b0) * n / s
+        S = oracle.swap_threshold(b0, b1, n, s, M)
+        if y <= 0:
+            assert S == TWO32
+        elif y > 44:
+            assert S == 0
+        else:
+            exact = mpmath.mpf(TWO32) * mpmath.exp(-y)
+            assert S == int(mpmath.floor(exact)) or abs(exact - mpmath.nint(exact)) < 1e-5
+        assert S >= oracle.swap_threshold(b0, b1, n, s) - 1
+        if 0 < abs(y) < 8:  # thresholds above 1.4e6: the floor moves a ratio by < 1e-6
+            Sm = oracle.swap_threshold(b0, b1, -n, s, M)
+            Bp, Bm = oracle.swap_threshold(b0, b1, n, s), oracle.swap_threshold(b0, b1, -n, s)
+            ratio_m, ratio_b = S / Sm, Bp / Bm
+            assert abs(ratio_m / float(mpmath.exp(-y)) - 1) < 3e-6
+            assert abs(ratio_m / ratio_b - 1) < 3e-6
+    assert oracle.swap_threshold(0.4, 0.4, 12345, 1, M) == TWO32   # equal temperatures
+    assert oracle.swap_threshold(0.0, 1.0, 45, 1, M) == 0
+    assert oracle.swap_threshold(0.0, 1.0, -45, 1, M) == TWO32
+
+
+def test_swap_rule_selects_the_formula():
+    """A problem created with the Metropolis rule takes exactly the Metropolis decisions: at
+    equal temperatures every swap is accepted (y = 0), under Barker half of them."""
+    a = oracle.OracleProblem(6, [0.4] * 6, seed=31, swap_rule=oracle.SWAP_METROPOLIS)
+    a.sweep(200, 1)
+    att, acc = a.swap_stats()
+    assert (acc == att).all() and att.sum() > 0
+    b = oracle.OracleProblem(6, [0.4] * 6, seed=31)
+    b.sweep(200, 1)
+    assert b.swap_stats()[1].sum() < att.sum()
+    with pytest.raises(ValueError):
+        oracle.OracleProblem(6, [0.4] * 6, seed=31, swap_rule=2)
+
+
 # --------------------------------------------------------------------------------------
 # Philox4x32-10 vs PyTorch's own engine (ATen/core/PhiloxRNGEngine.h), built on the CPU
 # --------------------------------------------------------------------------------------

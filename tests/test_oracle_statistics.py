@@ -22,8 +22,9 @@ import oracle
 from tests import stats
 
 
-def _run_trace(L, betas, J, h, seed, burn, n, m, threads=4, start=None):
-    p = oracle.OracleProblem(L, betas, J=J, h=h, seed=seed)
+def _run_trace(L, betas, J, h, seed, burn, n, m, threads=4, start=None,
+               swap_rule=oracle.SWAP_BARKER):
+    p = oracle.OracleProblem(L, betas, J=J, h=h, seed=seed, swap_rule=swap_rule)
     if start is not None:
         for k in range(len(betas)):
             p.set_spins(k, start)
@@ -66,16 +67,18 @@ def test_4x4_exact_enumeration_field():
         assert abs(mM - ex["M"]) < 3 * seM, (beta, mM, ex["M"], seM)
 
 
-def test_4x4_swap_acceptance_matches_exact_expectation():
+@pytest.mark.parametrize("rule", [oracle.SWAP_BARKER, oracle.SWAP_METROPOLIS])
+def test_4x4_swap_acceptance_matches_exact_expectation(rule):
     """Acceptance of each adjacent pair vs E_{pi_k x pi_k+1}[S(y)] / 2^32 with the exact
-    energy distributions: this also checks the sign convention of y (a reversed sign gives
-    a different, larger rate whenever the two distributions differ)."""
+    energy distributions, for both swap rules: this also checks the sign convention of y (a
+    reversed sign gives a different, larger rate whenever the two distributions differ)."""
     L, J, h = 4, 1.0, 0.0
     betas = np.array([0.2, 0.3, 0.4, 0.5, 0.6])
     En, _ = stats.enumerate_lattice(L, J, h)
     levels, inv = np.unique(En, return_inverse=True)
     n_sweeps = 200_000
-    p, _, _ = _run_trace(L, betas, J, h, seed=0x5A5A, burn=1000, n=10, m=1, threads=1)
+    p, _, _ = _run_trace(L, betas, J, h, seed=0x5A5A, burn=1000, n=10, m=1, threads=1,
+                         swap_rule=rule)
     att0, acc0 = p.swap_stats()
     p.sweep(n_sweeps, 1)
     att, acc = p.swap_stats()
@@ -94,8 +97,9 @@ def test_4x4_swap_acceptance_matches_exact_expectation():
                 if w < 1e-14:
                     continue
                 n = int(round((Ea - Eb) * s))
-                expect += w * oracle.swap_threshold(betas[k], betas[k + 1], n, s) / 2.0 ** 32
-                wrong_sign += w * oracle.swap_threshold(betas[k], betas[k + 1], -n, s) / 2.0 ** 32
+                expect += w * oracle.swap_threshold(betas[k], betas[k + 1], n, s, rule) / 2.0 ** 32
+                wrong_sign += w * oracle.swap_threshold(betas[k], betas[k + 1], -n, s,
+                                                        rule) / 2.0 ** 32
         rate = acc[k] / att[k]
         # successive attempts are correlated through the chain: allow 3 SE of a binomial with
         # an effective sample size reduced tenfold
