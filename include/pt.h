@@ -82,6 +82,28 @@ typedef struct pt_problem pt_problem; /* opaque; owned by the library until pt_d
 int pt_create(int L, const double* betas, int R, double J, double h, uint64_t seed,
               pt_problem** out);
 
+/* Options of pt_create_ex. `size` is sizeof(pt_options) as the caller was compiled (fields
+ * past it keep their defaults), so later versions can add fields.
+ *   swap_rule  PT_SWAP_BARKER (default; the paper's rule, Sec. 3): accept with probability
+ *              e^x / (1 + e^x) = 1 / (1 + e^y), S(y) = floor(2^32 / (1 + exp(y))), 0 above
+ *              y = 44 and 2^32 below -44;
+ *              PT_SWAP_METROPOLIS (an option the paper does not use): accept with
+ *              probability min(1, e^x) = min(1, e^-y), S(y) = 2^32 for y <= 0, 0 above
+ *              y = 44, floor(2^32 * exp(-y)) in between.
+ *   (x, y, n and s as in the swap rule at the top of this file.) Both rules satisfy detailed
+ *   balance for the pair, p(y) / p(-y) = e^-y. */
+#define PT_SWAP_BARKER 0
+#define PT_SWAP_METROPOLIS 1
+typedef struct pt_options {
+  uint32_t size;
+  int32_t swap_rule;
+} pt_options;
+
+/* pt_create with options (NULL: the defaults of pt_create). PT_EINVAL for an unknown swap
+ * rule or a size outside 4..4096. */
+int pt_create_ex(int L, const double* betas, int R, double J, double h, uint64_t seed,
+                 const pt_options* opt, pt_problem** out);
+
 /* Release the problem and its device memory (synchronises its stream first). NULL is a
  * no-op. */
 void pt_destroy(pt_problem* p);
@@ -213,6 +235,30 @@ int pt_chain_map(pt_problem* p, int32_t* slot_of_temp);
 /* Sweeps and swap iterations done since pt_create (either pointer may be NULL). */
 int pt_counters(pt_problem* p, uint64_t* sweeps_done, uint64_t* exchanges_done);
 
+/* Checkpoints. pt_save writes the problem's whole sampler state into buf (host memory of
+ * at least pt_checkpoint_bytes(p) bytes; synchronises the stream); pt_load creates a new
+ * problem (on the current device, through the current allocator) that continues exactly as
+ * the saved one would have: same spins, temperature map, sweep and swap counters, swap
+ * statistics, seed, couplings and swap rule. A trace ring is not part of the state. The
+ * bytes, little-endian, no padding:
+ *   0   "PTCKPT01"          8 bytes
+ *   8   L, R                uint32 each
+ *   16  J, h                double each
+ *   32  seed, t, e          uint64 each (sweeps and swap iterations done)
+ *   56  swap rule, 0        int32 each
+ *   64  betas[R]            double
+ *       slot_of_temp[R]     int32 (a permutation)
+ *       attempted[R-1], accepted[R-1]   uint64
+ *       spins               uint32 [W][2][L][L/2], W = ceil(R/32): slot r is bit r % 32 of
+ *                           plane r / 32, bit set = +1, site (x, y) with colour c = (x+y) & 1
+ *                           in word ((w*2 + c)*L + y)*L/2 + x/2; bits of unused slots are 0
+ *       FNV-1a 64 of all bytes before it
+ * pt_load checks the size, magic, checksum and contents (PT_EINVAL) before it touches a
+ * device. */
+size_t pt_checkpoint_bytes(const pt_problem* p);
+int pt_save(pt_problem* p, void* buf, size_t bytes);
+int pt_load(const void* buf, size_t bytes, pt_problem** out);
+
 /* Observable traces: the per-sweep chain of energies and magnetisations at every
  * temperature (the "stored chains" of the paper's CPU programs, Sec. 5), kept on the device in a ring
  * of bounded size. After pt_trace_start(p, capacity) (1 <= capacity <= 2^32 rows), every sweep
@@ -269,6 +315,9 @@ uint64_t pt_spin_threshold(double beta, int64_t dE_int, int64_t s);
  * temperatures beta_lo (index k) and beta_hi (index k+1) and energy difference n. Computed
  * from the table the device uses. */
 uint64_t pt_swap_threshold(double beta_lo, double beta_hi, int64_t n, int64_t s);
+/* pt_swap_threshold for either swap rule (PT_SWAP_BARKER, PT_SWAP_METROPOLIS); all ones for
+ * an unknown rule. */
+uint64_t pt_swap_threshold_ex(double beta_lo, double beta_hi, int64_t n, int64_t s, int rule);
 
 /* Library version string. */
 const char* pt_version(void);

@@ -29,6 +29,15 @@ PT_SWEEP_PERSISTENT = 2
 PT_MAX_L = 16384
 PT_MAX_R = 2048
 
+PT_SWAP_BARKER = 0
+PT_SWAP_METROPOLIS = 1
+
+
+class PTOptions(C.Structure):
+    """struct pt_options of include/pt.h."""
+    _fields_ = [("size", C.c_uint32), ("swap_rule", C.c_int32)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
@@ -37,6 +46,8 @@ P = C.c_void_p
 SIGNATURES = [
     ("pt_create", C.c_int, [C.c_int, C.POINTER(C.c_double), C.c_int, C.c_double, C.c_double,
                             C.c_uint64, C.POINTER(P)]),
+    ("pt_create_ex", C.c_int, [C.c_int, C.POINTER(C.c_double), C.c_int, C.c_double,
+                               C.c_double, C.c_uint64, C.POINTER(PTOptions), C.POINTER(P)]),
     ("pt_destroy", None, [P]),
     ("pt_set_stream", C.c_int, [P, P]),
     ("pt_sweep", C.c_int, [P, C.c_int64, C.c_int]),
@@ -61,6 +72,9 @@ SIGNATURES = [
     ("pt_set_spins", C.c_int, [P, C.c_int, C.POINTER(C.c_int8)]),
     ("pt_chain_map", C.c_int, [P, C.POINTER(C.c_int32)]),
     ("pt_counters", C.c_int, [P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
+    ("pt_checkpoint_bytes", C.c_size_t, [P]),
+    ("pt_save", C.c_int, [P, C.c_void_p, C.c_size_t]),
+    ("pt_load", C.c_int, [C.c_void_p, C.c_size_t, C.POINTER(P)]),
     ("pt_trace_start", C.c_int, [P, C.c_int64]),
     ("pt_trace_stop", C.c_int, [P]),
     ("pt_trace_read", C.c_int, [P, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
@@ -76,6 +90,8 @@ SIGNATURES = [
                               C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     ("pt_spin_threshold", C.c_uint64, [C.c_double, C.c_int64, C.c_int64]),
     ("pt_swap_threshold", C.c_uint64, [C.c_double, C.c_double, C.c_int64, C.c_int64]),
+    ("pt_swap_threshold_ex", C.c_uint64, [C.c_double, C.c_double, C.c_int64, C.c_int64,
+                                          C.c_int]),
     ("pt_version", C.c_char_p, []),
 ]
 

@@ -10,7 +10,7 @@ from typing import Optional, Sequence
 
 import numpy as np
 
-from ._lib import ALLOC_FN, FREE_FN, check, lib
+from ._lib import ALLOC_FN, FREE_FN, PTOptions, check, lib
 
 
 def _dptr(a, ct):
@@ -22,17 +22,45 @@ class PTProblem:
     temperatures (inverse temperatures `betas`), coupling J and field h."""
 
     def __init__(self, L: int, betas: Sequence[float], J: float = 1.0, h: float = 0.0,
-                 seed: int = 0, stream=None):
+                 seed: int = 0, stream=None, swap_rule: int = 0, _handle=None):
         b = np.ascontiguousarray(betas, dtype=np.float64)
-        h_ = C.c_void_p()
-        check(lib.pt_create(int(L), _dptr(b, C.c_double), int(b.size), float(J), float(h),
-                            int(seed) & 0xFFFFFFFFFFFFFFFF, C.byref(h_)), "pt_create")
+        if _handle is None:
+            h_ = C.c_void_p()
+            opt = PTOptions(C.sizeof(PTOptions), int(swap_rule))
+            check(lib.pt_create_ex(int(L), _dptr(b, C.c_double), int(b.size), float(J),
+                                   float(h), int(seed) & 0xFFFFFFFFFFFFFFFF, C.byref(opt),
+                                   C.byref(h_)), "pt_create_ex")
+        else:
+            h_ = _handle
         self._h = h_
         self.L, self.R = int(L), int(b.size)
         self.betas = b.copy()
         self.J, self.h, self.seed = float(J), float(h), int(seed)
+        self.swap_rule = int(swap_rule)
         if stream is not None:
             self.set_stream(stream)
+
+    # -- checkpoints ---------------------------------------------------------------------
+    def save(self) -> bytes:
+        """The problem's whole sampler state as a checkpoint (format in include/pt.h)."""
+        n = int(lib.pt_checkpoint_bytes(self._h))
+        buf = C.create_string_buffer(n)
+        check(lib.pt_save(self._h, buf, n), "pt_save")
+        return buf.raw
+
+    @classmethod
+    def load(cls, data: bytes, stream=None) -> "PTProblem":
+        """A new problem that continues exactly from a checkpoint made by `save`."""
+        import struct
+        buf = C.create_string_buffer(bytes(data), len(data))
+        h_ = C.c_void_p()
+        check(lib.pt_load(buf, len(data), C.byref(h_)), "pt_load")
+        L, R = struct.unpack_from("<II", data, 8)
+        J, h = struct.unpack_from("<dd", data, 16)
+        seed, = struct.unpack_from("<Q", data, 32)
+        rule, = struct.unpack_from("<i", data, 56)
+        betas = np.frombuffer(data, np.float64, R, 64)
+        return cls(L, betas, J=J, h=h, seed=seed, stream=stream, swap_rule=rule, _handle=h_)
 
     # -- lifetime ------------------------------------------------------------------------
     def close(self):
@@ -192,6 +220,12 @@ def quantise(J, h):
 
 def spin_threshold(beta, dE_int, s):
     return int(lib.pt_spin_threshold(float(beta), int(dE_int), int(s)))
+
+
+def swap_threshold_rule(beta_lo, beta_hi, n, s, rule):
+    """The device's exchange threshold for either swap rule (0 Barker, 1 Metropolis)."""
+    return int(lib.pt_swap_threshold_ex(float(beta_lo), float(beta_hi), int(n), int(s),
+                                        int(rule)))
 
 
 def swap_threshold(beta_lo, beta_hi, n, s):

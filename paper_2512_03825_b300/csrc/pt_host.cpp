@@ -3,6 +3,7 @@
 // include/pt.h. All compute happens in the kernels; nothing here falls back to the CPU.
 #include <cuda_runtime.h>
 #include <stdarg.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -75,29 +76,35 @@ uint64_t spin_threshold(double beta, int64_t dE_int, int64_t s) {
   return (uint64_t)std::floor(4294967296.0 * std::exp(-x));
 }
 
-// Barker swap threshold of Sec. 3 with the +-44 cut-offs.
-uint64_t swap_rule(double beta_lo, double beta_hi, int64_t n, int64_t s) {
+// Swap threshold of Sec. 3: the paper's Barker form 1 / (1 + e^y) with the +-44 cut-offs,
+// or (option) the Metropolis form min(1, e^-y), y = (beta_hi - beta_lo) n / s.
+uint64_t swap_rule(double beta_lo, double beta_hi, int64_t n, int64_t s, int rule) {
   const double y = ((beta_hi - beta_lo) * (double)n) / (double)s;
+  if (rule == PT_SWAP_METROPOLIS) {
+    if (y <= 0.0) return kTwo32;
+    if (y > 44.0) return 0;
+    return (uint64_t)std::floor(4294967296.0 * std::exp(-y));
+  }
   if (y > 44.0) return 0;
   if (y < -44.0) return kTwo32;
   return (uint64_t)std::floor(4294967296.0 / (1.0 + std::exp(y)));
 }
 
 // The exchange threshold of one temperature pair as a function of n: constant below n_lo
-// and above n_hi, tabulated in between. S(n) is monotone in n (y is linear in n and the
-// Barker form is monotone in y), so the saturated ranges are found by bisection and then
-// checked at their edges.
+// and above n_hi, tabulated in between. S(n) is monotone in n (y is linear in n and both
+// forms are monotone in y), so the saturated ranges are found by bisection and then checked
+// at their edges.
 struct PairTable {
   int64_t n_lo = 1, n_hi = 0;
   uint64_t S_below = 0, S_above = 0;
   std::vector<uint32_t> vals;
 };
 
-int build_pair_table(double blo, double bhi, int64_t s, PairTable* out) {
+int build_pair_table(double blo, double bhi, int64_t s, int rule, PairTable* out) {
   PairTable t;
   const double d = bhi - blo;
   if (d == 0.0) {  // y = 0 for every n
-    t.S_below = t.S_above = swap_rule(blo, bhi, 0, s);
+    t.S_below = t.S_above = swap_rule(blo, bhi, 0, s, rule);
     *out = std::move(t);
     return PT_OK;
   }
@@ -105,20 +112,20 @@ int build_pair_table(double blo, double bhi, int64_t s, PairTable* out) {
   const double nmax = std::ceil(45.0 * (double)s / std::fabs(d)) + 2.0;
   if (nmax > 4.0e9) return fail(PT_EINVAL, "temperature pair too close: |dbeta| = %g", d);
   const int64_t N = (int64_t)nmax;
-  t.S_below = swap_rule(blo, bhi, -N, s);
-  t.S_above = swap_rule(blo, bhi, N, s);
+  t.S_below = swap_rule(blo, bhi, -N, s, rule);
+  t.S_above = swap_rule(blo, bhi, N, s, rule);
   // n_lo = smallest n with S(n) != S_below
   int64_t lo = -N, hi = N;  // S(lo) == S_below, search in (lo, hi]
   while (hi - lo > 1) {
     const int64_t mid = lo + (hi - lo) / 2;
-    if (swap_rule(blo, bhi, mid, s) != t.S_below) hi = mid; else lo = mid;
+    if (swap_rule(blo, bhi, mid, s, rule) != t.S_below) hi = mid; else lo = mid;
   }
   t.n_lo = hi;
   lo = -N;
   hi = N;  // largest n with S(n) != S_above: S(hi) == S_above, search in [lo, hi)
   while (hi - lo > 1) {
     const int64_t mid = lo + (hi - lo) / 2;
-    if (swap_rule(blo, bhi, mid, s) != t.S_above) lo = mid; else hi = mid;
+    if (swap_rule(blo, bhi, mid, s, rule) != t.S_above) lo = mid; else hi = mid;
   }
   t.n_hi = lo;
   if (t.n_hi < t.n_lo) return fail(PT_EINTERNAL, "empty exchange table");
@@ -126,7 +133,7 @@ int build_pair_table(double blo, double bhi, int64_t s, PairTable* out) {
   t.vals.resize((size_t)len);
   uint64_t prev = t.S_below;
   for (int64_t j = 0; j < len; ++j) {
-    const uint64_t v = swap_rule(blo, bhi, t.n_lo + j, s);
+    const uint64_t v = swap_rule(blo, bhi, t.n_lo + j, s, rule);
     if (v >= kTwo32) return fail(PT_EINTERNAL, "exchange table entry saturates inside");
     if ((d > 0 && v > prev) || (d < 0 && v < prev))
       return fail(PT_EINTERNAL, "exchange threshold not monotone at n = %lld",
@@ -134,19 +141,21 @@ int build_pair_table(double blo, double bhi, int64_t s, PairTable* out) {
     prev = v;
     t.vals[(size_t)j] = (uint32_t)v;
   }
-  if (swap_rule(blo, bhi, t.n_lo - 1, s) != t.S_below ||
-      swap_rule(blo, bhi, t.n_hi + 1, s) != t.S_above)
+  if (swap_rule(blo, bhi, t.n_lo - 1, s, rule) != t.S_below ||
+      swap_rule(blo, bhi, t.n_hi + 1, s, rule) != t.S_above)
     return fail(PT_EINTERNAL, "exchange table edges inconsistent");
   *out = std::move(t);
   return PT_OK;
 }
 
-// Tables depend only on (beta_lo, beta_hi, s); requests with the same ladder share them.
+// Tables depend only on (beta_lo, beta_hi, s, rule); requests with the same ladder share
+// them.
 struct PairKey {
   uint64_t blo, bhi;
   int64_t s;
+  int rule;
   bool operator<(const PairKey& o) const {
-    return std::tie(blo, bhi, s) < std::tie(o.blo, o.bhi, o.s);
+    return std::tie(blo, bhi, s, rule) < std::tie(o.blo, o.bhi, o.s, o.rule);
   }
 };
 std::mutex g_table_mu;
@@ -154,11 +163,13 @@ std::map<PairKey, std::shared_ptr<const PairTable>> g_tables;
 size_t g_table_bytes = 0;
 constexpr size_t kTableCacheCap = size_t(2) << 30;
 
-int get_pair_table(double blo, double bhi, int64_t s, std::shared_ptr<const PairTable>* out) {
+int get_pair_table(double blo, double bhi, int64_t s, int rule,
+                   std::shared_ptr<const PairTable>* out) {
   PairKey key;
   memcpy(&key.blo, &blo, 8);
   memcpy(&key.bhi, &bhi, 8);
   key.s = s;
+  key.rule = rule;
   {
     std::lock_guard<std::mutex> lk(g_table_mu);
     auto it = g_tables.find(key);
@@ -168,7 +179,7 @@ int get_pair_table(double blo, double bhi, int64_t s, std::shared_ptr<const Pair
     }
   }
   auto t = std::make_shared<PairTable>();
-  const int rc = build_pair_table(blo, bhi, s, t.get());
+  const int rc = build_pair_table(blo, bhi, s, rule, t.get());
   if (rc != PT_OK) return rc;
   std::lock_guard<std::mutex> lk(g_table_mu);
   if (g_table_bytes > kTableCacheCap) {
@@ -373,6 +384,56 @@ int read_observables(pt_problem* p, std::vector<int64_t>* E, std::vector<int64_t
 // =======================================================================================
 // C ABI
 // =======================================================================================
+// ---------------------------------------------------------------------------------------
+// Checkpoints (include/pt.h documents the byte layout)
+// ---------------------------------------------------------------------------------------
+namespace {
+
+constexpr char kCkptMagic[8] = {'P', 'T', 'C', 'K', 'P', 'T', '0', '1'};
+constexpr size_t kCkptHeader = 64;
+
+size_t ckpt_bytes(int L, int R) {
+  const int W = (R + 31) / 32;
+  const size_t pairs = (size_t)std::max(R - 1, 0);
+  return kCkptHeader + (size_t)R * 8 + (size_t)R * 4 + pairs * 16 + (size_t)W * L * L * 4 + 8;
+}
+
+// FNV-1a, 64 bit (Fowler, Noll, Vo)
+uint64_t fnv1a64(const uint8_t* p, size_t n) {
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+struct Writer {
+  uint8_t* p;
+  template <class T>
+  void put(const T& v) {
+    memcpy(p, &v, sizeof(T));
+    p += sizeof(T);
+  }
+  void put_bytes(const void* src, size_t n) {
+    memcpy(p, src, n);
+    p += n;
+  }
+};
+
+struct Reader {
+  const uint8_t* p;
+  template <class T>
+  T get() {
+    T v;
+    memcpy(&v, p, sizeof(T));
+    p += sizeof(T);
+    return v;
+  }
+};
+
+}  // namespace
+
 extern "C" {
 
 const char* pt_version(void) { return "libpt 0.1 (sm_103a)"; }
@@ -404,12 +465,17 @@ uint64_t pt_spin_threshold(double beta, int64_t dE_int, int64_t s) {
   return spin_threshold(beta, dE_int, s);
 }
 
-uint64_t pt_swap_threshold(double beta_lo, double beta_hi, int64_t n, int64_t s) {
+uint64_t pt_swap_threshold_ex(double beta_lo, double beta_hi, int64_t n, int64_t s, int rule) {
+  if (rule != PT_SWAP_BARKER && rule != PT_SWAP_METROPOLIS) return ~uint64_t(0);
   std::shared_ptr<const PairTable> t;
-  if (get_pair_table(beta_lo, beta_hi, s, &t) != PT_OK) return ~uint64_t(0);
+  if (get_pair_table(beta_lo, beta_hi, s, rule, &t) != PT_OK) return ~uint64_t(0);
   if (n < t->n_lo) return t->S_below;
   if (n > t->n_hi) return t->S_above;
   return t->vals[(size_t)(n - t->n_lo)];
+}
+
+uint64_t pt_swap_threshold(double beta_lo, double beta_hi, int64_t n, int64_t s) {
+  return pt_swap_threshold_ex(beta_lo, beta_hi, n, s, PT_SWAP_BARKER);
 }
 
 int pt_set_allocator(pt_alloc_fn alloc, pt_free_fn free_fn, void* ctx) {
@@ -428,7 +494,7 @@ size_t pt_estimate_device_bytes(int L, const double* betas, int R, double J, dou
   size_t entries = 0;
   for (int k = 0; k + 1 < R; ++k) {
     std::shared_ptr<const PairTable> t;
-    if (get_pair_table(betas[k], betas[k + 1], s, &t) != PT_OK) return 0;
+    if (get_pair_table(betas[k], betas[k + 1], s, PT_SWAP_BARKER, &t) != PT_OK) return 0;
     entries += t->vals.size();
   }
   const int W = (R + 31) / 32;
@@ -437,8 +503,22 @@ size_t pt_estimate_device_bytes(int L, const double* betas, int R, double J, dou
 
 int pt_create(int L, const double* betas, int R, double J, double h, uint64_t seed,
               pt_problem** out) {
+  return pt_create_ex(L, betas, R, J, h, seed, nullptr, out);
+}
+
+int pt_create_ex(int L, const double* betas, int R, double J, double h, uint64_t seed,
+                 const pt_options* opt, pt_problem** out) {
   if (!out) return fail(PT_EINVAL, "out is NULL");
   *out = nullptr;
+  int swap_rule_opt = PT_SWAP_BARKER;
+  if (opt) {
+    if (opt->size < sizeof(uint32_t) || opt->size > 4096)
+      return fail(PT_EINVAL, "pt_options.size = %u", opt->size);
+    if (opt->size >= offsetof(pt_options, swap_rule) + sizeof(int32_t))
+      swap_rule_opt = opt->swap_rule;
+    if (swap_rule_opt != PT_SWAP_BARKER && swap_rule_opt != PT_SWAP_METROPOLIS)
+      return fail(PT_EINVAL, "unknown swap rule %d", swap_rule_opt);
+  }
   int64_t s, Ji, hi;
   int rc = check_args(L, betas, R, J, h, &s, &Ji, &hi);
   if (rc) return rc;
@@ -458,6 +538,7 @@ int pt_create(int L, const double* betas, int R, double J, double h, uint64_t se
   p->J_int = Ji;
   p->h_int = hi;
   p->seed = seed;
+  p->swap_rule = swap_rule_opt;
   p->dev_info = dev;
   p->stream = 0;
 
@@ -483,7 +564,7 @@ int pt_create(int L, const double* betas, int R, double J, double h, uint64_t se
   size_t entries = 0;
   for (int k = 0; k + 1 < R; ++k) {
     std::shared_ptr<const PairTable> t;
-    rc = get_pair_table(betas[k], betas[k + 1], s, &t);
+    rc = get_pair_table(betas[k], betas[k + 1], s, swap_rule_opt, &t);
     if (rc) return rc;
     pairs[k].n_lo = t->n_lo;
     pairs[k].n_hi = t->n_hi;
@@ -778,6 +859,147 @@ int pt_counters(pt_problem* p, uint64_t* sweeps_done, uint64_t* exchanges_done) 
 }
 
 size_t pt_device_bytes(const pt_problem* p) { return p ? p->dbytes + p->trace_bytes : 0; }
+
+size_t pt_checkpoint_bytes(const pt_problem* p) { return p ? ckpt_bytes(p->L, p->R) : 0; }
+
+int pt_save(pt_problem* p, void* buf, size_t bytes) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  if (!buf) return fail(PT_EINVAL, "buf is NULL");
+  const size_t need = ckpt_bytes(p->L, p->R);
+  if (bytes < need) return fail(PT_EINVAL, "checkpoint needs %zu bytes, got %zu", need, bytes);
+  if ((rc = problem_device_guard(p))) return rc;
+  const int R = p->R, W = p->W;
+  const size_t pairs = (size_t)std::max(R - 1, 0);
+  std::vector<int32_t> sot((size_t)R);
+  std::vector<uint64_t> att(pairs), acc(pairs);
+  uint8_t* out = (uint8_t*)buf;
+  const size_t spin_off = kCkptHeader + (size_t)R * 12 + pairs * 16;
+  cudaError_t err = cudaMemcpyAsync(sot.data(), p->dev.slot_of_temp, (size_t)R * 4,
+                                    cudaMemcpyDeviceToHost, p->stream);
+  if (err == cudaSuccess && pairs) {
+    err = cudaMemcpyAsync(att.data(), p->dev.attempted, pairs * 8, cudaMemcpyDeviceToHost,
+                          p->stream);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(acc.data(), p->dev.accepted, pairs * 8, cudaMemcpyDeviceToHost,
+                            p->stream);
+  }
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(out + spin_off, p->dev.spins, (size_t)W * p->L * p->L * 4,
+                          cudaMemcpyDeviceToHost, p->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(p->stream);
+  if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "reading the checkpoint", err);
+  if ((rc = pt_synchronize(p))) return rc;
+  Writer w{out};
+  w.put_bytes(kCkptMagic, 8);
+  w.put((uint32_t)p->L);
+  w.put((uint32_t)p->R);
+  w.put(p->J);
+  w.put(p->h);
+  w.put(p->seed);
+  w.put(p->t);
+  w.put(p->e);
+  w.put((int32_t)p->swap_rule);
+  w.put((int32_t)0);
+  w.put_bytes(p->betas.data(), (size_t)R * 8);
+  w.put_bytes(sot.data(), (size_t)R * 4);
+  if (pairs) {
+    w.put_bytes(att.data(), pairs * 8);
+    w.put_bytes(acc.data(), pairs * 8);
+  }
+  const uint64_t sum = fnv1a64(out, need - 8);
+  memcpy(out + need - 8, &sum, 8);
+  return PT_OK;
+}
+
+int pt_load(const void* buf, size_t bytes, pt_problem** out) {
+  if (!out) return fail(PT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!buf || bytes < kCkptHeader + 8) return fail(PT_EINVAL, "checkpoint too short");
+  const uint8_t* in = (const uint8_t*)buf;
+  if (memcmp(in, kCkptMagic, 8) != 0) return fail(PT_EINVAL, "not a checkpoint (magic)");
+  Reader r{in + 8};
+  const uint32_t L = r.get<uint32_t>(), R = r.get<uint32_t>();
+  const double J = r.get<double>(), h = r.get<double>();
+  const uint64_t seed = r.get<uint64_t>(), t = r.get<uint64_t>(), e = r.get<uint64_t>();
+  const int32_t rule = r.get<int32_t>();
+  if (L < 4 || L > PT_MAX_L || (L & 1) || R < 1 || R > PT_MAX_R)
+    return fail(PT_EINVAL, "checkpoint with L = %u, R = %u", L, R);
+  const size_t need = ckpt_bytes((int)L, (int)R);
+  if (bytes != need) return fail(PT_EINVAL, "checkpoint of %zu bytes, expected %zu", bytes, need);
+  uint64_t sum;
+  memcpy(&sum, in + need - 8, 8);
+  if (sum != fnv1a64(in, need - 8)) return fail(PT_EINVAL, "checkpoint checksum mismatch");
+  if (rule != PT_SWAP_BARKER && rule != PT_SWAP_METROPOLIS)
+    return fail(PT_EINVAL, "checkpoint with swap rule %d", rule);
+  const int W = ((int)R + 31) / 32;
+  const size_t pairs = (size_t)R - 1;
+  std::vector<double> betas(R);
+  std::vector<int32_t> sot(R);
+  std::vector<uint64_t> att(pairs), acc(pairs);
+  const uint8_t* q = in + kCkptHeader;
+  memcpy(betas.data(), q, (size_t)R * 8);
+  q += (size_t)R * 8;
+  memcpy(sot.data(), q, (size_t)R * 4);
+  q += (size_t)R * 4;
+  if (pairs) {
+    memcpy(att.data(), q, pairs * 8);
+    memcpy(acc.data(), q + pairs * 8, pairs * 8);
+  }
+  q += pairs * 16;
+  // the map must be a permutation; the counters consistent
+  std::vector<int32_t> tos(R, -1);
+  for (uint32_t k = 0; k < R; ++k) {
+    if (sot[k] < 0 || sot[k] >= (int32_t)R || tos[sot[k]] >= 0)
+      return fail(PT_EINVAL, "checkpoint temperature map is not a permutation");
+    tos[sot[k]] = (int32_t)k;
+  }
+  for (size_t k = 0; k < pairs; ++k)
+    if (acc[k] > att[k]) return fail(PT_EINVAL, "checkpoint pair %zu: accepted > attempted", k);
+  // unused bits of the last plane are zero
+  const int last = (int)R - 32 * (W - 1);
+  if (last < 32) {
+    const uint32_t unused = ~((1u << last) - 1u);
+    const size_t words = (size_t)L * L;
+    for (size_t i = 0; i < words; ++i) {
+      uint32_t v;
+      memcpy(&v, q + ((size_t)(W - 1) * words + i) * 4, 4);
+      if (v & unused) return fail(PT_EINVAL, "checkpoint sets bits of unused slots");
+    }
+  }
+  pt_options opt;
+  opt.size = sizeof opt;
+  opt.swap_rule = rule;
+  pt_problem* p = nullptr;
+  int rc = pt_create_ex((int)L, betas.data(), (int)R, J, h, seed, &opt, &p);
+  if (rc) return rc;
+  cudaError_t err = cudaMemcpyAsync(p->dev.spins, q, (size_t)W * L * L * 4,
+                                    cudaMemcpyHostToDevice, p->stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(p->dev.slot_of_temp, sot.data(), (size_t)R * 4,
+                          cudaMemcpyHostToDevice, p->stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(p->dev.temp_of_slot, tos.data(), (size_t)R * 4,
+                          cudaMemcpyHostToDevice, p->stream);
+  if (err == cudaSuccess && pairs) {
+    err = cudaMemcpyAsync(p->dev.attempted, att.data(), pairs * 8, cudaMemcpyHostToDevice,
+                          p->stream);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(p->dev.accepted, acc.data(), pairs * 8, cudaMemcpyHostToDevice,
+                            p->stream);
+  }
+  if (err == cudaSuccess) err = launch_exchange(p->dev, 0, kStepRebuild, p->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(p->stream);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    pt_destroy(p);
+    return fail(PT_ECUDA, "restoring the checkpoint: %s", cudaGetErrorString(err));
+  }
+  p->t = t;
+  p->e = e;
+  *out = p;
+  return PT_OK;
+}
 
 int pt_trace_start(pt_problem* p, int64_t capacity) {
   int rc = problem_check(p);

@@ -15,6 +15,7 @@ struct pt_problem {
   double J = 0, h = 0;
   int64_t s = 1, J_int = 0, h_int = 0;
   uint64_t seed = 0;
+  int swap_rule = PT_SWAP_BARKER;
   uint64_t t = 0, e = 0;  // sweeps and swap iterations enqueued so far
   cudaStream_t stream = 0;
   void* dmem = nullptr;   // the problem's single device allocation

@@ -123,3 +123,75 @@ def test_allocator_hooks_are_kept_alive(pt):
     api.use_torch_allocator(True)
     assert first in api._all_hooks
     api.use_torch_allocator(False)
+
+
+@pytest.mark.parametrize("blo,bhi,s", [(0.30, 0.30 + 0.25 / 31, 1), (0.5, 0.4, 1), (0.4, 0.4, 1),
+                                       (0.2, 0.6, 1), (1.0, 0.2, 10)])
+def test_metropolis_swap_table_equals_oracle(pt, blo, bhi, s):
+    """The host tables of the Metropolis swap option give the oracle's threshold for every n
+    around and far outside the range where they are tabulated."""
+    from paper_2512_03825_b300 import api
+    d = bhi - blo
+    N = int(np.ceil(46.0 * s / abs(d))) if d else 50
+    ns = list(range(-N, N + 1, max(1, N // 20000))) + [10 ** 9, -10 ** 9, 0, 1, -1]
+    for n in ns:
+        assert api.swap_threshold_rule(blo, bhi, n, s, 1) == \
+            oracle.swap_threshold(blo, bhi, n, s, oracle.SWAP_METROPOLIS), n
+        assert api.swap_threshold_rule(blo, bhi, n, s, 0) == oracle.swap_threshold(blo, bhi, n, s)
+    assert api.swap_threshold_rule(0.3, 0.4, 5, 1, 2) == (1 << 64) - 1
+
+
+def test_create_ex_rejects_bad_options(pt):
+    import ctypes as C
+    from paper_2512_03825_b300 import api
+    for rule in (2, -1):
+        with pytest.raises(pt.PTError) as ei:
+            api.PTProblem(8, [0.3, 0.4], swap_rule=rule)
+        assert ei.value.code == pt.PT_EINVAL
+    b = np.array([0.3, 0.4])
+    h = C.c_void_p()
+    opt = pt.PTOptions(2, 0)  # size too small
+    rc = pt.lib.pt_create_ex(8, b.ctypes.data_as(C.POINTER(C.c_double)), 2, 1.0, 0.0, 1,
+                             C.byref(opt), C.byref(h))
+    assert rc == pt.PT_EINVAL
+
+
+def _load_rc(pt, data):
+    import ctypes as C
+    buf = C.create_string_buffer(bytes(data), len(data))
+    h = C.c_void_p()
+    return pt.lib.pt_load(buf, len(data), C.byref(h))
+
+
+def test_load_validates_before_the_device(pt):
+    """pt_load checks the whole checkpoint on the host: a well-formed one gets past every
+    check to the device (PT_ENODEV here, no GPU); every kind of damage is PT_EINVAL."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from tests.helpers import checkpoint as ck
+    L, R = 6, 35
+    rng = np.random.Generator(np.random.PCG64(3))
+    betas = np.linspace(0.2, 0.6, R)
+    spins = np.where(rng.random((R, L, L)) < 0.5, 1, -1).astype(np.int8)
+    words = ck.spins_to_words(spins)
+    np.testing.assert_array_equal(ck.words_to_spins(words, R), spins)
+    sot = rng.permutation(R).astype(np.int32)
+    att = rng.integers(0, 100, R - 1).astype(np.uint64)
+    acc = (att // 2).astype(np.uint64)
+    good = ck.build(L, betas, 1.0, 0.0, 7, 40, 13, 1, sot, att, acc, words)
+    assert ck.parse(good)["t"] == 40
+    assert _load_rc(pt, good) == pt.PT_ENODEV
+    bad = []
+    bad.append(b"XTCKPT01" + good[8:])                                       # magic
+    bad.append(good[:-1])                                                    # size
+    b = bytearray(good); b[100] ^= 1; bad.append(bytes(b))                   # checksum
+    bad.append(ck.build(L, betas, 1.0, 0.0, 7, 40, 13, 1, np.zeros(R, np.int32), att, acc,
+                        words))                                              # not a permutation
+    bad.append(ck.build(L, betas, 1.0, 0.0, 7, 40, 13, 1, sot, att, att + 1, words))  # acc > att
+    w2 = words.copy(); w2[1, 0, 0, 0] |= 1 << 31
+    bad.append(ck.build(L, betas, 1.0, 0.0, 7, 40, 13, 1, sot, att, acc, w2))  # unused slot bit
+    bad.append(ck.build(L, betas, 1.0, 0.0, 7, 40, 13, 5, sot, att, acc, words))  # swap rule
+    bad.append(ck.build(5, betas, 1.0, 0.0, 7, 40, 13, 1, sot, att, acc, words))  # odd L
+    for k, data in enumerate(bad):
+        assert _load_rc(pt, data) == pt.PT_EINVAL, k
