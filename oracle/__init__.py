@@ -54,6 +54,12 @@ def lib():
         L.oracle_energy_int.restype = C.c_int64
         L.oracle_magnetisation.argtypes = [P, C.c_int]
         L.oracle_magnetisation.restype = C.c_int64
+        L.oracle_flip.argtypes = [P, C.c_int64, C.c_int]
+        L.oracle_flip.restype = C.c_int
+        L.oracle_iterations.argtypes = [P]
+        L.oracle_iterations.restype = C.c_uint64
+        L.oracle_set_iterations.argtypes = [P, C.c_uint64]
+        L.oracle_set_iterations.restype = None
         L.oracle_scale.argtypes = [P]
         L.oracle_scale.restype = C.c_int64
         L.oracle_get_spins.argtypes = [P, C.c_int, C.POINTER(C.c_int8)]
@@ -149,6 +155,20 @@ class OracleProblem:
         rc = lib().oracle_sweep(self._h, int(n), int(exchange_every))
         if rc != 0:
             raise ValueError("oracle_sweep failed (%d)" % rc)
+
+    def flip(self, n, exchange_every=0):
+        """n single-spin-flip iterations of every replica (one random site each), a swap
+        iteration after every iteration count that is a multiple of exchange_every."""
+        rc = lib().oracle_flip(self._h, int(n), int(exchange_every))
+        if rc != 0:
+            raise ValueError("oracle_flip failed (%d)" % rc)
+
+    @property
+    def iterations(self):
+        return int(lib().oracle_iterations(self._h))
+
+    def set_iterations(self, it):
+        lib().oracle_set_iterations(self._h, int(it))
 
     def trace(self, n, exchange_every=0):
         """Run n sweeps; return (E_int[n][R], M[n][R]) recorded after each sweep."""

@@ -18,6 +18,8 @@
  *   initial spin  (site i, slot r):           ctr = {i, 0, r>>2, TAG_INIT}                word r&3, bit 31
  *   spin update   (site i, slot r, sweep t):  ctr = {i, lo32(t), r>>2, TAG_SPIN|hi32(t)<<8} word r&3
  *   exchange      (pair k, exchange e):       ctr = {k, lo32(e), 0, TAG_EXCH|hi32(e)<<8}   word 0
+ *   single flip   (slot r, iteration i):      ctr = {lo32(i), r, 0, TAG_FLIP|hi32(i)<<8}
+ *                 word 0 picks the site floor(u0 * L^2 / 2^32), word 1 decides acceptance
  * The paper fixes no generator; the counter layout is this framework's choice and the CUDA
  * library uses the same one. Nothing here is blocked, fused or reordered for speed.
  */
@@ -36,6 +38,7 @@
 #define TAG_SPIN 0u
 #define TAG_EXCH 1u
 #define TAG_INIT 2u
+#define TAG_FLIP 3u
 
 /* ---------------------------------------------------------------------------------------
  * Philox4x32-10, written from the definition in Salmon et al., "Parallel Random Numbers: As
@@ -145,6 +148,7 @@ typedef struct oracle_pt {
     int32_t* temp_of_slot;  /* [R] */
     int32_t* slot_of_temp;  /* [R] */
     uint64_t t, e;    /* sweeps done, exchanges done */
+    uint64_t it;      /* single-spin-flip iterations done */
     uint64_t* attempted; /* [R-1] */
     uint64_t* accepted;  /* [R-1] */
 } oracle_pt;
@@ -273,6 +277,28 @@ static void sweep_once(oracle_pt* p) {
     p->t += 1;
 }
 
+/* One single-spin-flip Metropolis iteration of the replica in slot r (Sec. 2.1: the trial
+ * state x_trial = g(x) flips one spin, chosen uniformly at random; it is accepted with
+ * probability min(1, e^{-beta Delta E}), Eq. 1): iteration i draws one Philox block, word 0
+ * selects site floor(u0 * L^2 / 2^32) (row-major, i = y L + x) and word 1 is the acceptance
+ * draw, compared with the same threshold as a sweep's trial. */
+static void metropolis_flip(oracle_pt* p, int r, uint64_t i) {
+    const int L = p->L;
+    const uint32_t c3 = TAG_FLIP | ((uint32_t)(i >> 32) << 8);
+    const uint32_t u0 = philox_word(p->seed, (uint32_t)i, (uint32_t)r, 0u, c3, 0);
+    const uint32_t u1 = philox_word(p->seed, (uint32_t)i, (uint32_t)r, 0u, c3, 1);
+    const uint64_t site = ((uint64_t)u0 * (uint64_t)L * (uint64_t)L) >> 32;
+    const int x = (int)(site % (uint64_t)L), y = (int)(site / (uint64_t)L);
+    int8_t* sp = lattice(p, r);
+    int s = sp[y * L + x];
+    int nb = sp[y * L + (x + 1) % L] + sp[y * L + (x + L - 1) % L] +
+             sp[((y + 1) % L) * L + x] + sp[((y + L - 1) % L) * L + x];
+    int64_t dE_int = 2 * (int64_t)s * (p->J_int * nb - p->h_int);
+    double beta = p->beta[p->temp_of_slot[r]];
+    if (dE_int <= 0 || (uint64_t)u1 < oracle_spin_threshold(beta, dE_int, p->s))
+        sp[y * L + x] = (int8_t)-s;
+}
+
 /* Exchange the configurations at temperatures k and k+1 by swapping their slots. */
 static void swap_temperatures(oracle_pt* p, int k) {
     int a = p->slot_of_temp[k], b = p->slot_of_temp[k + 1];
@@ -329,6 +355,27 @@ int oracle_trace(oracle_pt* p, int64_t n, int m, int64_t* E_out, int64_t* M_out)
     }
     return ORACLE_OK;
 }
+
+/* The paper's "iteration" read as one single-spin flip per replica: n iterations of every
+ * replica; after every iteration that leaves the iteration count a
+ * multiple of m (> 0), one swap iteration, the same as after sweeps and sharing their swap
+ * index e). The iteration index i counts iterations since creation, independently of
+ * sweeps. */
+int oracle_flip(oracle_pt* p, int64_t n, int m) {
+    if (!p || n < 0 || m < 0) return ORACLE_EINVAL;
+    for (int64_t j = 0; j < n; ++j) {
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(threads_wanted) schedule(static)
+#endif
+        for (int r = 0; r < p->R; ++r) metropolis_flip(p, r, p->it);
+        p->it += 1;
+        if (m > 0 && p->it % (uint64_t)m == 0) exchange_once(p);
+    }
+    return ORACLE_OK;
+}
+
+uint64_t oracle_iterations(const oracle_pt* p) { return p->it; }
+void oracle_set_iterations(oracle_pt* p, uint64_t it) { p->it = it; }
 
 int64_t oracle_scale(const oracle_pt* p) { return p->s; }
 
