@@ -154,6 +154,27 @@ int pt_set_wait_limit(pt_problem* p, double seconds);
  * described above. Applies to one launch. */
 int pt_debug_stall_barrier(pt_problem* p, int arrivals);
 
+/* The single-spin-flip variant: the paper's "iteration" (Sec. 2.1, the MH step whose trial
+ * state flips one spin) read as one Metropolis trial at one uniformly chosen site of every
+ * replica. n >= 0 iterations of every replica; after every iteration that leaves the
+ * iteration count (since pt_create) a multiple of exchange_every (> 0; 0 = none), one swap
+ * iteration exactly as after sweeps, sharing their swap index e. Iteration i of the replica
+ * in slot r draws u = Philox4x32-10(key = seed, ctr = {lo32(i), r, 0, 3 | hi32(i) << 8}):
+ * the site is floor(u.word0 * L^2 / 2^32) (i = y*L + x) and the trial, with dE_int and the
+ * threshold T of a sweep's trial, flips when u.word1 < T. One cooperative launch per call
+ * (one thread per replica; waits bounded as for PT_SWEEP_PERSISTENT); trace rows are not
+ * written. Asynchronous like pt_sweep. */
+int pt_flip(pt_problem* p, int64_t n, int exchange_every);
+
+/* How pt_flip runs (results never depend on it): shared_memory != 0 (the default) keeps the
+ * replicas of a block in shared memory as private bit arrays when k >= 1 of them (a power of
+ * two) fit one CTA and the blocks one resident wave, else the kernel reads and flips the
+ * shared spin words in global memory (atomic XOR per flip). */
+int pt_set_flip_tuning(pt_problem* p, int shared_memory);
+
+/* Single-spin-flip iterations done since pt_create. */
+int pt_iterations(pt_problem* p, uint64_t* iterations_done);
+
 /* Advance `count` problems together in one persistent kernel: problem j runs n[j] >= 0
  * sweeps with exchange_every[j] (same meaning as pt_sweep). All problems must be on the
  * same stream. Results are bit-identical to calling pt_sweep on each problem alone. */
@@ -239,14 +260,16 @@ int pt_counters(pt_problem* p, uint64_t* sweeps_done, uint64_t* exchanges_done);
  * at least pt_checkpoint_bytes(p) bytes; synchronises the stream); pt_load creates a new
  * problem (on the current device, through the current allocator) that continues exactly as
  * the saved one would have: same spins, temperature map, sweep and swap counters, swap
- * statistics, seed, couplings and swap rule. A trace ring is not part of the state. The
+ * statistics, single-flip iterations, seed, couplings and swap rule. A trace ring is not part
+ * of the state. The
  * bytes, little-endian, no padding:
- *   0   "PTCKPT01"          8 bytes
+ *   0   "PTCKPT02"          8 bytes
  *   8   L, R                uint32 each
  *   16  J, h                double each
  *   32  seed, t, e          uint64 each (sweeps and swap iterations done)
  *   56  swap rule, 0        int32 each
- *   64  betas[R]            double
+ *   64  it                  uint64 (single-spin-flip iterations done)
+ *   72  betas[R]            double
  *       slot_of_temp[R]     int32 (a permutation)
  *       attempted[R-1], accepted[R-1]   uint64
  *       spins               uint32 [W][2][L][L/2], W = ceil(R/32): slot r is bit r % 32 of

@@ -51,6 +51,9 @@ SIGNATURES = [
     ("pt_destroy", None, [P]),
     ("pt_set_stream", C.c_int, [P, P]),
     ("pt_sweep", C.c_int, [P, C.c_int64, C.c_int]),
+    ("pt_flip", C.c_int, [P, C.c_int64, C.c_int]),
+    ("pt_iterations", C.c_int, [P, C.POINTER(C.c_uint64)]),
+    ("pt_set_flip_tuning", C.c_int, [P, C.c_int]),
     ("pt_set_sweep_tuning", C.c_int, [P, C.c_int, C.c_int]),
     ("pt_get_sweep_tuning", C.c_int, [P, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                       C.POINTER(C.c_int)]),

@@ -59,7 +59,7 @@ class PTProblem:
         J, h = struct.unpack_from("<dd", data, 16)
         seed, = struct.unpack_from("<Q", data, 32)
         rule, = struct.unpack_from("<i", data, 56)
-        betas = np.frombuffer(data, np.float64, R, 64)
+        betas = np.frombuffer(data, np.float64, R, 72)
         return cls(L, betas, J=J, h=h, seed=seed, stream=stream, swap_rule=rule, _handle=h_)
 
     # -- lifetime ------------------------------------------------------------------------
@@ -90,6 +90,19 @@ class PTProblem:
 
     def synchronize(self):
         check(lib.pt_synchronize(self._h), "pt_synchronize")
+
+    def flip(self, n: int, exchange_every: int = 0):
+        """n single-spin-flip iterations of every replica (one random site each)."""
+        check(lib.pt_flip(self._h, int(n), int(exchange_every)), "pt_flip")
+
+    def set_flip_tuning(self, shared_memory: bool = True):
+        check(lib.pt_set_flip_tuning(self._h, int(bool(shared_memory))), "pt_set_flip_tuning")
+
+    @property
+    def iterations(self) -> int:
+        it = C.c_uint64()
+        check(lib.pt_iterations(self._h, C.byref(it)), "pt_iterations")
+        return it.value
 
     def trace_start(self, capacity: int):
         """Record (E_int, M) of every temperature after each later sweep, in a device ring of

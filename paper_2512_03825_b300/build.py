@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpt.so")
-SOURCES = ["pt_host.cpp", "pt_kernels.cu", "pt_batch.cu", "pt_flat.cu", "pt_persist.cu", "pt_flow.cu"]
+SOURCES = ["pt_host.cpp", "pt_kernels.cu", "pt_batch.cu", "pt_flat.cu", "pt_persist.cu", "pt_flow.cu", "pt_flip.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 

@@ -1,0 +1,370 @@
+// pt_flip.cu -- the single-spin-flip variant: the paper's "iteration" read as one Metropolis
+// trial at one uniformly chosen site of each replica (Sec. 2.1: the trial state flips one
+// spin; Eq. 1 accepts it), the scheme of the paper's own CUDA program, where one thread runs
+// one replica.
+//
+// One cooperative launch per pt_flip call; thread r runs the replica in slot r. Iteration i
+// draws one Philox block with the counters {lo32(i), r, 0, TAG_FLIP | hi32(i) << 8}: word 0
+// picks the site floor(u0 * L^2 / 2^32) (row-major), word 1 is compared with the threshold
+// of the trial's class (anti-aligned neighbours k, sign of the spin) at the slot's current
+// temperature -- the same integer thresholds as a sweep's trials. The 32 replicas of a
+// plane share each spin word, so a flip is an atomic XOR of the replica's bit, and every
+// spin word is read through L2. Each thread keeps its replica's E_int and M, updated by the
+// exact integer Delta E of every accepted flip.
+//
+// After every iteration that leaves the iteration count a multiple of m, all threads store
+// their energies, meet at a bounded grid barrier, and every CTA computes the same swap
+// iteration (Sec. 3) on its own copy of the temperature map; block 0 keeps the statistics.
+// The energies alternate between two buffers, so a fast CTA storing the next ones never
+// overwrites those another CTA still reads.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pt.h"
+#include "pt_device.cuh"
+#include "pt_flip.h"
+#include "pt_grid.cuh"
+
+namespace ptb {
+
+namespace {
+
+constexpr int kFlipThreads = 64;
+
+struct FlipArgs {
+  DevProblem p;
+  uint64_t it0, e0;
+  int64_t n;  // iterations in this launch
+  int m;      // swap iteration after every m-th iteration (0: never)
+  int stall;  // test support: the first barrier waits for this many CTAs more
+  uint64_t limit_ns;
+  RoundKeys rk;
+};
+
+// Swap iteration e from the slots' energies eb[R], on this CTA's copy of the maps; `owner`
+// also counts attempts and acceptances. All decisions first (their loads independent of one
+// another), then the swaps: a thread takes at most 32 pairs (R <= 2048, 32 threads).
+__device__ void exchange_energies(const DevProblem& p, uint64_t e, const int64_t* eb,
+                                  int32_t* sot, int32_t* tos, bool owner) {
+  const int R = p.R;
+  const int parity = (int)(e & 1);
+  const uint32_t c3 = kTagExch | ((uint32_t)(e >> 32) << 8);
+  const int stride = 2 * (int)blockDim.x;
+  uint32_t accepted = 0;  // bit q: pair parity + 2 * threadIdx.x + q * stride accepted
+#pragma unroll 4
+  for (int q = 0; q < 32; ++q) {
+    const int k = parity + 2 * (int)threadIdx.x + q * stride;
+    if (k + 1 < R) {
+      const int64_t n = __ldcg(eb + sot[k]) - __ldcg(eb + sot[k + 1]);
+      const SwapPair sp = p.pairs[k];
+      uint64_t S;
+      if (n < sp.n_lo)
+        S = sp.S_below;
+      else if (n > sp.n_hi)
+        S = sp.S_above;
+      else
+        S = p.swap_table[sp.offset + (n - sp.n_lo)];
+      const Philox4 rnd = philox4x32_10((uint32_t)k, (uint32_t)e, 0u, c3, p.key0, p.key1);
+      if ((uint64_t)rnd.x < S) accepted |= 1u << q;
+    }
+  }
+  __syncthreads();
+  for (int q = 0; q < 32; ++q) {
+    const int k = parity + 2 * (int)threadIdx.x + q * stride;
+    if (k + 1 >= R) break;
+    const bool accept = (accepted >> q) & 1u;
+    if (owner) {
+      p.attempted[k] += 1;
+      if (accept) p.accepted[k] += 1;
+    }
+    if (accept) {
+      const int a = sot[k], b = sot[k + 1];
+      sot[k] = b;
+      sot[k + 1] = a;
+      tos[a] = k + 1;
+      tos[b] = k;
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kFlipThreads) k_flip(const __grid_constant__ FlipArgs a) {
+  extern __shared__ int32_t map_s[];  // [R] slot_of_temp, then [R] temp_of_slot
+  __shared__ int ok_s;
+  const DevProblem& p = a.p;
+  const int R = p.R, L = p.L, half = L >> 1;
+  int32_t* sot = map_s;
+  int32_t* tos = map_s + R;
+  for (int q = threadIdx.x; q < R; q += blockDim.x) {
+    sot[q] = p.slot_of_temp[q];
+    tos[q] = p.temp_of_slot[q];
+  }
+  __syncthreads();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = r < R;
+  int64_t E = active ? p.E_slot[r] : 0, M = active ? p.M_slot[r] : 0;
+  const uint32_t bit = 1u << (r & 31);
+  uint32_t* const plane = p.spins + word_index(L, active ? (r >> 5) : 0, 0, 0, 0);
+  const uint64_t L2 = (uint64_t)L * (uint64_t)L;
+  int64_t* const ebuf = reinterpret_cast<int64_t*>(p.cnt + 2 * p.W * 32);  // [2][R]
+  unsigned* const bar = p.cnt + 6 * p.W * 32;
+  unsigned target = 0;
+  unsigned swaps = 0;
+  uint64_t e = a.e0;
+  // iterations until the next swap iteration (after every m-th iteration count)
+  int64_t left = a.m > 0 ? (int64_t)a.m - (int64_t)(a.it0 % (uint64_t)a.m) : 0;
+  for (int64_t j = 0; j < a.n; ++j) {
+    if (active) {
+      const uint64_t i = a.it0 + (uint64_t)j;
+      const Philox4 u = philox4x32_10_rk((uint32_t)i, (uint32_t)r, 0u,
+                                         kTagFlip | ((uint32_t)(i >> 32) << 8), a.rk);
+      const uint64_t site = ((uint64_t)u.x * L2) >> 32;
+      const int y = (int)(site / (uint64_t)L), x = (int)(site - (uint64_t)y * L);
+      const int c = (x + y) & 1;
+      const int xm = x == 0 ? L - 1 : x - 1, xp = x == L - 1 ? 0 : x + 1;
+      const int ym = y == 0 ? L - 1 : y - 1, yp = y == L - 1 ? 0 : y + 1;
+      uint32_t* const sw = plane + ((size_t)c * L + y) * half + (x >> 1);
+      const uint32_t* const oth = plane + (size_t)(c ^ 1) * L * half;
+      const uint32_t s0 = __ldcg(sw) & bit;
+      const int k = (((__ldcg(oth + (size_t)y * half + (xm >> 1)) & bit) ^ s0) != 0) +
+                    (((__ldcg(oth + (size_t)y * half + (xp >> 1)) & bit) ^ s0) != 0) +
+                    (((__ldcg(oth + (size_t)ym * half + (x >> 1)) & bit) ^ s0) != 0) +
+                    (((__ldcg(oth + (size_t)yp * half + (x >> 1)) & bit) ^ s0) != 0);
+      const int up = s0 != 0;
+      const uint64_t T = p.T_temp[(size_t)tos[r] * kClasses + 2 * k + up];
+      if ((uint64_t)u.y < T) {
+        atomicXor(sw, bit);
+        const int64_t sigma = up ? 1 : -1;
+        // Delta E_int = 2 sigma (J_int sum_nb - h_int), sigma sum_nb = 4 - 2k
+        E += 2 * (p.J_int * (4 - 2 * k) - p.h_int * sigma);
+        M -= 2 * sigma;
+      }
+    }
+    if (a.m > 0 && --left == 0) {
+      left = a.m;
+      int64_t* const eb = ebuf + (size_t)(swaps & 1) * R;
+      if (active) eb[r] = E;
+      target += gridDim.x + (swaps == 0 ? (unsigned)a.stall : 0u);
+      if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s)) return;
+      exchange_energies(p, e, eb, sot, tos, blockIdx.x == 0);
+      e += 1;
+      swaps += 1;
+    }
+  }
+  if (active) {
+    p.E_slot[r] = E;
+    p.M_slot[r] = M;
+  }
+  if (swaps > 0 && blockIdx.x == 0) {
+    for (int q = threadIdx.x; q < R; q += blockDim.x) {
+      p.slot_of_temp[q] = sot[q];
+      p.temp_of_slot[q] = tos[q];
+    }
+  }
+}
+
+// The same iterations with each replica's lattice in shared memory. A block of 256 threads
+// holds k replicas of one plane (k a power of two, so 32 / k blocks share a plane's words):
+// every replica is a row-major bit array of L^2 bits (bit y*L + x) that lane l < k of warp 0
+// reads and flips without atomics. All 256 threads load the arrays at the start, decide the
+// swap iterations and merge the arrays back into the plane words at the end (an XOR of
+// exactly the bits that changed, so the blocks sharing a word never interfere); warps 1-7
+// otherwise only meet warp 0 at the swap iterations.
+constexpr int kFlipSmemThreads = 256;
+
+__global__ void __launch_bounds__(kFlipSmemThreads) k_flip_smem(const __grid_constant__ FlipArgs a,
+                                                                int k_per_block,
+                                                                int words_per_rep) {
+  extern __shared__ uint32_t smem[];  // [R] slot_of_temp, [R] temp_of_slot, [k][words] bits
+  __shared__ int ok_s;
+  const DevProblem& p = a.p;
+  const int R = p.R, L = p.L, half = L >> 1;
+  int32_t* sot = reinterpret_cast<int32_t*>(smem);
+  int32_t* tos = sot + R;
+  uint32_t* const bits = smem + 2 * R;
+  const int tid = threadIdx.x;
+  for (int q = tid; q < R; q += blockDim.x) {
+    sot[q] = p.slot_of_temp[q];
+    tos[q] = p.temp_of_slot[q];
+  }
+  const int r0 = blockIdx.x * k_per_block;  // first slot of this block
+  const int kb = min(k_per_block, R - r0);  // replicas of this block
+  const int b0 = r0 & 31;                   // their first bit in the plane words
+  uint32_t* const plane = p.spins + word_index(L, r0 >> 5, 0, 0, 0);
+  const int nsites = L * L;
+  auto word_of = [&](int site) {
+    const int y = site / L, x = site - y * L;
+    return plane + ((size_t)((x + y) & 1) * L + y) * half + (x >> 1);
+  };
+  // bit-array word w of every replica: 32 sites, one plane word each
+  for (int w = tid; w < words_per_rep; w += blockDim.x) {
+    uint32_t pw[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) pw[j] = w * 32 + j < nsites ? *word_of(w * 32 + j) : 0u;
+    for (int l = 0; l < kb; ++l) {
+      uint32_t acc = 0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc |= ((pw[j] >> (b0 + l)) & 1u) << j;
+      bits[(size_t)l * words_per_rep + w] = acc;
+    }
+  }
+  __syncthreads();
+  int64_t* const ebuf = reinterpret_cast<int64_t*>(p.cnt + 2 * p.W * 32);  // [2][R]
+  unsigned* const bar = p.cnt + 6 * p.W * 32;
+  unsigned target = 0;
+  unsigned swaps = 0;
+  uint64_t e = a.e0;
+  const bool flips = tid < 32;           // warp 0 runs the iterations
+  const bool active = tid < kb;          // and its first kb lanes own a replica
+  const int r = r0 + tid;
+  int64_t E = active ? p.E_slot[r] : 0, M = active ? p.M_slot[r] : 0;
+  uint32_t* const mine = bits + (size_t)(active ? tid : 0) * words_per_rep;
+  const uint64_t L2 = (uint64_t)nsites;
+  auto swap_point = [&]() -> bool {
+    int64_t* const eb = ebuf + (size_t)(swaps & 1) * R;
+    if (active) eb[r] = E;
+    target += gridDim.x + (swaps == 0 ? (unsigned)a.stall : 0u);
+    if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s)) return false;
+    exchange_energies(p, e, eb, sot, tos, blockIdx.x == 0);
+    e += 1;
+    swaps += 1;
+    return true;
+  };
+  if (flips) {
+    // iterations until the next swap iteration (after every m-th iteration count)
+    int64_t left = a.m > 0 ? (int64_t)a.m - (int64_t)(a.it0 % (uint64_t)a.m) : 0;
+    for (int64_t j = 0; j < a.n; ++j) {
+      if (active) {
+        const uint64_t i = a.it0 + (uint64_t)j;
+        const Philox4 u = philox4x32_10_rk((uint32_t)i, (uint32_t)r, 0u,
+                                           kTagFlip | ((uint32_t)(i >> 32) << 8), a.rk);
+        const int site = (int)(((uint64_t)u.x * L2) >> 32);
+        const int y = site / L, x = site - y * L;
+        const int xm = x == 0 ? L - 1 : x - 1, xp = x == L - 1 ? 0 : x + 1;
+        const int rowm = (y == 0 ? L - 1 : y - 1) * L, rowp = (y == L - 1 ? 0 : y + 1) * L;
+        const int row = y * L;
+        const uint32_t s0 = (mine[site >> 5] >> (site & 31)) & 1u;
+        const int k = (int)(((mine[(row + xm) >> 5] >> ((row + xm) & 31)) & 1u) ^ s0) +
+                      (int)(((mine[(row + xp) >> 5] >> ((row + xp) & 31)) & 1u) ^ s0) +
+                      (int)(((mine[(rowm + x) >> 5] >> ((rowm + x) & 31)) & 1u) ^ s0) +
+                      (int)(((mine[(rowp + x) >> 5] >> ((rowp + x) & 31)) & 1u) ^ s0);
+        const uint64_t T = p.T_temp[(size_t)tos[r] * kClasses + 2 * k + (int)s0];
+        if ((uint64_t)u.y < T) {
+          mine[site >> 5] ^= 1u << (site & 31);
+          const int64_t sigma = s0 ? 1 : -1;
+          E += 2 * (p.J_int * (4 - 2 * k) - p.h_int * sigma);
+          M -= 2 * sigma;
+        }
+      }
+      if (a.m > 0 && --left == 0) {
+        left = a.m;
+        if (!swap_point()) return;
+      }
+    }
+  } else if (a.m > 0) {
+    // the same swap points as warp 0, in the same order
+    const uint64_t m = (uint64_t)a.m;
+    const uint64_t nswaps = (a.it0 + (uint64_t)a.n) / m - a.it0 / m;
+    for (uint64_t q = 0; q < nswaps; ++q)
+      if (!swap_point()) return;
+  }
+  __syncthreads();
+  // merge: site s gets this block's bits, changed ones XORed into the plane word (only this
+  // block changes them, and not before this point)
+  const unsigned lanes = k_per_block >= 32 ? 0xffffffffu : ((1u << k_per_block) - 1u);
+  const uint32_t mask = lanes << b0;
+  for (int site = tid; site < nsites; site += blockDim.x) {
+    uint32_t now = 0;
+    for (int l = 0; l < kb; ++l)
+      now |= ((bits[(size_t)l * words_per_rep + (site >> 5)] >> (site & 31)) & 1u) << (b0 + l);
+    uint32_t* const wp = word_of(site);
+    const uint32_t delta = (__ldcg(wp) ^ now) & mask;
+    if (delta) atomicXor(wp, delta);
+  }
+  if (active) {
+    p.E_slot[r] = E;
+    p.M_slot[r] = M;
+  }
+  if (swaps > 0 && blockIdx.x == 0) {
+    for (int q = tid; q < R; q += blockDim.x) {
+      p.slot_of_temp[q] = sot[q];
+      p.temp_of_slot[q] = tos[q];
+    }
+  }
+}
+
+}  // namespace
+
+int flip_smem_plan(const DevProblem& p, int sms, size_t smem_optin, int* k_out, size_t* bytes_out) {
+  *k_out = 0;
+  *bytes_out = 0;
+  const int words = (p.L * p.L + 31) / 32;
+  for (int k = 32; k >= 1; k >>= 1) {
+    const size_t bytes = (size_t)2 * p.R * 4 + (size_t)k * words * 4;
+    if (bytes > smem_optin) continue;
+    if (cudaFuncSetAttribute(k_flip_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes) != cudaSuccess)
+      return PT_ECUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_flip_smem, kFlipSmemThreads,
+                                                      bytes) !=
+        cudaSuccess)
+      return PT_ECUDA;
+    const int blocks = (p.R + k - 1) / k;
+    if (per_sm >= 1 && blocks <= per_sm * sms) {
+      *k_out = k;
+      *bytes_out = bytes;
+      return PT_OK;
+    }
+  }
+  return PT_OK;
+}
+
+cudaError_t launch_flip_smem(const DevProblem& p, int k, size_t bytes, uint64_t it0,
+                             uint64_t e0, int64_t n, int m, int stall, uint64_t limit_ns,
+                             cudaStream_t st) {
+  cudaError_t err = cudaMemsetAsync(p.cnt + 6 * p.W * 32, 0, sizeof(unsigned), st);
+  if (err != cudaSuccess) return err;
+  FlipArgs a;
+  a.p = p;
+  a.it0 = it0;
+  a.e0 = e0;
+  a.n = n;
+  a.m = m;
+  a.stall = stall;
+  a.limit_ns = limit_ns;
+  for (int r = 0; r < 10; ++r) {
+    a.rk.k0[r] = p.key0 + (uint32_t)r * kPhiloxW0;
+    a.rk.k1[r] = p.key1 + (uint32_t)r * kPhiloxW1;
+  }
+  int words = (p.L * p.L + 31) / 32;
+  void* args[] = {&a, &k, &words};
+  const int grid = (p.R + k - 1) / k;
+  return cudaLaunchCooperativeKernel((const void*)k_flip_smem, dim3(grid),
+                                     dim3(kFlipSmemThreads), args, bytes, st);
+}
+
+cudaError_t launch_flip(const DevProblem& p, uint64_t it0, uint64_t e0, int64_t n, int m,
+                        int stall, uint64_t limit_ns, cudaStream_t st) {
+  // the barrier counter, after the energy buffers
+  cudaError_t err = cudaMemsetAsync(p.cnt + 6 * p.W * 32, 0, sizeof(unsigned), st);
+  if (err != cudaSuccess) return err;
+  FlipArgs a;
+  a.p = p;
+  a.it0 = it0;
+  a.e0 = e0;
+  a.n = n;
+  a.m = m;
+  a.stall = stall;
+  a.limit_ns = limit_ns;
+  for (int r = 0; r < 10; ++r) {
+    a.rk.k0[r] = p.key0 + (uint32_t)r * kPhiloxW0;
+    a.rk.k1[r] = p.key1 + (uint32_t)r * kPhiloxW1;
+  }
+  void* args[] = {&a};
+  const int grid = (p.R + kFlipThreads - 1) / kFlipThreads;
+  return cudaLaunchCooperativeKernel((const void*)k_flip, dim3(grid), dim3(kFlipThreads), args,
+                                     (size_t)2 * p.R * sizeof(int32_t), st);
+}
+
+}  // namespace ptb

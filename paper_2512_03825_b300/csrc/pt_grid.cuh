@@ -1,0 +1,40 @@
+// pt_grid.cuh -- the bounded grid barrier of the cooperative (persistent) kernels.
+#pragma once
+#include <stdint.h>
+
+#include "pt.h"
+#include "pt_device.cuh"
+
+namespace ptb {
+
+// Every CTA arrives once; returns false when the wait gave up (time limit or a status set
+// by another CTA): the caller leaves the kernel. Thread 0 polls the counter with relaxed
+// loads and orders the CTA's later reads with one fence after the wait.
+__device__ inline bool grid_barrier(unsigned* bar, unsigned target, int* status,
+                                    uint64_t limit_ns, int* ok_s) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();  // the CTA's writes (ordered before by the block barrier) go first
+    atomicAdd(bar, 1u);
+    const uint64_t t0 = global_ns();
+    while ((int)(ld_relaxed_u32(bar) - target) < 0) {
+      if (*(volatile int*)status != 0) {
+        ok = 0;
+        break;
+      }
+      if (global_ns() - t0 > limit_ns) {
+        atomicCAS(status, 0, PT_ETIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(20);
+    }
+    __threadfence();
+    *ok_s = ok;
+  }
+  __syncthreads();
+  return *ok_s != 0;
+}
+
+}  // namespace ptb

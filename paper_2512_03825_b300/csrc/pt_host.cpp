@@ -20,6 +20,7 @@
 #include "pt_batch.h"
 #include "pt_internal.h"
 #include "pt_launch.h"
+#include "pt_flip.h"
 #include "pt_persist.h"
 
 using namespace ptb;
@@ -389,8 +390,8 @@ int read_observables(pt_problem* p, std::vector<int64_t>* E, std::vector<int64_t
 // ---------------------------------------------------------------------------------------
 namespace {
 
-constexpr char kCkptMagic[8] = {'P', 'T', 'C', 'K', 'P', 'T', '0', '1'};
-constexpr size_t kCkptHeader = 64;
+constexpr char kCkptMagic[8] = {'P', 'T', 'C', 'K', 'P', 'T', '0', '2'};
+constexpr size_t kCkptHeader = 72;
 
 size_t ckpt_bytes(int L, int R) {
   const int W = (R + 31) / 32;
@@ -725,6 +726,52 @@ int pt_sweep(pt_problem* p, int64_t n, int exchange_every) {
   return PT_OK;
 }
 
+int pt_flip(pt_problem* p, int64_t n, int exchange_every) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  if (n < 0 || exchange_every < 0)
+    return fail(PT_EINVAL, "n = %lld and exchange_every = %d must be >= 0", (long long)n,
+                exchange_every);
+  if ((rc = problem_device_guard(p))) return rc;
+  if (n == 0) return PT_OK;
+  if ((rc = refresh_observables(p))) return rc;  // E_slot, M_slot of the current state
+  const uint64_t m = (uint64_t)exchange_every;
+  int k = 0;
+  size_t smem = 0;
+  if (p->flip_shared && (rc = flip_smem_plan(p->dev, p->dev_info.sms, p->dev_info.smem_optin,
+                                             &k, &smem)))
+    return fail(rc, "planning the shared-memory single-flip kernel");
+  while (n > 0) {
+    const int64_t c = std::min<int64_t>(n, (int64_t)1 << 24);
+    const cudaError_t err =
+        k > 0 ? launch_flip_smem(p->dev, k, smem, p->it, p->e, c, exchange_every, p->stall,
+                                 p->wait_limit_ns, p->stream)
+              : launch_flip(p->dev, p->it, p->e, c, exchange_every, p->stall, p->wait_limit_ns,
+                            p->stream);
+    p->stall = 0;
+    if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "single-flip launch", err);
+    const uint64_t it1 = p->it + (uint64_t)c;
+    if (m > 0) p->e += it1 / m - p->it / m;
+    p->it = it1;
+    n -= c;
+  }
+  return PT_OK;
+}
+
+int pt_set_flip_tuning(pt_problem* p, int shared_memory) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  p->flip_shared = shared_memory != 0;
+  return PT_OK;
+}
+
+int pt_iterations(pt_problem* p, uint64_t* iterations_done) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  if (iterations_done) *iterations_done = p->it;
+  return PT_OK;
+}
+
 int pt_set_sweep_tuning(pt_problem* p, int strategy, int words_per_thread) {
   int rc = problem_check(p);
   if (rc) return rc;
@@ -901,6 +948,7 @@ int pt_save(pt_problem* p, void* buf, size_t bytes) {
   w.put(p->e);
   w.put((int32_t)p->swap_rule);
   w.put((int32_t)0);
+  w.put(p->it);
   w.put_bytes(p->betas.data(), (size_t)R * 8);
   w.put_bytes(sot.data(), (size_t)R * 4);
   if (pairs) {
@@ -923,6 +971,8 @@ int pt_load(const void* buf, size_t bytes, pt_problem** out) {
   const double J = r.get<double>(), h = r.get<double>();
   const uint64_t seed = r.get<uint64_t>(), t = r.get<uint64_t>(), e = r.get<uint64_t>();
   const int32_t rule = r.get<int32_t>();
+  r.get<int32_t>();
+  const uint64_t it = r.get<uint64_t>();
   if (L < 4 || L > PT_MAX_L || (L & 1) || R < 1 || R > PT_MAX_R)
     return fail(PT_EINVAL, "checkpoint with L = %u, R = %u", L, R);
   const size_t need = ckpt_bytes((int)L, (int)R);
@@ -997,6 +1047,7 @@ int pt_load(const void* buf, size_t bytes, pt_problem** out) {
   }
   p->t = t;
   p->e = e;
+  p->it = it;
   *out = p;
   return PT_OK;
 }

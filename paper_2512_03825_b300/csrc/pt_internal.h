@@ -17,6 +17,8 @@ struct pt_problem {
   uint64_t seed = 0;
   int swap_rule = PT_SWAP_BARKER;
   uint64_t t = 0, e = 0;  // sweeps and swap iterations enqueued so far
+  uint64_t it = 0;        // single-spin-flip iterations enqueued so far
+  bool flip_shared = true;  // pt_flip keeps the replicas in shared memory when they fit
   cudaStream_t stream = 0;
   void* dmem = nullptr;   // the problem's single device allocation
   size_t dbytes = 0;

@@ -27,6 +27,7 @@
 
 #include "pt.h"
 #include "pt_device.cuh"
+#include "pt_grid.cuh"
 #include "pt_persist.h"
 
 namespace ptb {
@@ -44,35 +45,6 @@ struct PersistArgs {
   uint64_t limit_ns;
   RoundKeys rk;  // Philox round keys of the seed (constant-bank operands)
 };
-
-// Every CTA arrives once; returns false when the wait gave up (time limit or a status set
-// by another CTA): the caller leaves the kernel.
-__device__ bool grid_barrier(unsigned* bar, unsigned target, int* status, uint64_t limit_ns,
-                             int* ok_s) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    __threadfence();  // the CTA's writes (ordered before by the block barrier) go first
-    atomicAdd(bar, 1u);
-    const uint64_t t0 = global_ns();
-    while ((int)(ld_acquire_u32(bar) - target) < 0) {
-      if (*(volatile int*)status != 0) {
-        ok = 0;
-        break;
-      }
-      if (global_ns() - t0 > limit_ns) {
-        atomicCAS(status, 0, PT_ETIMEOUT);
-        ok = 0;
-        break;
-      }
-      __nanosleep(20);
-    }
-    __threadfence();
-    *ok_s = ok;
-  }
-  __syncthreads();
-  return *ok_s != 0;
-}
 
 // The plane's thresholds under the temperature map tos, staged in shared memory by warp 0
 // (same rule as the plane rebuild of the exchange kernel).

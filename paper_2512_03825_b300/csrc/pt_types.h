@@ -14,6 +14,7 @@ namespace ptb {
 constexpr uint32_t kTagSpin = 0u;
 constexpr uint32_t kTagExch = 1u;
 constexpr uint32_t kTagInit = 2u;
+constexpr uint32_t kTagFlip = 3u;  // single-spin-flip iterations
 constexpr int kClasses = 10;  // class c = 2 k + (sigma == +1), k = anti-aligned neighbours 0..4
 
 enum Mode : int {

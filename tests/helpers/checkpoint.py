@@ -6,7 +6,7 @@ import struct
 
 import numpy as np
 
-MAGIC = b"PTCKPT01"
+MAGIC = b"PTCKPT02"
 
 
 def fnv1a64(data: bytes) -> int:
@@ -44,9 +44,10 @@ def words_to_spins(words: np.ndarray, R: int) -> np.ndarray:
     return out
 
 
-def build(L, betas, J, h, seed, t, e, rule, slot_of_temp, attempted, accepted, words) -> bytes:
+def build(L, betas, J, h, seed, t, e, rule, slot_of_temp, attempted, accepted, words,
+          it=0) -> bytes:
     R = len(betas)
-    head = MAGIC + struct.pack("<IIddQQQii", L, R, J, h, seed, t, e, rule, 0)
+    head = MAGIC + struct.pack("<IIddQQQiiQ", L, R, J, h, seed, t, e, rule, 0, it)
     body = (np.asarray(betas, "<f8").tobytes() + np.asarray(slot_of_temp, "<i4").tobytes() +
             np.asarray(attempted, "<u8").tobytes() + np.asarray(accepted, "<u8").tobytes() +
             np.ascontiguousarray(words, "<u4").tobytes())
@@ -60,7 +61,8 @@ def parse(data: bytes) -> dict:
     J, h = struct.unpack_from("<dd", data, 16)
     seed, t, e = struct.unpack_from("<QQQ", data, 32)
     rule, _ = struct.unpack_from("<ii", data, 56)
-    off = 64
+    it, = struct.unpack_from("<Q", data, 64)
+    off = 72
     betas = np.frombuffer(data, "<f8", R, off); off += 8 * R
     sot = np.frombuffer(data, "<i4", R, off); off += 4 * R
     P = max(R - 1, 0)
@@ -71,5 +73,5 @@ def parse(data: bytes) -> dict:
     off += 4 * words.size
     checksum, = struct.unpack_from("<Q", data, off)
     assert off + 8 == len(data) and checksum == fnv1a64(data[:off])
-    return dict(L=L, R=R, J=J, h=h, seed=seed, t=t, e=e, rule=rule, betas=betas,
+    return dict(L=L, R=R, J=J, h=h, seed=seed, t=t, e=e, rule=rule, it=it, betas=betas,
                 slot_of_temp=sot, attempted=att, accepted=acc, words=words)
