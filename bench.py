@@ -36,11 +36,11 @@ IMUL_WIDE_PER_CLK_SM = 32.0  # 32x32->64 integer products per clock per SM (4 SM
 # DRAM traffic of one k_flat_half launch (colour 0) on the batched-256 workload from the ncu
 # capture summarised in profiles/k_flat_half_batched-256.md (cold caches: one read of the
 # whole state). Valid only for the kernel source it was taken on.
-FLAT_TRAFFIC_BYTES = 25.938176e6 + 7.680e3
+FLAT_TRAFFIC_BYTES = 25.947136e6 + 7.424e3
 FLAT_TRAFFIC_SOURCES = ("paper_2512_03825_b300/csrc/pt_device.cuh",
                         "paper_2512_03825_b300/csrc/pt_flat.cuh",
                         "paper_2512_03825_b300/csrc/pt_flat.cu")
-FLAT_TRAFFIC_SOURCE_HASH = "544dd6d3ff97a650"
+FLAT_TRAFFIC_SOURCE_HASH = "f53760f29c250b33"
 
 
 def _flat_traffic():
@@ -58,7 +58,10 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["batched", "single", "serve"], default="batched")
+    ap.add_argument("--workload", choices=["batched", "single", "serve", "flip"],
+                    default="batched")
+    ap.add_argument("--iterations", type=int, default=300_000,
+                    help="single-spin-flip iterations per replica per step (--workload flip)")
     ap.add_argument("--sweeps", type=int, default=2000, help="sweeps per problem per step")
     ap.add_argument("--problems", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=300,
@@ -220,6 +223,8 @@ def run_ours(args, rank, world, local):
 
     if args.workload == "single":
         return run_single(args, rank, world, stream, sms)
+    if args.workload == "flip":
+        return run_flip(args, rank, world, stream)
     if args.workload == "serve":
         from paper_2512_03825_b300 import serve
         res = serve.bench_serve(args, rank, world, stream)
@@ -525,7 +530,42 @@ def run_single(args, rank, world, stream, sms):
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": "single L=1024 R=64 betas 0.35-0.50, 1000 sweeps, "
                                    "exchange every 5, plain path"},
-            "clocks": clk, "gpu_launches": args.steps * (2 * p.sweeps + 2 * p.sweeps // p.every)}
+            "clocks": clk, "gpu_launches": args.steps}  # one cooperative launch per call
+
+
+def run_flip(args, rank, world, stream):
+    """The paper's performance run read as single-spin flips (Sec. 4.2): 300 x 300, J = 1,
+    B = 0, 1500 replicas at T_i = 1 + 3i/|R|, args.iterations iterations per replica per
+    step, a swap iteration every 100 iterations."""
+    import torch
+    from paper_2512_03825_b300 import api
+    from paper_2512_03825_b300 import workloads as W
+    p = W.paper_problem()
+    h = api.PTProblem(p.L, p.betas, seed=p.seed, stream=stream)
+    for _ in range(args.warmup):
+        h.flip(min(args.iterations, 3000), 100)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    barrier(world)
+    clocks.start()
+    a.record(stream)
+    for _ in range(args.steps):
+        h.flip(args.iterations, 100)
+    b.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    s = max_over_ranks(a.elapsed_time(b) / 1e3, world)
+    per_step = float(p.R) * args.iterations
+    return {"metric": "single-spin-flip attempts/sec (all replicas, 1 B300)",
+            "value": per_step * args.steps * world / s, "unit": "attempts/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * s / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "the paper's run as single flips: L=300, 1500 replicas, "
+                                   "T_i = 1 + 3i/1500, %d iterations, swap every 100"
+                                   % args.iterations},
+            "clocks": clk, "gpu_launches": args.steps}
 
 
 # ---------------------------------------------------------------------------------------
