@@ -64,6 +64,14 @@ __device__ __forceinline__ Philox4 philox4x32_10_rk(uint32_t c0, uint32_t c1, ui
   return Philox4{c0, c1, c2, c3};
 }
 
+// One swap attempt of pair k in the statistics: reductions at L2, so the counting thread
+// does not wait for the old values (and a later CTA never reads a stale L1 copy).
+__device__ __forceinline__ void count_swap(uint64_t* attempted, uint64_t* accepted, int k,
+                                           bool accept) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(attempted + k), 1ull);
+  if (accept) atomicAdd(reinterpret_cast<unsigned long long*>(accepted + k), 1ull);
+}
+
 // The eight blocks j of one site in one sweep have the counters {site, lo32(t), blk0 + j, c3}:
 // they differ in counter word 2 only. In round 1 the product of word 0 depends on the site
 // alone and that of word 2 on j alone; in round 2 the product of word 0 (which came from

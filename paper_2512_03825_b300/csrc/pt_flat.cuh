@@ -97,9 +97,9 @@ __device__ inline void exchange_warp(const DevProblem& p, uint64_t e) {
     else
       S = p.swap_table[sp.offset + (n - sp.n_lo)];
     const Philox4 rnd = philox4x32_10((uint32_t)k, (uint32_t)e, 0u, c3, p.key0, p.key1);
-    p.attempted[k] = __ldcg(p.attempted + k) + 1;
-    if ((uint64_t)rnd.x < S) {
-      p.accepted[k] = __ldcg(p.accepted + k) + 1;
+    const bool accept = (uint64_t)rnd.x < S;
+    count_swap(p.attempted, p.accepted, k, accept);
+    if (accept) {
       p.slot_of_temp[k] = b;
       p.slot_of_temp[k + 1] = a;
       p.temp_of_slot[a] = k + 1;

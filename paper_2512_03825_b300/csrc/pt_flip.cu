@@ -73,10 +73,7 @@ __device__ void exchange_energies(const DevProblem& p, uint64_t e, const int64_t
     const int k = parity + 2 * (int)threadIdx.x + q * stride;
     if (k + 1 >= R) break;
     const bool accept = (accepted >> q) & 1u;
-    if (owner) {
-      p.attempted[k] += 1;
-      if (accept) p.accepted[k] += 1;
-    }
+    if (owner) count_swap(p.attempted, p.accepted, k, accept);
     if (accept) {
       const int a = sot[k], b = sot[k + 1];
       sot[k] = b;
@@ -119,7 +116,8 @@ __global__ void __launch_bounds__(kFlipThreads) k_flip(const __grid_constant__ F
       const Philox4 u = philox4x32_10_rk((uint32_t)i, (uint32_t)r, 0u,
                                          kTagFlip | ((uint32_t)(i >> 32) << 8), a.rk);
       const uint64_t site = ((uint64_t)u.x * L2) >> 32;
-      const int y = (int)(site / (uint64_t)L), x = (int)(site - (uint64_t)y * L);
+      // floor(site / L) = floor(u0 L^2 / (2^32 L)) = floor(u0 L / 2^32): one high product
+      const int y = (int)__umulhi(u.x, (uint32_t)L), x = (int)(site - (uint64_t)y * L);
       const int c = (x + y) & 1;
       const int xm = x == 0 ? L - 1 : x - 1, xp = x == L - 1 ? 0 : x + 1;
       const int ym = y == 0 ? L - 1 : y - 1, yp = y == L - 1 ? 0 : y + 1;
@@ -177,6 +175,7 @@ __global__ void __launch_bounds__(kFlipSmemThreads) k_flip_smem(const __grid_con
                                                                 int words_per_rep) {
   extern __shared__ uint32_t smem[];  // [R] slot_of_temp, [R] temp_of_slot, [k][words] bits
   __shared__ int ok_s;
+  __shared__ uint64_t thr_s[kClasses][32];  // lane l's thresholds at its current temperature
   const DevProblem& p = a.p;
   const int R = p.R, L = p.L, half = L >> 1;
   int32_t* sot = reinterpret_cast<int32_t*>(smem);
@@ -220,12 +219,23 @@ __global__ void __launch_bounds__(kFlipSmemThreads) k_flip_smem(const __grid_con
   int64_t E = active ? p.E_slot[r] : 0, M = active ? p.M_slot[r] : 0;
   uint32_t* const mine = bits + (size_t)(active ? tid : 0) * words_per_rep;
   const uint64_t L2 = (uint64_t)nsites;
+  // a replica's temperature changes only at swap iterations: its ten thresholds are staged
+  // in shared memory then, off the chain of dependent iterations
+  auto stage_thresholds = [&]() {
+    if (active) {
+      const uint64_t* const src = p.T_temp + (size_t)tos[r] * kClasses;
+#pragma unroll
+      for (int c = 0; c < kClasses; ++c) thr_s[c][tid] = src[c];
+    }
+  };
+  stage_thresholds();
   auto swap_point = [&]() -> bool {
     int64_t* const eb = ebuf + (size_t)(swaps & 1) * R;
     if (active) eb[r] = E;
     target += gridDim.x + (swaps == 0 ? (unsigned)a.stall : 0u);
     if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s)) return false;
     exchange_energies(p, e, eb, sot, tos, blockIdx.x == 0);
+    stage_thresholds();
     e += 1;
     swaps += 1;
     return true;
@@ -233,13 +243,20 @@ __global__ void __launch_bounds__(kFlipSmemThreads) k_flip_smem(const __grid_con
   if (flips) {
     // iterations until the next swap iteration (after every m-th iteration count)
     int64_t left = a.m > 0 ? (int64_t)a.m - (int64_t)(a.it0 % (uint64_t)a.m) : 0;
+    // the draws do not depend on the lattice: the next iteration's block is formed while
+    // this one's loads are in flight
+    auto draw = [&](uint64_t i) {
+      return philox4x32_10_rk((uint32_t)i, (uint32_t)r, 0u,
+                              kTagFlip | ((uint32_t)(i >> 32) << 8), a.rk);
+    };
+    Philox4 next = draw(a.it0);
     for (int64_t j = 0; j < a.n; ++j) {
       if (active) {
-        const uint64_t i = a.it0 + (uint64_t)j;
-        const Philox4 u = philox4x32_10_rk((uint32_t)i, (uint32_t)r, 0u,
-                                           kTagFlip | ((uint32_t)(i >> 32) << 8), a.rk);
+        const Philox4 u = next;
+        next = draw(a.it0 + (uint64_t)j + 1);
         const int site = (int)(((uint64_t)u.x * L2) >> 32);
-        const int y = site / L, x = site - y * L;
+        // floor(site / L) = floor(u0 L / 2^32): one high product instead of a division
+        const int y = (int)__umulhi(u.x, (uint32_t)L), x = site - y * L;
         const int xm = x == 0 ? L - 1 : x - 1, xp = x == L - 1 ? 0 : x + 1;
         const int rowm = (y == 0 ? L - 1 : y - 1) * L, rowp = (y == L - 1 ? 0 : y + 1) * L;
         const int row = y * L;
@@ -248,8 +265,7 @@ __global__ void __launch_bounds__(kFlipSmemThreads) k_flip_smem(const __grid_con
                       (int)(((mine[(row + xp) >> 5] >> ((row + xp) & 31)) & 1u) ^ s0) +
                       (int)(((mine[(rowm + x) >> 5] >> ((rowm + x) & 31)) & 1u) ^ s0) +
                       (int)(((mine[(rowp + x) >> 5] >> ((rowp + x) & 31)) & 1u) ^ s0);
-        const uint64_t T = p.T_temp[(size_t)tos[r] * kClasses + 2 * k + (int)s0];
-        if ((uint64_t)u.y < T) {
+        if ((uint64_t)u.y < thr_s[2 * k + (int)s0][tid]) {
           mine[site >> 5] ^= 1u << (site & 31);
           const int64_t sigma = s0 ? 1 : -1;
           E += 2 * (p.J_int * (4 - 2 * k) - p.h_int * sigma);
@@ -299,9 +315,11 @@ int flip_smem_plan(const DevProblem& p, int sms, size_t smem_optin, int* k_out, 
   *k_out = 0;
   *bytes_out = 0;
   const int words = (p.L * p.L + 31) / 32;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, k_flip_smem) != cudaSuccess) return PT_ECUDA;
   for (int k = 32; k >= 1; k >>= 1) {
     const size_t bytes = (size_t)2 * p.R * 4 + (size_t)k * words * 4;
-    if (bytes > smem_optin) continue;
+    if (bytes + fa.sharedSizeBytes > smem_optin) continue;
     if (cudaFuncSetAttribute(k_flip_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bytes) != cudaSuccess)
       return PT_ECUDA;

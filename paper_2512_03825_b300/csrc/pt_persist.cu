@@ -116,10 +116,7 @@ __device__ void exchange_local(const DevProblem& p, uint64_t e, const uint32_t* 
       S = p.swap_table[sp.offset + (n - sp.n_lo)];
     const Philox4 rnd = philox4x32_10((uint32_t)k, (uint32_t)e, 0u, c3, p.key0, p.key1);
     const bool accept = (uint64_t)rnd.x < S;
-    if (owner) {
-      p.attempted[k] += 1;
-      if (accept) p.accepted[k] += 1;
-    }
+    if (owner) count_swap(p.attempted, p.accepted, k, accept);
     if (accept) {
       sot[k] = b;
       sot[k + 1] = a;
