@@ -48,10 +48,18 @@ __global__ void __launch_bounds__(kFlatThreads, 2) k_flat_half(const FlatProblem
 }
 
 // ---------------------------------------------------------------------------------------
-// exchange step: one block per problem due for one (same three parts as k_exchange)
+// End of sweep j for every problem counted after it (a swap iteration or a trace row
+// follows), one block per problem: energies from the counts (then cleared), the swap
+// iteration of Sec. 3, the plane thresholds of the new map, the trace row. What the step
+// reads that does not depend on its own results -- the counts, both maps, the thread's
+// first pair and the threshold row of every temperature -- is loaded at once, into shared
+// memory; after that only the pairs' table lookups and the stores touch global memory.
+// Shared memory: flat_exchange_smem(R, mode) bytes.
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kFlatThreads) k_flat_exchange(const FlatProblem* __restrict__ probs,
                                                                  int nprobs, int64_t j) {
+  extern __shared__ __align__(16) unsigned char xs[];
+  constexpr uint64_t kTwo32 = 1ull << 32;
   for (int pi = blockIdx.x; pi < nprobs; pi += gridDim.x) {
     const FlatProblem& fp = probs[pi];
     if (!counts_after(fp, j)) continue;
@@ -60,81 +68,140 @@ __global__ void __launch_bounds__(kFlatThreads) k_flat_exchange(const FlatProble
     const uint64_t e = ex ? exchange_index(fp, j) : 0;
     const int R = p.R, W = p.W;
     const int64_t L2 = (int64_t)p.L * p.L;
-    __syncthreads();
+    const bool ferro = p.mode == kModeFerro;
+    const int ncls = ferro ? 2 : kClasses;  // threshold row entries per temperature
+    int64_t* const E_s = reinterpret_cast<int64_t*>(xs);  // [R] by slot
+    int64_t* const M_s = E_s + R;                          // [R] by slot
+    uint64_t* const T_s = reinterpret_cast<uint64_t*>(M_s + R);  // [R][ncls] by temperature
+    int32_t* const sot = reinterpret_cast<int32_t*>(T_s + (size_t)ncls * R);
+    int32_t* const tos = sot + R;
+    const int parity = (int)(e & 1);
+    const int k0 = parity + 2 * (int)threadIdx.x;  // this thread's first pair
+    __syncthreads();  // the previous problem's readers are done
+    SwapPair sp0{};
+    if (ex && k0 + 1 < R) sp0 = p.pairs[k0];
     for (int r = threadIdx.x; r < R; r += blockDim.x) {
       const int64_t U = p.cnt[r];
       const int64_t ones = p.cnt[W * 32 + r];
+      sot[r] = p.slot_of_temp[r];
+      tos[r] = p.temp_of_slot[r];
+      if (ex) {
+        if (ferro) {
+          T_s[2 * r] = p.T_temp[(size_t)r * kClasses + 1];
+          T_s[2 * r + 1] = p.T_temp[(size_t)r * kClasses + 3];
+        } else {
+#pragma unroll
+          for (int c = 0; c < kClasses; ++c)
+            T_s[(size_t)r * kClasses + c] = p.T_temp[(size_t)r * kClasses + c];
+        }
+      }
+      p.cnt[r] = 0;
+      p.cnt[W * 32 + r] = 0;
       const int64_t bonds = 2 * L2 - 2 * U;
       const int64_t M = 2 * ones - L2;
-      p.E_slot[r] = -p.J_int * bonds + p.h_int * M;
+      const int64_t E = -p.J_int * bonds + p.h_int * M;
+      E_s[r] = E;
+      M_s[r] = M;
+      p.E_slot[r] = E;
       p.M_slot[r] = M;
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < 2 * W * 32; q += blockDim.x) p.cnt[q] = 0;
-    const int parity = (int)(e & 1);
-    const uint32_t c3 = kTagExch | ((uint32_t)(e >> 32) << 8);
-    for (int k = parity + 2 * threadIdx.x; ex && k + 1 < R; k += 2 * blockDim.x) {
-      const int a = p.slot_of_temp[k], b = p.slot_of_temp[k + 1];
-      const int64_t n = p.E_slot[a] - p.E_slot[b];
-      const SwapPair sp = p.pairs[k];
-      uint64_t S;
-      if (n < sp.n_lo)
-        S = sp.S_below;
-      else if (n > sp.n_hi)
-        S = sp.S_above;
-      else
-        S = p.swap_table[sp.offset + (n - sp.n_lo)];
-      const Philox4 rnd = philox4x32_10((uint32_t)k, (uint32_t)e, 0u, c3, p.key0, p.key1);
-      const bool accept = (uint64_t)rnd.x < S;
-      count_swap(p.attempted, p.accepted, k, accept);
-      if (accept) {
-        p.slot_of_temp[k] = b;
-        p.slot_of_temp[k + 1] = a;
-        p.temp_of_slot[a] = k + 1;
-        p.temp_of_slot[b] = k;
-      }
-    }
-    __syncthreads();
-    constexpr uint64_t kTwo32 = 1ull << 32;
-    for (int r = threadIdx.x; ex && r < W * 32; r += blockDim.x) {
-      const int w = r >> 5, b = r & 31;
-      const bool in_use = r < R;
-      const int temp = in_use ? p.temp_of_slot[r] : 0;
-      if (p.mode == kModeFerro) {
-        PlaneFerro* pl = reinterpret_cast<PlaneFerro*>(p.planes) + w;
-        const uint64_t t0 = in_use ? p.T_temp[(size_t)temp * kClasses + 1] : 0;
-        const uint64_t t1 = in_use ? p.T_temp[(size_t)temp * kClasses + 3] : 0;
-        pl->T0[b] = (uint32_t)min(t0, kTwo32 - 1);
-        pl->T1[b] = (uint32_t)min(t1, kTwo32 - 1);
-        const uint32_t a0 = __ballot_sync(0xffffffffu, in_use && t0 >= kTwo32);
-        const uint32_t a1 = __ballot_sync(0xffffffffu, in_use && t1 >= kTwo32);
-        if (b == 0) {
-          pl->alw0 = a0;
-          pl->alw1 = a1;
+    if (ex) {
+      const uint32_t c3 = kTagExch | ((uint32_t)(e >> 32) << 8);
+      for (int k = k0; k + 1 < R; k += 2 * blockDim.x) {
+        const int a = sot[k], b = sot[k + 1];
+        const int64_t n = E_s[a] - E_s[b];
+        const SwapPair sp = k == k0 ? sp0 : p.pairs[k];
+        uint64_t S;
+        if (n < sp.n_lo)
+          S = sp.S_below;
+        else if (n > sp.n_hi)
+          S = sp.S_above;
+        else
+          S = p.swap_table[sp.offset + (n - sp.n_lo)];
+        const Philox4 rnd = philox4x32_10((uint32_t)k, (uint32_t)e, 0u, c3, p.key0, p.key1);
+        const bool accept = (uint64_t)rnd.x < S;
+        count_swap(p.attempted, p.accepted, k, accept);
+        if (accept) {  // pairs of one parity are disjoint
+          sot[k] = b;
+          sot[k + 1] = a;
+          tos[a] = k + 1;
+          tos[b] = k;
         }
-      } else {
-        PlaneGeneric* pl = reinterpret_cast<PlaneGeneric*>(p.planes) + w;
+      }
+      __syncthreads();
+      for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        p.slot_of_temp[r] = sot[r];
+        p.temp_of_slot[r] = tos[r];
+      }
+      for (int r = threadIdx.x; r < W * 32; r += blockDim.x) {  // whole warps
+        const int w = r >> 5, b = r & 31;
+        const bool in_use = r < R;
+        const int temp = in_use ? tos[r] : 0;
+        if (ferro) {
+          PlaneFerro* pl = reinterpret_cast<PlaneFerro*>(p.planes) + w;
+          const uint64_t t0 = in_use ? T_s[2 * temp] : 0;
+          const uint64_t t1 = in_use ? T_s[2 * temp + 1] : 0;
+          pl->T0[b] = (uint32_t)min(t0, kTwo32 - 1);
+          pl->T1[b] = (uint32_t)min(t1, kTwo32 - 1);
+          const uint32_t a0 = __ballot_sync(0xffffffffu, in_use && t0 >= kTwo32);
+          const uint32_t a1 = __ballot_sync(0xffffffffu, in_use && t1 >= kTwo32);
+          if (b == 0) {
+            pl->alw0 = a0;
+            pl->alw1 = a1;
+          }
+        } else {
+          PlaneGeneric* pl = reinterpret_cast<PlaneGeneric*>(p.planes) + w;
 #pragma unroll
-        for (int c = 0; c < kClasses; ++c) {
-          const uint64_t tc = in_use ? p.T_temp[(size_t)temp * kClasses + c] : 0;
-          pl->T[c][b] = (uint32_t)min(tc, kTwo32 - 1);
-          const uint32_t a = __ballot_sync(0xffffffffu, in_use && tc >= kTwo32);
-          if (b == 0) pl->alw[c] = a;
+          for (int c = 0; c < kClasses; ++c) {
+            const uint64_t tc = in_use ? T_s[(size_t)temp * kClasses + c] : 0;
+            pl->T[c][b] = (uint32_t)min(tc, kTwo32 - 1);
+            const uint32_t a = __ballot_sync(0xffffffffu, in_use && tc >= kTwo32);
+            if (b == 0) pl->alw[c] = a;
+          }
         }
       }
     }
     if (p.trace_E != nullptr) {
       // the trace row of this sweep, by temperature index after its swap iteration
-      __syncthreads();
       const uint64_t t = fp.t0 + (uint64_t)j;
       const int64_t row = (int64_t)((t - p.trace_t0) % (uint64_t)p.trace_cap);
       for (int r = threadIdx.x; r < R; r += blockDim.x) {
-        const int k = p.temp_of_slot[r];
-        p.trace_E[row * R + k] = p.E_slot[r];
-        p.trace_M[row * R + k] = p.M_slot[r];
+        const int k = tos[r];
+        p.trace_E[row * R + k] = E_s[r];
+        p.trace_M[row * R + k] = M_s[r];
       }
     }
   }
+}
+
+size_t flat_exchange_smem(int R, int mode) {
+  return (size_t)R * (2 * sizeof(int64_t) + 2 * sizeof(int32_t) +
+                      (mode == kModeFerro ? 2 : kClasses) * sizeof(uint64_t));
+}
+
+// The exchange launch of sweep j with `smem` bytes of shared memory (the largest problem's
+// need, flat_exchange_smem).
+cudaError_t launch_flat_exchange(const FlatProblem* d_probs, int np, int64_t j, size_t smem,
+                                 int sms, cudaStream_t st) {
+  k_flat_exchange<<<std::min(np, sms * 8), kFlatThreads, smem, st>>>(d_probs, np, j);
+  return cudaGetLastError();
+}
+
+// Half sweep `colour` of sweep j over one mode's tile list.
+template <int MODE, bool COUNT>
+cudaError_t launch_flat_half(int grid, const FlatProblem* d_probs, const Tile* d_tiles,
+                             const int* d_first, int colour, int64_t j, cudaStream_t st) {
+  k_flat_half<MODE, COUNT><<<grid, kFlatThreads, 0, st>>>(d_probs, d_tiles, d_first, colour, j);
+  return cudaGetLastError();
+}
+
+// Shared memory of the batch's exchange launches; raises the kernel's limit above the
+// default 48 KB when a problem needs it (at most 208 KB, R = 2048 generic).
+cudaError_t flat_exchange_prepare(size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(k_flat_exchange, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
 }
 
 }  // namespace
@@ -271,19 +338,23 @@ int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const i
           (fp.m > 0 && (fp.t0 + (uint64_t)j + 1) % (uint64_t)fp.m == 0))
         any_exchange[(size_t)j] = 1;
   const int np = (int)probs.size();
+  size_t xsmem = 0;
+  for (const FlatProblem& fp : probs)
+    xsmem = std::max(xsmem, flat_exchange_smem(fp.p.R, fp.p.mode));
+  if (err == cudaSuccess) err = flat_exchange_prepare(xsmem);
   for (int64_t j = 0; j < n_max && err == cudaSuccess; ++j) {
     const bool ex = any_exchange[(size_t)j] != 0;
-    if (grid[0]) k_flat_half<kModeFerro, false><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles[0], d_first[0], 0, j);
-    if (grid[1]) k_flat_half<kModeGeneric, false><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles[1], d_first[1], 0, j);
+    if (grid[0] && err == cudaSuccess) err = launch_flat_half<kModeFerro, false>(grid[0], d_probs, d_tiles[0], d_first[0], 0, j, st);
+    if (grid[1] && err == cudaSuccess) err = launch_flat_half<kModeGeneric, false>(grid[1], d_probs, d_tiles[1], d_first[1], 0, j, st);
     if (ex) {
-      if (grid[0]) k_flat_half<kModeFerro, true><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles[0], d_first[0], 1, j);
-      if (grid[1]) k_flat_half<kModeGeneric, true><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles[1], d_first[1], 1, j);
-      k_flat_exchange<<<std::min(np, di.sms * 8), kFlatThreads, 0, st>>>(d_probs, np, j);
+      if (grid[0] && err == cudaSuccess) err = launch_flat_half<kModeFerro, true>(grid[0], d_probs, d_tiles[0], d_first[0], 1, j, st);
+      if (grid[1] && err == cudaSuccess) err = launch_flat_half<kModeGeneric, true>(grid[1], d_probs, d_tiles[1], d_first[1], 1, j, st);
+      if (err == cudaSuccess) err = launch_flat_exchange(d_probs, np, j, xsmem, di.sms, st);
     } else {
-      if (grid[0]) k_flat_half<kModeFerro, false><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles[0], d_first[0], 1, j);
-      if (grid[1]) k_flat_half<kModeGeneric, false><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles[1], d_first[1], 1, j);
+      if (grid[0] && err == cudaSuccess) err = launch_flat_half<kModeFerro, false>(grid[0], d_probs, d_tiles[0], d_first[0], 1, j, st);
+      if (grid[1] && err == cudaSuccess) err = launch_flat_half<kModeGeneric, false>(grid[1], d_probs, d_tiles[1], d_first[1], 1, j, st);
     }
-    err = cudaGetLastError();
+    if (err == cudaSuccess) err = cudaGetLastError();
   }
   const cudaError_t err2 = cudaFreeAsync(scratch, st);
   if (err == cudaSuccess) err = err2;
@@ -491,6 +562,10 @@ int sweep_batch_static(pt_problem* const* ps, int count, const int64_t* n, const
   const Tile* d_tiles1 = d_tiles0 + split;
   const int* d_first0 = (const int*)(base + off_first0);
   const int* d_first1 = (const int*)(base + off_first1);
+  size_t xsmem = 0;
+  for (int k = 0; k < np; ++k)
+    xsmem = std::max(xsmem, flat_exchange_smem(g_sp_probs[k].p.R, g_sp_probs[k].p.mode));
+  if (err == cudaSuccess) err = flat_exchange_prepare(xsmem);
   for (int64_t j = 0; j < n_max && err == cudaSuccess; ++j) {
     bool ex = false;  // counted for at least one problem (a swap iteration or a trace row)
     for (int k = 0; k < np && !ex; ++k) {
@@ -498,17 +573,17 @@ int sweep_batch_static(pt_problem* const* ps, int count, const int64_t* n, const
       ex = j < fp.n && (fp.p.trace_E != nullptr ||
                         (fp.m > 0 && (fp.t0 + (uint64_t)j + 1) % (uint64_t)fp.m == 0));
     }
-    if (grid[0]) k_flat_half<kModeFerro, false><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles0, d_first0, 0, j);
-    if (grid[1]) k_flat_half<kModeGeneric, false><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles1, d_first1, 0, j);
+    if (grid[0] && err == cudaSuccess) err = launch_flat_half<kModeFerro, false>(grid[0], d_probs, d_tiles0, d_first0, 0, j, st);
+    if (grid[1] && err == cudaSuccess) err = launch_flat_half<kModeGeneric, false>(grid[1], d_probs, d_tiles1, d_first1, 0, j, st);
     if (ex) {
-      if (grid[0]) k_flat_half<kModeFerro, true><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles0, d_first0, 1, j);
-      if (grid[1]) k_flat_half<kModeGeneric, true><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles1, d_first1, 1, j);
-      k_flat_exchange<<<std::min(np, di.sms * 8), kFlatThreads, 0, st>>>(d_probs, np, j);
+      if (grid[0] && err == cudaSuccess) err = launch_flat_half<kModeFerro, true>(grid[0], d_probs, d_tiles0, d_first0, 1, j, st);
+      if (grid[1] && err == cudaSuccess) err = launch_flat_half<kModeGeneric, true>(grid[1], d_probs, d_tiles1, d_first1, 1, j, st);
+      if (err == cudaSuccess) err = launch_flat_exchange(d_probs, np, j, xsmem, di.sms, st);
     } else {
-      if (grid[0]) k_flat_half<kModeFerro, false><<<grid[0], kFlatThreads, 0, st>>>(d_probs, d_tiles0, d_first0, 1, j);
-      if (grid[1]) k_flat_half<kModeGeneric, false><<<grid[1], kFlatThreads, 0, st>>>(d_probs, d_tiles1, d_first1, 1, j);
+      if (grid[0] && err == cudaSuccess) err = launch_flat_half<kModeFerro, false>(grid[0], d_probs, d_tiles0, d_first0, 1, j, st);
+      if (grid[1] && err == cudaSuccess) err = launch_flat_half<kModeGeneric, false>(grid[1], d_probs, d_tiles1, d_first1, 1, j, st);
     }
-    err = cudaGetLastError();
+    if (err == cudaSuccess) err = cudaGetLastError();
   }
   if (err != cudaSuccess) {
     for (int j = 0; j < count; ++j) ps[j]->poisoned = PT_ECUDA;
