@@ -228,6 +228,17 @@ int pt_sweep_batch_static(pt_problem* const* problems, int count, const int64_t*
 int pt_set_batch_tuning(int strategy, int cluster, int joint_min_L);
 int pt_get_batch_tuning(int* strategy, int* cluster, int* joint_min_L);
 
+/* Tile size of PT_BATCH_FLAT, PT_BATCH_FLOW and pt_sweep_batch_static: each problem's words
+ * of one colour and plane are cut into max(1, round(words / tile_words)) equal tiles, one
+ * warp's unit of work (tile_words / 32 words per lane; default 512). Smaller tiles balance
+ * the warps better and cost more per-tile setup; results never depend on it. tile_words: a
+ * multiple of 32 in [PT_TILE_WORDS_MIN, PT_TILE_WORDS_MAX], else PT_EINVAL. Applies to
+ * later batches of every problem. */
+#define PT_TILE_WORDS_MIN 64
+#define PT_TILE_WORDS_MAX 1024
+int pt_set_batch_tile_words(int tile_words);
+int pt_get_batch_tile_words(int* tile_words);
+
 /* Energies E = E_int / s of the configurations at each temperature index, out[R]. */
 int pt_energies(pt_problem* p, double* out);
 

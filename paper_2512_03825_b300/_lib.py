@@ -66,6 +66,8 @@ SIGNATURES = [
     ("pt_set_batch_tuning", C.c_int, [C.c_int, C.c_int, C.c_int]),
     ("pt_get_batch_tuning", C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_int),
                                       C.POINTER(C.c_int)]),
+    ("pt_set_batch_tile_words", C.c_int, [C.c_int]),
+    ("pt_get_batch_tile_words", C.c_int, [C.POINTER(C.c_int)]),
     ("pt_energies", C.c_int, [P, C.POINTER(C.c_double)]),
     ("pt_magnetisations", C.c_int, [P, C.POINTER(C.c_double)]),
     ("pt_swap_stats", C.c_int, [P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),

@@ -205,17 +205,39 @@ class PTProblem:
         return int(lib.pt_device_bytes(self._h))
 
 
-def sweep_batch(problems: Sequence[PTProblem], n, exchange_every):
-    """Advance all problems together with the batched strategy (n, exchange_every: an int
-    or one value per problem)."""
+def _batch_call(fn, name, problems, n, exchange_every):
     k = len(problems)
     if k == 0:
         return
     ns = np.ascontiguousarray(np.broadcast_to(np.asarray(n, np.int64), (k,)))
     ms = np.ascontiguousarray(np.broadcast_to(np.asarray(exchange_every, np.int32), (k,)))
     hs = (C.c_void_p * k)(*[p.handle.value for p in problems])
-    check(lib.pt_sweep_batch(hs, k, _dptr(ns, C.c_int64), _dptr(ms, C.c_int32)),
-          "pt_sweep_batch")
+    check(fn(hs, k, _dptr(ns, C.c_int64), _dptr(ms, C.c_int32)), name)
+
+
+def sweep_batch(problems: Sequence[PTProblem], n, exchange_every):
+    """Advance all problems together with the batched strategy (n, exchange_every: an int
+    or one value per problem)."""
+    _batch_call(lib.pt_sweep_batch, "pt_sweep_batch", problems, n, exchange_every)
+
+
+def sweep_batch_static(problems: Sequence[PTProblem], n, exchange_every):
+    """The same batch through pt_sweep_batch_static: the lock-step strategy with its work
+    lists in the library's fixed device array (no device allocation; returns after the
+    lists are uploaded, the sweeps still queued on the problems' stream)."""
+    _batch_call(lib.pt_sweep_batch_static, "pt_sweep_batch_static", problems, n,
+                exchange_every)
+
+
+def set_batch_tile_words(tile_words: int) -> None:
+    """Words per warp tile of the tile strategies (a multiple of 32 in [64, 1024])."""
+    check(lib.pt_set_batch_tile_words(int(tile_words)), "pt_set_batch_tile_words")
+
+
+def batch_tile_words() -> int:
+    w = C.c_int()
+    check(lib.pt_get_batch_tile_words(C.byref(w)), "pt_get_batch_tile_words")
+    return w.value
 
 
 def estimate_device_bytes(L, betas, J=1.0, h=0.0):

@@ -1,9 +1,10 @@
 """Autotuner for the batched kernel's launch shape.
 
 Knobs: the batched strategy (lock-step tiles, the same tiles in one dataflow launch, or
-one persistent cluster kernel), and for the cluster kernel the CTAs per thread-block
-cluster and the lattice size from which a problem is spread over a whole cluster instead
-of one CTA. They change only how work is
+one persistent cluster kernel); for the tile strategies the words per warp tile (the words
+each lane updates per tile: tile_words / 32); for the cluster kernel the CTAs per
+thread-block cluster and the lattice size from which a problem is spread over a whole
+cluster instead of one CTA. They change only how work is
 distributed, never a result: `tune` checks that every candidate leaves every problem in the
 same state (spins, temperature map, swap counters) before it compares times.
 
@@ -22,22 +23,28 @@ from ._lib import check, lib
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "autotune_cache.json")
 FLAT, CLUSTER, FLOW = 0, 1, 2
-DEFAULT = {"strategy": FLAT, "cluster": 4, "joint_min_L": 128}
-CANDIDATES: Tuple[Tuple[int, int, int], ...] = (
-    (FLAT, 1, 128), (FLOW, 1, 128), (CLUSTER, 1, 1 << 20), (CLUSTER, 2, 128), (CLUSTER, 3, 128),
-    (CLUSTER, 4, 256), (CLUSTER, 4, 128), (CLUSTER, 4, 96), (CLUSTER, 6, 128),
-    (CLUSTER, 8, 128))
+DEFAULT = {"strategy": FLAT, "cluster": 4, "joint_min_L": 128, "tile_words": 512}
+# (strategy, cluster, joint_min_L, tile_words)
+CANDIDATES: Tuple[Tuple[int, int, int, int], ...] = (
+    (FLAT, 1, 128, 128), (FLAT, 1, 128, 256), (FLAT, 1, 128, 512), (FLAT, 1, 128, 1024),
+    (FLOW, 1, 128, 256), (FLOW, 1, 128, 512),
+    (CLUSTER, 1, 1 << 20, 512), (CLUSTER, 2, 128, 512), (CLUSTER, 3, 128, 512),
+    (CLUSTER, 4, 256, 512), (CLUSTER, 4, 128, 512), (CLUSTER, 4, 96, 512),
+    (CLUSTER, 6, 128, 512), (CLUSTER, 8, 128, 512))
 
 
-def set_tuning(strategy: int, cluster: int, joint_min_L: int) -> None:
+def set_tuning(strategy: int, cluster: int, joint_min_L: int, tile_words: int = 512) -> None:
     check(lib.pt_set_batch_tuning(int(strategy), int(cluster), int(joint_min_L)),
           "pt_set_batch_tuning")
+    check(lib.pt_set_batch_tile_words(int(tile_words)), "pt_set_batch_tile_words")
 
 
 def get_tuning() -> Dict[str, int]:
-    s, c, j = C.c_int(), C.c_int(), C.c_int()
+    s, c, j, w = C.c_int(), C.c_int(), C.c_int(), C.c_int()
     check(lib.pt_get_batch_tuning(C.byref(s), C.byref(c), C.byref(j)), "pt_get_batch_tuning")
-    return {"strategy": s.value, "cluster": c.value, "joint_min_L": j.value}
+    check(lib.pt_get_batch_tile_words(C.byref(w)), "pt_get_batch_tile_words")
+    return {"strategy": s.value, "cluster": c.value, "joint_min_L": j.value,
+            "tile_words": w.value}
 
 
 def _device_key() -> str:
@@ -59,7 +66,8 @@ def _load_cache() -> dict:
 def apply_cached_or_default(workload: str = "batched") -> Dict[str, int]:
     """Apply the cached choice for this device (or the default) and return it."""
     entry = _load_cache().get(_device_key(), {}).get(workload, DEFAULT)
-    set_tuning(entry.get("strategy", FLAT), entry["cluster"], entry["joint_min_L"])
+    set_tuning(entry.get("strategy", FLAT), entry["cluster"], entry["joint_min_L"],
+               entry.get("tile_words", DEFAULT["tile_words"]))
     return get_tuning()
 
 
@@ -72,7 +80,7 @@ def _snapshot(handles):
 
 
 def tune(problems: Sequence, sweeps: int = 200, every: int = 1,
-         candidates: Sequence[Tuple[int, int, int]] = CANDIDATES, workload: str = "batched",
+         candidates: Sequence[Tuple[int, int, int, int]] = CANDIDATES, workload: str = "batched",
          repeats: int = 2, save: bool = True, log=None) -> Dict[str, object]:
     """Time every candidate launch shape on `problems` (workload Problems); keep the fastest.
     Raises if two candidates disagree on any problem's final state."""
@@ -102,11 +110,12 @@ def tune(problems: Sequence, sweeps: int = 200, every: int = 1,
                 h.close()
         results.append((best, cand))
         if log:
-            log("strategy=%d cluster=%d joint_min_L=%d: %.4f s" % (cand + (best,)))
+            log("strategy=%d cluster=%d joint_min_L=%d tile_words=%d: %.4f s"
+                % (tuple(cand) + (best,)))
     results.sort()
-    best_t, (st, cl, jm) = results[0]
-    choice = {"strategy": st, "cluster": cl, "joint_min_L": jm}
-    set_tuning(st, cl, jm)
+    best_t, (st, cl, jm, tw) = results[0]
+    choice = {"strategy": st, "cluster": cl, "joint_min_L": jm, "tile_words": tw}
+    set_tuning(st, cl, jm, tw)
     if save:
         cache = _load_cache()
         cache.setdefault(_device_key(), {})[workload] = dict(choice, seconds=best_t,

@@ -482,7 +482,7 @@ int sweep_batch_static_entry(pt_problem* const* ps, int count, const int64_t* n,
   cudaStream_t st = 0;
   int rc = check_batch(ps, count, n, every, &st);
   if (rc) return rc;
-  rc = sweep_batch_static(ps, count, n, every, st, ps[0]->dev_info);
+  rc = sweep_batch_static(ps, count, n, every, st, ps[0]->dev_info, g_batch_tuning.tile_words);
   if (rc) return rc;
   advance_counters(ps, count, n, every);
   return PT_OK;
@@ -516,8 +516,9 @@ int sweep_batch(pt_problem* const* ps, int count, const int64_t* n, const int* e
   for (int j = 0; j < count; ++j)  // trace rows are written by the lock-step exchange launch
     if (ps[j]->dev.trace_E != nullptr) tune.strategy = PT_BATCH_FLAT;
   if (tune.strategy == PT_BATCH_FLAT || tune.strategy == PT_BATCH_FLOW) {
-    rc = tune.strategy == PT_BATCH_FLAT ? sweep_batch_flat(ps, count, n, every, st, di)
-                                        : sweep_batch_flow(ps, count, n, every, st, di);
+    rc = tune.strategy == PT_BATCH_FLAT
+             ? sweep_batch_flat(ps, count, n, every, st, di, tune.tile_words)
+             : sweep_batch_flow(ps, count, n, every, st, di, tune.tile_words);
     if (rc) return rc;
     advance_counters(ps, count, n, every);
     return PT_OK;

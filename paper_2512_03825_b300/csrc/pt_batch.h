@@ -12,25 +12,28 @@ namespace ptb {
 // kernel of whole problems, pt_batch.cu). For the last, cluster = CTAs per cluster (1 = no
 // clusters); problems with L >= joint_min_L are spread over a whole cluster, smaller ones run
 // on one CTA.
+// For the tile strategies, tile_words = target words per warp tile (tile_words / 32 words
+// of one colour per lane).
 struct BatchTuning {
   int strategy = PT_BATCH_FLAT;
   int cluster = 4;
   int joint_min_L = 128;
+  int tile_words = 512;
 };
 extern BatchTuning g_batch_tuning;
 
 struct DeviceInfo;
 // The lock-step path (pt_flat.cu); problems are already checked.
 int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const int* every,
-                     cudaStream_t st, const DeviceInfo& di);
+                     cudaStream_t st, const DeviceInfo& di, int tile_words);
 
 // The dataflow path (pt_flow.cu); problems are already checked.
 int sweep_batch_flow(pt_problem* const* ps, int count, const int64_t* n, const int* every,
-                     cudaStream_t st, const DeviceInfo& di);
+                     cudaStream_t st, const DeviceInfo& di, int tile_words);
 
 // The allocation-free variant of the lock-step path (pt_flat.cu); problems are checked.
 int sweep_batch_static(pt_problem* const* ps, int count, const int64_t* n, const int* every,
-                       cudaStream_t st, const DeviceInfo& di);
+                       cudaStream_t st, const DeviceInfo& di, int tile_words);
 
 int sweep_batch(pt_problem* const* problems, int count, const int64_t* n,
                 const int* exchange_every);

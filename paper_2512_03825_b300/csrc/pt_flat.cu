@@ -244,7 +244,8 @@ void deal_tiles(const std::vector<Tile>& in, const std::vector<FlatProblem>& pro
 }
 
 int64_t build_flat_lists(pt_problem* const* ps, int count, const int64_t* n, const int* every,
-                         std::vector<FlatProblem>* probs, std::vector<Tile> tiles[2]) {
+                         int tile_words, std::vector<FlatProblem>* probs,
+                         std::vector<Tile> tiles[2]) {
   int64_t n_max = 0;
   for (int j = 0; j < count; ++j) {
     if (n[j] <= 0) continue;
@@ -259,7 +260,7 @@ int64_t build_flat_lists(pt_problem* const* ps, int count, const int64_t* n, con
     fp.stall = p->stall;
     const int pi = (int)probs->size();
     const int words = p->L * (p->L / 2);
-    const int ntile = std::max(1, (words + kTileWords / 2) / kTileWords);
+    const int ntile = std::max(1, (words + tile_words / 2) / tile_words);
     fp.ntiles = ntile * p->W;
     probs->push_back(fp);
     n_max = std::max(n_max, n[j]);
@@ -277,10 +278,10 @@ int64_t build_flat_lists(pt_problem* const* ps, int count, const int64_t* n, con
 }
 
 int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const int* every,
-                     cudaStream_t st, const DeviceInfo& di) {
+                     cudaStream_t st, const DeviceInfo& di, int tile_words) {
   std::vector<FlatProblem> probs;
   std::vector<Tile> tiles[2];  // by mode
-  const int64_t n_max = build_flat_lists(ps, count, n, every, &probs, tiles);
+  const int64_t n_max = build_flat_lists(ps, count, n, every, tile_words, &probs, tiles);
   if (probs.empty()) return PT_OK;
   // one persistent wave per launch: as many CTAs as are resident at once, each warp with
   // its own share of the tiles
@@ -461,7 +462,7 @@ void static_deal(int lo, int hi, int nwarps, int* first) {
 }  // namespace
 
 int sweep_batch_static(pt_problem* const* ps, int count, const int64_t* n, const int* every,
-                       cudaStream_t st, const DeviceInfo& di) {
+                       cudaStream_t st, const DeviceInfo& di, int tile_words) {
   std::lock_guard<std::mutex> lk(g_static_mu);
   if (di.device < 0 || di.device >= 64) return fail(PT_ENODEV, "device index %d", di.device);
   // set-up, once per device, with that device current: the device address of the array
@@ -495,7 +496,7 @@ int sweep_batch_static(pt_problem* const* ps, int count, const int64_t* n, const
       fp.m = every[j];
       n_max = std::max(n_max, n[j]);
       const int words = p->L * (p->L / 2);
-      const int ntile = std::max(1, (words + kTileWords / 2) / kTileWords);
+      const int ntile = std::max(1, (words + tile_words / 2) / tile_words);
       if ((int64_t)nt + (int64_t)ntile * p->W > kStaticMaxTiles)
         return fail(PT_EINVAL, "pt_sweep_batch_static: more than %d work tiles (the batch is "
                     "too large for the %zu-byte static work area)", kStaticMaxTiles,

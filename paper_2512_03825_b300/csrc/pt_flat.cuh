@@ -14,7 +14,6 @@
 namespace ptb {
 
 constexpr int kFlatThreads = 256;
-constexpr int kTileWords = 512;  // target words per warp tile (16 per lane)
 
 struct FlatProblem {
   DevProblem p;
@@ -311,8 +310,12 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
 // ---------------------------------------------------------------------------------------
 // Problems with n > 0 and their tiles (split by mode: [0] ferro, [1] generic); returns the
 // largest n.
+// Tiles hold about tile_words words (a problem's words of one colour and plane in
+// max(1, round(words / tile_words)) equal parts, so at most 1.5 tile_words: a lane's counts
+// over one tile stay below 2^8).
 int64_t build_flat_lists(pt_problem* const* ps, int count, const int64_t* n, const int* every,
-                         std::vector<FlatProblem>* probs, std::vector<Tile> tiles[2]);
+                         int tile_words, std::vector<FlatProblem>* probs,
+                         std::vector<Tile> tiles[2]);
 // Longest-processing-time-first assignment of tiles to `nwarps` warps: the tiles reordered
 // warp by warp and the CSR offsets first[0..nwarps].
 void deal_tiles(const std::vector<Tile>& in, const std::vector<FlatProblem>& probs,

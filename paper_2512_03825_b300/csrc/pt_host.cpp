@@ -1190,6 +1190,22 @@ int pt_set_batch_tuning(int strategy, int cluster, int joint_min_L) {
   return PT_OK;
 }
 
+int pt_set_batch_tile_words(int tile_words) {
+  if (tile_words < PT_TILE_WORDS_MIN || tile_words > PT_TILE_WORDS_MAX || tile_words % 32 != 0)
+    return fail(PT_EINVAL, "tile_words = %d (a multiple of 32 in [%d, %d])", tile_words,
+                PT_TILE_WORDS_MIN, PT_TILE_WORDS_MAX);
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_batch_tuning.tile_words = tile_words;
+  return PT_OK;
+}
+
+int pt_get_batch_tile_words(int* tile_words) {
+  if (!tile_words) return fail(PT_EINVAL, "null output");
+  std::lock_guard<std::mutex> lk(g_mu);
+  *tile_words = g_batch_tuning.tile_words;
+  return PT_OK;
+}
+
 int pt_get_batch_tuning(int* strategy, int* cluster, int* joint_min_L) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (strategy) *strategy = g_batch_tuning.strategy;

@@ -195,3 +195,20 @@ def test_load_validates_before_the_device(pt):
     bad.append(ck.build(5, betas, 1.0, 0.0, 7, 40, 13, 1, sot, att, acc, words))  # odd L
     for k, data in enumerate(bad):
         assert _load_rc(pt, data) == pt.PT_EINVAL, k
+
+
+def test_batch_tile_words_validated(pt):
+    """The tile size knob: multiples of 32 in [64, 1024] only; host state, no device."""
+    old = C.c_int()
+    assert pt.lib.pt_get_batch_tile_words(C.byref(old)) == 0
+    assert old.value % 32 == 0 and 64 <= old.value <= 1024
+    try:
+        for bad in (0, 32, 63, 100, 1056, 4096, -64):
+            assert pt.lib.pt_set_batch_tile_words(bad) == pt.PT_EINVAL, bad
+        for good in (64, 256, 1024):
+            assert pt.lib.pt_set_batch_tile_words(good) == 0
+            got = C.c_int()
+            assert pt.lib.pt_get_batch_tile_words(C.byref(got)) == 0 and got.value == good
+        assert pt.lib.pt_get_batch_tile_words(None) == pt.PT_EINVAL
+    finally:
+        pt.lib.pt_set_batch_tile_words(old.value)

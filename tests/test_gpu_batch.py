@@ -115,6 +115,35 @@ def test_batched_workload_sample_vs_oracle(api, tuning, strategy):
             np.testing.assert_array_equal(x, y)
 
 
+@pytest.mark.parametrize("tile_words", [64, 160, 1024])
+def test_tile_size_never_changes_a_result(api, tuning, tile_words):
+    """Lock-step, dataflow and allocation-free batches at several tile sizes equal the plain
+    path (the mixed problem set: ragged L, R from 1 to 69, every mode)."""
+    import ctypes as C
+    from paper_2512_03825_b300._lib import lib
+    probs = mixed_problems(n=16, seed=11)
+    plain = []
+    for pr in probs:
+        g = api.PTProblem(pr.L, pr.betas, J=pr.J, h=pr.h, seed=pr.seed)
+        g.sweep(pr.sweeps, pr.every)
+        plain.append(state(g))
+    old = C.c_int()
+    lib.pt_get_batch_tile_words(C.byref(old))
+    try:
+        assert lib.pt_set_batch_tile_words(tile_words) == 0
+        for st in (0, 2, "static"):
+            if st != "static":
+                tuning(1, 4, st)
+            batch = [api.PTProblem(pr.L, pr.betas, J=pr.J, h=pr.h, seed=pr.seed) for pr in probs]
+            run = api.sweep_batch_static if st == "static" else api.sweep_batch
+            run(batch, [pr.sweeps for pr in probs], [pr.every for pr in probs])
+            for j, (b, ref) in enumerate(zip(batch, plain)):
+                assert_state_equal(state(b), ref, "tile %d strategy %s problem %d"
+                                   % (tile_words, st, j))
+    finally:
+        lib.pt_set_batch_tile_words(old.value)
+
+
 def test_batch_rejects_bad_input(api):
     from paper_2512_03825_b300._lib import PTError
     g = api.PTProblem(8, [0.3, 0.4], seed=1)
@@ -171,3 +200,16 @@ def test_flow_wait_runs_out_and_context_survives(api, tuning):
         o.sweep(6, 1)
         np.testing.assert_array_equal(h.spins(), o.spins())
         np.testing.assert_array_equal(h.chain_map(), o.chain_map())
+
+
+def test_autotuner_compares_equal_results(api, tuning):
+    """The autotuner times a few candidates (tile sizes, strategies), checks that they all
+    leave the problems in the same state, and applies the fastest without saving it."""
+    from paper_2512_03825_b300 import autotune
+    probs = W.batched_problems(n=10)
+    cands = [(0, 1, 128, 128), (0, 1, 128, 1024), (2, 1, 128, 256), (1, 2, 64, 512)]
+    out = autotune.tune(probs, sweeps=4, every=1, candidates=cands, repeats=1, save=False)
+    assert tuple(out["choice"].values()) in cands
+    assert len(out["timings"]) == len(cands)
+    assert autotune.get_tuning() == out["choice"]
+    autotune.set_tuning(**autotune.DEFAULT)
