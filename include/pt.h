@@ -209,7 +209,12 @@ int pt_sweep_batch_static(pt_problem* const* problems, int count, const int64_t*
 /* How pt_sweep_batch runs (chosen by the autotuner; results never depend on it):
  *   PT_BATCH_FLAT    -- all problems advance sweep by sweep together; every half sweep is
  *                       one launch over equal-sized word tiles of all problems, followed by
- *                       an exchange launch when any problem is due;
+ *                       an exchange launch when any problem is due; the host deals the
+ *                       tiles to the warps (longest processing time first);
+ *   PT_BATCH_QUEUE   -- PT_BATCH_FLAT with the tiles handed out on the device: one tile per
+ *                       warp first, then each warp that finishes a tile takes the next
+ *                       (largest first) from a counter, so the warps finish together
+ *                       however the SMs' loads differ;
  *   PT_BATCH_CLUSTER -- one persistent kernel; a problem with L >= joint_min_L runs on a
  *                       whole thread-block cluster of `cluster` CTAs (1 to 16) for all of its
  *                       sweeps, smaller ones on a single CTA;
@@ -220,20 +225,24 @@ int pt_sweep_batch_static(pt_problem* const* problems, int count, const int64_t*
  *                       the problem's wait limit (pt_set_wait_limit); a wait that runs out
  *                       marks every problem of the call PT_ETIMEOUT, reported by the next
  *                       pt_synchronize or getter. pt_debug_stall_barrier applies to it too.
- * Applies to later batches of every problem. PT_EINVAL for an unknown strategy, cluster
- * outside 1..16 or joint_min_L < 4. */
+ * pt_sweep_batch_static hands its tiles out as PT_BATCH_QUEUE does when that strategy is
+ * set, and as PT_BATCH_FLAT does otherwise. A batch with a traced problem runs
+ * PT_BATCH_QUEUE when it is set, and PT_BATCH_FLAT otherwise. Applies to later batches of
+ * every problem. PT_EINVAL for an unknown strategy, cluster outside 1..16 or
+ * joint_min_L < 4. */
 #define PT_BATCH_FLAT 0
 #define PT_BATCH_CLUSTER 1
 #define PT_BATCH_FLOW 2
+#define PT_BATCH_QUEUE 3
 int pt_set_batch_tuning(int strategy, int cluster, int joint_min_L);
 int pt_get_batch_tuning(int* strategy, int* cluster, int* joint_min_L);
 
-/* Tile size of PT_BATCH_FLAT, PT_BATCH_FLOW and pt_sweep_batch_static: each problem's words
- * of one colour and plane are cut into max(1, round(words / tile_words)) equal tiles, one
- * warp's unit of work (tile_words / 32 words per lane; default 512). Smaller tiles balance
- * the warps better and cost more per-tile setup; results never depend on it. tile_words: a
- * multiple of 32 in [PT_TILE_WORDS_MIN, PT_TILE_WORDS_MAX], else PT_EINVAL. Applies to
- * later batches of every problem. */
+/* Tile size of PT_BATCH_FLAT, PT_BATCH_QUEUE, PT_BATCH_FLOW and pt_sweep_batch_static:
+ * each problem's words of one colour and plane are cut into max(1, round(words /
+ * tile_words)) equal tiles, one warp's unit of work (tile_words / 32 words per lane;
+ * default 512). Smaller tiles balance the warps better and cost more per-tile setup;
+ * results never depend on it. tile_words: a multiple of 32 in [PT_TILE_WORDS_MIN,
+ * PT_TILE_WORDS_MAX], else PT_EINVAL. Applies to later batches of every problem. */
 #define PT_TILE_WORDS_MIN 64
 #define PT_TILE_WORDS_MAX 1024
 int pt_set_batch_tile_words(int tile_words);

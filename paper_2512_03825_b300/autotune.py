@@ -1,7 +1,7 @@
 """Autotuner for the batched kernel's launch shape.
 
-Knobs: the batched strategy (lock-step tiles, the same tiles in one dataflow launch, or
-one persistent cluster kernel); for the tile strategies the words per warp tile (the words
+Knobs: the batched strategy (lock-step tiles dealt by the host or handed out by a device
+queue, the same tiles in one dataflow launch, or one persistent cluster kernel); for the tile strategies the words per warp tile (the words
 each lane updates per tile: tile_words / 32); for the cluster kernel the CTAs per
 thread-block cluster and the lattice size from which a problem is spread over a whole
 cluster instead of one CTA. They change only how work is
@@ -22,11 +22,12 @@ from ._lib import check, lib
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "autotune_cache.json")
-FLAT, CLUSTER, FLOW = 0, 1, 2
+FLAT, CLUSTER, FLOW, QUEUE = 0, 1, 2, 3
 DEFAULT = {"strategy": FLAT, "cluster": 4, "joint_min_L": 128, "tile_words": 512}
 # (strategy, cluster, joint_min_L, tile_words)
 CANDIDATES: Tuple[Tuple[int, int, int, int], ...] = (
-    (FLAT, 1, 128, 128), (FLAT, 1, 128, 256), (FLAT, 1, 128, 512), (FLAT, 1, 128, 1024),
+    (FLAT, 1, 128, 256), (FLAT, 1, 128, 512), (FLAT, 1, 128, 1024),
+    (QUEUE, 1, 128, 256), (QUEUE, 1, 128, 512), (QUEUE, 1, 128, 1024),
     (FLOW, 1, 128, 256), (FLOW, 1, 128, 512),
     (CLUSTER, 1, 1 << 20, 512), (CLUSTER, 2, 128, 512), (CLUSTER, 3, 128, 512),
     (CLUSTER, 4, 256, 512), (CLUSTER, 4, 128, 512), (CLUSTER, 4, 96, 512),

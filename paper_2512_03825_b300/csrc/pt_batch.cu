@@ -482,7 +482,8 @@ int sweep_batch_static_entry(pt_problem* const* ps, int count, const int64_t* n,
   cudaStream_t st = 0;
   int rc = check_batch(ps, count, n, every, &st);
   if (rc) return rc;
-  rc = sweep_batch_static(ps, count, n, every, st, ps[0]->dev_info, g_batch_tuning.tile_words);
+  rc = sweep_batch_static(ps, count, n, every, st, ps[0]->dev_info, g_batch_tuning.tile_words,
+                          g_batch_tuning.strategy == PT_BATCH_QUEUE);
   if (rc) return rc;
   advance_counters(ps, count, n, every);
   return PT_OK;
@@ -514,11 +515,14 @@ int sweep_batch(pt_problem* const* ps, int count, const int64_t* n, const int* e
   const DeviceInfo& di = ps[0]->dev_info;
   BatchTuning tune = g_batch_tuning;
   for (int j = 0; j < count; ++j)  // trace rows are written by the lock-step exchange launch
-    if (ps[j]->dev.trace_E != nullptr) tune.strategy = PT_BATCH_FLAT;
-  if (tune.strategy == PT_BATCH_FLAT || tune.strategy == PT_BATCH_FLOW) {
-    rc = tune.strategy == PT_BATCH_FLAT
-             ? sweep_batch_flat(ps, count, n, every, st, di, tune.tile_words)
-             : sweep_batch_flow(ps, count, n, every, st, di, tune.tile_words);
+    if (ps[j]->dev.trace_E != nullptr && tune.strategy != PT_BATCH_QUEUE)
+      tune.strategy = PT_BATCH_FLAT;
+  if (tune.strategy == PT_BATCH_FLAT || tune.strategy == PT_BATCH_QUEUE ||
+      tune.strategy == PT_BATCH_FLOW) {
+    rc = tune.strategy == PT_BATCH_FLOW
+             ? sweep_batch_flow(ps, count, n, every, st, di, tune.tile_words)
+             : sweep_batch_flat(ps, count, n, every, st, di, tune.tile_words,
+                                tune.strategy == PT_BATCH_QUEUE);
     if (rc) return rc;
     advance_counters(ps, count, n, every);
     return PT_OK;

@@ -7,7 +7,8 @@
 #include "pt.h"
 
 namespace ptb {
-// Batched path: strategy PT_BATCH_FLAT (lock-step tiles, pt_flat.cu), PT_BATCH_FLOW (the same
+// Batched path: strategy PT_BATCH_FLAT or PT_BATCH_QUEUE (lock-step tiles, dealt by the
+// host or handed out by a device queue, pt_flat.cu), PT_BATCH_FLOW (the same
 // tiles in one persistent dataflow launch, pt_flow.cu) or PT_BATCH_CLUSTER (one persistent
 // kernel of whole problems, pt_batch.cu). For the last, cluster = CTAs per cluster (1 = no
 // clusters); problems with L >= joint_min_L are spread over a whole cluster, smaller ones run
@@ -24,8 +25,9 @@ extern BatchTuning g_batch_tuning;
 
 struct DeviceInfo;
 // The lock-step path (pt_flat.cu); problems are already checked.
+// queued: tiles handed out by the device queue (PT_BATCH_QUEUE) instead of dealt by the host.
 int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const int* every,
-                     cudaStream_t st, const DeviceInfo& di, int tile_words);
+                     cudaStream_t st, const DeviceInfo& di, int tile_words, bool queued);
 
 // The dataflow path (pt_flow.cu); problems are already checked.
 int sweep_batch_flow(pt_problem* const* ps, int count, const int64_t* n, const int* every,
@@ -33,7 +35,7 @@ int sweep_batch_flow(pt_problem* const* ps, int count, const int64_t* n, const i
 
 // The allocation-free variant of the lock-step path (pt_flat.cu); problems are checked.
 int sweep_batch_static(pt_problem* const* ps, int count, const int64_t* n, const int* every,
-                       cudaStream_t st, const DeviceInfo& di, int tile_words);
+                       cudaStream_t st, const DeviceInfo& di, int tile_words, bool queued);
 
 int sweep_batch(pt_problem* const* problems, int count, const int64_t* n,
                 const int* exchange_every);

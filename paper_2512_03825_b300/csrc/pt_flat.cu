@@ -23,27 +23,60 @@ namespace ptb {
 namespace {
 
 // ---------------------------------------------------------------------------------------
-// Half sweep over all warp tiles; tiles are dealt to warps by the host (longest-processing-
-// time first on their Philox work), warp g taking tiles [first[g], first[g + 1]) of the
-// list. With COUNT (colour 1 only) warps whose problem is due for an exchange after this
-// sweep also count bonds (and up spins) for it.
+// Two ways to hand a launch's tiles to its warps (the host sorts a mode's tiles by their
+// Philox work, largest first, for both):
+//  * dealt (PT_BATCH_FLAT): the host deals the sorted tiles to the warps longest-processing-
+//    time first, warp g taking tiles [first[g], first[g + 1]);
+//  * queued (PT_BATCH_QUEUE): the first G tiles (G = the launch's warps) are dealt one per
+//    warp, round robin over the CTAs (warp i of CTA c takes tile i * gridDim.x + c), so the
+//    largest tiles spread evenly over the SMs; after that a warp that finishes a tile takes
+//    the next one from a device counter, so the rest go greedily to whichever warp is free
+//    (list scheduling) and the warps finish together whatever their SM's load. A warp takes
+//    a counter value only when it is free: taking one a tile ahead would let the warps that
+//    start first claim two tiles each while others still have none.
+// The queue counter runs on across the launches of a batch: a launch takes ntiles - G
+// values from it when ntiles > G (one per queued tile and one that ends each warp's loop)
+// and ntiles when ntiles <= G (one per warp with a tile) -- ntiles either way -- so launch
+// number k of the mode starts at base = k ntiles, which the host passes in.
 // ---------------------------------------------------------------------------------------
-template <int MODE, bool COUNT>
+struct TileQueue {
+  unsigned long long* ctr;  // values taken so far by this mode's launches in the batch
+  unsigned long long base;  // the counter's value when this launch starts
+  int ntiles;
+};
+
+// Half sweep over all tiles of the launch (QUEUED: handed out by the queue; else dealt,
+// `first` the per-warp offsets). With COUNT (colour 1 only) warps whose problem is due for
+// an exchange after this sweep also count bonds (and up spins) for it.
+template <int MODE, bool COUNT, bool QUEUED>
 __global__ void __launch_bounds__(kFlatThreads, 2) k_flat_half(const FlatProblem* __restrict__ probs,
                                                              const Tile* __restrict__ tiles,
                                                              const int* __restrict__ first,
-                                                             int colour, int64_t j) {
+                                                             const TileQueue q, int colour,
+                                                             int64_t j) {
   __shared__ PlaneGeneric gen[kFlatThreads / 32];
   __shared__ uint4 thr_s[kFlatThreads / 32][16];  // ferro thresholds of each warp's tile
-  const int wib = threadIdx.x >> 5;
-  const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int tend = first[g + 1];
-  for (int tix = first[g]; tix < tend; ++tix) {
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto run = [&](long long tix) {
     const Tile tl = tiles[tix];
     const FlatProblem& fp = probs[tl.prob];
-    if (j >= fp.n) continue;  // warp-uniform
+    if (j >= fp.n) return;  // warp-uniform
     const bool count = COUNT && counts_after(fp, j);
     tile_half<MODE, COUNT, false>(fp, tl, colour, j, count, thr_s[wib], &gen[wib]);
+  };
+  if (!QUEUED) {
+    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int tend = first[g + 1];
+    for (int tix = first[g]; tix < tend; ++tix) run(tix);
+    return;
+  }
+  const long long G = (long long)gridDim.x * (kFlatThreads / 32);
+  long long tix = (long long)wib * gridDim.x + blockIdx.x;  // the dealt first tile
+  while (tix < q.ntiles) {
+    run(tix);
+    unsigned long long v = 0;
+    if (lane == 0) v = atomicAdd(q.ctr, 1ull) - q.base;
+    tix = G + (long long)__shfl_sync(0xffffffffu, v, 0);
   }
 }
 
@@ -188,12 +221,48 @@ cudaError_t launch_flat_exchange(const FlatProblem* d_probs, int np, int64_t j, 
   return cudaGetLastError();
 }
 
-// Half sweep `colour` of sweep j over one mode's tile list.
+// One mode's tiles on the device and the state of its queue in a batch.
+struct ModeTiles {
+  int grid = 0;  // CTAs of each launch (0: the mode has no tiles)
+  const Tile* tiles = nullptr;
+  int ntiles = 0;
+  const int* first = nullptr;         // dealt: per-warp offsets; queued: nullptr
+  unsigned long long* ctr = nullptr;  // queued: zeroed before the batch's first launch
+  unsigned long long base = 0;
+};
+
+// Half sweep `colour` of sweep j over one mode's tiles.
 template <int MODE, bool COUNT>
-cudaError_t launch_flat_half(int grid, const FlatProblem* d_probs, const Tile* d_tiles,
-                             const int* d_first, int colour, int64_t j, cudaStream_t st) {
-  k_flat_half<MODE, COUNT><<<grid, kFlatThreads, 0, st>>>(d_probs, d_tiles, d_first, colour, j);
+cudaError_t launch_flat_half(ModeTiles& mt, const FlatProblem* d_probs, int colour, int64_t j,
+                             cudaStream_t st) {
+  if (mt.grid == 0) return cudaSuccess;
+  const TileQueue q{mt.ctr, mt.base, mt.ntiles};
+  if (mt.first != nullptr) {
+    k_flat_half<MODE, COUNT, false><<<mt.grid, kFlatThreads, 0, st>>>(d_probs, mt.tiles,
+                                                                      mt.first, q, colour, j);
+  } else {
+    k_flat_half<MODE, COUNT, true><<<mt.grid, kFlatThreads, 0, st>>>(d_probs, mt.tiles, nullptr,
+                                                                     q, colour, j);
+    mt.base += (unsigned long long)mt.ntiles;
+  }
   return cudaGetLastError();
+}
+
+// The launches of sweep j: half sweep 0, half sweep 1 (counting when `counted`: some
+// problem's swap iteration or trace row follows), then the exchange step when counted.
+cudaError_t launch_flat_sweep(ModeTiles mt[2], const FlatProblem* d_probs, int np, int64_t j,
+                              bool counted, size_t xsmem, int sms, cudaStream_t st) {
+  cudaError_t err = launch_flat_half<kModeFerro, false>(mt[0], d_probs, 0, j, st);
+  if (err == cudaSuccess) err = launch_flat_half<kModeGeneric, false>(mt[1], d_probs, 0, j, st);
+  if (counted) {
+    if (err == cudaSuccess) err = launch_flat_half<kModeFerro, true>(mt[0], d_probs, 1, j, st);
+    if (err == cudaSuccess) err = launch_flat_half<kModeGeneric, true>(mt[1], d_probs, 1, j, st);
+    if (err == cudaSuccess) err = launch_flat_exchange(d_probs, np, j, xsmem, sms, st);
+  } else {
+    if (err == cudaSuccess) err = launch_flat_half<kModeFerro, false>(mt[0], d_probs, 1, j, st);
+    if (err == cudaSuccess) err = launch_flat_half<kModeGeneric, false>(mt[1], d_probs, 1, j, st);
+  }
+  return err;
 }
 
 // Shared memory of the batch's exchange launches; raises the kernel's limit above the
@@ -243,6 +312,13 @@ void deal_tiles(const std::vector<Tile>& in, const std::vector<FlatProblem>& pro
   (*first)[nwarps] = (int)out->size();
 }
 
+// A mode's tiles sorted by tile_cost, largest first (ties keep their order).
+void sort_tiles(std::vector<Tile>* tiles, const std::vector<FlatProblem>& probs) {
+  std::stable_sort(tiles->begin(), tiles->end(), [&](const Tile& a, const Tile& b) {
+    return tile_cost(a, probs[a.prob].p.R) > tile_cost(b, probs[b.prob].p.R);
+  });
+}
+
 int64_t build_flat_lists(pt_problem* const* ps, int count, const int64_t* n, const int* every,
                          int tile_words, std::vector<FlatProblem>* probs,
                          std::vector<Tile> tiles[2]) {
@@ -278,59 +354,70 @@ int64_t build_flat_lists(pt_problem* const* ps, int count, const int64_t* n, con
 }
 
 int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const int* every,
-                     cudaStream_t st, const DeviceInfo& di, int tile_words) {
+                     cudaStream_t st, const DeviceInfo& di, int tile_words, bool queued) {
   std::vector<FlatProblem> probs;
   std::vector<Tile> tiles[2];  // by mode
   const int64_t n_max = build_flat_lists(ps, count, n, every, tile_words, &probs, tiles);
   if (probs.empty()) return PT_OK;
-  // one persistent wave per launch: as many CTAs as are resident at once, each warp with
-  // its own share of the tiles
+  // one wave per launch: as many CTAs as are resident at once, their warps taking the
+  // tiles from the mode's queue
   int per_sm[2] = {1, 1};
   cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm[0], k_flat_half<kModeFerro, true>, kFlatThreads, 0);
+      &per_sm[0], k_flat_half<kModeFerro, true, false>, kFlatThreads, 0);
   if (err == cudaSuccess)
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm[1], k_flat_half<kModeGeneric, true>, kFlatThreads, 0);
+        &per_sm[1], k_flat_half<kModeGeneric, true, false>, kFlatThreads, 0);
   if (err != cudaSuccess) return fail(PT_ECUDA, "occupancy: %s", cudaGetErrorString(err));
   const int wpb = kFlatThreads / 32;
-  std::vector<Tile> dealt[2];
-  std::vector<int> first[2];
-  int grid[2] = {0, 0};
+  ModeTiles mt[2];
+  std::vector<int> first[2];  // dealt: per-warp offsets
   for (int md = 0; md < 2; ++md) {
     if (tiles[md].empty()) continue;
     const int blocks = std::max(1, per_sm[md]) * di.sms;
     const int needed = (int)((tiles[md].size() + wpb - 1) / wpb);
-    grid[md] = std::max(1, std::min(blocks, needed));
-    deal_tiles(tiles[md], probs, grid[md] * wpb, &dealt[md], &first[md]);
+    mt[md].grid = std::max(1, std::min(blocks, needed));
+    mt[md].ntiles = (int)tiles[md].size();
+    if (queued) {
+      sort_tiles(&tiles[md], probs);
+    } else {
+      std::vector<Tile> dealt;
+      deal_tiles(tiles[md], probs, mt[md].grid * wpb, &dealt, &first[md]);
+      tiles[md].swap(dealt);
+    }
   }
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t pb = probs.size() * sizeof(FlatProblem);
-  const size_t tb[2] = {dealt[0].size() * sizeof(Tile), dealt[1].size() * sizeof(Tile)};
+  const size_t tb[2] = {tiles[0].size() * sizeof(Tile), tiles[1].size() * sizeof(Tile)};
   const size_t fb[2] = {first[0].size() * sizeof(int), first[1].size() * sizeof(int)};
-  const size_t total = al(pb) + al(tb[0]) + al(tb[1]) + al(fb[0]) + al(fb[1]) + 256;
+  const size_t qb = 2 * sizeof(unsigned long long);  // the two modes' queue counters
+  const size_t total = al(pb) + al(tb[0]) + al(tb[1]) + al(fb[0]) + al(fb[1]) + al(qb) + 256;
   void* scratch = nullptr;
   err = cudaMallocAsync(&scratch, total, st);
   if (err != cudaSuccess) return fail(PT_ENOMEM, "batch scratch: %s", cudaGetErrorString(err));
   char* cur = (char*)scratch;
   FlatProblem* d_probs = (FlatProblem*)cur;
   cur += al(pb);
-  Tile* d_tiles[2];
-  int* d_first[2];
   for (int md = 0; md < 2; ++md) {
-    d_tiles[md] = (Tile*)cur;
+    mt[md].tiles = (const Tile*)cur;
     cur += al(tb[md]);
   }
   for (int md = 0; md < 2; ++md) {
-    d_first[md] = (int*)cur;
+    if (fb[md]) mt[md].first = (const int*)cur;
     cur += al(fb[md]);
   }
+  unsigned long long* d_ctr = (unsigned long long*)cur;
+  mt[0].ctr = d_ctr;
+  mt[1].ctr = d_ctr + 1;
   err = cudaMemcpyAsync(d_probs, probs.data(), pb, cudaMemcpyHostToDevice, st);
   for (int md = 0; md < 2 && err == cudaSuccess; ++md) {
     if (!tb[md]) continue;
-    err = cudaMemcpyAsync(d_tiles[md], dealt[md].data(), tb[md], cudaMemcpyHostToDevice, st);
-    if (err == cudaSuccess)
-      err = cudaMemcpyAsync(d_first[md], first[md].data(), fb[md], cudaMemcpyHostToDevice, st);
+    err = cudaMemcpyAsync((void*)mt[md].tiles, tiles[md].data(), tb[md], cudaMemcpyHostToDevice,
+                          st);
+    if (err == cudaSuccess && fb[md])
+      err = cudaMemcpyAsync((void*)mt[md].first, first[md].data(), fb[md],
+                            cudaMemcpyHostToDevice, st);
   }
+  if (err == cudaSuccess) err = cudaMemsetAsync(d_ctr, 0, qb, st);
   // which sweeps are counted for at least one problem (a swap iteration or a trace row)
   std::vector<char> any_exchange((size_t)n_max, 0);
   for (const FlatProblem& fp : probs)
@@ -343,20 +430,8 @@ int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const i
   for (const FlatProblem& fp : probs)
     xsmem = std::max(xsmem, flat_exchange_smem(fp.p.R, fp.p.mode));
   if (err == cudaSuccess) err = flat_exchange_prepare(xsmem);
-  for (int64_t j = 0; j < n_max && err == cudaSuccess; ++j) {
-    const bool ex = any_exchange[(size_t)j] != 0;
-    if (grid[0] && err == cudaSuccess) err = launch_flat_half<kModeFerro, false>(grid[0], d_probs, d_tiles[0], d_first[0], 0, j, st);
-    if (grid[1] && err == cudaSuccess) err = launch_flat_half<kModeGeneric, false>(grid[1], d_probs, d_tiles[1], d_first[1], 0, j, st);
-    if (ex) {
-      if (grid[0] && err == cudaSuccess) err = launch_flat_half<kModeFerro, true>(grid[0], d_probs, d_tiles[0], d_first[0], 1, j, st);
-      if (grid[1] && err == cudaSuccess) err = launch_flat_half<kModeGeneric, true>(grid[1], d_probs, d_tiles[1], d_first[1], 1, j, st);
-      if (err == cudaSuccess) err = launch_flat_exchange(d_probs, np, j, xsmem, di.sms, st);
-    } else {
-      if (grid[0] && err == cudaSuccess) err = launch_flat_half<kModeFerro, false>(grid[0], d_probs, d_tiles[0], d_first[0], 1, j, st);
-      if (grid[1] && err == cudaSuccess) err = launch_flat_half<kModeGeneric, false>(grid[1], d_probs, d_tiles[1], d_first[1], 1, j, st);
-    }
-    if (err == cudaSuccess) err = cudaGetLastError();
-  }
+  for (int64_t j = 0; j < n_max && err == cudaSuccess; ++j)
+    err = launch_flat_sweep(mt, d_probs, np, j, any_exchange[(size_t)j] != 0, xsmem, di.sms, st);
   const cudaError_t err2 = cudaFreeAsync(scratch, st);
   if (err == cudaSuccess) err = err2;
   if (err != cudaSuccess) {
@@ -404,10 +479,18 @@ Tile g_sp_dealt[kStaticMaxTiles];
 int64_t g_sp_cost[kStaticMaxTiles];
 int g_sp_order[kStaticMaxTiles];
 int g_sp_owner[kStaticMaxTiles];
-int g_sp_first0[kStaticMaxWarps + 1];
-int g_sp_first1[kStaticMaxWarps + 1];
+int g_sp_first[2][kStaticMaxWarps + 1];
 int64_t g_sp_heap_load[kStaticMaxWarps];
 int g_sp_heap_warp[kStaticMaxWarps];
+
+// Tiles [lo, hi) of g_sp_tiles sorted by tile_cost, largest first (ties keep their order),
+// written to g_sp_dealt[lo..hi).
+void static_sort(int lo, int hi) {
+  std::copy(g_sp_tiles + lo, g_sp_tiles + hi, g_sp_dealt + lo);
+  std::stable_sort(g_sp_dealt + lo, g_sp_dealt + hi, [](const Tile& x, const Tile& y) {
+    return tile_cost(x, g_sp_probs[x.prob].p.R) > tile_cost(y, g_sp_probs[y.prob].p.R);
+  });
+}
 
 // Longest-processing-time-first dealing of tiles [lo, hi) of g_sp_tiles to `nwarps` warps,
 // written to g_sp_dealt[lo..hi) warp by warp with offsets first[0..nwarps] (relative to lo).
@@ -462,7 +545,7 @@ void static_deal(int lo, int hi, int nwarps, int* first) {
 }  // namespace
 
 int sweep_batch_static(pt_problem* const* ps, int count, const int64_t* n, const int* every,
-                       cudaStream_t st, const DeviceInfo& di, int tile_words) {
+                       cudaStream_t st, const DeviceInfo& di, int tile_words, bool queued) {
   std::lock_guard<std::mutex> lk(g_static_mu);
   if (di.device < 0 || di.device >= 64) return fail(PT_ENODEV, "device index %d", di.device);
   // set-up, once per device, with that device current: the device address of the array
@@ -516,10 +599,10 @@ int sweep_batch_static(pt_problem* const* ps, int count, const int64_t* n, const
   if (np == 0) return PT_OK;
   int per_sm[2] = {1, 1};
   cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm[0], k_flat_half<kModeFerro, true>, kFlatThreads, 0);
+      &per_sm[0], k_flat_half<kModeFerro, true, false>, kFlatThreads, 0);
   if (err == cudaSuccess)
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm[1], k_flat_half<kModeGeneric, true>, kFlatThreads, 0);
+        &per_sm[1], k_flat_half<kModeGeneric, true, false>, kFlatThreads, 0);
   if (err != cudaSuccess) return fail(PT_ECUDA, "occupancy: %s", cudaGetErrorString(err));
   const int wpb = kFlatThreads / 32;
   const int lo[2] = {0, split}, hi[2] = {split, nt};
@@ -533,36 +616,47 @@ int sweep_batch_static(pt_problem* const* ps, int count, const int64_t* n, const
   }
   if (nwarps[0] > kStaticMaxWarps || nwarps[1] > kStaticMaxWarps)
     return fail(PT_EINTERNAL, "pt_sweep_batch_static: warp table too small");
-  // layout inside the static array: problems | tiles | offsets (mode 0) | offsets (mode 1)
+  // layout inside the static array: problems | tiles (mode 0, then mode 1) | per-warp
+  // offsets (mode 0) | per-warp offsets (mode 1) | queue counters
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t off_tiles = al((size_t)np * sizeof(FlatProblem));
   const size_t off_first0 = off_tiles + al((size_t)nt * sizeof(Tile));
   const size_t off_first1 = off_first0 + al((size_t)(nwarps[0] + 1) * sizeof(int));
-  const size_t need = off_first1 + al((size_t)(nwarps[1] + 1) * sizeof(int));
+  const size_t off_ctr = off_first1 + al((size_t)(nwarps[1] + 1) * sizeof(int));
+  const size_t need = off_ctr + al(2 * sizeof(unsigned long long));
   if (need > kStaticScratchBytes)
     return fail(PT_EINVAL, "pt_sweep_batch_static: the batch needs %zu bytes of work lists, "
                 "more than the %zu-byte static work area", need, kStaticScratchBytes);
-  if (grid[0]) static_deal(lo[0], hi[0], nwarps[0], g_sp_first0);
-  if (grid[1]) static_deal(lo[1], hi[1], nwarps[1], g_sp_first1);
   char* base = (char*)sd.ptr;
+  const size_t off_first[2] = {off_first0, off_first1};
+  ModeTiles mt[2];
+  for (int md = 0; md < 2; ++md) {
+    if (grid[md] == 0) continue;
+    mt[md].grid = grid[md];
+    mt[md].ntiles = hi[md] - lo[md];
+    mt[md].tiles = (const Tile*)(base + off_tiles) + lo[md];
+    mt[md].ctr = (unsigned long long*)(base + off_ctr) + md;
+    if (queued) {
+      static_sort(lo[md], hi[md]);
+    } else {
+      static_deal(lo[md], hi[md], nwarps[md], g_sp_first[md]);
+      mt[md].first = (const int*)(base + off_first[md]);
+    }
+  }
   err = cudaMemcpyAsync(base, g_sp_probs, (size_t)np * sizeof(FlatProblem),
                         cudaMemcpyHostToDevice, st);
-  if (err == cudaSuccess && grid[0])
-    err = cudaMemcpyAsync(base + off_first0, g_sp_first0, (size_t)(nwarps[0] + 1) * sizeof(int),
-                          cudaMemcpyHostToDevice, st);
-  if (err == cudaSuccess && grid[1])
-    err = cudaMemcpyAsync(base + off_first1, g_sp_first1, (size_t)(nwarps[1] + 1) * sizeof(int),
-                          cudaMemcpyHostToDevice, st);
   if (err == cudaSuccess)
     err = cudaMemcpyAsync(base + off_tiles, g_sp_dealt, (size_t)nt * sizeof(Tile),
                           cudaMemcpyHostToDevice, st);
+  for (int md = 0; md < 2 && err == cudaSuccess; ++md)
+    if (mt[md].first != nullptr)
+      err = cudaMemcpyAsync(base + off_first[md], g_sp_first[md],
+                            (size_t)(nwarps[md] + 1) * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (err == cudaSuccess)
+    err = cudaMemsetAsync(base + off_ctr, 0, 2 * sizeof(unsigned long long), st);
   // the host arrays are reused by the next call: wait until the copies have read them
   if (err == cudaSuccess) err = cudaStreamSynchronize(st);
   const FlatProblem* d_probs = (const FlatProblem*)base;
-  const Tile* d_tiles0 = (const Tile*)(base + off_tiles);
-  const Tile* d_tiles1 = d_tiles0 + split;
-  const int* d_first0 = (const int*)(base + off_first0);
-  const int* d_first1 = (const int*)(base + off_first1);
   size_t xsmem = 0;
   for (int k = 0; k < np; ++k)
     xsmem = std::max(xsmem, flat_exchange_smem(g_sp_probs[k].p.R, g_sp_probs[k].p.mode));
@@ -574,17 +668,7 @@ int sweep_batch_static(pt_problem* const* ps, int count, const int64_t* n, const
       ex = j < fp.n && (fp.p.trace_E != nullptr ||
                         (fp.m > 0 && (fp.t0 + (uint64_t)j + 1) % (uint64_t)fp.m == 0));
     }
-    if (grid[0] && err == cudaSuccess) err = launch_flat_half<kModeFerro, false>(grid[0], d_probs, d_tiles0, d_first0, 0, j, st);
-    if (grid[1] && err == cudaSuccess) err = launch_flat_half<kModeGeneric, false>(grid[1], d_probs, d_tiles1, d_first1, 0, j, st);
-    if (ex) {
-      if (grid[0] && err == cudaSuccess) err = launch_flat_half<kModeFerro, true>(grid[0], d_probs, d_tiles0, d_first0, 1, j, st);
-      if (grid[1] && err == cudaSuccess) err = launch_flat_half<kModeGeneric, true>(grid[1], d_probs, d_tiles1, d_first1, 1, j, st);
-      if (err == cudaSuccess) err = launch_flat_exchange(d_probs, np, j, xsmem, di.sms, st);
-    } else {
-      if (grid[0] && err == cudaSuccess) err = launch_flat_half<kModeFerro, false>(grid[0], d_probs, d_tiles0, d_first0, 1, j, st);
-      if (grid[1] && err == cudaSuccess) err = launch_flat_half<kModeGeneric, false>(grid[1], d_probs, d_tiles1, d_first1, 1, j, st);
-    }
-    if (err == cudaSuccess) err = cudaGetLastError();
+    err = launch_flat_sweep(mt, d_probs, np, j, ex, xsmem, di.sms, st);
   }
   if (err != cudaSuccess) {
     for (int j = 0; j < count; ++j) ps[j]->poisoned = PT_ECUDA;

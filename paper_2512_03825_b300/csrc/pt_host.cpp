@@ -1178,7 +1178,8 @@ int pt_set_spins(pt_problem* p, int k, const int8_t* in) {
 }
 
 int pt_set_batch_tuning(int strategy, int cluster, int joint_min_L) {
-  if ((strategy != PT_BATCH_FLAT && strategy != PT_BATCH_CLUSTER && strategy != PT_BATCH_FLOW) ||
+  if ((strategy != PT_BATCH_FLAT && strategy != PT_BATCH_CLUSTER && strategy != PT_BATCH_FLOW &&
+       strategy != PT_BATCH_QUEUE) ||
       cluster < 1 ||
       cluster > 16 || joint_min_L < 4)
     return fail(PT_EINVAL, "strategy = %d, cluster = %d, joint_min_L = %d", strategy, cluster,

@@ -66,8 +66,8 @@ def test_batch_equals_plain_and_oracle(api, tuning):
         g = api.PTProblem(pr.L, pr.betas, J=pr.J, h=pr.h, seed=pr.seed)
         g.sweep(pr.sweeps, pr.every)
         plain.append(state(g))
-    for st, cl, jm in [(0, 1, 4), (2, 1, 4), (1, 4, 16), (1, 1, 4), (1, 2, 8), (1, 8, 16),
-                       (1, 3, 8), (1, 6, 12), (1, 4, 1 << 20)]:
+    for st, cl, jm in [(0, 1, 4), (3, 1, 4), (2, 1, 4), (1, 4, 16), (1, 1, 4), (1, 2, 8),
+                       (1, 8, 16), (1, 3, 8), (1, 6, 12), (1, 4, 1 << 20)]:
         tuning(cl, jm, st)
         batch = [api.PTProblem(pr.L, pr.betas, J=pr.J, h=pr.h, seed=pr.seed) for pr in probs]
         api.sweep_batch(batch, [pr.sweeps for pr in probs], [pr.every for pr in probs])
@@ -85,7 +85,7 @@ def test_batch_equals_plain_and_oracle(api, tuning):
         np.testing.assert_array_equal(g.energies_int(), o.energies_int())
 
 
-@pytest.mark.parametrize("strategy", [0, 1, 2])
+@pytest.mark.parametrize("strategy", [0, 1, 2, 3])
 def test_batch_composes_with_plain(api, tuning, strategy):
     tuning(4, 16, strategy)
     pr = W.Problem(L=64, betas=W.linear_ladder(0.3, 0.6, 40), seed=77)
@@ -98,7 +98,7 @@ def test_batch_composes_with_plain(api, tuning, strategy):
     assert_state_equal(a, b)
 
 
-@pytest.mark.parametrize("strategy", [0, 1, 2])
+@pytest.mark.parametrize("strategy", [0, 1, 2, 3])
 def test_batched_workload_sample_vs_oracle(api, tuning, strategy):
     """A sample of the 256-problem batched workload, short runs, against the oracle."""
     tuning(4, 128, strategy)
@@ -131,11 +131,13 @@ def test_tile_size_never_changes_a_result(api, tuning, tile_words):
     lib.pt_get_batch_tile_words(C.byref(old))
     try:
         assert lib.pt_set_batch_tile_words(tile_words) == 0
-        for st in (0, 2, "static"):
-            if st != "static":
+        for st in (0, 3, 2, "static-dealt", "static-queued"):
+            if isinstance(st, int):
                 tuning(1, 4, st)
+            else:  # the allocation-free entry hands tiles out as the strategy set says
+                tuning(1, 4, 3 if st == "static-queued" else 0)
             batch = [api.PTProblem(pr.L, pr.betas, J=pr.J, h=pr.h, seed=pr.seed) for pr in probs]
-            run = api.sweep_batch_static if st == "static" else api.sweep_batch
+            run = api.sweep_batch_static if isinstance(st, str) else api.sweep_batch
             run(batch, [pr.sweeps for pr in probs], [pr.every for pr in probs])
             for j, (b, ref) in enumerate(zip(batch, plain)):
                 assert_state_equal(state(b), ref, "tile %d strategy %s problem %d"
@@ -207,7 +209,7 @@ def test_autotuner_compares_equal_results(api, tuning):
     leave the problems in the same state, and applies the fastest without saving it."""
     from paper_2512_03825_b300 import autotune
     probs = W.batched_problems(n=10)
-    cands = [(0, 1, 128, 128), (0, 1, 128, 1024), (2, 1, 128, 256), (1, 2, 64, 512)]
+    cands = [(0, 1, 128, 128), (3, 1, 128, 1024), (2, 1, 128, 256), (1, 2, 64, 512)]
     out = autotune.tune(probs, sweeps=4, every=1, candidates=cands, repeats=1, save=False)
     assert tuple(out["choice"].values()) in cands
     assert len(out["timings"]) == len(cands)

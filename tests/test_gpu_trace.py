@@ -88,9 +88,23 @@ def test_ring_wraps_and_late_start(api, strategy):
     np.testing.assert_array_equal(g.energies_int(), o.energies_int())
 
 
-def test_batch_with_traced_and_untraced_problems(api):
-    """The batch runs the lock-step path when a problem is traced; the traced problems'
-    rows equal the oracle's and the untraced ones are unaffected."""
+@pytest.mark.parametrize("strategy", [0, 1, 3])
+def test_batch_with_traced_and_untraced_problems(api, strategy):
+    """The batch runs a lock-step path when a problem is traced (the queued one when it is
+    set, else the dealt one); the traced problems' rows equal the oracle's and the untraced
+    ones are unaffected."""
+    import ctypes as C
+    from paper_2512_03825_b300._lib import lib
+    s, c, jm = C.c_int(), C.c_int(), C.c_int()
+    lib.pt_get_batch_tuning(C.byref(s), C.byref(c), C.byref(jm))
+    assert lib.pt_set_batch_tuning(strategy, 4, 128) == 0
+    try:
+        _traced_batch(api)
+    finally:
+        lib.pt_set_batch_tuning(s.value, c.value, jm.value)
+
+
+def _traced_batch(api):
     probs = PROBS + [W.Problem(L=32, betas=W.linear_ladder(0.3, 0.6, 20), seed=44)]
     gs = [api.PTProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed) for p in probs]
     for g in gs[::2]:
