@@ -12,7 +12,9 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <atomic>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -94,14 +96,35 @@ uint64_t swap_rule(double beta_lo, double beta_hi, int64_t n, int64_t s, int rul
 // The exchange threshold of one temperature pair as a function of n: constant below n_lo
 // and above n_hi, tabulated in between. S(n) is monotone in n (y is linear in n and both
 // forms are monotone in y), so the saturated ranges are found by bisection and then checked
-// at their edges.
+// at their edges. With reach > 0 only |n| <= reach can occur (a lattice's largest energy
+// difference): the table then covers the non-saturated n within [-reach, reach] only, and
+// when that is all of [-reach, reach] it is tabulated whole, without a search; a lookup of
+// any |n| <= reach gives S(n) either way.
 struct PairTable {
   int64_t n_lo = 1, n_hi = 0;
   uint64_t S_below = 0, S_above = 0;
   std::vector<uint32_t> vals;
 };
 
-int build_pair_table(double blo, double bhi, int64_t s, int rule, PairTable* out) {
+int fill_pair_table(double blo, double bhi, int64_t s, int rule, PairTable* t) {
+  const double d = bhi - blo;
+  const int64_t len = t->n_hi - t->n_lo + 1;
+  t->vals.resize((size_t)std::max<int64_t>(len, 0));
+  uint64_t prev = swap_rule(blo, bhi, t->n_lo - 1, s, rule);
+  for (int64_t j = 0; j < len; ++j) {
+    const uint64_t v = swap_rule(blo, bhi, t->n_lo + j, s, rule);
+    if (v >= kTwo32) return fail(PT_EINTERNAL, "exchange table entry saturates inside");
+    if ((d > 0 && v > prev) || (d < 0 && v < prev))
+      return fail(PT_EINTERNAL, "exchange threshold not monotone at n = %lld",
+                  (long long)(t->n_lo + j));
+    prev = v;
+    t->vals[(size_t)j] = (uint32_t)v;
+  }
+  return PT_OK;
+}
+
+int build_pair_table(double blo, double bhi, int64_t s, int rule, int64_t reach,
+                     PairTable* out) {
   PairTable t;
   const double d = bhi - blo;
   if (d == 0.0) {  // y = 0 for every n
@@ -111,6 +134,21 @@ int build_pair_table(double blo, double bhi, int64_t s, int rule, PairTable* out
   }
   // beyond +-N the cut-offs decide (|y| > 44)
   const double nmax = std::ceil(45.0 * (double)s / std::fabs(d)) + 2.0;
+  if (reach > 0 && (double)reach + 2.0 < nmax) {
+    // every reachable n lies inside the search range: tabulate [-reach, reach] whole
+    t.n_lo = -reach;
+    t.n_hi = reach;
+    t.S_below = swap_rule(blo, bhi, -reach - 1, s, rule);
+    t.S_above = swap_rule(blo, bhi, reach + 1, s, rule);
+    if (t.S_below >= kTwo32 || t.S_above >= kTwo32 || t.S_below == 0 || t.S_above == 0) {
+      // a saturated end inside [-reach - 1, reach + 1]: search for the edges instead
+    } else {
+      const int rc = fill_pair_table(blo, bhi, s, rule, &t);
+      if (rc) return rc;
+      *out = std::move(t);
+      return PT_OK;
+    }
+  }
   if (nmax > 4.0e9) return fail(PT_EINVAL, "temperature pair too close: |dbeta| = %g", d);
   const int64_t N = (int64_t)nmax;
   t.S_below = swap_rule(blo, bhi, -N, s, rule);
@@ -130,33 +168,39 @@ int build_pair_table(double blo, double bhi, int64_t s, int rule, PairTable* out
   }
   t.n_hi = lo;
   if (t.n_hi < t.n_lo) return fail(PT_EINTERNAL, "empty exchange table");
-  const int64_t len = t.n_hi - t.n_lo + 1;
-  t.vals.resize((size_t)len);
-  uint64_t prev = t.S_below;
-  for (int64_t j = 0; j < len; ++j) {
-    const uint64_t v = swap_rule(blo, bhi, t.n_lo + j, s, rule);
-    if (v >= kTwo32) return fail(PT_EINTERNAL, "exchange table entry saturates inside");
-    if ((d > 0 && v > prev) || (d < 0 && v < prev))
-      return fail(PT_EINTERNAL, "exchange threshold not monotone at n = %lld",
-                  (long long)(t.n_lo + j));
-    prev = v;
-    t.vals[(size_t)j] = (uint32_t)v;
-  }
   if (swap_rule(blo, bhi, t.n_lo - 1, s, rule) != t.S_below ||
       swap_rule(blo, bhi, t.n_hi + 1, s, rule) != t.S_above)
     return fail(PT_EINTERNAL, "exchange table edges inconsistent");
+  if (reach > 0) {
+    // keep the reachable part; an empty one still sends every |n| <= reach to the right
+    // constant
+    const int64_t lo_r = std::max(t.n_lo, -reach), hi_r = std::min(t.n_hi, reach);
+    if (lo_r <= hi_r) {
+      t.n_lo = lo_r;
+      t.n_hi = hi_r;
+    } else if (t.n_lo > reach) {  // every reachable n is below the table
+      t.n_lo = reach + 1;
+      t.n_hi = reach;
+    } else {  // every reachable n is above it
+      t.n_lo = -reach;
+      t.n_hi = -reach - 1;
+    }
+  }
+  const int rc = fill_pair_table(blo, bhi, s, rule, &t);
+  if (rc) return rc;
   *out = std::move(t);
   return PT_OK;
 }
 
-// Tables depend only on (beta_lo, beta_hi, s, rule); requests with the same ladder share
-// them.
+// Tables depend only on (beta_lo, beta_hi, s, rule, reach); requests with the same ladder
+// and lattice reach share them.
 struct PairKey {
   uint64_t blo, bhi;
   int64_t s;
   int rule;
+  int64_t reach;
   bool operator<(const PairKey& o) const {
-    return std::tie(blo, bhi, s, rule) < std::tie(o.blo, o.bhi, o.s, o.rule);
+    return std::tie(blo, bhi, s, rule, reach) < std::tie(o.blo, o.bhi, o.s, o.rule, o.reach);
   }
 };
 std::mutex g_table_mu;
@@ -164,13 +208,22 @@ std::map<PairKey, std::shared_ptr<const PairTable>> g_tables;
 size_t g_table_bytes = 0;
 constexpr size_t kTableCacheCap = size_t(2) << 30;
 
-int get_pair_table(double blo, double bhi, int64_t s, int rule,
+// The largest |n| = |E_int(a) - E_int(b)| on an L x L lattice: |E_int| <= 2 L^2 |J_int| +
+// L^2 |h_int| (2 L^2 bonds, L^2 spins).
+int64_t energy_reach(int L, int64_t Ji, int64_t hi) {
+  const int64_t L2 = (int64_t)L * L;
+  return 2 * (2 * L2 * (Ji < 0 ? -Ji : Ji) + L2 * (hi < 0 ? -hi : hi));
+}
+
+// reach: the largest |n| that can occur (0: any n).
+int get_pair_table(double blo, double bhi, int64_t s, int rule, int64_t reach,
                    std::shared_ptr<const PairTable>* out) {
   PairKey key;
   memcpy(&key.blo, &blo, 8);
   memcpy(&key.bhi, &bhi, 8);
   key.s = s;
   key.rule = rule;
+  key.reach = reach;
   {
     std::lock_guard<std::mutex> lk(g_table_mu);
     auto it = g_tables.find(key);
@@ -180,7 +233,7 @@ int get_pair_table(double blo, double bhi, int64_t s, int rule,
     }
   }
   auto t = std::make_shared<PairTable>();
-  const int rc = build_pair_table(blo, bhi, s, rule, t.get());
+  const int rc = build_pair_table(blo, bhi, s, rule, reach, t.get());
   if (rc != PT_OK) return rc;
   std::lock_guard<std::mutex> lk(g_table_mu);
   if (g_table_bytes > kTableCacheCap) {
@@ -190,6 +243,42 @@ int get_pair_table(double blo, double bhi, int64_t s, int rule,
   g_table_bytes += t->vals.size() * 4;
   g_tables[key] = t;
   *out = t;
+  return PT_OK;
+}
+
+// The tables of a ladder's R - 1 adjacent pairs; long ladders are built on up to 16 host
+// threads (the tables are independent and the cache is shared). An error in any of them is
+// reported on the calling thread.
+int get_ladder_tables(const double* betas, int R, int64_t s, int rule, int64_t reach,
+                      std::vector<std::shared_ptr<const PairTable>>* out) {
+  const int npairs = std::max(R - 1, 0);
+  out->assign((size_t)npairs, nullptr);
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int nthreads = npairs < 64 ? 1 : std::min(std::min(hw, 16), npairs / 32);
+  std::atomic<int> next{0};
+  std::vector<int> rcs((size_t)nthreads, PT_OK);
+  std::vector<std::string> msgs((size_t)nthreads);
+  auto work = [&](int w) {
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= npairs) return;
+      const int rc = get_pair_table(betas[k], betas[k + 1], s, rule, reach, &(*out)[(size_t)k]);
+      if (rc) {
+        rcs[(size_t)w] = rc;
+        msgs[(size_t)w] = g_last_error;
+        return;
+      }
+    }
+  };
+  if (nthreads == 1) {
+    work(0);
+  } else {
+    std::vector<std::thread> pool;
+    for (int w = 0; w < nthreads; ++w) pool.emplace_back(work, w);
+    for (std::thread& th : pool) th.join();
+  }
+  for (int w = 0; w < nthreads; ++w)
+    if (rcs[(size_t)w]) return fail(rcs[(size_t)w], "%s", msgs[(size_t)w].c_str());
   return PT_OK;
 }
 
@@ -469,7 +558,7 @@ uint64_t pt_spin_threshold(double beta, int64_t dE_int, int64_t s) {
 uint64_t pt_swap_threshold_ex(double beta_lo, double beta_hi, int64_t n, int64_t s, int rule) {
   if (rule != PT_SWAP_BARKER && rule != PT_SWAP_METROPOLIS) return ~uint64_t(0);
   std::shared_ptr<const PairTable> t;
-  if (get_pair_table(beta_lo, beta_hi, s, rule, &t) != PT_OK) return ~uint64_t(0);
+  if (get_pair_table(beta_lo, beta_hi, s, rule, 0, &t) != PT_OK) return ~uint64_t(0);
   if (n < t->n_lo) return t->S_below;
   if (n > t->n_hi) return t->S_above;
   return t->vals[(size_t)(n - t->n_lo)];
@@ -493,11 +582,10 @@ size_t pt_estimate_device_bytes(int L, const double* betas, int R, double J, dou
   int64_t s, Ji, hi;
   if (check_args(L, betas, R, J, h, &s, &Ji, &hi) != PT_OK) return 0;
   size_t entries = 0;
-  for (int k = 0; k + 1 < R; ++k) {
-    std::shared_ptr<const PairTable> t;
-    if (get_pair_table(betas[k], betas[k + 1], s, PT_SWAP_BARKER, &t) != PT_OK) return 0;
-    entries += t->vals.size();
-  }
+  std::vector<std::shared_ptr<const PairTable>> tabs;
+  if (get_ladder_tables(betas, R, s, PT_SWAP_BARKER, energy_reach(L, Ji, hi), &tabs) != PT_OK)
+    return 0;
+  for (const auto& t : tabs) entries += t->vals.size();
   const int W = (R + 31) / 32;
   return make_layout(L, R, W, mode_for(Ji, hi), entries).total;
 }
@@ -563,17 +651,16 @@ int pt_create_ex(int L, const double* betas, int R, double J, double h, uint64_t
   std::vector<std::shared_ptr<const PairTable>> tabs;
   std::vector<SwapPair> pairs((size_t)npairs);
   size_t entries = 0;
+  rc = get_ladder_tables(betas, R, s, swap_rule_opt, energy_reach(L, Ji, hi), &tabs);
+  if (rc) return rc;
   for (int k = 0; k + 1 < R; ++k) {
-    std::shared_ptr<const PairTable> t;
-    rc = get_pair_table(betas[k], betas[k + 1], s, swap_rule_opt, &t);
-    if (rc) return rc;
+    const std::shared_ptr<const PairTable>& t = tabs[(size_t)k];
     pairs[k].n_lo = t->n_lo;
     pairs[k].n_hi = t->n_hi;
     pairs[k].S_below = t->S_below;
     pairs[k].S_above = t->S_above;
     pairs[k].offset = (int64_t)entries;
     entries += t->vals.size();
-    tabs.push_back(t);
   }
 
   // device memory: one allocation

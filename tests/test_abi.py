@@ -212,3 +212,17 @@ def test_batch_tile_words_validated(pt):
         assert pt.lib.pt_get_batch_tile_words(None) == pt.PT_EINVAL
     finally:
         pt.lib.pt_set_batch_tile_words(old.value)
+
+
+def test_exchange_tables_limited_to_reachable_energies(pt):
+    """A problem's exchange tables cover only the energy differences its lattice can reach
+    (|n| <= 2 (2 L^2 |J_int| + L^2 |h_int|)): a long, dense ladder on a small lattice needs a
+    few MiB, not the GiB that the whole non-saturated range of every pair would take."""
+    from paper_2512_03825_b300 import api
+    from paper_2512_03825_b300 import workloads as W
+    small = api.estimate_device_bytes(8, W.linear_ladder(0.05, 1.0, 2048))
+    assert 0 < small < 64 * 2 ** 20
+    # a lattice that reaches the whole range keeps every entry: L = 300 with the paper's
+    # ladder T_i = 1 + 3 i / 1500 holds more than 1 GiB of tables
+    paper = api.estimate_device_bytes(300, [1.0 / (1.0 + 3.0 * i / 1500) for i in range(1500)])
+    assert paper > 2 ** 30
