@@ -577,8 +577,13 @@ int sweep_batch(pt_problem* const* ps, int count, const int64_t* n, const int* e
   // one persistent launch: as many clusters as fit; with clusters, a second launch of
   // plain CTAs on a forked stream drains the single queue on the SMs the clusters leave idle
   const int G = std::max(1, tune.cluster);
+  // the limit belongs to the kernel, not to this batch: all the device allows, so that a
+  // concurrent smaller batch never lowers it under this one's launch
+  cudaFuncAttributes fa;
+  if (err == cudaSuccess) err = cudaFuncGetAttributes(&fa, k_batch);
   if (err == cudaSuccess)
-    err = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    err = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(di.smem_optin - fa.sharedSizeBytes));
   if (err == cudaSuccess && G > 8)
     err = cudaFuncSetAttribute(k_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaLaunchConfig_t cfg = {};

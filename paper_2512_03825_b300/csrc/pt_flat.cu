@@ -265,12 +265,14 @@ cudaError_t launch_flat_sweep(ModeTiles mt[2], const FlatProblem* d_probs, int n
   return err;
 }
 
-// Shared memory of the batch's exchange launches; raises the kernel's limit above the
-// default 48 KB when a problem needs it (at most 208 KB, R = 2048 generic).
+// Shared memory of the batch's exchange launches: when a problem needs more than the
+// default 48 KB, the kernel's limit is raised to what the largest problem can need
+// (R = 2048, generic: 208 KB). The limit belongs to the kernel, so it is never lowered under
+// another batch's launch.
 cudaError_t flat_exchange_prepare(size_t smem) {
   if (smem <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(k_flat_exchange, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem);
+                              (int)flat_exchange_smem(PT_MAX_R, kModeGeneric));
 }
 
 }  // namespace

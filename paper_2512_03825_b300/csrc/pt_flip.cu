@@ -504,12 +504,15 @@ int flip_smem_plan(const DevProblem& p, int sms, size_t smem_optin, int* k_out, 
   const void* fn = flip_smem_fn(p.mode);
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return PT_ECUDA;
+  if (fa.sharedSizeBytes >= smem_optin) return PT_OK;
+  // the limit belongs to the kernel, not to a problem: set to all the device allows, so that
+  // planning one problem never lowers it under another problem's launch
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(smem_optin - fa.sharedSizeBytes)) != cudaSuccess)
+    return PT_ECUDA;
   for (int k = 32; k >= 1; k >>= 1) {
     const size_t bytes = flip_smem_bytes(p.R, k, words);
     if (bytes + fa.sharedSizeBytes > smem_optin) continue;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
-        cudaSuccess)
-      return PT_ECUDA;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFlipSmemThreads, bytes) !=
         cudaSuccess)

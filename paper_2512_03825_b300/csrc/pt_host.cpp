@@ -215,9 +215,15 @@ int64_t energy_reach(int L, int64_t Ji, int64_t hi) {
   return 2 * (2 * L2 * (Ji < 0 ? -Ji : Ji) + L2 * (hi < 0 ? -hi : hi));
 }
 
-// reach: the largest |n| that can occur (0: any n).
+// reach: the largest |n| that can occur (0: any n). The reach shapes the table only when
+// it is inside the pair's saturation range (a small lattice on a dense ladder); otherwise
+// the whole table is built and shared by every lattice size, so problems that differ only
+// in L share it.
 int get_pair_table(double blo, double bhi, int64_t s, int rule, int64_t reach,
                    std::shared_ptr<const PairTable>* out) {
+  const double d = std::fabs(bhi - blo);
+  const double nmax = d == 0.0 ? 0.0 : std::ceil(45.0 * (double)s / d) + 2.0;
+  if (!(reach > 0 && (double)reach + 2.0 < nmax)) reach = 0;
   PairKey key;
   memcpy(&key.blo, &blo, 8);
   memcpy(&key.bhi, &bhi, 8);

@@ -47,18 +47,21 @@ struct PersistArgs {
 };
 
 // The plane's thresholds under the temperature map tos, staged in shared memory by warp 0
-// (same rule as the plane rebuild of the exchange kernel).
+// (same rule as the plane rebuild of the exchange kernel). Ferro: from Tf[temp] = the
+// thresholds of k = 0 and k = 1 at every temperature, which the kernel keeps in shared
+// memory, so a swap iteration's restaging reads no global memory.
 template <int MODE>
 __device__ void stage_plane(const DevProblem& p, const int32_t* tos, int w, PlaneFerro& fer,
-                            PlaneGeneric& gen) {
+                            PlaneGeneric& gen, const ulonglong2* Tf) {
   if (threadIdx.x < 32) {
     const int b = threadIdx.x, r = 32 * w + b;
     const bool in_use = r < p.R;
     const int temp = in_use ? tos[r] : 0;
     const uint32_t used = __ballot_sync(0xffffffffu, in_use);
     if (MODE == kModeFerro) {
-      const uint64_t t0 = in_use ? p.T_temp[(size_t)temp * kClasses + 1] : 0;
-      const uint64_t t1 = in_use ? p.T_temp[(size_t)temp * kClasses + 3] : 0;
+      const ulonglong2 tt = Tf[temp];
+      const uint64_t t0 = in_use ? tt.x : 0;
+      const uint64_t t1 = in_use ? tt.y : 0;
       fer.T0[b] = (uint32_t)min(t0, kTwo32 - 1);
       fer.T1[b] = (uint32_t)min(t1, kTwo32 - 1);
       const uint32_t a0 = __ballot_sync(0xffffffffu, in_use && t0 >= kTwo32);
@@ -180,7 +183,9 @@ __device__ __forceinline__ void half_pass(const DevProblem& p, int w, int colour
 
 template <int MODE>
 __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_constant__ PersistArgs a) {
-  extern __shared__ int32_t map_s[];  // [R] slot_of_temp, then [R] temp_of_slot
+  // [R] ferro thresholds (k = 0, k = 1) by temperature, then [R] slot_of_temp and [R]
+  // temp_of_slot; persist_smem(R, mode) bytes
+  extern __shared__ __align__(16) int32_t map_s[];
   __shared__ PlaneFerro fer;
   __shared__ uint4 thr[16];  // ferro thresholds, interleaved for 16-byte broadcast loads
   __shared__ PlaneGeneric gen;
@@ -188,11 +193,14 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
   __shared__ int ok_s;
   const DevProblem& p = a.p;
   const int R = p.R, W = p.W;
-  int32_t* sot = map_s;
-  int32_t* tos = map_s + R;
+  ulonglong2* const Tf = reinterpret_cast<ulonglong2*>(map_s);
+  int32_t* sot = map_s + (MODE == kModeFerro ? 4 * R : 0);
+  int32_t* tos = sot + R;
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
     sot[r] = p.slot_of_temp[r];
     tos[r] = p.temp_of_slot[r];
+    if (MODE == kModeFerro)
+      Tf[r] = make_ulonglong2(p.T_temp[(size_t)r * kClasses + 1], p.T_temp[(size_t)r * kClasses + 3]);
   }
   __syncthreads();
 
@@ -207,7 +215,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
 
   uint32_t alw0 = 0, alw1 = 0, used = 0;
   auto load_plane = [&]() {
-    stage_plane<MODE>(p, tos, w, fer, gen);
+    stage_plane<MODE>(p, tos, w, fer, gen, Tf);
     if (MODE == kModeFerro) {
       if (threadIdx.x < 16) {
         const int b = 2 * threadIdx.x;
@@ -319,15 +327,25 @@ const void* persist_fn(int mode) {
 
 }  // namespace
 
-size_t persist_smem(int R) { return (size_t)2 * R * sizeof(int32_t); }
+size_t persist_smem(int R, int mode) {
+  return (size_t)2 * R * sizeof(int32_t) + (mode == kModeFerro ? (size_t)R * 16 : 0);
+}
 
 cudaError_t persist_plan(const DevProblem& p, const DeviceInfo& dev, int words_per_thread,
                          PersistPlan* plan) {
   plan->grid = 0;
   plan->words_per_thread = 0;
   int per_sm = 0;
-  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, persist_fn(p.mode), kPersistThreads, persist_smem(p.R));
+  // the maps and (ferro) the thresholds by temperature can pass the default 48 KB per block.
+  // The limit belongs to the kernel, not to a problem: it is set to what the largest
+  // problem needs, so that planning a smaller one never lowers it under a larger one's launch
+  cudaError_t err = cudaFuncSetAttribute(persist_fn(p.mode),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)persist_smem(PT_MAX_R, p.mode));
+  if (err != cudaSuccess) return err;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persist_fn(p.mode),
+                                                      kPersistThreads,
+                                                      persist_smem(p.R, p.mode));
   if (err != cudaSuccess) return err;
   const int64_t planes_fit = (int64_t)per_sm * dev.sms / p.W;  // CTAs per plane at most
   if (planes_fit < 1) return cudaSuccess;
@@ -363,7 +381,7 @@ cudaError_t launch_persist(const DevProblem& p, const PersistPlan& plan, uint64_
   }
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel(persist_fn(p.mode), dim3(plan.grid), dim3(kPersistThreads),
-                                     args, persist_smem(p.R), st);
+                                     args, persist_smem(p.R, p.mode), st);
 }
 
 }  // namespace ptb

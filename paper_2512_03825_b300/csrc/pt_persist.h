@@ -25,7 +25,7 @@ struct PersistPlan {
 inline size_t count_words(int W) { return (size_t)6 * W * 32 + 16; }
 inline size_t persist_clear_bytes(int W) { return ((size_t)4 * W * 32 + 1) * 4; }
 
-size_t persist_smem(int R);
+size_t persist_smem(int R, int mode);
 cudaError_t persist_plan(const DevProblem& p, const DeviceInfo& dev, int words_per_thread,
                          PersistPlan* plan);
 cudaError_t launch_persist(const DevProblem& p, const PersistPlan& plan, uint64_t t0,

@@ -170,3 +170,27 @@ def test_barrier_wait_runs_out_and_context_survives(api):
     h.sweep(12, 1)
     o.sweep(12, 1)
     assert_same(h, o, "after a timed-out launch")
+
+
+def test_kernel_smem_limits_survive_smaller_problems(api):
+    """A kernel's dynamic shared-memory limit is process-wide: planning a small problem must
+    not lower it under a larger problem that was planned before (persistent sweep and the
+    shared-memory single-flip kernel)."""
+    big = W.Problem(L=64, betas=W.linear_ladder(0.3, 0.6, 2048), seed=61)
+    small = W.Problem(L=16, betas=W.linear_ladder(0.3, 0.6, 4), seed=62)
+    a = api.PTProblem(big.L, big.betas, seed=big.seed)
+    b = api.PTProblem(small.L, small.betas, seed=small.seed)
+    a.set_sweep_tuning(2)
+    b.set_sweep_tuning(2)
+    a.sweep(2, 1)       # plans the large problem
+    b.sweep(2, 1)       # plans the small one
+    a.sweep(2, 1)       # the large problem's launch still fits the kernel's limit
+    a.flip(40, 10)
+    b.flip(40, 10)
+    a.flip(40, 10)
+    o = oracle.OracleProblem(big.L, big.betas, seed=big.seed)
+    oracle.set_threads(8)
+    o.sweep(4, 1)
+    o.flip(80, 10)
+    np.testing.assert_array_equal(a.energies_int(), o.energies_int())
+    np.testing.assert_array_equal(a.chain_map(), o.chain_map())
