@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kFlipThreads) k_flip(const __grid_constant__ F
       int64_t* const eb = ebuf + (size_t)(swaps & 1) * R;
       if (active) eb[r] = E;
       target += gridDim.x + (swaps == 0 ? (unsigned)a.stall : 0u);
-      if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s)) return;
+      if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s, a.stall != 0)) return;
       exchange_energies(p, e, eb, sot, tos, blockIdx.x == 0);
       e += 1;
       swaps += 1;
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(kFlipSmemThreads) k_flip_smem(const __grid_con
     SwapPrefetch pf;
     prefetch_swaps(p, e, pf);
     target += gridDim.x + (swaps == 0 ? (unsigned)a.stall : 0u);
-    if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s)) return false;
+    if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s, a.stall != 0)) return false;
     exchange_prefetched(p, e, eb, sot, tos, blockIdx.x == 0, pf);
     stage_thresholds(false);
     e += 1;

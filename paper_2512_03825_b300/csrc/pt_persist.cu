@@ -242,14 +242,14 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
     half_pass<MODE, false>(p, w, 0, t, a.rk, bt, q0, step, y0, i0, dy, di, thr, alw0, alw1,
                            used, gen, false, U, N);
     target += gridDim.x + (j == 0 ? (unsigned)a.stall : 0u);
-    if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s)) return;
+    if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s, a.stall != 0)) return;
     const bool ex = a.m > 0 && (t + 1) % (uint64_t)a.m == 0;
     if (!ex && !trace) {
       half_pass<MODE, false>(p, w, 1, t, a.rk, bt, q0, step, y0, i0, dy, di, thr, alw0, alw1,
                              used, gen, false, U, N);
       if (j + 1 == a.n) break;  // the kernel's end orders this half sweep before what follows
       target += gridDim.x;
-      if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s)) return;
+      if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s, a.stall != 0)) return;
       continue;
     }
     // a swap iteration or a trace row follows: count this sweep into buffer `counted & 1`
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
       if (acc[1][threadIdx.x]) atomicAdd(&cb[W * 32 + w * 32 + threadIdx.x], acc[1][threadIdx.x]);
     }
     target += gridDim.x;
-    if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s)) return;
+    if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s, a.stall != 0)) return;
     if (ex) exchange_local(p, e, cb, sot, tos, blockIdx.x == 0);
     if (blockIdx.x == 0) {
       if (trace) {
