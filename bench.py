@@ -453,7 +453,8 @@ def bench_paper_flip(stream, iterations=300_000, every=100):
 def bench_e2e(probs, sweeps, stream, world):
     """The same step through the C ABI from host buffers: create every problem from host
     betas (tables copied to the device), run the batch, read energies, magnetisations,
-    temperature maps and swap counters back, destroy."""
+    temperature maps and swap counters of every problem back in one transfer
+    (pt_read_batch), destroy."""
     import torch
     from paper_2512_03825_b300 import api
 
@@ -462,12 +463,8 @@ def bench_e2e(probs, sweeps, stream, world):
         h2d = sum(h.device_bytes - h.L * h.L * ((h.R + 31) // 32) * 4 for h in hs)
         api.sweep_batch(hs, sweeps, 1)
         d2h = 0
-        for h in hs:
-            E = h.energies_int()
-            M = h.magnetisations()
-            c = h.chain_map()
-            att, acc = h.swap_stats()
-            d2h += E.nbytes + M.nbytes + c.nbytes + att.nbytes + acc.nbytes
+        for r in api.read_batch(hs):
+            d2h += sum(a.nbytes for a in r.values())
         for h in hs:
             h.close()
         return h2d, d2h

@@ -276,6 +276,22 @@ int pt_chain_map(pt_problem* p, int32_t* slot_of_temp);
 /* Sweeps and swap iterations done since pt_create (either pointer may be NULL). */
 int pt_counters(pt_problem* p, uint64_t* sweeps_done, uint64_t* exchanges_done);
 
+/* The results of `count` problems in one transfer. For problem j: E_int[j] and M[j] (R_j
+ * values each, by temperature index, as pt_energies_int), slot_of_temp[j] (R_j, as
+ * pt_chain_map), attempted[j] and accepted[j] (R_j - 1 values, as pt_swap_stats; nothing for
+ * R_j = 1). Any of the five pointer arrays may be NULL, and so may any entry of one; the
+ * caller owns every array. The problems must share a stream and a device (as in
+ * pt_sweep_batch). Recomputes the energies from the current spins like the single getters,
+ * packs every problem's record with one kernel into a stream-ordered scratch buffer and
+ * copies it back once: one synchronisation instead of several per problem and getter. A
+ * problem whose device work reported a status (PT_ETIMEOUT, ...) is poisoned as by
+ * pt_synchronize and its arrays are left untouched; the call returns the first such error
+ * after filling the others. PT_EINVAL for count < 0, a NULL or repeated-on-another-stream
+ * problem; PT_ENOMEM if the scratch buffer cannot be had. */
+int pt_read_batch(pt_problem* const* problems, int count, int64_t* const* E_int,
+                  int64_t* const* M, int32_t* const* slot_of_temp, uint64_t* const* attempted,
+                  uint64_t* const* accepted);
+
 /* Checkpoints. pt_save writes the problem's whole sampler state into buf (host memory of
  * at least pt_checkpoint_bytes(p) bytes; synchronises the stream); pt_load creates a new
  * problem (on the current device, through the current allocator) that continues exactly as

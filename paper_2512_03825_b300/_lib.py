@@ -67,6 +67,10 @@ SIGNATURES = [
     ("pt_get_batch_tuning", C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_int),
                                       C.POINTER(C.c_int)]),
     ("pt_set_batch_tile_words", C.c_int, [C.c_int]),
+    ("pt_read_batch", C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.POINTER(C.c_int64)),
+                                C.POINTER(C.POINTER(C.c_int64)), C.POINTER(C.POINTER(C.c_int32)),
+                                C.POINTER(C.POINTER(C.c_uint64)),
+                                C.POINTER(C.POINTER(C.c_uint64))]),
     ("pt_get_batch_tile_words", C.c_int, [C.POINTER(C.c_int)]),
     ("pt_energies", C.c_int, [P, C.POINTER(C.c_double)]),
     ("pt_magnetisations", C.c_int, [P, C.POINTER(C.c_double)]),

@@ -229,6 +229,33 @@ def sweep_batch_static(problems: Sequence[PTProblem], n, exchange_every):
                 exchange_every)
 
 
+def read_batch(problems: Sequence[PTProblem]):
+    """Energies (E_int), magnetisations, temperature maps and swap counters of many problems
+    in one transfer (pt_read_batch): a list of dicts with keys E_int, M, chain_map,
+    attempted, accepted (numpy arrays by temperature index / pair)."""
+    k = len(problems)
+    if k == 0:
+        return []
+    out = []
+    for p in problems:
+        npairs = max(p.R - 1, 0)
+        out.append({"E_int": np.empty(p.R, np.int64), "M": np.empty(p.R, np.int64),
+                    "chain_map": np.empty(p.R, np.int32),
+                    "attempted": np.empty(npairs, np.uint64),
+                    "accepted": np.empty(npairs, np.uint64)})
+
+    def ptrs(key, ctype):
+        arr = (C.POINTER(ctype) * k)()
+        for j, o in enumerate(out):
+            arr[j] = o[key].ctypes.data_as(C.POINTER(ctype))
+        return arr
+    hs = (C.c_void_p * k)(*[p.handle.value for p in problems])
+    check(lib.pt_read_batch(hs, k, ptrs("E_int", C.c_int64), ptrs("M", C.c_int64),
+                            ptrs("chain_map", C.c_int32), ptrs("attempted", C.c_uint64),
+                            ptrs("accepted", C.c_uint64)), "pt_read_batch")
+    return out
+
+
 def set_batch_tile_words(tile_words: int) -> None:
     """Words per warp tile of the tile strategies (a multiple of 32 in [64, 1024])."""
     check(lib.pt_set_batch_tile_words(int(tile_words)), "pt_set_batch_tile_words")

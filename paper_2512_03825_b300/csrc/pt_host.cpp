@@ -978,6 +978,87 @@ int pt_swap_stats(pt_problem* p, uint64_t* attempted, uint64_t* accepted) {
   return pt_synchronize(p);
 }
 
+int pt_read_batch(pt_problem* const* ps, int count, int64_t* const* E_int, int64_t* const* M,
+                  int32_t* const* slot_of_temp, uint64_t* const* attempted,
+                  uint64_t* const* accepted) {
+  if (count < 0 || (count > 0 && !ps)) return fail(PT_EINVAL, "count = %d, problems", count);
+  if (count == 0) return PT_OK;
+  cudaStream_t st = ps[0] ? ps[0]->stream : 0;
+  for (int j = 0; j < count; ++j) {
+    int rc = problem_check(ps[j]);
+    if (rc) return rc;
+    if (ps[j]->stream != st) return fail(PT_EINVAL, "problems of one read must share a stream");
+    if (ps[j]->dev_info.device != ps[0]->dev_info.device)
+      return fail(PT_EINVAL, "problems on different devices");
+  }
+  int rc = problem_device_guard(ps[0]);
+  if (rc) return rc;
+  // energies from the current spins (as the single getters), then one gather, one copy
+  std::vector<GatherItem> items((size_t)count);
+  int64_t words = 0;
+  for (int j = 0; j < count; ++j) {
+    pt_problem* p = ps[j];
+    if ((rc = refresh_observables(p))) return rc;
+    GatherItem& it = items[(size_t)j];
+    it.E_slot = p->dev.E_slot;
+    it.M_slot = p->dev.M_slot;
+    it.slot_of_temp = p->dev.slot_of_temp;
+    it.attempted = p->dev.attempted;
+    it.accepted = p->dev.accepted;
+    it.status = p->dev.status;
+    it.R = p->R;
+    it.npairs = p->R >= 2 ? p->R - 1 : 0;
+    it.out = words;
+    words += 1 + 3 * (int64_t)it.R + 2 * (int64_t)it.npairs;
+  }
+  const size_t ib = ((size_t)count * sizeof(GatherItem) + 255) & ~size_t(255);
+  void* scratch = nullptr;
+  cudaError_t err = cudaMallocAsync(&scratch, ib + (size_t)words * 8, st);
+  if (err != cudaSuccess) return fail(PT_ENOMEM, "read scratch: %s", cudaGetErrorString(err));
+  GatherItem* d_items = (GatherItem*)scratch;
+  uint64_t* d_out = (uint64_t*)((char*)scratch + ib);
+  std::vector<uint64_t> host((size_t)words);
+  err = cudaMemcpyAsync(d_items, items.data(), (size_t)count * sizeof(GatherItem),
+                        cudaMemcpyHostToDevice, st);
+  if (err == cudaSuccess) err = launch_gather(d_items, count, d_out, ps[0]->dev_info.sms, st);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(host.data(), d_out, (size_t)words * 8, cudaMemcpyDeviceToHost, st);
+  const cudaError_t err2 = cudaFreeAsync(scratch, st);
+  if (err == cudaSuccess) err = err2;
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+  if (err != cudaSuccess) {
+    for (int j = 0; j < count; ++j) ps[j]->poisoned = PT_ECUDA;
+    return fail(PT_ECUDA, "batched read: %s", cudaGetErrorString(err));
+  }
+  int first_rc = PT_OK;
+  for (int j = 0; j < count; ++j) {
+    pt_problem* p = ps[j];
+    const uint64_t* rec = host.data() + items[(size_t)j].out;
+    const int R = p->R, P = items[(size_t)j].npairs;
+    const int32_t status = (int32_t)(int64_t)rec[0];
+    if (status != 0) {
+      p->poisoned = status == PT_ETIMEOUT ? PT_ETIMEOUT : PT_EINTERNAL;
+      if (first_rc == PT_OK)
+        first_rc = fail(p->poisoned, "problem %d: device reported status %d", j, status);
+      continue;
+    }
+    const uint64_t* E = rec + 1;
+    const uint64_t* Ms = rec + 1 + R;
+    const uint64_t* sot = rec + 1 + 2 * R;
+    for (int k = 0; k < R; ++k) {
+      const int a = (int)(int64_t)sot[k];
+      if (E_int && E_int[j]) E_int[j][k] = (int64_t)E[a];
+      if (M && M[j]) M[j][k] = (int64_t)Ms[a];
+      if (slot_of_temp && slot_of_temp[j]) slot_of_temp[j][k] = a;
+    }
+    for (int k = 0; k < P; ++k) {
+      if (attempted && attempted[j]) attempted[j][k] = rec[1 + 3 * R + k];
+      if (accepted && accepted[j]) accepted[j][k] = rec[1 + 3 * R + P + k];
+    }
+  }
+  return first_rc;
+}
+
 int pt_chain_map(pt_problem* p, int32_t* slot_of_temp) {
   int rc = problem_check(p);
   if (rc) return rc;

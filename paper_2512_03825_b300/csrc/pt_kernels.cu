@@ -303,7 +303,44 @@ int grid_x_for(int nwords, int W, int sms, int per_sm) {
   return want < cap ? (want > 0 ? want : 1) : cap;
 }
 
+// ---------------------------------------------------------------------------------------
+// Results of many problems packed into one buffer (one block per problem record): status,
+// E_int and M by slot, slot_of_temp, and the pair counters, each as an 8-byte word.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_gather(const GatherItem* __restrict__ items, int n,
+                                                     uint64_t* __restrict__ out) {
+  for (int j = blockIdx.x; j < n; j += gridDim.x) {
+    const GatherItem it = items[j];
+    uint64_t* const o = out + it.out;
+    const int R = it.R, P = it.npairs;
+    const int total = 1 + 3 * R + 2 * P;
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+      uint64_t v;
+      if (q == 0)
+        v = (uint64_t)(int64_t)*it.status;
+      else if (q <= R)
+        v = (uint64_t)it.E_slot[q - 1];
+      else if (q <= 2 * R)
+        v = (uint64_t)it.M_slot[q - 1 - R];
+      else if (q <= 3 * R)
+        v = (uint64_t)(int64_t)it.slot_of_temp[q - 1 - 2 * R];
+      else if (q <= 3 * R + P)
+        v = it.attempted[q - 1 - 3 * R];
+      else
+        v = it.accepted[q - 1 - 3 * R - P];
+      o[q] = v;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_gather(const GatherItem* items, int n, uint64_t* out, int sms,
+                          cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_gather<<<n < 8 * sms ? n : 8 * sms, kThreads, 0, st>>>(items, n, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_init(const DevProblem& p, const DeviceInfo& dev, cudaStream_t st) {
   const int nwords = p.L * (p.L >> 1);

@@ -28,4 +28,19 @@ cudaError_t launch_energy(const DevProblem& p, const DeviceInfo& dev, cudaStream
 cudaError_t launch_exchange(const DevProblem& p, uint64_t e, int flags, cudaStream_t st,
                             uint64_t t = 0);
 
+// One problem's part of a batched read (pt_read_batch): its record of 1 + 3 R + 2 npairs
+// 8-byte words starts `out` words into the packed buffer.
+struct GatherItem {
+  const int64_t* E_slot;
+  const int64_t* M_slot;
+  const int32_t* slot_of_temp;
+  const uint64_t* attempted;
+  const uint64_t* accepted;
+  const int32_t* status;
+  int R, npairs;  // npairs = R - 1 (0 for R = 1)
+  int64_t out;
+};
+cudaError_t launch_gather(const GatherItem* items, int n, uint64_t* out, int sms,
+                          cudaStream_t st);
+
 }  // namespace ptb

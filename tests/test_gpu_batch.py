@@ -215,3 +215,20 @@ def test_autotuner_compares_equal_results(api, tuning):
     assert len(out["timings"]) == len(cands)
     assert autotune.get_tuning() == out["choice"]
     autotune.set_tuning(**autotune.DEFAULT)
+
+
+def test_read_batch_equals_single_getters(api):
+    """pt_read_batch returns, for every problem of a mixed set (one slot, several planes,
+    the generic mode), exactly what the single getters return."""
+    probs = mixed_problems(n=12, seed=17) + [W.Problem(L=8, betas=(0.4,), seed=5)]
+    gs = [api.PTProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed) for p in probs]
+    api.sweep_batch(gs, [max(p.sweeps, 1) for p in probs], [p.every for p in probs])
+    got = api.read_batch(gs)
+    for j, (g, r) in enumerate(zip(gs, got)):
+        np.testing.assert_array_equal(r["E_int"], g.energies_int(), err_msg=str(j))
+        np.testing.assert_array_equal(r["M"], g.magnetisations(), err_msg=str(j))
+        np.testing.assert_array_equal(r["chain_map"], g.chain_map(), err_msg=str(j))
+        att, acc = g.swap_stats()
+        np.testing.assert_array_equal(r["attempted"], att, err_msg=str(j))
+        np.testing.assert_array_equal(r["accepted"], acc, err_msg=str(j))
+    assert api.read_batch([]) == []
