@@ -22,6 +22,12 @@
 // The barrier counter and both count buffers are cleared by the host before each launch.
 // A barrier wait that exceeds its time limit stores PT_ETIMEOUT in the status word; every
 // waiting CTA that sees a non-zero status (or runs out of time itself) leaves the kernel.
+//
+// A grid of at most 16 CTAs can instead run as one thread-block cluster (CLUSTER): its CTAs
+// are resident together by construction and meet at the hardware cluster barrier
+// (barrier.cluster, release on arrival and acquire on the wait, at cluster scope), with no
+// counter in memory and no waiting on one.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -181,7 +187,7 @@ __device__ __forceinline__ void half_pass(const DevProblem& p, int w, int colour
   }
 }
 
-template <int MODE>
+template <int MODE, bool CLUSTER>
 __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_constant__ PersistArgs a) {
   // [R] ferro thresholds (k = 0, k = 1) by temperature, then [R] slot_of_temp and [R]
   // temp_of_slot; persist_smem(R, mode) bytes
@@ -234,6 +240,15 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
   unsigned target = 0;
   uint64_t e = a.e0;
   bool exchanged = false;
+  // every CTA meets every other; false when a bounded wait gave up (the kernel then ends)
+  auto sync_all = [&](unsigned extra) -> bool {
+    if (CLUSTER) {
+      cooperative_groups::this_cluster().sync();
+      return true;
+    }
+    target += gridDim.x + extra;
+    return grid_barrier(bar, target, p.status, a.limit_ns, &ok_s, a.stall != 0);
+  };
   for (int j = 0; j < a.n; ++j) {
     const uint64_t t = a.t0 + (uint64_t)j;
     BlockTerms bt;
@@ -241,15 +256,13 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
     BitCounter<15, 10> U, N;
     half_pass<MODE, false>(p, w, 0, t, a.rk, bt, q0, step, y0, i0, dy, di, thr, alw0, alw1,
                            used, gen, false, U, N);
-    target += gridDim.x + (j == 0 ? (unsigned)a.stall : 0u);
-    if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s, a.stall != 0)) return;
+    if (!sync_all(j == 0 ? (unsigned)a.stall : 0u)) return;
     const bool ex = a.m > 0 && (t + 1) % (uint64_t)a.m == 0;
     if (!ex && !trace) {
       half_pass<MODE, false>(p, w, 1, t, a.rk, bt, q0, step, y0, i0, dy, di, thr, alw0, alw1,
                              used, gen, false, U, N);
       if (j + 1 == a.n) break;  // the kernel's end orders this half sweep before what follows
-      target += gridDim.x;
-      if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s, a.stall != 0)) return;
+      if (!sync_all(0)) return;
       continue;
     }
     // a swap iteration or a trace row follows: count this sweep into buffer `counted & 1`
@@ -271,8 +284,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
       if (acc[0][threadIdx.x]) atomicAdd(&cb[w * 32 + threadIdx.x], acc[0][threadIdx.x]);
       if (acc[1][threadIdx.x]) atomicAdd(&cb[W * 32 + w * 32 + threadIdx.x], acc[1][threadIdx.x]);
     }
-    target += gridDim.x;
-    if (!grid_barrier(bar, target, p.status, a.limit_ns, &ok_s, a.stall != 0)) return;
+    if (!sync_all(0)) return;
     if (ex) exchange_local(p, e, cb, sot, tos, blockIdx.x == 0);
     if (blockIdx.x == 0) {
       if (trace) {
@@ -320,9 +332,12 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
   }
 }
 
-const void* persist_fn(int mode) {
-  return mode == kModeFerro ? (const void*)k_persist<kModeFerro>
-                            : (const void*)k_persist<kModeGeneric>;
+const void* persist_fn(int mode, bool cluster = false) {
+  if (cluster)
+    return mode == kModeFerro ? (const void*)k_persist<kModeFerro, true>
+                              : (const void*)k_persist<kModeGeneric, true>;
+  return mode == kModeFerro ? (const void*)k_persist<kModeFerro, false>
+                            : (const void*)k_persist<kModeGeneric, false>;
 }
 
 }  // namespace
@@ -335,13 +350,19 @@ cudaError_t persist_plan(const DevProblem& p, const DeviceInfo& dev, int words_p
                          PersistPlan* plan) {
   plan->grid = 0;
   plan->words_per_thread = 0;
+  plan->cluster = false;
   int per_sm = 0;
   // the maps and (ferro) the thresholds by temperature can pass the default 48 KB per block.
   // The limit belongs to the kernel, not to a problem: it is set to what the largest
   // problem needs, so that planning a smaller one never lowers it under a larger one's launch
-  cudaError_t err = cudaFuncSetAttribute(persist_fn(p.mode),
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)persist_smem(PT_MAX_R, p.mode));
+  cudaError_t err = cudaSuccess;
+  for (int c = 0; c < 2 && err == cudaSuccess; ++c)
+    err = cudaFuncSetAttribute(persist_fn(p.mode, c == 1),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)persist_smem(PT_MAX_R, p.mode));
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(persist_fn(p.mode, true),
+                               cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (err != cudaSuccess) return err;
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persist_fn(p.mode),
                                                       kPersistThreads,
@@ -358,6 +379,27 @@ cudaError_t persist_plan(const DevProblem& p, const DeviceInfo& dev, int words_p
   if (wpt > kPersistMaxWordsPerThread) return cudaSuccess;
   plan->grid = (int)(g * p.W);
   plan->words_per_thread = (int)wpt;
+  if (plan->grid <= kPersistMaxCluster) {
+    // one cluster of the whole grid, if the device can place one
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)plan->grid;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)plan->grid);
+    cfg.blockDim = dim3(kPersistThreads);
+    cfg.dynamicSmemBytes = persist_smem(p.R, p.mode);
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    err = cudaOccupancyMaxActiveClusters(&clusters, persist_fn(p.mode, true), &cfg);
+    if (err != cudaSuccess) {
+      cudaGetLastError();  // not placeable: keep the cooperative launch
+      return cudaSuccess;
+    }
+    plan->cluster = clusters >= 1;
+  }
   return cudaSuccess;
 }
 
@@ -380,6 +422,22 @@ cudaError_t launch_persist(const DevProblem& p, const PersistPlan& plan, uint64_
     a.rk.k1[r] = p.key1 + (uint32_t)r * kPhiloxW1;
   }
   void* args[] = {&a};
+  if (plan.cluster && stall == 0) {
+    // the test hook (stall) needs the counting barrier: it waits for a CTA that never comes
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)plan.grid;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)plan.grid);
+    cfg.blockDim = dim3(kPersistThreads);
+    cfg.dynamicSmemBytes = persist_smem(p.R, p.mode);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, persist_fn(p.mode, true), args);
+  }
   return cudaLaunchCooperativeKernel(persist_fn(p.mode), dim3(plan.grid), dim3(kPersistThreads),
                                      args, persist_smem(p.R, p.mode), st);
 }

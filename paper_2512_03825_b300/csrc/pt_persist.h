@@ -15,9 +15,13 @@ constexpr int kPersistMaxWordsPerThread = 255;
 constexpr int kPersistChunk = 1 << 16;
 constexpr int kPersistDefaultWords = 1;
 
+// The largest grid that runs as one thread-block cluster (non-portable size on B300).
+constexpr int kPersistMaxCluster = 16;
+
 struct PersistPlan {
   int grid;              // CTAs (a multiple of W), 0 when the problem does not fit one wave
   int words_per_thread;  // words of each colour per thread
+  bool cluster;          // the grid can run as one cluster (hardware cluster barrier)
 };
 
 // The device count buffer holds, in 32-bit words: [2][W * 32] for the per-launch kernels,
