@@ -379,8 +379,9 @@ cudaError_t persist_plan(const DevProblem& p, const DeviceInfo& dev, int words_p
   if (wpt > kPersistMaxWordsPerThread) return cudaSuccess;
   plan->grid = (int)(g * p.W);
   plan->words_per_thread = (int)wpt;
-  if (plan->grid <= kPersistMaxCluster) {
-    // one cluster of the whole grid, if the device can place one
+  if (plan->grid >= 2 && plan->grid <= kPersistMaxCluster) {
+    // one cluster of the whole grid, if the device can place one (a single CTA keeps the
+    // cooperative launch, whose barrier is then the block barrier)
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
