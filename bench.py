@@ -482,8 +482,10 @@ def bench_e2e(probs, sweeps, stream, world):
             "s_per_step": dt}
 
 
-def cpu_baseline_sample(probs, n_problems=16, sweeps=40):
-    """The oracle, as it stands, on a bounded sample of the same workload."""
+def cpu_baseline_sample(probs, n_problems=32, sweeps=100):
+    """The oracle, as it stands, on a bounded sample of the same workload: 32 of the 256
+    problems (every 8th, so the sample keeps the mix of L and R), 100 sweeps each, about
+    10 s of work on 16 host cores."""
     import oracle
     threads = os.cpu_count() or 1
     oracle.set_threads(threads)
