@@ -287,7 +287,7 @@ def run_ours(args, rank, world, local):
     peaks = measured_peaks()
     clock_mhz = float(peaks.get("sm_max_mhz", 2032.0))
     peak_mul = sms * IMUL_WIDE_PER_CLK_SM * clock_mhz * 1e6
-    flat = tuning.get("strategy", 0) == 0
+    flat = tuning.get("strategy", 0) in (0, 3)  # lock-step: dealt or queued tiles
     if flat:
         # the dominant kernel on its own: a batch without exchanges is nothing but
         # k_flat_half launches (two per sweep), timed on the problems' stream. Two batch
@@ -347,12 +347,12 @@ def run_ours(args, rank, world, local):
 
 
 def launches_per_batch(probs, sweeps, tuning):
-    """Kernel launches of one pt_sweep_batch call: the lock-step strategy launches two
-    half sweeps per sweep plus one exchange launch after every sweep with an exchange (one
-    mode here: h = 0); the dataflow strategy is one cooperative launch per mode; the
-    cluster strategy is one persistent launch plus a helper."""
+    """Kernel launches of one pt_sweep_batch call: the lock-step strategies (dealt or queued
+    tiles) launch two half sweeps per sweep plus one exchange launch after every sweep with
+    an exchange (one mode here: h = 0); the dataflow strategy is one cooperative launch per
+    mode; the cluster strategy is one persistent launch plus a helper."""
     strategy = tuning.get("strategy", 0)
-    if strategy == 0:
+    if strategy in (0, 3):
         return sweeps * 3
     if strategy == 2:
         return len({p.h == 0.0 and p.J > 0 for p in probs})

@@ -214,7 +214,8 @@ int pt_sweep_batch_static(pt_problem* const* problems, int count, const int64_t*
  *   PT_BATCH_QUEUE   -- PT_BATCH_FLAT with the tiles handed out on the device: one tile per
  *                       warp first, then each warp that finishes a tile takes the next
  *                       (largest first) from a counter, so the warps finish together
- *                       however the SMs' loads differ;
+ *                       however the SMs' loads differ; the tiles of the cheapest quarter of
+ *                       the work are cut in two, so each launch ends on small tiles;
  *   PT_BATCH_CLUSTER -- one persistent kernel; a problem with L >= joint_min_L runs on a
  *                       whole thread-block cluster of `cluster` CTAs (1 to 16) for all of its
  *                       sweeps, smaller ones on a single CTA;

@@ -312,9 +312,11 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
 // largest n.
 // Tiles hold about tile_words words (a problem's words of one colour and plane in
 // max(1, round(words / tile_words)) equal parts, so at most 1.5 tile_words: a lane's counts
-// over one tile stay below 2^8).
+// over one tile stay below 2^8); with `refine` (the queued schedule) the tiles of the
+// cheapest quarter of the work are then cut in two. Returns the largest n, or -1 when a
+// tile would fall outside its plane.
 int64_t build_flat_lists(pt_problem* const* ps, int count, const int64_t* n, const int* every,
-                         int tile_words, std::vector<FlatProblem>* probs,
+                         int tile_words, bool refine, std::vector<FlatProblem>* probs,
                          std::vector<Tile> tiles[2]);
 // Longest-processing-time-first assignment of tiles to `nwarps` warps: the tiles reordered
 // warp by warp and the CSR offsets first[0..nwarps].

@@ -158,7 +158,8 @@ int sweep_batch_flow(pt_problem* const* ps, int count, const int64_t* n, const i
                      cudaStream_t st, const DeviceInfo& di, int tile_words) {
   std::vector<FlatProblem> probs;
   std::vector<Tile> tiles[2];  // by mode
-  const int64_t n_max = build_flat_lists(ps, count, n, every, tile_words, &probs, tiles);
+  const int64_t n_max = build_flat_lists(ps, count, n, every, tile_words, false, &probs, tiles);
+  if (n_max < 0) return fail(PT_EINTERNAL, "batch work tiles outside their planes");
   for (int j = 0; j < count; ++j) ps[j]->stall = 0;  // test support applies to one call
   if (probs.empty()) return PT_OK;
   // one resident wave per mode (the cooperative launch needs every CTA resident)

@@ -274,6 +274,21 @@ def bench_serve(args, rank, world, stream):
     throughput measured just before, on one GPU."""
     import torch
 
+    from . import autotune
+    from . import workloads as W
+    # the launch shape tuned for this request mix (the batched workload's may differ); the
+    # caller's shape is put back at the end
+    before = autotune.get_tuning()
+    autotune.apply_cached_or_default("serve")
+    try:
+        return _bench_serve(args, stream)
+    finally:
+        autotune.set_tuning(**before)
+
+
+def _bench_serve(args, stream):
+    import torch
+
     from . import workloads as W
     eng = LibEngine(stream=stream)
     # the service rate: batched throughput on a sample of the same request mix
