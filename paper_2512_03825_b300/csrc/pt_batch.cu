@@ -482,8 +482,9 @@ int sweep_batch_static_entry(pt_problem* const* ps, int count, const int64_t* n,
   cudaStream_t st = 0;
   int rc = check_batch(ps, count, n, every, &st);
   if (rc) return rc;
-  rc = sweep_batch_static(ps, count, n, every, st, ps[0]->dev_info, g_batch_tuning.tile_words,
-                          g_batch_tuning.strategy == PT_BATCH_QUEUE);
+  const BatchTuning tune = batch_tuning();
+  rc = sweep_batch_static(ps, count, n, every, st, ps[0]->dev_info, tune.tile_words,
+                          tune.strategy == PT_BATCH_QUEUE);
   if (rc) return rc;
   advance_counters(ps, count, n, every);
   return PT_OK;
@@ -513,7 +514,7 @@ int sweep_batch(pt_problem* const* ps, int count, const int64_t* n, const int* e
   int rc = problem_device_guard(ps[0]);
   if (rc) return rc;
   const DeviceInfo& di = ps[0]->dev_info;
-  BatchTuning tune = g_batch_tuning;
+  BatchTuning tune = batch_tuning();
   for (int j = 0; j < count; ++j)  // trace rows are written by the lock-step exchange launch
     if (ps[j]->dev.trace_E != nullptr && tune.strategy != PT_BATCH_QUEUE)
       tune.strategy = PT_BATCH_FLAT;

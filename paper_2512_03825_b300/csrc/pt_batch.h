@@ -21,7 +21,9 @@ struct BatchTuning {
   int joint_min_L = 128;
   int tile_words = 512;
 };
-extern BatchTuning g_batch_tuning;
+extern BatchTuning g_batch_tuning;  // written and read under the library lock only
+// A copy of the batch tuning, read under the library lock (the setters take it too).
+BatchTuning batch_tuning();
 
 struct DeviceInfo;
 // The lock-step path (pt_flat.cu); problems are already checked.

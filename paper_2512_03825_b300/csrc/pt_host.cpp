@@ -53,6 +53,17 @@ Allocator g_alloc;
 
 constexpr uint64_t kTwo32 = 1ull << 32;
 
+}  // namespace
+
+namespace ptb {
+BatchTuning batch_tuning() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_batch_tuning;
+}
+}  // namespace ptb
+
+namespace {
+
 // ---------------------------------------------------------------------------------------
 // Exact integer energies (the quantisation of include/pt.h)
 // ---------------------------------------------------------------------------------------
