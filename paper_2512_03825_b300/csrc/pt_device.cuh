@@ -72,6 +72,16 @@ __device__ __forceinline__ void count_swap(uint64_t* attempted, uint64_t* accept
   if (accept) atomicAdd(reinterpret_cast<unsigned long long*>(accepted + k), 1ull);
 }
 
+// The exchange threshold of one temperature pair at energy difference n (SwapPair): the
+// saturated constants outside the tabulated range, else the table entry; the index stays
+// inside the table for every n in [n_lo, n_hi].
+__device__ __forceinline__ uint64_t pair_threshold(const SwapPair& sp, const uint32_t* table,
+                                                   int shift, int64_t n) {
+  if (n < sp.n_lo) return sp.S_below;
+  if (n > sp.n_hi) return sp.S_above;
+  return table[sp.offset + ((n - sp.n_lo) >> shift)];
+}
+
 // The eight blocks j of one site in one sweep have the counters {site, lo32(t), blk0 + j, c3}:
 // they differ in counter word 2 only. In round 1 the product of word 0 depends on the site
 // alone and that of word 2 on j alone; in round 2 the product of word 0 (which came from

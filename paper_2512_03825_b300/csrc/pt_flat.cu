@@ -145,13 +145,7 @@ __global__ void __launch_bounds__(kFlatThreads) k_flat_exchange(const FlatProble
         const int a = sot[k], b = sot[k + 1];
         const int64_t n = E_s[a] - E_s[b];
         const SwapPair sp = k == k0 ? sp0 : p.pairs[k];
-        uint64_t S;
-        if (n < sp.n_lo)
-          S = sp.S_below;
-        else if (n > sp.n_hi)
-          S = sp.S_above;
-        else
-          S = p.swap_table[sp.offset + (n - sp.n_lo)];
+        const uint64_t S = pair_threshold(sp, p.swap_table, p.table_shift, n);
         const Philox4 rnd = philox4x32_10((uint32_t)k, (uint32_t)e, 0u, c3, p.key0, p.key1);
         const bool accept = (uint64_t)rnd.x < S;
         count_swap(p.attempted, p.accepted, k, accept);

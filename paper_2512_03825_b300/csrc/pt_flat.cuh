@@ -88,13 +88,7 @@ __device__ inline void exchange_warp(const DevProblem& p, uint64_t e) {
     const int a = __ldcg(p.slot_of_temp + k), b = __ldcg(p.slot_of_temp + k + 1);
     const int64_t n = __ldcg(p.E_slot + a) - __ldcg(p.E_slot + b);
     const SwapPair sp = p.pairs[k];
-    uint64_t S;
-    if (n < sp.n_lo)
-      S = sp.S_below;
-    else if (n > sp.n_hi)
-      S = sp.S_above;
-    else
-      S = p.swap_table[sp.offset + (n - sp.n_lo)];
+    const uint64_t S = pair_threshold(sp, p.swap_table, p.table_shift, n);
     const Philox4 rnd = philox4x32_10((uint32_t)k, (uint32_t)e, 0u, c3, p.key0, p.key1);
     const bool accept = (uint64_t)rnd.x < S;
     count_swap(p.attempted, p.accepted, k, accept);

@@ -57,13 +57,7 @@ __device__ void exchange_energies(const DevProblem& p, uint64_t e, const int64_t
     if (k + 1 < R) {
       const int64_t n = __ldcg(eb + sot[k]) - __ldcg(eb + sot[k + 1]);
       const SwapPair sp = p.pairs[k];
-      uint64_t S;
-      if (n < sp.n_lo)
-        S = sp.S_below;
-      else if (n > sp.n_hi)
-        S = sp.S_above;
-      else
-        S = p.swap_table[sp.offset + (n - sp.n_lo)];
+      const uint64_t S = pair_threshold(sp, p.swap_table, p.table_shift, n);
       const Philox4 rnd = philox4x32_10((uint32_t)k, (uint32_t)e, 0u, c3, p.key0, p.key1);
       if ((uint64_t)rnd.x < S) accepted |= 1u << q;
     }
@@ -122,13 +116,7 @@ __device__ void exchange_prefetched(const DevProblem& p, uint64_t e, const int64
     if (k + 1 < R) {
       const int64_t n = __ldcg(eb + sot[k]) - __ldcg(eb + sot[k + 1]);
       const SwapPair& sp = pf.sp[q];
-      uint64_t S;
-      if (n < sp.n_lo)
-        S = sp.S_below;
-      else if (n > sp.n_hi)
-        S = sp.S_above;
-      else
-        S = p.swap_table[sp.offset + (n - sp.n_lo)];
+      const uint64_t S = pair_threshold(sp, p.swap_table, p.table_shift, n);
       if ((uint64_t)pf.u[q] < S) accepted |= 1u << q;
     }
   }

@@ -105,7 +105,8 @@ uint64_t swap_rule(double beta_lo, double beta_hi, int64_t n, int64_t s, int rul
 }
 
 // The exchange threshold of one temperature pair as a function of n: constant below n_lo
-// and above n_hi, tabulated in between. S(n) is monotone in n (y is linear in n and both
+// and above n_hi, tabulated in between at the n that are multiples of 2^shift (table_shift:
+// no other n can occur). S(n) is monotone in n (y is linear in n and both
 // forms are monotone in y), so the saturated ranges are found by bisection and then checked
 // at their edges. With reach > 0 only |n| <= reach can occur (a lattice's largest energy
 // difference): the table then covers the non-saturated n within [-reach, reach] only, and
@@ -117,24 +118,58 @@ struct PairTable {
   std::vector<uint32_t> vals;
 };
 
-int fill_pair_table(double blo, double bhi, int64_t s, int rule, PairTable* t) {
+// The largest multiple of step <= x, and the smallest >= x (step > 0).
+int64_t floor_multiple(int64_t x, int64_t step) {
+  const int64_t q = x / step;
+  return (q * step > x ? q - 1 : q) * step;
+}
+int64_t ceil_multiple(int64_t x, int64_t step) { return -floor_multiple(-x, step); }
+
+// Every energy difference n = E_int(a) - E_int(b) is a multiple of gcd(4 J_int, 2 h_int):
+// flipping one spin changes the number of unsatisfied bonds by 4 - 2 k (even), so the bond
+// sum of Eq. 3 moves in steps of 4 from its all-up value 2 L^2, and the magnetisation in
+// steps of 2 from L^2. The exchange tables keep only the n that are multiples of the power
+// of two in that gcd (4 for J = 1, h = 0): a quarter of the entries.
+int table_shift(int64_t Ji, int64_t hi) {
+  uint64_t a = 4 * (uint64_t)(Ji < 0 ? -Ji : Ji), b = 2 * (uint64_t)(hi < 0 ? -hi : hi);
+  while (b) {
+    const uint64_t r = a % b;
+    a = b;
+    b = r;
+  }
+  if (a == 0) return 0;
+  int k = 0;
+  while (!(a & 1)) {
+    a >>= 1;
+    ++k;
+  }
+  return k;
+}
+
+// Tabulates S at n_lo, n_lo + 2^shift, ..., n_hi, after rounding n_lo up and n_hi down to
+// multiples of 2^shift (no multiple lies in the parts cut off, so lookups of multiples
+// below or above the new range still get S_below / S_above).
+int fill_pair_table(double blo, double bhi, int64_t s, int rule, int shift, PairTable* t) {
   const double d = bhi - blo;
-  const int64_t len = t->n_hi - t->n_lo + 1;
-  t->vals.resize((size_t)std::max<int64_t>(len, 0));
-  uint64_t prev = swap_rule(blo, bhi, t->n_lo - 1, s, rule);
+  const int64_t step = (int64_t)1 << shift;
+  t->n_lo = ceil_multiple(t->n_lo, step);
+  t->n_hi = floor_multiple(t->n_hi, step);
+  const int64_t len = t->n_hi >= t->n_lo ? (t->n_hi - t->n_lo) / step + 1 : 0;
+  t->vals.resize((size_t)len);
+  uint64_t prev = swap_rule(blo, bhi, t->n_lo - step, s, rule);
   for (int64_t j = 0; j < len; ++j) {
-    const uint64_t v = swap_rule(blo, bhi, t->n_lo + j, s, rule);
+    const int64_t n = t->n_lo + j * step;
+    const uint64_t v = swap_rule(blo, bhi, n, s, rule);
     if (v >= kTwo32) return fail(PT_EINTERNAL, "exchange table entry saturates inside");
     if ((d > 0 && v > prev) || (d < 0 && v < prev))
-      return fail(PT_EINTERNAL, "exchange threshold not monotone at n = %lld",
-                  (long long)(t->n_lo + j));
+      return fail(PT_EINTERNAL, "exchange threshold not monotone at n = %lld", (long long)n);
     prev = v;
     t->vals[(size_t)j] = (uint32_t)v;
   }
   return PT_OK;
 }
 
-int build_pair_table(double blo, double bhi, int64_t s, int rule, int64_t reach,
+int build_pair_table(double blo, double bhi, int64_t s, int rule, int64_t reach, int shift,
                      PairTable* out) {
   PairTable t;
   const double d = bhi - blo;
@@ -154,7 +189,7 @@ int build_pair_table(double blo, double bhi, int64_t s, int rule, int64_t reach,
     if (t.S_below >= kTwo32 || t.S_above >= kTwo32 || t.S_below == 0 || t.S_above == 0) {
       // a saturated end inside [-reach - 1, reach + 1]: search for the edges instead
     } else {
-      const int rc = fill_pair_table(blo, bhi, s, rule, &t);
+      const int rc = fill_pair_table(blo, bhi, s, rule, shift, &t);
       if (rc) return rc;
       *out = std::move(t);
       return PT_OK;
@@ -197,21 +232,23 @@ int build_pair_table(double blo, double bhi, int64_t s, int rule, int64_t reach,
       t.n_hi = -reach - 1;
     }
   }
-  const int rc = fill_pair_table(blo, bhi, s, rule, &t);
+  const int rc = fill_pair_table(blo, bhi, s, rule, shift, &t);
   if (rc) return rc;
   *out = std::move(t);
   return PT_OK;
 }
 
-// Tables depend only on (beta_lo, beta_hi, s, rule, reach); requests with the same ladder
-// and lattice reach share them.
+// Tables depend only on (beta_lo, beta_hi, s, rule, reach, shift); requests with the same
+// ladder, lattice reach and stride share them.
 struct PairKey {
   uint64_t blo, bhi;
   int64_t s;
   int rule;
   int64_t reach;
+  int shift;
   bool operator<(const PairKey& o) const {
-    return std::tie(blo, bhi, s, rule, reach) < std::tie(o.blo, o.bhi, o.s, o.rule, o.reach);
+    return std::tie(blo, bhi, s, rule, reach, shift) <
+           std::tie(o.blo, o.bhi, o.s, o.rule, o.reach, o.shift);
   }
 };
 std::mutex g_table_mu;
@@ -230,7 +267,7 @@ int64_t energy_reach(int L, int64_t Ji, int64_t hi) {
 // it is inside the pair's saturation range (a small lattice on a dense ladder); otherwise
 // the whole table is built and shared by every lattice size, so problems that differ only
 // in L share it.
-int get_pair_table(double blo, double bhi, int64_t s, int rule, int64_t reach,
+int get_pair_table(double blo, double bhi, int64_t s, int rule, int64_t reach, int shift,
                    std::shared_ptr<const PairTable>* out) {
   const double d = std::fabs(bhi - blo);
   const double nmax = d == 0.0 ? 0.0 : std::ceil(45.0 * (double)s / d) + 2.0;
@@ -241,6 +278,7 @@ int get_pair_table(double blo, double bhi, int64_t s, int rule, int64_t reach,
   key.s = s;
   key.rule = rule;
   key.reach = reach;
+  key.shift = shift;
   {
     std::lock_guard<std::mutex> lk(g_table_mu);
     auto it = g_tables.find(key);
@@ -250,7 +288,7 @@ int get_pair_table(double blo, double bhi, int64_t s, int rule, int64_t reach,
     }
   }
   auto t = std::make_shared<PairTable>();
-  const int rc = build_pair_table(blo, bhi, s, rule, reach, t.get());
+  const int rc = build_pair_table(blo, bhi, s, rule, reach, shift, t.get());
   if (rc != PT_OK) return rc;
   std::lock_guard<std::mutex> lk(g_table_mu);
   if (g_table_bytes > kTableCacheCap) {
@@ -267,7 +305,7 @@ int get_pair_table(double blo, double bhi, int64_t s, int rule, int64_t reach,
 // threads (the tables are independent and the cache is shared). An error in any of them is
 // reported on the calling thread.
 int get_ladder_tables(const double* betas, int R, int64_t s, int rule, int64_t reach,
-                      std::vector<std::shared_ptr<const PairTable>>* out) {
+                      int shift, std::vector<std::shared_ptr<const PairTable>>* out) {
   const int npairs = std::max(R - 1, 0);
   out->assign((size_t)npairs, nullptr);
   const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
@@ -279,7 +317,8 @@ int get_ladder_tables(const double* betas, int R, int64_t s, int rule, int64_t r
     for (;;) {
       const int k = next.fetch_add(1);
       if (k >= npairs) return;
-      const int rc = get_pair_table(betas[k], betas[k + 1], s, rule, reach, &(*out)[(size_t)k]);
+      const int rc =
+          get_pair_table(betas[k], betas[k + 1], s, rule, reach, shift, &(*out)[(size_t)k]);
       if (rc) {
         rcs[(size_t)w] = rc;
         msgs[(size_t)w] = g_last_error;
@@ -575,7 +614,7 @@ uint64_t pt_spin_threshold(double beta, int64_t dE_int, int64_t s) {
 uint64_t pt_swap_threshold_ex(double beta_lo, double beta_hi, int64_t n, int64_t s, int rule) {
   if (rule != PT_SWAP_BARKER && rule != PT_SWAP_METROPOLIS) return ~uint64_t(0);
   std::shared_ptr<const PairTable> t;
-  if (get_pair_table(beta_lo, beta_hi, s, rule, 0, &t) != PT_OK) return ~uint64_t(0);
+  if (get_pair_table(beta_lo, beta_hi, s, rule, 0, 0, &t) != PT_OK) return ~uint64_t(0);
   if (n < t->n_lo) return t->S_below;
   if (n > t->n_hi) return t->S_above;
   return t->vals[(size_t)(n - t->n_lo)];
@@ -600,7 +639,8 @@ size_t pt_estimate_device_bytes(int L, const double* betas, int R, double J, dou
   if (check_args(L, betas, R, J, h, &s, &Ji, &hi) != PT_OK) return 0;
   size_t entries = 0;
   std::vector<std::shared_ptr<const PairTable>> tabs;
-  if (get_ladder_tables(betas, R, s, PT_SWAP_BARKER, energy_reach(L, Ji, hi), &tabs) != PT_OK)
+  if (get_ladder_tables(betas, R, s, PT_SWAP_BARKER, energy_reach(L, Ji, hi),
+                        table_shift(Ji, hi), &tabs) != PT_OK)
     return 0;
   for (const auto& t : tabs) entries += t->vals.size();
   const int W = (R + 31) / 32;
@@ -668,7 +708,8 @@ int pt_create_ex(int L, const double* betas, int R, double J, double h, uint64_t
   std::vector<std::shared_ptr<const PairTable>> tabs;
   std::vector<SwapPair> pairs((size_t)npairs);
   size_t entries = 0;
-  rc = get_ladder_tables(betas, R, s, swap_rule_opt, energy_reach(L, Ji, hi), &tabs);
+  const int shift = table_shift(Ji, hi);
+  rc = get_ladder_tables(betas, R, s, swap_rule_opt, energy_reach(L, Ji, hi), shift, &tabs);
   if (rc) return rc;
   for (int k = 0; k + 1 < R; ++k) {
     const std::shared_ptr<const PairTable>& t = tabs[(size_t)k];
@@ -698,6 +739,7 @@ int pt_create_ex(int L, const double* betas, int R, double J, double h, uint64_t
   d.mode = p->mode;
   d.key0 = (uint32_t)seed;
   d.key1 = (uint32_t)(seed >> 32);
+  d.table_shift = shift;
   d.J_int = Ji;
   d.h_int = hi;
   d.s = s;

@@ -116,13 +116,7 @@ __device__ void exchange_local(const DevProblem& p, uint64_t e, const uint32_t* 
     const int64_t Eb = slot_energy(p, L2, __ldcg(cb + b), __ldcg(cb + W * 32 + b));
     const int64_t n = Ea - Eb;
     const SwapPair sp = p.pairs[k];
-    uint64_t S;
-    if (n < sp.n_lo)
-      S = sp.S_below;
-    else if (n > sp.n_hi)
-      S = sp.S_above;
-    else
-      S = p.swap_table[sp.offset + (n - sp.n_lo)];
+    const uint64_t S = pair_threshold(sp, p.swap_table, p.table_shift, n);
     const Philox4 rnd = philox4x32_10((uint32_t)k, (uint32_t)e, 0u, c3, p.key0, p.key1);
     const bool accept = (uint64_t)rnd.x < S;
     if (owner) count_swap(p.attempted, p.accepted, k, accept);

@@ -41,8 +41,9 @@ struct PlaneGeneric {
 };
 
 // Exchange threshold of temperature pair (k, k+1) as a function of n = E_int(k) - E_int(k+1):
-// table[offset + n - n_lo] for n_lo <= n <= n_hi, S_below / S_above outside. Values in
-// [0, 2^32]; table entries are < 2^32.
+// table[offset + ((n - n_lo) >> table_shift)] for n_lo <= n <= n_hi, S_below / S_above
+// outside. Every n that can occur is a multiple of 2^table_shift (DevProblem), and so are
+// n_lo and n_hi: the table holds those n only. Values in [0, 2^32]; table entries are < 2^32.
 struct SwapPair {
   int64_t n_lo, n_hi;
   uint64_t S_below, S_above;
@@ -54,6 +55,8 @@ struct DevProblem {
   uint32_t* spins;         // [W][2][L][L/2]
   int L, R, W, mode;
   uint32_t key0, key1;     // Philox key = seed
+  int32_t table_shift;     // log2 of the exchange tables' stride in n (SwapPair)
+  int32_t reserved;
   int64_t J_int, h_int, s;
   const uint64_t* T_temp;  // [R][kClasses] thresholds by temperature index, in [0, 2^32]
   void* planes;            // PlaneFerro[W] or PlaneGeneric[W]

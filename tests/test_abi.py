@@ -222,7 +222,8 @@ def test_exchange_tables_limited_to_reachable_energies(pt):
     from paper_2512_03825_b300 import workloads as W
     small = api.estimate_device_bytes(8, W.linear_ladder(0.05, 1.0, 2048))
     assert 0 < small < 64 * 2 ** 20
-    # a lattice that reaches the whole range keeps every entry: L = 300 with the paper's
-    # ladder T_i = 1 + 3 i / 1500 holds more than 1 GiB of tables
+    # a lattice that reaches the whole range keeps every entry it can look up: L = 300 with
+    # the paper's ladder T_i = 1 + 3 i / 1500 holds more than 256 MiB of tables (every n
+    # would take 1.2 GiB; only multiples of 4 occur, and only those are kept)
     paper = api.estimate_device_bytes(300, [1.0 / (1.0 + 3.0 * i / 1500) for i in range(1500)])
-    assert paper > 2 ** 30
+    assert 2 ** 28 < paper < 2 ** 30

@@ -93,6 +93,11 @@ def test_config_L1024_R64_prefix(api):
     W.Problem(L=14, betas=W.linear_ladder(0.2, 0.7, 9), J=-1.0, h=0.25, seed=8),  # antiferro
     W.Problem(L=20, betas=W.linear_ladder(0.3, 0.5, 40), J=0.5, h=-0.3, seed=9),
     W.Problem(L=96, betas=W.linear_ladder(0.3, 0.6, 48), seed=10),
+    # exchange tables strided by 2^k in n (k = 1, 3, 1): no coupling, J_int = 2, and
+    # gcd(4 J_int, 2 h_int) = 2
+    W.Problem(L=10, betas=W.linear_ladder(0.1, 0.8, 12), J=0.0, h=0.5, seed=13),
+    W.Problem(L=12, betas=W.linear_ladder(0.1, 0.4, 12), J=2.0, seed=14),
+    W.Problem(L=8, betas=W.linear_ladder(0.05, 0.3, 10), J=3.0, h=1.0, seed=15),
 ], ids=lambda p: "L%d_R%d_J%g_h%g" % (p.L, p.R, p.J, p.h))
 @pytest.mark.parametrize("every", [0, 1, 3])
 def test_edge_cases(api, prob, every):

@@ -196,6 +196,25 @@ def test_energy_symmetries():
             assert e0 - e1 == 2 * hi * m
 
 
+@pytest.mark.parametrize("J,h", [(1.0, 0.0), (1.0, 0.1), (-1.0, 0.25), (0.0, 0.5), (2.0, 0.0),
+                                 (3.0, 1.0)])
+def test_energy_differences_lie_on_a_lattice(J, h):
+    """Two spin states' E_int differ by a multiple of g = gcd(4 J_int, 2 h_int), and random
+    states reach differences whose gcd is g itself: the number of unsatisfied bonds is even
+    (one flip changes it by 4 - 2k), so the bond sum moves in steps of 4, and M in steps of
+    2. The exchange tables hold the threshold only at multiples of the power of two in g."""
+    import math
+    rng = np.random.Generator(np.random.PCG64(11))
+    s, Ji, hi = oracle.quantise(J, h)
+    g = math.gcd(4 * abs(Ji), 2 * abs(hi))
+    for L in (4, 6, 10):
+        es = [_with_state(L, rng.choice(np.array([-1, 1], np.int8), size=(L, L)), J, h)
+              .energies_int()[0] for _ in range(24)]
+        diffs = [int(e - es[0]) for e in es[1:]]
+        assert all(d % g == 0 for d in diffs), (L, diffs)
+        assert math.gcd(*diffs) == g, (L, diffs)
+
+
 # --------------------------------------------------------------------------------------
 # Threshold formulas vs high-precision arithmetic
 # --------------------------------------------------------------------------------------
