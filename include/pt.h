@@ -91,16 +91,28 @@ int pt_create(int L, const double* betas, int R, double J, double h, uint64_t se
  *              probability min(1, e^x) = min(1, e^-y), S(y) = 2^32 for y <= 0, 0 above
  *              y = 44, floor(2^32 * exp(-y)) in between.
  *   (x, y, n and s as in the swap rule at the top of this file.) Both rules satisfy detailed
- *   balance for the pair, p(y) / p(-y) = e^-y. */
+ *   balance for the pair, p(y) / p(-y) = e^-y.
+ *   stream     the problem's stream from the start (a cudaStream_t, as pt_set_stream).
+ *              NULL (default): the legacy default stream, and pt_create_ex returns once the
+ *              problem is initialised. Otherwise the initialisation (one host-to-device copy
+ *              of thresholds and tables, the initial spins, the plane thresholds) is queued
+ *              on that stream and pt_create_ex returns without waiting; a device failure
+ *              during it is reported, and poisons the problem, at the next call that
+ *              synchronises. */
 #define PT_SWAP_BARKER 0
 #define PT_SWAP_METROPOLIS 1
 typedef struct pt_options {
   uint32_t size;
   int32_t swap_rule;
+  void* stream;
 } pt_options;
 
 /* pt_create with options (NULL: the defaults of pt_create). PT_EINVAL for an unknown swap
- * rule or a size outside 4..4096. */
+ * rule or a size outside 4..4096. The thresholds and tables that a problem's creation copies
+ * to the device depend only on its ladder, J, h, swap rule and (for small lattices) L, not
+ * on the seed: up to 64 MiB of them per problem are kept in page-locked host memory after
+ * the first creation (at most 1 GiB in all) and copied from there by later creations with
+ * the same parameters. */
 int pt_create_ex(int L, const double* betas, int R, double J, double h, uint64_t seed,
                  const pt_options* opt, pt_problem** out);
 

@@ -35,7 +35,7 @@ PT_SWAP_METROPOLIS = 1
 
 class PTOptions(C.Structure):
     """struct pt_options of include/pt.h."""
-    _fields_ = [("size", C.c_uint32), ("swap_rule", C.c_int32)]
+    _fields_ = [("size", C.c_uint32), ("swap_rule", C.c_int32), ("stream", C.c_void_p)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)

@@ -26,7 +26,8 @@ class PTProblem:
         b = np.ascontiguousarray(betas, dtype=np.float64)
         if _handle is None:
             h_ = C.c_void_p()
-            opt = PTOptions(C.sizeof(PTOptions), int(swap_rule))
+            raw = int(getattr(stream, "cuda_stream", stream) or 0)
+            opt = PTOptions(C.sizeof(PTOptions), int(swap_rule), C.c_void_p(raw))
             check(lib.pt_create_ex(int(L), _dptr(b, C.c_double), int(b.size), float(J),
                                    float(h), int(seed) & 0xFFFFFFFFFFFFFFFF, C.byref(opt),
                                    C.byref(h_)), "pt_create_ex")
@@ -37,7 +38,7 @@ class PTProblem:
         self.betas = b.copy()
         self.J, self.h, self.seed = float(J), float(h), int(seed)
         self.swap_rule = int(swap_rule)
-        if stream is not None:
+        if stream is not None and _handle is not None:
             self.set_stream(stream)
 
     # -- checkpoints ---------------------------------------------------------------------

@@ -267,11 +267,15 @@ int64_t energy_reach(int L, int64_t Ji, int64_t hi) {
 // it is inside the pair's saturation range (a small lattice on a dense ladder); otherwise
 // the whole table is built and shared by every lattice size, so problems that differ only
 // in L share it.
-int get_pair_table(double blo, double bhi, int64_t s, int rule, int64_t reach, int shift,
-                   std::shared_ptr<const PairTable>* out) {
+bool reach_shapes(double blo, double bhi, int64_t s, int64_t reach) {
   const double d = std::fabs(bhi - blo);
   const double nmax = d == 0.0 ? 0.0 : std::ceil(45.0 * (double)s / d) + 2.0;
-  if (!(reach > 0 && (double)reach + 2.0 < nmax)) reach = 0;
+  return reach > 0 && (double)reach + 2.0 < nmax;
+}
+
+int get_pair_table(double blo, double bhi, int64_t s, int rule, int64_t reach, int shift,
+                   std::shared_ptr<const PairTable>* out) {
+  if (!reach_shapes(blo, bhi, s, reach)) reach = 0;
   PairKey key;
   memcpy(&key.blo, &blo, 8);
   memcpy(&key.bhi, &bhi, 8);
@@ -422,6 +426,156 @@ int check_args(int L, const double* betas, int R, double J, double h, int64_t* s
 
 int mode_for(int64_t J_int, int64_t h_int) {
   return (h_int == 0 && J_int > 0) ? kModeFerro : kModeGeneric;
+}
+
+// ---------------------------------------------------------------------------------------
+// Creation images. A problem's allocation from its thresholds to its end (thresholds by
+// temperature, identity maps, zeroed planes, counts, energies and counters, pair
+// descriptors, exchange tables) is a function of the ladder, the quantised couplings, the
+// swap rule and the lattice reach where it shapes a table; the seed only drives the initial
+// spins, which are drawn on the device. Its offsets from the thresholds do not depend on L.
+// Images up to kImageMaxBytes are built once into page-locked host memory and kept (up to
+// kImageCacheBytes in all), so a creation queues one asynchronous copy and does no table
+// work on the host. Larger ones (long ladders on large lattices) are built per creation in
+// pageable memory. A problem holds its page-locked image until pt_destroy has synchronised
+// its stream, so dropping images from the cache never frees one that a copy still reads.
+// ---------------------------------------------------------------------------------------
+struct ImageKey {
+  std::vector<uint64_t> betas;  // bit patterns
+  int64_t s, Ji, hi, reach;     // reach: 0 unless it shapes one of the tables
+  int rule;
+  bool operator<(const ImageKey& o) const {
+    return std::tie(s, Ji, hi, reach, rule, betas) <
+           std::tie(o.s, o.Ji, o.hi, o.reach, o.rule, o.betas);
+  }
+};
+
+struct Image {
+  std::vector<uint8_t> pageable;  // the bytes, unless page-locked
+  uint8_t* locked = nullptr;      // cudaHostAlloc'd bytes
+  size_t bytes = 0;
+  size_t entries = 0;             // exchange table entries (for the layout)
+  const uint8_t* data() const { return locked ? locked : pageable.data(); }
+  Image() = default;
+  Image(const Image&) = delete;
+  Image& operator=(const Image&) = delete;
+  ~Image() {
+    if (locked) cudaFreeHost(locked);
+  }
+};
+
+std::mutex g_image_mu;
+std::map<ImageKey, std::shared_ptr<const Image>> g_images;
+size_t g_image_bytes = 0;
+constexpr size_t kImageMaxBytes = size_t(64) << 20;
+constexpr size_t kImageCacheBytes = size_t(1) << 30;
+
+// Builds the image of a problem with this ladder and layout parameters.
+int build_image(int L, const double* betas, int R, int64_t s, int64_t Ji, int64_t hi, int rule,
+                int64_t reach, int shift, int mode, bool lock, std::shared_ptr<Image>* out) {
+  // thresholds by temperature, class c = 2 k + (sigma == +1)
+  std::vector<uint64_t> T_temp((size_t)R * kClasses);
+  for (int k = 0; k < R; ++k)
+    for (int kk = 0; kk <= 4; ++kk)
+      for (int up = 0; up <= 1; ++up) {
+        const int64_t sigma = up ? 1 : -1;
+        const int64_t nb = 4 - 2 * kk;  // sigma * sum of neighbour spins
+        const int64_t dE = 2 * (Ji * nb - hi * sigma);
+        T_temp[(size_t)k * kClasses + 2 * kk + up] = spin_threshold(betas[k], dE, s);
+      }
+  if (mode == kModeFerro)
+    for (int k = 0; k < R; ++k)
+      if (T_temp[(size_t)k * kClasses + 1] > T_temp[(size_t)k * kClasses + 3])
+        return fail(PT_EINTERNAL, "threshold order violated at temperature %d", k);
+
+  // exchange tables
+  const int npairs = std::max(R - 1, 1);
+  std::vector<std::shared_ptr<const PairTable>> tabs;
+  std::vector<SwapPair> pairs((size_t)npairs);
+  size_t entries = 0;
+  int rc = get_ladder_tables(betas, R, s, rule, reach, shift, &tabs);
+  if (rc) return rc;
+  for (int k = 0; k + 1 < R; ++k) {
+    const std::shared_ptr<const PairTable>& t = tabs[(size_t)k];
+    pairs[k].n_lo = t->n_lo;
+    pairs[k].n_hi = t->n_hi;
+    pairs[k].S_below = t->S_below;
+    pairs[k].S_above = t->S_above;
+    pairs[k].offset = (int64_t)entries;
+    entries += t->vals.size();
+  }
+
+  const int W = (R + 31) / 32;
+  const Layout lay = make_layout(L, R, W, mode, entries);
+  auto img = std::make_shared<Image>();
+  img->bytes = lay.total - lay.T_temp;
+  img->entries = entries;
+  uint8_t* dst = nullptr;
+  if (lock && img->bytes <= kImageMaxBytes &&
+      cudaHostAlloc((void**)&img->locked, img->bytes, cudaHostAllocPortable) == cudaSuccess) {
+    dst = img->locked;
+    memset(dst, 0, img->bytes);
+  } else {
+    cudaGetLastError();
+    img->locked = nullptr;
+    img->pageable.assign(img->bytes, 0);
+    dst = img->pageable.data();
+  }
+  auto put = [&](size_t off, const void* src, size_t bytes) {
+    memcpy(dst + (off - lay.T_temp), src, bytes);
+  };
+  put(lay.T_temp, T_temp.data(), T_temp.size() * 8);
+  std::vector<int32_t> ident(R);
+  for (int r = 0; r < R; ++r) ident[r] = r;
+  put(lay.temp_of_slot, ident.data(), R * 4);
+  put(lay.slot_of_temp, ident.data(), R * 4);
+  put(lay.pairs, pairs.data(), pairs.size() * sizeof(SwapPair));
+  for (int k = 0; k + 1 < R; ++k)
+    if (!tabs[k]->vals.empty())
+      put(lay.table + (size_t)pairs[k].offset * 4, tabs[k]->vals.data(), tabs[k]->vals.size() * 4);
+  *out = std::move(img);
+  return PT_OK;
+}
+
+// The creation image of a problem: from the cache, or built (and cached when it could be
+// page-locked).
+int get_image(int L, const double* betas, int R, int64_t s, int64_t Ji, int64_t hi, int rule,
+              int mode, std::shared_ptr<const Image>* out) {
+  int64_t reach = energy_reach(L, Ji, hi);
+  bool shapes = false;
+  for (int k = 0; k + 1 < R && !shapes; ++k) shapes = reach_shapes(betas[k], betas[k + 1], s, reach);
+  if (!shapes) reach = 0;
+  ImageKey key;
+  key.betas.resize((size_t)R);
+  memcpy(key.betas.data(), betas, (size_t)R * 8);
+  key.s = s;
+  key.Ji = Ji;
+  key.hi = hi;
+  key.reach = reach;
+  key.rule = rule;
+  {
+    std::lock_guard<std::mutex> lk(g_image_mu);
+    auto it = g_images.find(key);
+    if (it != g_images.end()) {
+      *out = it->second;
+      return PT_OK;
+    }
+  }
+  std::shared_ptr<Image> img;
+  const int rc = build_image(L, betas, R, s, Ji, hi, rule, reach, table_shift(Ji, hi), mode,
+                             true, &img);
+  if (rc) return rc;
+  if (img->locked) {
+    std::lock_guard<std::mutex> lk(g_image_mu);
+    if (g_image_bytes + img->bytes > kImageCacheBytes) {
+      g_images.clear();  // images still held by problems stay alive until their destroy
+      g_image_bytes = 0;
+    }
+    auto ins = g_images.emplace(std::move(key), img);
+    if (ins.second) g_image_bytes += img->bytes;
+  }
+  *out = std::move(img);
+  return PT_OK;
 }
 
 }  // namespace
@@ -657,6 +811,7 @@ int pt_create_ex(int L, const double* betas, int R, double J, double h, uint64_t
   if (!out) return fail(PT_EINVAL, "out is NULL");
   *out = nullptr;
   int swap_rule_opt = PT_SWAP_BARKER;
+  cudaStream_t stream = 0;
   if (opt) {
     if (opt->size < sizeof(uint32_t) || opt->size > 4096)
       return fail(PT_EINVAL, "pt_options.size = %u", opt->size);
@@ -664,6 +819,8 @@ int pt_create_ex(int L, const double* betas, int R, double J, double h, uint64_t
       swap_rule_opt = opt->swap_rule;
     if (swap_rule_opt != PT_SWAP_BARKER && swap_rule_opt != PT_SWAP_METROPOLIS)
       return fail(PT_EINVAL, "unknown swap rule %d", swap_rule_opt);
+    if (opt->size >= offsetof(pt_options, stream) + sizeof(void*))
+      stream = (cudaStream_t)opt->stream;
   }
   int64_t s, Ji, hi;
   int rc = check_args(L, betas, R, J, h, &s, &Ji, &hi);
@@ -686,43 +843,16 @@ int pt_create_ex(int L, const double* betas, int R, double J, double h, uint64_t
   p->seed = seed;
   p->swap_rule = swap_rule_opt;
   p->dev_info = dev;
-  p->stream = 0;
+  p->stream = stream;
 
-  // thresholds by temperature, class c = 2 k + (sigma == +1)
-  std::vector<uint64_t> T_temp((size_t)R * kClasses);
-  for (int k = 0; k < R; ++k)
-    for (int kk = 0; kk <= 4; ++kk)
-      for (int up = 0; up <= 1; ++up) {
-        const int64_t sigma = up ? 1 : -1;
-        const int64_t nb = 4 - 2 * kk;  // sigma * sum of neighbour spins
-        const int64_t dE = 2 * (Ji * nb - hi * sigma);
-        T_temp[(size_t)k * kClasses + 2 * kk + up] = spin_threshold(betas[k], dE, s);
-      }
-  if (p->mode == kModeFerro)
-    for (int k = 0; k < R; ++k)
-      if (T_temp[(size_t)k * kClasses + 1] > T_temp[(size_t)k * kClasses + 3])
-        return fail(PT_EINTERNAL, "threshold order violated at temperature %d", k);
-
-  // exchange tables
-  const int npairs = std::max(R - 1, 1);
-  std::vector<std::shared_ptr<const PairTable>> tabs;
-  std::vector<SwapPair> pairs((size_t)npairs);
-  size_t entries = 0;
-  const int shift = table_shift(Ji, hi);
-  rc = get_ladder_tables(betas, R, s, swap_rule_opt, energy_reach(L, Ji, hi), shift, &tabs);
+  // thresholds, maps, zeroed buffers, pair descriptors and exchange tables: one image
+  std::shared_ptr<const Image> img;
+  rc = get_image(L, betas, R, s, Ji, hi, swap_rule_opt, p->mode, &img);
   if (rc) return rc;
-  for (int k = 0; k + 1 < R; ++k) {
-    const std::shared_ptr<const PairTable>& t = tabs[(size_t)k];
-    pairs[k].n_lo = t->n_lo;
-    pairs[k].n_hi = t->n_hi;
-    pairs[k].S_below = t->S_below;
-    pairs[k].S_above = t->S_above;
-    pairs[k].offset = (int64_t)entries;
-    entries += t->vals.size();
-  }
 
   // device memory: one allocation
-  const Layout lay = make_layout(L, R, p->W, p->mode, entries);
+  const Layout lay = make_layout(L, R, p->W, p->mode, img->entries);
+  if (lay.total - lay.T_temp != img->bytes) return fail(PT_EINTERNAL, "creation image size");
   Allocator used;
   void* mem = dev_alloc(lay.total, p->stream, &used);
   if (!mem) return fail(PT_ENOMEM, "device allocation of %zu bytes failed", lay.total);
@@ -739,7 +869,7 @@ int pt_create_ex(int L, const double* betas, int R, double J, double h, uint64_t
   d.mode = p->mode;
   d.key0 = (uint32_t)seed;
   d.key1 = (uint32_t)(seed >> 32);
-  d.table_shift = shift;
+  d.table_shift = table_shift(Ji, hi);
   d.J_int = Ji;
   d.h_int = hi;
   d.s = s;
@@ -756,31 +886,21 @@ int pt_create_ex(int L, const double* betas, int R, double J, double h, uint64_t
   d.swap_table = (const uint32_t*)(base + lay.table);
   d.status = (int32_t*)(base + lay.status);
 
-  // one staging image of everything from T_temp to the end, copied in one transfer
-  const size_t img_off = lay.T_temp, img_len = lay.total - lay.T_temp;
-  std::vector<uint8_t> img(img_len, 0);
-  auto put = [&](size_t off, const void* src, size_t bytes) {
-    memcpy(img.data() + (off - img_off), src, bytes);
-  };
-  put(lay.T_temp, T_temp.data(), T_temp.size() * 8);
-  std::vector<int32_t> ident(R);
-  for (int r = 0; r < R; ++r) ident[r] = r;
-  put(lay.temp_of_slot, ident.data(), R * 4);
-  put(lay.slot_of_temp, ident.data(), R * 4);
-  put(lay.pairs, pairs.data(), pairs.size() * sizeof(SwapPair));
-  for (int k = 0; k + 1 < R; ++k)
-    if (!tabs[k]->vals.empty())
-      put(lay.table + (size_t)pairs[k].offset * 4, tabs[k]->vals.data(), tabs[k]->vals.size() * 4);
-  cudaError_t err = cudaMemcpyAsync(base + img_off, img.data(), img_len, cudaMemcpyHostToDevice,
-                                    p->stream);
+  // one copy of the image (asynchronous from page-locked memory; from pageable memory the
+  // call returns once the bytes are staged), the initial spins and the plane thresholds
+  cudaError_t err = cudaMemcpyAsync(base + lay.T_temp, img->data(), img->bytes,
+                                    cudaMemcpyHostToDevice, p->stream);
   if (err == cudaSuccess) err = launch_init(d, dev, p->stream);
   if (err == cudaSuccess) err = launch_exchange(d, 0, kStepRebuild, p->stream);
-  if (err == cudaSuccess) err = cudaStreamSynchronize(p->stream);
+  if (err == cudaSuccess && !stream) err = cudaStreamSynchronize(p->stream);
   if (err != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamSynchronize(p->stream);
     cudaGetLastError();
     dev_free(mem, p->stream, used);
     return fail(PT_ECUDA, "initialising problem: %s", cudaGetErrorString(err));
   }
+  if (img->locked) p->image = img;
   *out = p.release();
   return PT_OK;
 }
@@ -1244,7 +1364,7 @@ int pt_load(const void* buf, size_t bytes, pt_problem** out) {
       if (v & unused) return fail(PT_EINVAL, "checkpoint sets bits of unused slots");
     }
   }
-  pt_options opt;
+  pt_options opt{};
   opt.size = sizeof opt;
   opt.swap_rule = rule;
   pt_problem* p = nullptr;

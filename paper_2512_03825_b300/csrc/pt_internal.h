@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <vector>
 
 #include "pt.h"
@@ -37,6 +38,9 @@ struct pt_problem {
   size_t trace_bytes = 0;
   pt_free_fn trace_free = nullptr;
   void* trace_ctx = nullptr;
+  // the page-locked creation image the first copy was queued from: kept until destroy, when
+  // the stream has been synchronised (null when the image was not page-locked)
+  std::shared_ptr<const void> image;
 };
 
 namespace ptb {
