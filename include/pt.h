@@ -294,9 +294,11 @@ int pt_counters(pt_problem* p, uint64_t* sweeps_done, uint64_t* exchanges_done);
  * pt_chain_map), attempted[j] and accepted[j] (R_j - 1 values, as pt_swap_stats; nothing for
  * R_j = 1). Any of the five pointer arrays may be NULL, and so may any entry of one; the
  * caller owns every array. The problems must share a stream and a device (as in
- * pt_sweep_batch). Recomputes the energies from the current spins like the single getters,
- * packs every problem's record with one kernel into a stream-ordered scratch buffer and
- * copies it back once: one synchronisation instead of several per problem and getter. A
+ * pt_sweep_batch). Recomputes the energies from the current spins like the single getters
+ * (one count launch over the words of every problem), packs every problem's record with one
+ * kernel into a stream-ordered scratch buffer and copies it back once: one synchronisation
+ * instead of several per problem and getter. A problem listed more than once is read once
+ * and its record given to each of its entries. A
  * problem whose device work reported a status (PT_ETIMEOUT, ...) is poisoned as by
  * pt_synchronize and its arrays are left untouched; the call returns the first such error
  * after filling the others. PT_EINVAL for count < 0, a NULL or repeated-on-another-stream

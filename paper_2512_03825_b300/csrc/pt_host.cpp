@@ -1166,34 +1166,64 @@ int pt_read_batch(pt_problem* const* ps, int count, int64_t* const* E_int, int64
   }
   int rc = problem_device_guard(ps[0]);
   if (rc) return rc;
-  // energies from the current spins (as the single getters), then one gather, one copy
-  std::vector<GatherItem> items((size_t)count);
+  // energies from the current spins (as the single getters): one count launch over every
+  // problem's words and one gather that finishes the energies and packs the records, then
+  // one copy. A problem listed more than once is read once (its counts are shared).
+  std::vector<GatherItem> items;
+  std::vector<EnergyChunk> chunks;
+  std::vector<int64_t> rec_of((size_t)count);
+  std::map<const pt_problem*, int64_t> seen;
   int64_t words = 0;
   for (int j = 0; j < count; ++j) {
     pt_problem* p = ps[j];
-    if ((rc = refresh_observables(p))) return rc;
-    GatherItem& it = items[(size_t)j];
-    it.E_slot = p->dev.E_slot;
-    it.M_slot = p->dev.M_slot;
-    it.slot_of_temp = p->dev.slot_of_temp;
-    it.attempted = p->dev.attempted;
-    it.accepted = p->dev.accepted;
-    it.status = p->dev.status;
+    auto dup = seen.find(p);
+    if (dup != seen.end()) {
+      rec_of[(size_t)j] = dup->second;
+      continue;
+    }
+    seen.emplace(p, words);
+    rec_of[(size_t)j] = words;
+    const DevProblem& d = p->dev;
+    items.emplace_back();
+    GatherItem& it = items.back();
+    it.E_slot = d.E_slot;
+    it.M_slot = d.M_slot;
+    it.slot_of_temp = d.slot_of_temp;
+    it.attempted = d.attempted;
+    it.accepted = d.accepted;
+    it.status = d.status;
+    it.cnt = d.cnt;
+    it.J_int = d.J_int;
+    it.h_int = d.h_int;
+    it.L = d.L;
+    it.W = d.W;
     it.R = p->R;
     it.npairs = p->R >= 2 ? p->R - 1 : 0;
     it.out = words;
     words += 1 + 3 * (int64_t)it.R + 2 * (int64_t)it.npairs;
+    const int nwords = d.L * (d.L >> 1);
+    for (int w = 0; w < d.W; ++w)
+      for (int first = 0; first < nwords; first += kEnergyChunkWords)
+        chunks.push_back(EnergyChunk{d.spins, d.cnt, d.L, d.W, w, first,
+                                     std::min(kEnergyChunkWords, nwords - first)});
   }
-  const size_t ib = ((size_t)count * sizeof(GatherItem) + 255) & ~size_t(255);
+  if (chunks.size() > (size_t)INT32_MAX) return fail(PT_EINVAL, "batched read too large");
+  const int nitems = (int)items.size();
+  const size_t ib = ((size_t)nitems * sizeof(GatherItem) + 255) & ~size_t(255);
+  const size_t cb = (chunks.size() * sizeof(EnergyChunk) + 255) & ~size_t(255);
+  std::vector<uint8_t> staging(ib + cb);
+  memcpy(staging.data(), items.data(), (size_t)nitems * sizeof(GatherItem));
+  memcpy(staging.data() + ib, chunks.data(), chunks.size() * sizeof(EnergyChunk));
   void* scratch = nullptr;
-  cudaError_t err = cudaMallocAsync(&scratch, ib + (size_t)words * 8, st);
+  cudaError_t err = cudaMallocAsync(&scratch, ib + cb + (size_t)words * 8, st);
   if (err != cudaSuccess) return fail(PT_ENOMEM, "read scratch: %s", cudaGetErrorString(err));
   GatherItem* d_items = (GatherItem*)scratch;
-  uint64_t* d_out = (uint64_t*)((char*)scratch + ib);
+  EnergyChunk* d_chunks = (EnergyChunk*)((char*)scratch + ib);
+  uint64_t* d_out = (uint64_t*)((char*)scratch + ib + cb);
   std::vector<uint64_t> host((size_t)words);
-  err = cudaMemcpyAsync(d_items, items.data(), (size_t)count * sizeof(GatherItem),
-                        cudaMemcpyHostToDevice, st);
-  if (err == cudaSuccess) err = launch_gather(d_items, count, d_out, ps[0]->dev_info.sms, st);
+  err = cudaMemcpyAsync(scratch, staging.data(), staging.size(), cudaMemcpyHostToDevice, st);
+  if (err == cudaSuccess) err = launch_energy_batch(d_chunks, (int)chunks.size(), st);
+  if (err == cudaSuccess) err = launch_gather(d_items, nitems, d_out, ps[0]->dev_info.sms, st);
   if (err == cudaSuccess)
     err = cudaMemcpyAsync(host.data(), d_out, (size_t)words * 8, cudaMemcpyDeviceToHost, st);
   const cudaError_t err2 = cudaFreeAsync(scratch, st);
@@ -1206,8 +1236,8 @@ int pt_read_batch(pt_problem* const* ps, int count, int64_t* const* E_int, int64
   int first_rc = PT_OK;
   for (int j = 0; j < count; ++j) {
     pt_problem* p = ps[j];
-    const uint64_t* rec = host.data() + items[(size_t)j].out;
-    const int R = p->R, P = items[(size_t)j].npairs;
+    const uint64_t* rec = host.data() + rec_of[(size_t)j];
+    const int R = p->R, P = R >= 2 ? R - 1 : 0;
     const int32_t status = (int32_t)(int64_t)rec[0];
     if (status != 0) {
       p->poisoned = status == PT_ETIMEOUT ? PT_ETIMEOUT : PT_EINTERNAL;

@@ -147,20 +147,19 @@ __global__ void __launch_bounds__(kThreads) k_half_sweep(DevProblem p, int colou
 // ---------------------------------------------------------------------------------------
 constexpr int kMaxWordsPerThread = 4000;  // 4 * 4000 < 2^14 (per-thread counter depth)
 
-__global__ void __launch_bounds__(kThreads) k_energy(DevProblem p) {
-  const int w = blockIdx.y;
-  const int L = p.L, half = L >> 1;
-  const uint32_t* c0 = p.spins + word_index(L, w, 0, 0, 0);
-  const uint32_t* c1 = p.spins + word_index(L, w, 1, 0, 0);
-  const int nwords = L * half;
-  const int start = blockIdx.x * blockDim.x + threadIdx.x;
-  const int stride = gridDim.x * blockDim.x;
+// The counts of colour-0 words start, start + stride, ... below end of plane w, added to
+// cnt (one call per block).
+__device__ __forceinline__ void energy_count(const uint32_t* spins, uint32_t* cnt, int L, int W,
+                                             int w, int start, int stride, int end) {
+  const int half = L >> 1;
+  const uint32_t* c0 = spins + word_index(L, w, 0, 0, 0);
+  const uint32_t* c1 = spins + word_index(L, w, 1, 0, 0);
   BitCounter<20, 14> U, N;
   U.zero();
   N.zero();
-  if (start < nwords) {
+  if (start < end) {
     RowWalker rw(start, stride, half);
-    for (int idx = start; idx < nwords; idx += stride, rw.step()) {
+    for (int idx = start; idx < end; idx += stride, rw.step()) {
       const int y = rw.y, i = rw.i;
       const int par = y & 1;
       const int ym = (y == 0) ? L - 1 : y - 1;
@@ -184,10 +183,21 @@ __global__ void __launch_bounds__(kThreads) k_energy(DevProblem p) {
   atomicAdd(&acc[1][lane], n);
   __syncthreads();
   if (threadIdx.x < 32) {
-    if (acc[0][threadIdx.x]) atomicAdd(&p.cnt[w * 32 + threadIdx.x], acc[0][threadIdx.x]);
-    if (acc[1][threadIdx.x])
-      atomicAdd(&p.cnt[p.W * 32 + w * 32 + threadIdx.x], acc[1][threadIdx.x]);
+    if (acc[0][threadIdx.x]) atomicAdd(&cnt[w * 32 + threadIdx.x], acc[0][threadIdx.x]);
+    if (acc[1][threadIdx.x]) atomicAdd(&cnt[W * 32 + w * 32 + threadIdx.x], acc[1][threadIdx.x]);
   }
+}
+
+__global__ void __launch_bounds__(kThreads) k_energy(DevProblem p) {
+  energy_count(p.spins, p.cnt, p.L, p.W, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x,
+               gridDim.x * blockDim.x, p.L * (p.L >> 1));
+}
+
+// One chunk per block: kEnergyChunkWords / kThreads = 8 words per thread.
+__global__ void __launch_bounds__(kThreads) k_energy_batch(const EnergyChunk* __restrict__ chunks) {
+  const EnergyChunk c = chunks[blockIdx.x];
+  energy_count(c.spins, c.cnt, c.L, c.W, c.w, c.first + (int)threadIdx.x, blockDim.x,
+               c.first + c.count);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -308,6 +318,18 @@ __global__ void __launch_bounds__(kThreads) k_gather(const GatherItem* __restric
     uint64_t* const o = out + it.out;
     const int R = it.R, P = it.npairs;
     const int total = 1 + 3 * R + 2 * P;
+    // the energy step: E_int and M per slot from the counts, then the counts cleared
+    const int64_t L2 = (int64_t)it.L * it.L;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+      const int64_t U = it.cnt[r];
+      const int64_t ones = it.cnt[it.W * 32 + r];
+      const int64_t bonds = 2 * L2 - 2 * U;  // sum over bonds of sigma_i sigma_j
+      const int64_t M = 2 * ones - L2;
+      it.E_slot[r] = -it.J_int * bonds + it.h_int * M;
+      it.M_slot[r] = M;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 2 * it.W * 32; q += blockDim.x) it.cnt[q] = 0;
     for (int q = threadIdx.x; q < total; q += blockDim.x) {
       uint64_t v;
       if (q == 0)
@@ -324,6 +346,7 @@ __global__ void __launch_bounds__(kThreads) k_gather(const GatherItem* __restric
         v = it.accepted[q - 1 - 3 * R - P];
       o[q] = v;
     }
+    __syncthreads();  // the next record's energy step reuses the block
   }
 }
 
@@ -333,6 +356,12 @@ cudaError_t launch_gather(const GatherItem* items, int n, uint64_t* out, int sms
                           cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_gather<<<n < 8 * sms ? n : 8 * sms, kThreads, 0, st>>>(items, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_batch(const EnergyChunk* chunks, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_energy_batch<<<n, kThreads, 0, st>>>(chunks);
   return cudaGetLastError();
 }
 

@@ -30,17 +30,35 @@ cudaError_t launch_exchange(const DevProblem& p, uint64_t e, int flags, cudaStre
 
 // One problem's part of a batched read (pt_read_batch): its record of 1 + 3 R + 2 npairs
 // 8-byte words starts `out` words into the packed buffer.
+// One problem's record for k_gather. The gather first finishes the energy count as the
+// energy exchange step does: E_slot / M_slot from the counts in cnt ([2][W * 32]), which
+// it then clears.
 struct GatherItem {
-  const int64_t* E_slot;
-  const int64_t* M_slot;
+  int64_t* E_slot;
+  int64_t* M_slot;
   const int32_t* slot_of_temp;
   const uint64_t* attempted;
   const uint64_t* accepted;
   const int32_t* status;
+  uint32_t* cnt;
+  int64_t J_int, h_int;
+  int L, W;
   int R, npairs;  // npairs = R - 1 (0 for R = 1)
   int64_t out;
 };
 cudaError_t launch_gather(const GatherItem* items, int n, uint64_t* out, int sms,
                           cudaStream_t st);
+
+// A run of colour-0 words of one plane of one problem for the batched energy count:
+// words [first, first + count) of plane w, at most kEnergyChunkWords.
+struct EnergyChunk {
+  const uint32_t* spins;
+  uint32_t* cnt;
+  int L, W, w, first, count;
+};
+constexpr int kEnergyChunkWords = 2048;
+// Counts unsatisfied bonds and up spins of every chunk into its problem's cnt (one block
+// per chunk; the counts must start at zero).
+cudaError_t launch_energy_batch(const EnergyChunk* chunks, int n, cudaStream_t st);
 
 }  // namespace ptb

@@ -223,8 +223,11 @@ def test_read_batch_equals_single_getters(api):
     probs = mixed_problems(n=12, seed=17) + [W.Problem(L=8, betas=(0.4,), seed=5)]
     gs = [api.PTProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed) for p in probs]
     api.sweep_batch(gs, [max(p.sweeps, 1) for p in probs], [p.every for p in probs])
-    got = api.read_batch(gs)
-    for j, (g, r) in enumerate(zip(gs, got)):
+    api.sweep_batch(gs, 3, 2)  # ends between swap iterations: the counts are recomputed
+    listed = gs + [gs[3], gs[0], gs[3]]  # a problem listed again is read once
+    got = api.read_batch(listed)
+    assert len(got) == len(listed)
+    for j, (g, r) in enumerate(zip(listed, got)):
         np.testing.assert_array_equal(r["E_int"], g.energies_int(), err_msg=str(j))
         np.testing.assert_array_equal(r["M"], g.magnetisations(), err_msg=str(j))
         np.testing.assert_array_equal(r["chain_map"], g.chain_map(), err_msg=str(j))
