@@ -363,6 +363,17 @@ size_t pt_device_bytes(const pt_problem* p);
  * for admission against a memory budget before creating. */
 size_t pt_estimate_device_bytes(int L, const double* betas, int R, double J, double h);
 
+/* Page-locked host memory that the creation-image cache may hold (default 1 GiB). A
+ * creation copies its problem's thresholds and tables from an image; images of at most
+ * min(64 MiB, limit) bytes are built once into page-locked memory and kept, larger ones are
+ * built per creation in pageable memory (0: every image). When the cache would exceed the
+ * limit it is emptied; an image that a live problem was created from stays allocated until
+ * that problem is destroyed. Always PT_OK. */
+int pt_set_image_cache_limit(size_t bytes);
+
+/* Page-locked bytes the creation-image cache holds now. */
+size_t pt_image_cache_bytes(void);
+
 /* Route device allocations of later pt_create calls through alloc/free (e.g. the PyTorch
  * caching allocator). alloc(bytes, stream, ctx) returns a device pointer aligned to 256
  * bytes or NULL; free(ptr, stream, ctx) releases it. Pass NULLs to restore cudaMalloc. */

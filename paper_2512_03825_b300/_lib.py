@@ -92,6 +92,8 @@ SIGNATURES = [
     ("pt_device_bytes", C.c_size_t, [P]),
     ("pt_estimate_device_bytes", C.c_size_t, [C.c_int, C.POINTER(C.c_double), C.c_int,
                                               C.c_double, C.c_double]),
+    ("pt_set_image_cache_limit", C.c_int, [C.c_size_t]),
+    ("pt_image_cache_bytes", C.c_size_t, []),
     ("pt_set_allocator", C.c_int, [ALLOC_FN, FREE_FN, P]),
     ("pt_strerror", C.c_char_p, [C.c_int]),
     ("pt_last_error", C.c_char_p, []),

@@ -274,6 +274,16 @@ def estimate_device_bytes(L, betas, J=1.0, h=0.0):
                                             float(J), float(h)))
 
 
+def set_image_cache_limit(nbytes: int) -> None:
+    """Page-locked host bytes the creation-image cache may hold (default 1 GiB)."""
+    check(lib.pt_set_image_cache_limit(int(nbytes)), "pt_set_image_cache_limit")
+
+
+def image_cache_bytes() -> int:
+    """Page-locked host bytes the creation-image cache holds now."""
+    return int(lib.pt_image_cache_bytes())
+
+
 def quantise(J, h):
     s, ji, hi = C.c_int64(), C.c_int64(), C.c_int64()
     check(lib.pt_quantise(float(J), float(h), C.byref(s), C.byref(ji), C.byref(hi)),

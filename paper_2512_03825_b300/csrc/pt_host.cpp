@@ -435,7 +435,8 @@ int mode_for(int64_t J_int, int64_t h_int) {
 // swap rule and the lattice reach where it shapes a table; the seed only drives the initial
 // spins, which are drawn on the device. Its offsets from the thresholds do not depend on L.
 // Images up to kImageMaxBytes are built once into page-locked host memory and kept (up to
-// kImageCacheBytes in all), so a creation queues one asynchronous copy and does no table
+// g_image_limit in all, pt_set_image_cache_limit), so a creation queues one asynchronous
+// copy and does no table
 // work on the host. Larger ones (long ladders on large lattices) are built per creation in
 // pageable memory. A problem holds its page-locked image until pt_destroy has synchronised
 // its stream, so dropping images from the cache never frees one that a copy still reads.
@@ -468,11 +469,13 @@ std::mutex g_image_mu;
 std::map<ImageKey, std::shared_ptr<const Image>> g_images;
 size_t g_image_bytes = 0;
 constexpr size_t kImageMaxBytes = size_t(64) << 20;
-constexpr size_t kImageCacheBytes = size_t(1) << 30;
+size_t g_image_limit = size_t(1) << 30;
 
 // Builds the image of a problem with this ladder and layout parameters.
+// The bytes go to page-locked memory when they are at most lock_max.
 int build_image(int L, const double* betas, int R, int64_t s, int64_t Ji, int64_t hi, int rule,
-                int64_t reach, int shift, int mode, bool lock, std::shared_ptr<Image>* out) {
+                int64_t reach, int shift, int mode, size_t lock_max,
+                std::shared_ptr<Image>* out) {
   // thresholds by temperature, class c = 2 k + (sigma == +1)
   std::vector<uint64_t> T_temp((size_t)R * kClasses);
   for (int k = 0; k < R; ++k)
@@ -511,7 +514,7 @@ int build_image(int L, const double* betas, int R, int64_t s, int64_t Ji, int64_
   img->bytes = lay.total - lay.T_temp;
   img->entries = entries;
   uint8_t* dst = nullptr;
-  if (lock && img->bytes <= kImageMaxBytes &&
+  if (img->bytes <= lock_max &&
       cudaHostAlloc((void**)&img->locked, img->bytes, cudaHostAllocPortable) == cudaSuccess) {
     dst = img->locked;
     memset(dst, 0, img->bytes);
@@ -561,13 +564,18 @@ int get_image(int L, const double* betas, int R, int64_t s, int64_t Ji, int64_t 
       return PT_OK;
     }
   }
+  size_t lock_max;
+  {
+    std::lock_guard<std::mutex> lk(g_image_mu);
+    lock_max = std::min(kImageMaxBytes, g_image_limit);
+  }
   std::shared_ptr<Image> img;
   const int rc = build_image(L, betas, R, s, Ji, hi, rule, reach, table_shift(Ji, hi), mode,
-                             true, &img);
+                             lock_max, &img);
   if (rc) return rc;
   if (img->locked) {
     std::lock_guard<std::mutex> lk(g_image_mu);
-    if (g_image_bytes + img->bytes > kImageCacheBytes) {
+    if (g_image_bytes + img->bytes > g_image_limit) {
       g_images.clear();  // images still held by problems stay alive until their destroy
       g_image_bytes = 0;
     }
@@ -799,6 +807,21 @@ size_t pt_estimate_device_bytes(int L, const double* betas, int R, double J, dou
   for (const auto& t : tabs) entries += t->vals.size();
   const int W = (R + 31) / 32;
   return make_layout(L, R, W, mode_for(Ji, hi), entries).total;
+}
+
+int pt_set_image_cache_limit(size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_image_mu);
+  g_image_limit = bytes;
+  if (g_image_bytes > g_image_limit) {
+    g_images.clear();  // images still held by problems stay alive until their destroy
+    g_image_bytes = 0;
+  }
+  return PT_OK;
+}
+
+size_t pt_image_cache_bytes(void) {
+  std::lock_guard<std::mutex> lk(g_image_mu);
+  return g_image_bytes;
 }
 
 int pt_create(int L, const double* betas, int R, double J, double h, uint64_t seed,

@@ -227,3 +227,11 @@ def test_exchange_tables_limited_to_reachable_energies(pt):
     # would take 1.2 GiB; only multiples of 4 occur, and only those are kept)
     paper = api.estimate_device_bytes(300, [1.0 / (1.0 + 3.0 * i / 1500) for i in range(1500)])
     assert 2 ** 28 < paper < 2 ** 30
+
+
+def test_image_cache_limit_without_a_device(pt):
+    """The cache limit is a host setting: it can be set and read with no GPU, and nothing
+    is cached when no problem could be created."""
+    assert pt.lib.pt_set_image_cache_limit(1 << 20) == 0
+    assert pt.lib.pt_image_cache_bytes() == 0
+    assert pt.lib.pt_set_image_cache_limit(1 << 30) == 0

@@ -100,3 +100,41 @@ def test_large_image_takes_the_pageable_copy(api):
         np.testing.assert_array_equal(a.spins(k), b.spins(k))
     a.close()
     b.close()
+
+
+def test_small_cache_limit_evicts_without_freeing_live_images(api):
+    """A 96 KiB cache limit: the images (5-25 KiB) are page-locked and the cache is emptied
+    again and again while the problems created from them are alive and still running. With
+    a limit of 0 every image goes through pageable memory. Every problem matches the
+    oracle."""
+    import torch
+    st = torch.cuda.Stream()
+    limit = 96 << 10
+    api.set_image_cache_limit(limit)
+    try:
+        probs = [W.Problem(L=8 + 2 * (k % 3), betas=W.linear_ladder(0.2 + 0.01 * k, 0.6, 6 + 3 * k),
+                           seed=50 + k) for k in range(10)]
+        gs = []
+        for p in probs:
+            gs.append(api.PTProblem(p.L, p.betas, seed=p.seed, stream=st))
+            gs[-1].sweep(3, 1)
+            assert api.image_cache_bytes() <= limit
+        api.sweep_batch(gs, 4, 2)
+        for j, (p, g) in enumerate(zip(probs, gs)):
+            o = oracle.OracleProblem(p.L, p.betas, seed=p.seed)
+            o.sweep(3, 1)
+            o.sweep(4, 2)
+            assert_same(g, o, "problem %d" % j)
+        for g in gs:
+            g.close()
+        api.set_image_cache_limit(0)
+        assert api.image_cache_bytes() == 0
+        g = api.PTProblem(probs[0].L, probs[0].betas, seed=probs[0].seed, stream=st)
+        assert api.image_cache_bytes() == 0
+        o = oracle.OracleProblem(probs[0].L, probs[0].betas, seed=probs[0].seed)
+        g.sweep(5, 1)
+        o.sweep(5, 1)
+        assert_same(g, o, "no cache")
+        g.close()
+    finally:
+        api.set_image_cache_limit(1 << 30)
