@@ -178,33 +178,55 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
     const uint32_t alw0 = pl->alw0, alw1 = pl->alw1, used = pl->used;
     BitCounter<13, 8> Uf;
     if (COUNT) Uf.zero();
-    for (int q = q_start; q < tl.q1; q += 32) {
-      const int par = (y + colour) & 1;
-      const int ym = (y == 0) ? L - 1 : y - 1;
-      const int yp = (y == L - 1) ? 0 : y + 1;
-      const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
-      const uint32_t s = own[q];  // written by this lane only
-      const uint32_t n0 = ld_nb<NB_L2>(oth + ym * half + i);
-      const uint32_t n1 = ld_nb<NB_L2>(oth + yp * half + i);
-      const uint32_t n2 = ld_nb<NB_L2>(oth + q);
-      const uint32_t n3 = ld_nb<NB_L2>(oth + y * half + ih);
-      const uint32_t site = (uint32_t)(y * L + 2 * i + par);
-      const SiteTerms st = site_terms(site, c3, rk);
-      const uint32_t ns = update_word_ferro_smem(
-          s, n0, n1, n2, n3, nblk, thr, alw0, alw1, used,
-          [&](int jb) { return philox_site_block(st, bt, jb, rk); });
-      own[q] = ns;
-      if (COUNT && count) {
-        // with h = 0 the exchange needs only the bonds: U of the new state, all four bonds
-        // of this colour-1 site (the colour-0 neighbours are final for this sweep)
-        const NbCount k = count4(ns ^ n0, ns ^ n1, ns ^ n2, ns ^ n3);
-        Uf.add3(k.b0, k.b1, k.b2);
+    // one loop per block count: the count-free kernel gets the word update with NB blocks
+    // fixed at compile time (measured: 131.5 -> 122.9 us per batched-256 sweep without
+    // swaps); the counting kernel keeps the count at run time (NB = 0), because with it
+    // fixed the extra live registers of the count made it slower
+    const auto word_loop = [&](auto nbc) {
+      constexpr int NB = decltype(nbc)::value;
+      for (int q = q_start; q < tl.q1; q += 32) {
+        const int par = (y + colour) & 1;
+        const int ym = (y == 0) ? L - 1 : y - 1;
+        const int yp = (y == L - 1) ? 0 : y + 1;
+        const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
+        const uint32_t s = own[q];  // written by this lane only
+        const uint32_t n0 = ld_nb<NB_L2>(oth + ym * half + i);
+        const uint32_t n1 = ld_nb<NB_L2>(oth + yp * half + i);
+        const uint32_t n2 = ld_nb<NB_L2>(oth + q);
+        const uint32_t n3 = ld_nb<NB_L2>(oth + y * half + ih);
+        const uint32_t site = (uint32_t)(y * L + 2 * i + par);
+        const SiteTerms st = site_terms(site, c3, rk);
+        const auto draw = [&](int jb) { return philox_site_block(st, bt, jb, rk); };
+        const uint32_t ns =
+            NB == 0 ? update_word_ferro_smem(s, n0, n1, n2, n3, nblk, thr, alw0, alw1, used, draw)
+                    : update_word_ferro_smem_nb<NB>(s, n0, n1, n2, n3, thr, alw0, alw1, used, draw);
+        own[q] = ns;
+        if (COUNT && count) {
+          // with h = 0 the exchange needs only the bonds: U of the new state, all four bonds
+          // of this colour-1 site (the colour-0 neighbours are final for this sweep)
+          const NbCount k = count4(ns ^ n0, ns ^ n1, ns ^ n2, ns ^ n3);
+          Uf.add3(k.b0, k.b1, k.b2);
+        }
+        i += di;
+        y += dy;
+        if (i >= half) {
+          i -= half;
+          y += 1;
+        }
       }
-      i += di;
-      y += dy;
-      if (i >= half) {
-        i -= half;
-        y += 1;
+    };
+    if (COUNT) {
+      word_loop(BlockCount<0>{});  // the block count at run time
+    } else {
+      switch (nblk) {
+      case 1: word_loop(BlockCount<1>{}); break;
+      case 2: word_loop(BlockCount<2>{}); break;
+      case 3: word_loop(BlockCount<3>{}); break;
+      case 4: word_loop(BlockCount<4>{}); break;
+      case 5: word_loop(BlockCount<5>{}); break;
+      case 6: word_loop(BlockCount<6>{}); break;
+      case 7: word_loop(BlockCount<7>{}); break;
+      default: word_loop(BlockCount<8>{}); break;
       }
     }
     if (COUNT && count) {
