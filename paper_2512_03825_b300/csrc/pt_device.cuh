@@ -232,13 +232,14 @@ __device__ __forceinline__ uint32_t update_word_ferro(uint32_t s, uint32_t n0, u
 // update_word_ferro with the thresholds in shared memory, interleaved so that one 16-byte
 // broadcast load serves two slots: thr[m] = {T0[2m], T1[2m], T0[2m+1], T1[2m+1]}.
 // `draw(j)` returns Philox block j of this site (slots 4j .. 4j+3). Same decisions, bit for
-// bit.
-template <class Draw>
+// bit. NBC > 0 fixes the block count at compile time (nblk is then ignored).
+template <int NBC = 0, class Draw>
 __device__ __forceinline__ uint32_t update_word_ferro_smem(uint32_t s, uint32_t n0, uint32_t n1,
-                                                           uint32_t n2, uint32_t n3, int nblk,
+                                                           uint32_t n2, uint32_t n3, int nblk_rt,
                                                            const uint4* thr, uint32_t alw0,
                                                            uint32_t alw1, uint32_t used,
                                                            const Draw& draw) {
+  const int nblk = NBC > 0 ? NBC : nblk_rt;
   const uint32_t a0 = s ^ n0, a1 = s ^ n1, a2 = s ^ n2, a3 = s ^ n3;
   const uint32_t x01 = a0 ^ a1, x23 = a2 ^ a3;
   const uint32_t ge2 = (a0 & a1) | (a2 & a3) | (x01 & x23);
@@ -265,42 +266,13 @@ __device__ __forceinline__ uint32_t update_word_ferro_smem(uint32_t s, uint32_t 
   return s ^ flip;
 }
 
-// update_word_ferro_smem with the number of blocks fixed at compile time: the blocks of a
-// word carry no runtime condition and can be scheduled together.
+// The Philox block count of a word as a type: BlockCount<n> fixes it at compile time, so the
+// blocks of the word carry no runtime condition and can be interleaved; BlockCount<0> leaves
+// it to the nblk argument.
 template <int NB>
 struct BlockCount {
   static constexpr int value = NB;
 };
-
-template <int NB, class Draw>
-__device__ __forceinline__ uint32_t update_word_ferro_smem_nb(uint32_t s, uint32_t n0,
-                                                              uint32_t n1, uint32_t n2,
-                                                              uint32_t n3, const uint4* thr,
-                                                              uint32_t alw0, uint32_t alw1,
-                                                              uint32_t used, const Draw& draw) {
-  const uint32_t a0 = s ^ n0, a1 = s ^ n1, a2 = s ^ n2, a3 = s ^ n3;
-  const uint32_t x01 = a0 ^ a1, x23 = a2 ^ a3;
-  const uint32_t ge2 = (a0 & a1) | (a2 & a3) | (x01 & x23);
-  const uint32_t eq1 = (x01 ^ x23) & ~ge2;
-  uint32_t rej0 = NB >= 8 ? 0u : (0xffffffffu >> (4 * NB));
-  uint32_t rej1 = rej0;
-#pragma unroll
-  for (int j = NB - 1; j >= 0; --j) {
-    const Philox4 r = draw(j);
-    const uint4 lo = thr[2 * j], hi = thr[2 * j + 1];
-    rej0 = shift_in_reject(rej0, r.w, hi.z);
-    rej1 = shift_in_reject(rej1, r.w, hi.w);
-    rej0 = shift_in_reject(rej0, r.z, hi.x);
-    rej1 = shift_in_reject(rej1, r.z, hi.y);
-    rej0 = shift_in_reject(rej0, r.y, lo.z);
-    rej1 = shift_in_reject(rej1, r.y, lo.w);
-    rej0 = shift_in_reject(rej0, r.x, lo.x);
-    rej1 = shift_in_reject(rej1, r.x, lo.y);
-  }
-  const uint32_t acc = ~rej0 | (eq1 & ~rej1);
-  const uint32_t flip = (ge2 | alw0 | (eq1 & alw1) | acc) & used;
-  return s ^ flip;
-}
 
 // Any J, h: class c = 2 k + (sigma == +1) per bit; thresholds from the plane table.
 // `draw(j)` returns Philox block j of this site (slots 4j .. 4j+3).
