@@ -36,11 +36,11 @@ IMUL_WIDE_PER_CLK_SM = 32.0  # 32x32->64 integer products per clock per SM (4 SM
 # DRAM traffic of one k_flat_half launch (colour 0) on the batched-256 workload from the ncu
 # capture summarised in profiles/k_flat_half_batched-256.md (cold caches: one read of the
 # whole state). Valid only for the kernel source it was taken on.
-FLAT_TRAFFIC_BYTES = 25.946112e6 + 0.0
+FLAT_TRAFFIC_BYTES = 25.946368e6 + 0.0
 FLAT_TRAFFIC_SOURCES = ("paper_2512_03825_b300/csrc/pt_device.cuh",
                         "paper_2512_03825_b300/csrc/pt_flat.cuh",
                         "paper_2512_03825_b300/csrc/pt_flat.cu")
-FLAT_TRAFFIC_SOURCE_HASH = "cc25d926b3c167bd"
+FLAT_TRAFFIC_SOURCE_HASH = "ebd52be9ac291b6a"
 
 
 def _flat_traffic():
