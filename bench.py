@@ -68,6 +68,8 @@ def parse_args(argv=None):
                     help="requests in the short serving run of the default line")
     ap.add_argument("--requests", type=int, default=2000,
                     help="requests of --workload serve")
+    ap.add_argument("--sweep-strategy", choices=["auto", "launches", "persistent"],
+                    default="auto", help="plain-path strategy of --workload single")
     ap.add_argument("--quick", action="store_true",
                     help="skip the side measurements (plain path, L1024, e2e, CPU baseline)")
     return ap.parse_args(argv)
@@ -508,6 +510,8 @@ def run_single(args, rank, world, stream, sms):
     from paper_2512_03825_b300 import workloads as W
     p = W.SINGLE["L1024_R64"]
     h = api.PTProblem(p.L, p.betas, seed=p.seed, stream=stream)
+    strategy = {"auto": 0, "launches": 1, "persistent": 2}[args.sweep_strategy]
+    h.set_sweep_tuning(strategy)
     for _ in range(args.warmup):
         h.sweep(p.sweeps // 10, p.every)
     torch.cuda.synchronize()
@@ -523,13 +527,18 @@ def run_single(args, rank, world, stream, sms):
     clk = clocks.stop()
     s = max_over_ranks(a.elapsed_time(b) / 1e3, world)
     per_step = float(p.L * p.L * p.R * p.sweeps)
+    if h.sweep_tuning()[2] > 0:  # persistent: one cooperative launch per call
+        launches = args.steps
+    else:  # two half sweeps per sweep, an energy count and an exchange per swap iteration
+        launches = args.steps * (2 * p.sweeps + 2 * (p.sweeps // p.every if p.every else 0))
     return {"metric": METRIC, "value": per_step * args.steps * world / s, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * s / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": "single L=1024 R=64 betas 0.35-0.50, 1000 sweeps, "
-                                   "exchange every 5, plain path"},
-            "clocks": clk, "gpu_launches": args.steps}  # one cooperative launch per call
+                                   "exchange every 5, plain path",
+                       "sweep_strategy": args.sweep_strategy},
+            "clocks": clk, "gpu_launches": launches}
 
 
 def run_flip(args, rank, world, stream):
