@@ -96,10 +96,23 @@ def test_L128_R32_full_run_batched_and_plain(api):
     np.testing.assert_array_equal(b.chain_map(), p.chain_map())
 
 
-def test_batched_256_full_run(api):
+@pytest.fixture
+def bench_tuning(api):
+    """The batch launch shape bench.py times (the autotuner's cached choice for this GPU),
+    restored to the previous one afterwards."""
+    from paper_2512_03825_b300 import autotune
+    before = autotune.get_tuning()
+    chosen = autotune.apply_cached_or_default("batched")
+    yield chosen
+    autotune.set_tuning(**before)
+
+
+def test_batched_256_full_run(api, bench_tuning):
+    import torch
     probs = W.batched_problems()
     n = probs[0].sweeps
-    gs = [api.PTProblem(p.L, p.betas, seed=p.seed) for p in probs]
+    st = torch.cuda.Stream()  # as bench.py: problems created on a side stream, no host wait
+    gs = [api.PTProblem(p.L, p.betas, seed=p.seed, stream=st) for p in probs]
     api.sweep_batch(gs, n - 1, 1)
     order = sorted(range(len(probs)), key=lambda j: probs[j].L ** 2 * probs[j].R)
     sample = [order[0], order[len(order) // 2], order[-1]]
