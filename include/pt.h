@@ -283,8 +283,14 @@ int pt_get_spins(pt_problem* p, int k, int8_t* out);
  * else PT_EINVAL). */
 int pt_set_spins(pt_problem* p, int k, const int8_t* in);
 
-/* slot_of_temp[R]: the replica slot (chain) currently at each temperature index. */
+/* slot_of_temp[R]: the replica slot (chain) currently at each temperature index (Sec. 3:
+ * a swap exchanges the temperatures of two slots, so this map is the result of every swap
+ * so far). Synchronises the problem's stream. PT_EINVAL for a NULL output. */
 int pt_chain_map(pt_problem* p, int32_t* slot_of_temp);
+
+/* The same map under the name of the exchange step's permutation: identical to
+ * pt_chain_map. */
+int pt_temperature_map(pt_problem* p, int32_t* slot_of_temp);
 
 /* Sweeps and swap iterations done since pt_create (either pointer may be NULL). */
 int pt_counters(pt_problem* p, uint64_t* sweeps_done, uint64_t* exchanges_done);

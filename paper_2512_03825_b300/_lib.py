@@ -80,6 +80,7 @@ SIGNATURES = [
     ("pt_get_spins", C.c_int, [P, C.c_int, C.POINTER(C.c_int8)]),
     ("pt_set_spins", C.c_int, [P, C.c_int, C.POINTER(C.c_int8)]),
     ("pt_chain_map", C.c_int, [P, C.POINTER(C.c_int32)]),
+    ("pt_temperature_map", C.c_int, [P, C.POINTER(C.c_int32)]),
     ("pt_counters", C.c_int, [P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     ("pt_checkpoint_bytes", C.c_size_t, [P]),
     ("pt_save", C.c_int, [P, C.c_void_p, C.c_size_t]),

@@ -1297,6 +1297,10 @@ int pt_chain_map(pt_problem* p, int32_t* slot_of_temp) {
   return pt_synchronize(p);
 }
 
+int pt_temperature_map(pt_problem* p, int32_t* slot_of_temp) {
+  return pt_chain_map(p, slot_of_temp);
+}
+
 int pt_counters(pt_problem* p, uint64_t* sweeps_done, uint64_t* exchanges_done) {
   int rc = problem_check(p);
   if (rc) return rc;

@@ -235,3 +235,16 @@ def test_image_cache_limit_without_a_device(pt):
     assert pt.lib.pt_set_image_cache_limit(1 << 20) == 0
     assert pt.lib.pt_image_cache_bytes() == 0
     assert pt.lib.pt_set_image_cache_limit(1 << 30) == 0
+
+
+def test_getters_reject_a_null_problem(pt):
+    """Every per-problem getter answers PT_EINVAL for a NULL handle, before touching a
+    device."""
+    import ctypes as C
+    out32 = (C.c_int32 * 4)()
+    out64 = (C.c_int64 * 4)()
+    outd = (C.c_double * 4)()
+    assert pt.lib.pt_chain_map(None, out32) == pt.PT_EINVAL
+    assert pt.lib.pt_temperature_map(None, out32) == pt.PT_EINVAL
+    assert pt.lib.pt_energies(None, outd) == pt.PT_EINVAL
+    assert pt.lib.pt_energies_int(None, out64, None, None) == pt.PT_EINVAL

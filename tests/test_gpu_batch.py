@@ -5,6 +5,8 @@ plain sweeps and with each other. The dataflow launch's bounded waits are made t
 once, on purpose, by a wait for tiles that do not exist."""
 from __future__ import annotations
 
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -231,6 +233,10 @@ def test_read_batch_equals_single_getters(api):
         np.testing.assert_array_equal(r["E_int"], g.energies_int(), err_msg=str(j))
         np.testing.assert_array_equal(r["M"], g.magnetisations(), err_msg=str(j))
         np.testing.assert_array_equal(r["chain_map"], g.chain_map(), err_msg=str(j))
+        tm = np.empty(g.R, np.int32)
+        from paper_2512_03825_b300._lib import lib
+        assert lib.pt_temperature_map(g.handle, tm.ctypes.data_as(C.POINTER(C.c_int32))) == 0
+        np.testing.assert_array_equal(tm, r["chain_map"], err_msg=str(j))
         att, acc = g.swap_stats()
         np.testing.assert_array_equal(r["attempted"], att, err_msg=str(j))
         np.testing.assert_array_equal(r["accepted"], acc, err_msg=str(j))
