@@ -27,6 +27,12 @@
 // are resident together by construction and meet at the hardware cluster barrier
 // (barrier.cluster, release on arrival and acquire on the wait, at cluster scope), with no
 // counter in memory and no waiting on one.
+//
+// When each plane has a single CTA (LOCAL: small lattices), no other CTA ever reads that
+// CTA's words: the plane (both colours) is copied into shared memory at the start of the
+// launch, every half sweep reads and writes it there, and it is copied back at the end. The
+// half sweeps then meet at the block barrier alone; only the swap iterations, which need
+// every plane's counts, still meet at the grid barrier.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -134,19 +140,23 @@ __device__ void exchange_local(const DevProblem& p, uint64_t e, const uint32_t* 
 // new colour-1 words' anti-aligned neighbours (every bond has exactly one colour-1 end) and,
 // with `ones` (always in the generic case), the up spins of the colour-1 word and of the
 // colour-0 word one row up (a one-to-one pairing of the colours) are added to U / N.
-template <int MODE, bool COUNT>
-__device__ __forceinline__ void half_pass(const DevProblem& p, int w, int colour, uint64_t t,
-                                          const RoundKeys& rk, const BlockTerms& bt, int q0,
-                                          int step, int y0, int i0, int dy, int di,
-                                          const uint4* thr, uint32_t alw0, uint32_t alw1,
-                                          uint32_t used, const PlaneGeneric& gen, bool ones,
-                                          BitCounter<15, 10>& U, BitCounter<15, 10>& N) {
+// plane: the first word of plane w (colour 0, then colour 1), in global memory or (LOCAL)
+// in this CTA's shared memory.
+template <int MODE, bool COUNT, bool LOCAL>
+__device__ __forceinline__ void half_pass(const DevProblem& p, uint32_t* plane, int w,
+                                          int colour, uint64_t t, const RoundKeys& rk,
+                                          const BlockTerms& bt, int q0, int step, int y0, int i0,
+                                          int dy, int di, const uint4* thr, uint32_t alw0,
+                                          uint32_t alw1, uint32_t used, const PlaneGeneric& gen,
+                                          bool ones, BitCounter<15, 10>& U,
+                                          BitCounter<15, 10>& N) {
   const uint32_t c3 = kTagSpin | ((uint32_t)(t >> 32) << 8);
   const int L = p.L, half = L >> 1;
   const int nwords = L * half;
   const int nblk = (min(32, p.R - 32 * w) + 3) >> 2;
-  uint32_t* own = p.spins + word_index(L, w, colour, 0, 0);
-  const uint32_t* oth = p.spins + word_index(L, w, colour ^ 1, 0, 0);
+  uint32_t* own = plane + (size_t)colour * nwords;
+  const uint32_t* oth = plane + (size_t)(colour ^ 1) * nwords;
+  const auto nb = [&](const uint32_t* q) { return LOCAL ? *q : __ldcg(q); };
   int y = y0, i = i0;
   for (int q = q0; q < nwords; q += step) {
     const int par = (y + colour) & 1;
@@ -154,10 +164,10 @@ __device__ __forceinline__ void half_pass(const DevProblem& p, int w, int colour
     const int yp = (y == L - 1) ? 0 : y + 1;
     const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
     const uint32_t s = own[q];
-    const uint32_t n0 = __ldcg(oth + ym * half + i);
-    const uint32_t n1 = __ldcg(oth + yp * half + i);
-    const uint32_t n2 = __ldcg(oth + q);
-    const uint32_t n3 = __ldcg(oth + y * half + ih);
+    const uint32_t n0 = nb(oth + ym * half + i);
+    const uint32_t n1 = nb(oth + yp * half + i);
+    const uint32_t n2 = nb(oth + q);
+    const uint32_t n3 = nb(oth + y * half + ih);
     const uint32_t site = (uint32_t)(y * L + 2 * i + par);
     const SiteTerms st = site_terms(site, c3, rk);
     const auto draw = [&](int j) { return philox_site_block(st, bt, j, rk); };
@@ -181,10 +191,10 @@ __device__ __forceinline__ void half_pass(const DevProblem& p, int w, int colour
   }
 }
 
-template <int MODE, bool CLUSTER>
+template <int MODE, bool CLUSTER, bool LOCAL>
 __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_constant__ PersistArgs a) {
   // [R] ferro thresholds (k = 0, k = 1) by temperature, then [R] slot_of_temp and [R]
-  // temp_of_slot; persist_smem(R, mode) bytes
+  // temp_of_slot; persist_smem(R, mode) bytes; then (LOCAL) the plane's L * L words
   extern __shared__ __align__(16) int32_t map_s[];
   __shared__ PlaneFerro fer;
   __shared__ uint4 thr[16];  // ferro thresholds, interleaved for 16-byte broadcast loads
@@ -205,6 +215,24 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
   __syncthreads();
 
   const int w = blockIdx.x % W;
+  const int plane_words = p.L * p.L;
+  uint32_t* const plane_g = p.spins + word_index(p.L, w, 0, 0, 0);
+  // after the persist_smem(R, MODE) bytes of thresholds and maps, 16-byte aligned
+  const size_t maps_bytes = (size_t)2 * R * 4 + (MODE == kModeFerro ? (size_t)R * 16 : 0);
+  uint32_t* const plane_s = reinterpret_cast<uint32_t*>(
+      reinterpret_cast<unsigned char*>(map_s) + ((maps_bytes + 15) & ~size_t(15)));
+  uint32_t* const plane = LOCAL ? plane_s : plane_g;
+  if (LOCAL) {
+    for (int q = threadIdx.x; q < plane_words; q += blockDim.x) plane_s[q] = plane_g[q];
+    __syncthreads();
+  }
+  // LOCAL: the plane goes back to global memory at every exit of the kernel
+  const auto flush = [&]() {
+    if (LOCAL) {
+      __syncthreads();
+      for (int q = threadIdx.x; q < plane_words; q += blockDim.x) plane_g[q] = plane_s[q];
+    }
+  };
   const int q0 = (blockIdx.x / W) * kPersistThreads + threadIdx.x;
   const int step = (gridDim.x / W) * kPersistThreads;
   const int half = p.L >> 1;
@@ -243,20 +271,28 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
     target += gridDim.x + extra;
     return grid_barrier(bar, target, p.status, a.limit_ns, &ok_s, a.stall != 0);
   };
+  // between half sweeps: LOCAL planes are read by their own CTA only
+  const auto sync_half = [&](unsigned extra) -> bool {
+    if (LOCAL && extra == 0) {
+      __syncthreads();
+      return true;
+    }
+    return sync_all(extra);
+  };
   for (int j = 0; j < a.n; ++j) {
     const uint64_t t = a.t0 + (uint64_t)j;
     BlockTerms bt;
     block_terms((uint32_t)(8 * w), (uint32_t)t, a.rk, bt);
     BitCounter<15, 10> U, N;
-    half_pass<MODE, false>(p, w, 0, t, a.rk, bt, q0, step, y0, i0, dy, di, thr, alw0, alw1,
-                           used, gen, false, U, N);
-    if (!sync_all(j == 0 ? (unsigned)a.stall : 0u)) return;
+    half_pass<MODE, false, LOCAL>(p, plane, w, 0, t, a.rk, bt, q0, step, y0, i0, dy, di, thr,
+                                  alw0, alw1, used, gen, false, U, N);
+    if (!sync_half(j == 0 ? (unsigned)a.stall : 0u)) return flush();
     const bool ex = a.m > 0 && (t + 1) % (uint64_t)a.m == 0;
     if (!ex && !trace) {
-      half_pass<MODE, false>(p, w, 1, t, a.rk, bt, q0, step, y0, i0, dy, di, thr, alw0, alw1,
-                             used, gen, false, U, N);
+      half_pass<MODE, false, LOCAL>(p, plane, w, 1, t, a.rk, bt, q0, step, y0, i0, dy, di, thr,
+                                    alw0, alw1, used, gen, false, U, N);
       if (j + 1 == a.n) break;  // the kernel's end orders this half sweep before what follows
-      if (!sync_all(0)) return;
+      if (!sync_half(0)) return flush();
       continue;
     }
     // a swap iteration or a trace row follows: count this sweep into buffer `counted & 1`
@@ -264,8 +300,8 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
     uint32_t* const cb = cnt_base + (counted & 1) * 2 * W * 32;
     U.zero();
     N.zero();
-    half_pass<MODE, true>(p, w, 1, t, a.rk, bt, q0, step, y0, i0, dy, di, thr, alw0, alw1,
-                          used, gen, trace, U, N);
+    half_pass<MODE, true, LOCAL>(p, plane, w, 1, t, a.rk, bt, q0, step, y0, i0, dy, di, thr,
+                                 alw0, alw1, used, gen, trace, U, N);
     const uint32_t u = U.warp_total_for_lane();
     const uint32_t nn = (MODE == kModeFerro && !trace) ? 0u : N.warp_total_for_lane();
     if (threadIdx.x < 64) (&acc[0][0])[threadIdx.x] = 0;
@@ -278,7 +314,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
       if (acc[0][threadIdx.x]) atomicAdd(&cb[w * 32 + threadIdx.x], acc[0][threadIdx.x]);
       if (acc[1][threadIdx.x]) atomicAdd(&cb[W * 32 + w * 32 + threadIdx.x], acc[1][threadIdx.x]);
     }
-    if (!sync_all(0)) return;
+    if (!sync_all(0)) return flush();
     if (ex) exchange_local(p, e, cb, sot, tos, blockIdx.x == 0);
     if (blockIdx.x == 0) {
       if (trace) {
@@ -304,6 +340,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
     }
   }
 
+  flush();
   if (exchanged) {
     if (blockIdx.x == 0)
       for (int r = threadIdx.x; r < R; r += blockDim.x) {
@@ -326,12 +363,15 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
   }
 }
 
-const void* persist_fn(int mode, bool cluster = false) {
+const void* persist_fn(int mode, bool cluster = false, bool local = false) {
   if (cluster)
-    return mode == kModeFerro ? (const void*)k_persist<kModeFerro, true>
-                              : (const void*)k_persist<kModeGeneric, true>;
-  return mode == kModeFerro ? (const void*)k_persist<kModeFerro, false>
-                            : (const void*)k_persist<kModeGeneric, false>;
+    return mode == kModeFerro ? (const void*)k_persist<kModeFerro, true, false>
+                              : (const void*)k_persist<kModeGeneric, true, false>;
+  if (local)
+    return mode == kModeFerro ? (const void*)k_persist<kModeFerro, false, true>
+                              : (const void*)k_persist<kModeGeneric, false, true>;
+  return mode == kModeFerro ? (const void*)k_persist<kModeFerro, false, false>
+                            : (const void*)k_persist<kModeGeneric, false, false>;
 }
 
 }  // namespace
@@ -340,11 +380,17 @@ size_t persist_smem(int R, int mode) {
   return (size_t)2 * R * sizeof(int32_t) + (mode == kModeFerro ? (size_t)R * 16 : 0);
 }
 
+size_t persist_launch_smem(int L, int R, int mode, bool local) {
+  const size_t base = persist_smem(R, mode);
+  return local ? ((base + 15) & ~size_t(15)) + (size_t)L * L * sizeof(uint32_t) : base;
+}
+
 cudaError_t persist_plan(const DevProblem& p, const DeviceInfo& dev, int words_per_thread,
                          PersistPlan* plan) {
   plan->grid = 0;
   plan->words_per_thread = 0;
   plan->cluster = false;
+  plan->local = false;
   int per_sm = 0;
   // the maps and (ferro) the thresholds by temperature can pass the default 48 KB per block.
   // The limit belongs to the kernel, not to a problem: it is set to what the largest
@@ -354,6 +400,11 @@ cudaError_t persist_plan(const DevProblem& p, const DeviceInfo& dev, int words_p
     err = cudaFuncSetAttribute(persist_fn(p.mode, c == 1),
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)persist_smem(PT_MAX_R, p.mode));
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(persist_fn(p.mode, false, true),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(((persist_smem(PT_MAX_R, p.mode) + 15) & ~size_t(15)) +
+                                     kPersistMaxLocalBytes));
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(persist_fn(p.mode, true),
                                cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -373,6 +424,18 @@ cudaError_t persist_plan(const DevProblem& p, const DeviceInfo& dev, int words_p
   if (wpt > kPersistMaxWordsPerThread) return cudaSuccess;
   plan->grid = (int)(g * p.W);
   plan->words_per_thread = (int)wpt;
+  if (g == 1 && (int64_t)p.L * p.L * 4 <= kPersistMaxLocalBytes) {
+    // one CTA per plane: its plane in shared memory, if every plane's CTA stays resident
+    int per_sm_local = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm_local, persist_fn(p.mode, false, true), kPersistThreads,
+        persist_launch_smem(p.L, p.R, p.mode, true));
+    if (err != cudaSuccess) return err;
+    if ((int64_t)per_sm_local * dev.sms >= plan->grid) {
+      plan->local = true;
+      return cudaSuccess;
+    }
+  }
   if (plan->grid >= 2 && plan->grid <= kPersistMaxCluster) {
     // one cluster of the whole grid, if the device can place one (a single CTA keeps the
     // cooperative launch, whose barrier is then the block barrier)
@@ -433,8 +496,9 @@ cudaError_t launch_persist(const DevProblem& p, const PersistPlan& plan, uint64_
     cfg.numAttrs = 1;
     return cudaLaunchKernelExC(&cfg, persist_fn(p.mode, true), args);
   }
-  return cudaLaunchCooperativeKernel(persist_fn(p.mode), dim3(plan.grid), dim3(kPersistThreads),
-                                     args, persist_smem(p.R, p.mode), st);
+  return cudaLaunchCooperativeKernel(persist_fn(p.mode, false, plan.local), dim3(plan.grid),
+                                     dim3(kPersistThreads), args,
+                                     persist_launch_smem(p.L, p.R, p.mode, plan.local), st);
 }
 
 }  // namespace ptb
