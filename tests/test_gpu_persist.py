@@ -54,6 +54,11 @@ CASES = [
     (64, 70, 1.0, 0.1, 3, 20, 4),      # three planes, generic, ragged shares
     (130, 40, 0.5, 0.0, 7, 12, 5),     # s = 2, ragged shares
     (128, 32, 1.0, 0.0, 0, 15, 0),     # no exchanges
+    # one CTA per plane, the plane in shared memory: two planes (the swap iterations meet
+    # at the grid barrier), 8 words per thread; and the largest such plane (L = 128: 64 KB)
+    # in the generic mode
+    (64, 40, 1.0, 0.0, 8, 20, 1),
+    (128, 33, 1.0, 0.1, 32, 6, 2),
 ]
 
 
@@ -68,6 +73,8 @@ def test_strategy_matches_oracle(api, strategy, L, R, J, h, wpt, n, m):
     if strategy == PERSISTENT:
         W_planes = (R + 31) // 32
         assert grid > 0 and grid % W_planes == 0
+        if wpt * 256 >= L * L // 2:  # one CTA per plane
+            assert grid == W_planes
     for k in (1, n - 1):                # two calls: the state carries over between launches
         g.sweep(k, m)
         o.sweep(k, m)
