@@ -309,6 +309,51 @@ __device__ __forceinline__ uint32_t update_word_generic_with(uint32_t s, uint32_
   return s ^ flip;
 }
 
+// update_word_generic_with for a problem whose classes with dE > 0 are few (NC of them,
+// cls[0..NC-1]; every other class has dE <= 0, so its threshold is 2^32 and its slots are in
+// the always-masks): each trial is compared with the thresholds of all NC classes (read four
+// slots at a time), and bit-sliced class masks pick the result of the slot's own class,
+// instead of a class extracted and looked up per slot. Same decisions, bit for bit.
+template <int NC, class Draw>
+__device__ __forceinline__ uint32_t update_word_generic_cmp(uint32_t s, uint32_t n0, uint32_t n1,
+                                                            uint32_t n2, uint32_t n3, int nblk,
+                                                            const PlaneGeneric& pl,
+                                                            const int (&cls)[NC],
+                                                            const Draw& draw) {
+  const NbCount k = count4(s ^ n0, s ^ n1, s ^ n2, s ^ n3);
+  const uint32_t z[5] = {~(k.b0 | k.b1 | k.b2), k.b0 & ~k.b1 & ~k.b2, ~k.b0 & k.b1 & ~k.b2,
+                         k.b0 & k.b1, k.b2};
+  uint32_t always = 0;
+#pragma unroll
+  for (int kk = 0; kk < 5; ++kk)
+    always |= z[kk] & ((s & pl.alw[2 * kk + 1]) | (~s & pl.alw[2 * kk]));
+  uint32_t rej[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) rej[c] = nblk >= 8 ? 0u : (0xffffffffu >> (4 * nblk));
+#pragma unroll
+  for (int j = 7; j >= 0; --j) {
+    if (j < nblk) {
+      const Philox4 r = draw(j);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const uint4 t = *reinterpret_cast<const uint4*>(&pl.T[cls[c]][4 * j]);
+        rej[c] = shift_in_reject(rej[c], r.w, t.w);
+        rej[c] = shift_in_reject(rej[c], r.z, t.z);
+        rej[c] = shift_in_reject(rej[c], r.y, t.y);
+        rej[c] = shift_in_reject(rej[c], r.x, t.x);
+      }
+    }
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const uint32_t mine = z[cls[c] >> 1] & ((cls[c] & 1) ? s : ~s);
+    acc |= mine & ~rej[c];
+  }
+  const uint32_t flip = (always | acc) & pl.used;
+  return s ^ flip;
+}
+
 __device__ __forceinline__ uint32_t update_word_generic(uint32_t s, uint32_t n0, uint32_t n1,
                                                         uint32_t n2, uint32_t n3,
                                                         uint32_t site, uint32_t blk0, int nblk,

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kFlatThreads, 2) k_flat_half(const FlatProblem
                                                              const int* __restrict__ first,
                                                              const TileQueue q, int colour,
                                                              int64_t j) {
-  __shared__ PlaneGeneric gen[kFlatThreads / 32];
+  __shared__ __align__(16) PlaneGeneric gen[kFlatThreads / 32];  // 16-byte rows (uint4 reads)
   __shared__ uint4 thr_s[kFlatThreads / 32][16];  // ferro thresholds of each warp's tile
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto run = [&](long long tix) {

@@ -272,27 +272,49 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
     // the generic kernel keeps the block count at run time: with it fixed (one loop per
     // count) a batch with a field ran 17% slower
     const PlaneGeneric& pl = *gen;
-    for (int q = q_start; q < tl.q1; q += 32) {
-      const int par = (y + colour) & 1;
-      const int ym = (y == 0) ? L - 1 : y - 1;
-      const int yp = (y == L - 1) ? 0 : y + 1;
-      const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
-      const uint32_t s = own[q];
-      const uint32_t n0 = ld_nb<NB_L2>(oth + ym * half + i);
-      const uint32_t n1 = ld_nb<NB_L2>(oth + yp * half + i);
-      const uint32_t n2 = ld_nb<NB_L2>(oth + q);
-      const uint32_t n3 = ld_nb<NB_L2>(oth + y * half + ih);
-      const uint32_t site = (uint32_t)(y * L + 2 * i + par);
-      const SiteTerms st = site_terms(site, c3, rk);
-      own[q] = update_word_generic_with(s, n0, n1, n2, n3, nblk, pl, [&](int jb) {
-        return philox_site_block(st, bt, jb, rk);
-      });
-      i += di;
-      y += dy;
-      if (i >= half) {
-        i -= half;
-        y += 1;
+    const auto gen_loop = [&](const auto& update) {
+      for (int q = q_start; q < tl.q1; q += 32) {
+        const int par = (y + colour) & 1;
+        const int ym = (y == 0) ? L - 1 : y - 1;
+        const int yp = (y == L - 1) ? 0 : y + 1;
+        const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
+        const uint32_t s = own[q];
+        const uint32_t n0 = ld_nb<NB_L2>(oth + ym * half + i);
+        const uint32_t n1 = ld_nb<NB_L2>(oth + yp * half + i);
+        const uint32_t n2 = ld_nb<NB_L2>(oth + q);
+        const uint32_t n3 = ld_nb<NB_L2>(oth + y * half + ih);
+        const uint32_t site = (uint32_t)(y * L + 2 * i + par);
+        const SiteTerms st = site_terms(site, c3, rk);
+        own[q] = update(s, n0, n1, n2, n3, [&](int jb) {
+          return philox_site_block(st, bt, jb, rk);
+        });
+        i += di;
+        y += dy;
+        if (i >= half) {
+          i -= half;
+          y += 1;
+        }
       }
+    };
+    // few classes with dE > 0 (five for J > 0, 0 < |h| < 2 J): compare with all of them
+    const uint32_t cm = (uint32_t)p.cmp_classes;
+    if (__popc(cm) == 5) {
+      int cls[5];
+      uint32_t rest = cm;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        cls[c] = __ffs(rest) - 1;
+        rest &= rest - 1;
+      }
+      gen_loop([&](uint32_t s, uint32_t n0, uint32_t n1, uint32_t n2, uint32_t n3,
+                   const auto& draw) {
+        return update_word_generic_cmp<5>(s, n0, n1, n2, n3, nblk, pl, cls, draw);
+      });
+    } else {
+      gen_loop([&](uint32_t s, uint32_t n0, uint32_t n1, uint32_t n2, uint32_t n3,
+                   const auto& draw) {
+        return update_word_generic_with(s, n0, n1, n2, n3, nblk, pl, draw);
+      });
     }
     if (COUNT && count) {
       // second pass over the words this lane just wrote and their colour-0 neighbours

@@ -96,7 +96,7 @@ __device__ __forceinline__ void warp_release_add(unsigned* ctr) {
 
 template <int MODE>
 __global__ void __launch_bounds__(kFlatThreads, 2) k_flow(const __grid_constant__ FlowArgs a) {
-  __shared__ PlaneGeneric gen[kFlatThreads / 32];
+  __shared__ __align__(16) PlaneGeneric gen[kFlatThreads / 32];  // 16-byte rows (uint4 reads)
   __shared__ uint4 thr_s[kFlatThreads / 32][16];  // ferro thresholds of each warp's tile
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;

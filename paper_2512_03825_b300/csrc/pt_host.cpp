@@ -893,6 +893,10 @@ int pt_create_ex(int L, const double* betas, int R, double J, double h, uint64_t
   d.key0 = (uint32_t)seed;
   d.key1 = (uint32_t)(seed >> 32);
   d.table_shift = table_shift(Ji, hi);
+  d.cmp_classes = 0;
+  for (int kk = 0; kk <= 4; ++kk)
+    for (int up = 0; up <= 1; ++up)
+      if (2 * (Ji * (4 - 2 * kk) - hi * (up ? 1 : -1)) > 0) d.cmp_classes |= 1 << (2 * kk + up);
   d.J_int = Ji;
   d.h_int = hi;
   d.s = s;

@@ -39,6 +39,9 @@ struct PlaneGeneric {
   uint32_t used;
   uint32_t pad;
 };
+// Kept a multiple of 16 bytes, so that in a 16-byte aligned array every table row T[c]
+// starts on a 16-byte boundary (rows are read four slots at a time).
+static_assert(sizeof(PlaneGeneric) % 16 == 0, "PlaneGeneric size");
 
 // Exchange threshold of temperature pair (k, k+1) as a function of n = E_int(k) - E_int(k+1):
 // table[offset + ((n - n_lo) >> table_shift)] for n_lo <= n <= n_hi, S_below / S_above
@@ -56,7 +59,7 @@ struct DevProblem {
   int L, R, W, mode;
   uint32_t key0, key1;     // Philox key = seed
   int32_t table_shift;     // log2 of the exchange tables' stride in n (SwapPair)
-  int32_t reserved;
+  int32_t cmp_classes;     // bit c: class c (= 2 k + (sigma == +1)) has dE > 0 (a random draw decides)
   int64_t J_int, h_int, s;
   const uint64_t* T_temp;  // [R][kClasses] thresholds by temperature index, in [0, 2^32]
   void* planes;            // PlaneFerro[W] or PlaneGeneric[W]
