@@ -40,7 +40,7 @@ FLAT_TRAFFIC_BYTES = 25.946368e6 + 0.0
 FLAT_TRAFFIC_SOURCES = ("paper_2512_03825_b300/csrc/pt_device.cuh",
                         "paper_2512_03825_b300/csrc/pt_flat.cuh",
                         "paper_2512_03825_b300/csrc/pt_flat.cu")
-FLAT_TRAFFIC_SOURCE_HASH = "ebd52be9ac291b6a"
+FLAT_TRAFFIC_SOURCE_HASH = "85f0fc28eafd68ea"
 
 
 def _flat_traffic():
