@@ -148,8 +148,8 @@ __device__ __forceinline__ void half_pass(const DevProblem& p, uint32_t* plane, 
                                           const BlockTerms& bt, int q0, int step, int y0, int i0,
                                           int dy, int di, const uint4* thr, uint32_t alw0,
                                           uint32_t alw1, uint32_t used, const PlaneGeneric& gen,
-                                          bool ones, BitCounter<15, 10>& U,
-                                          BitCounter<15, 10>& N) {
+                                          bool five, const int (&cls5)[5], bool ones,
+                                          BitCounter<15, 10>& U, BitCounter<15, 10>& N) {
   const uint32_t c3 = kTagSpin | ((uint32_t)(t >> 32) << 8);
   const int L = p.L, half = L >> 1;
   const int nwords = L * half;
@@ -174,6 +174,8 @@ __device__ __forceinline__ void half_pass(const DevProblem& p, uint32_t* plane, 
     uint32_t ns;
     if (MODE == kModeFerro)
       ns = update_word_ferro_smem(s, n0, n1, n2, n3, nblk, thr, alw0, alw1, used, draw);
+    else if (five)
+      ns = update_word_generic_cmp<5>(s, n0, n1, n2, n3, nblk, gen, cls5, draw);
     else
       ns = update_word_generic_with(s, n0, n1, n2, n3, nblk, gen, draw);
     own[q] = ns;
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
   extern __shared__ __align__(16) int32_t map_s[];
   __shared__ PlaneFerro fer;
   __shared__ uint4 thr[16];  // ferro thresholds, interleaved for 16-byte broadcast loads
-  __shared__ PlaneGeneric gen;
+  __shared__ __align__(16) PlaneGeneric gen;  // rows read four slots at a time
   __shared__ uint32_t acc[2][32];
   __shared__ int ok_s;
   const DevProblem& p = a.p;
@@ -242,6 +244,18 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
   unsigned* const bar = p.cnt + 6 * W * 32;
 
   uint32_t alw0 = 0, alw1 = 0, used = 0;
+  // generic: the classes with dE > 0, when there are exactly five of them (each trial is
+  // then compared with all five; update_word_generic_cmp)
+  const bool five = MODE != kModeFerro && __popc((uint32_t)p.cmp_classes) == 5;
+  int cls5[5] = {0, 0, 0, 0, 0};
+  if (five) {
+    uint32_t rest = (uint32_t)p.cmp_classes;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      cls5[c] = __ffs(rest) - 1;
+      rest &= rest - 1;
+    }
+  }
   auto load_plane = [&]() {
     stage_plane<MODE>(p, tos, w, fer, gen, Tf);
     if (MODE == kModeFerro) {
@@ -285,12 +299,12 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
     block_terms((uint32_t)(8 * w), (uint32_t)t, a.rk, bt);
     BitCounter<15, 10> U, N;
     half_pass<MODE, false, LOCAL>(p, plane, w, 0, t, a.rk, bt, q0, step, y0, i0, dy, di, thr,
-                                  alw0, alw1, used, gen, false, U, N);
+                                  alw0, alw1, used, gen, five, cls5, false, U, N);
     if (!sync_half(j == 0 ? (unsigned)a.stall : 0u)) return flush();
     const bool ex = a.m > 0 && (t + 1) % (uint64_t)a.m == 0;
     if (!ex && !trace) {
       half_pass<MODE, false, LOCAL>(p, plane, w, 1, t, a.rk, bt, q0, step, y0, i0, dy, di, thr,
-                                    alw0, alw1, used, gen, false, U, N);
+                                    alw0, alw1, used, gen, five, cls5, false, U, N);
       if (j + 1 == a.n) break;  // the kernel's end orders this half sweep before what follows
       if (!sync_half(0)) return flush();
       continue;
@@ -301,7 +315,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
     U.zero();
     N.zero();
     half_pass<MODE, true, LOCAL>(p, plane, w, 1, t, a.rk, bt, q0, step, y0, i0, dy, di, thr,
-                                 alw0, alw1, used, gen, trace, U, N);
+                                 alw0, alw1, used, gen, five, cls5, trace, U, N);
     const uint32_t u = U.warp_total_for_lane();
     const uint32_t nn = (MODE == kModeFerro && !trace) ? 0u : N.warp_total_for_lane();
     if (threadIdx.x < 64) (&acc[0][0])[threadIdx.x] = 0;
