@@ -33,9 +33,9 @@ UNIT = "attempts/s"
 MUL_PER_ATTEMPT = 5.0  # Philox4x32-10: 20 32x32->64 products per block of 4 draws
 IMUL_WIDE_PER_CLK_SM = 32.0  # 32x32->64 integer products per clock per SM (4 SMSPs x 8)
 
-# DRAM traffic of one k_flat_half launch (colour 0) on the batched-256 workload from the ncu
-# capture summarised in profiles/k_flat_half_batched-256.md (cold caches: one read of the
-# whole state). Valid only for the kernel source it was taken on.
+# DRAM traffic of one k_flat_half launch (colour 0) on the batched-256 workload, from an ncu
+# capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum; cold caches: one read
+# of the whole state). Valid only for the kernel source it was taken on.
 FLAT_TRAFFIC_BYTES = 25.946368e6 + 0.0
 FLAT_TRAFFIC_SOURCES = ("paper_2512_03825_b300/csrc/pt_device.cuh",
                         "paper_2512_03825_b300/csrc/pt_flat.cuh",

@@ -197,24 +197,27 @@ int pt_sweep_batch(pt_problem* const* problems, int count, const int64_t* n,
  * exists for callers that cannot allocate device memory while they run -- code inside a
  * memory budget it has already fixed, code whose device memory belongs to an allocator this
  * library cannot see, or code that must not let an allocation synchronise the device or fail
- * part-way. It does exactly what pt_sweep_batch does with the PT_BATCH_FLAT strategy (same
- * kernels, bit-identical results) but keeps the per-call work lists (problem descriptors,
- * work tiles, per-warp tile offsets) in one 1 MiB array of device memory that the library
- * defines at file scope; every GPU that loads the library holds that array until the
- * process exits. The work lists of a batch take about 256 bytes per problem plus 16 bytes
- * per 512-word tile of every 32-replica plane plus 4 bytes per resident warp; a batch that
- * does not fit (or has more than 2048 problems, or 65536 tiles) is rejected with PT_EINVAL
- * and a message saying so, before anything is launched. No call allocates: not on the
- * device (no cudaMalloc, cudaMallocAsync or cudaFree) and not on the host heap; the host
- * side builds the lists in fixed arrays.
+ * part-way. It runs the lock-step kernels of pt_sweep_batch (bit-identical results), handing
+ * the tiles out as PT_BATCH_QUEUE does when that strategy is set (pt_set_batch_tuning) and
+ * as PT_BATCH_FLAT does under any other strategy, but keeps the per-call work lists
+ * (problem descriptors, work tiles, per-warp tile offsets) in one 1 MiB array of device
+ * memory that the library defines at file scope; every GPU that loads the library holds
+ * that array until the process exits. The work lists of a batch take about 256 bytes per
+ * problem plus 16 bytes per 512-word tile of every 32-replica plane plus 4 bytes per
+ * resident warp; a batch that does not fit (or lists more than 2048 problems, or needs more
+ * than 65536 tiles) is rejected with PT_EINVAL and a message saying so, before anything is
+ * launched. No call allocates: not on the device (no cudaMalloc, cudaMallocAsync or
+ * cudaFree) and not on the host heap; the host side builds the lists in fixed arrays.
  *
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture starts. Every
- * call shares the one array and overwrites what the previous call left there (nothing in it
- * has to start at zero: each call writes every part it reads). Calls are serialised on the
- * host and each call waits until its lists have been copied to the device, but two calls
- * whose kernels overlap on the GPU (different streams, different problems) race on the
- * array: issue them on one stream, or synchronise between them. */
+ * with that device current. Every call shares the one array and overwrites what the
+ * previous call left there (nothing in it has to start at zero: each call writes every part
+ * it reads). Calls are serialised on the host and each call waits until its lists have been
+ * copied to the device, but two calls whose kernels overlap on the GPU (different streams,
+ * different problems) race on the array: issue them on one stream, or synchronise between
+ * them. The call cannot be recorded into a CUDA graph (its copies read host arrays that the
+ * next call overwrites, and it waits for them): while the problems' stream is being
+ * captured it returns PT_EINVAL before queuing anything, and the problems stay usable. */
 int pt_sweep_batch_static(pt_problem* const* problems, int count, const int64_t* n,
                           const int* exchange_every);
 

@@ -446,10 +446,15 @@ static void advance_counters(pt_problem* const* ps, int count, const int64_t* n,
   }
 }
 
-// Checks shared by both batch entry points: valid problems, counts, one stream, one device,
-// no problem twice. Returns the stream through *st.
-static int check_batch(pt_problem* const* ps, int count, const int64_t* n, const int* every,
-                       cudaStream_t* st_out) {
+// Checks of the allocation-free entry point: valid problems, counts, one stream, one device,
+// no problem twice, and a stream that is not being captured. Nothing here allocates: the
+// duplicate check compares pairs (count is at most kStaticMaxBatch). Returns the stream
+// through *st.
+static int check_batch_static(pt_problem* const* ps, int count, const int64_t* n,
+                              const int* every, cudaStream_t* st_out) {
+  if (count > kStaticMaxBatch)
+    return fail(PT_EINVAL, "pt_sweep_batch_static: %d problems, more than %d", count,
+                kStaticMaxBatch);
   cudaStream_t st = ps[0] ? ps[0]->stream : 0;
   int dev = -1;
   for (int j = 0; j < count; ++j) {
@@ -463,18 +468,32 @@ static int check_batch(pt_problem* const* ps, int count, const int64_t* n, const
     if (dev < 0) dev = p->dev_info.device;
     if (p->dev_info.device != dev) return fail(PT_EINVAL, "problems on different devices");
   }
-  std::vector<pt_problem*> sorted(ps, ps + count);
-  std::sort(sorted.begin(), sorted.end());
-  if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
-    return fail(PT_EINVAL, "a problem appears twice in one batch");
+  for (int a = 1; a < count; ++a)
+    for (int b = 0; b < a; ++b)
+      if (ps[a] == ps[b]) return fail(PT_EINVAL, "a problem appears twice in one batch");
+  int rc = problem_device_guard(ps[0]);
+  if (rc) return rc;
+  // The call copies its work lists from host arrays that the next call overwrites, and it
+  // waits for those copies: neither can be recorded into a graph. Refused before anything
+  // is queued, so no problem is touched.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const cudaError_t err = cudaStreamIsCapturing(st, &cap);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PT_EINVAL, "pt_sweep_batch_static: the stream's capture state cannot be read "
+                "(%s)", cudaGetErrorString(err));
+  }
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(PT_EINVAL, "pt_sweep_batch_static: the problems' stream is being captured; "
+                "this entry point cannot be captured into a CUDA graph");
   *st_out = st;
-  return problem_device_guard(ps[0]);
+  return PT_OK;
 }
 
 int sweep_batch_static_entry(pt_problem* const* ps, int count, const int64_t* n,
                              const int* every) {
   cudaStream_t st = 0;
-  int rc = check_batch(ps, count, n, every, &st);
+  int rc = check_batch_static(ps, count, n, every, &st);
   if (rc) return rc;
   const BatchTuning tune = batch_tuning();
   rc = sweep_batch_static(ps, count, n, every, st, ps[0]->dev_info, tune.tile_words,

@@ -36,6 +36,8 @@ int sweep_batch_flow(pt_problem* const* ps, int count, const int64_t* n, const i
                      cudaStream_t st, const DeviceInfo& di, int tile_words);
 
 // The allocation-free variant of the lock-step path (pt_flat.cu); problems are checked.
+// At most kStaticMaxBatch problems per call.
+constexpr int kStaticMaxBatch = 2048;
 int sweep_batch_static(pt_problem* const* ps, int count, const int64_t* n, const int* every,
                        cudaStream_t st, const DeviceInfo& di, int tile_words, bool queued);
 

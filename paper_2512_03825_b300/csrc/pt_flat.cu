@@ -518,7 +518,7 @@ int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const i
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(1) << 20;  // 1 MiB on every device
-constexpr int kStaticMaxProblems = 2048;
+constexpr int kStaticMaxProblems = kStaticMaxBatch;
 constexpr int kStaticMaxTiles = 65536;
 constexpr int kStaticMaxWarps = 16384;
 

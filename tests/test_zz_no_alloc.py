@@ -85,3 +85,36 @@ def test_static_batch_rejects_oversize(lib):
     assert big.counters() == (0, 0)
     big.sweep(1, 0)  # the problem is still usable
     big.synchronize()
+
+
+def test_static_batch_refuses_stream_capture(lib):
+    """Under stream capture the call must refuse cleanly: its copies read host arrays that the
+    next call overwrites, so it cannot be recorded. The refusal comes before anything is
+    queued, and the problems stay usable and exact."""
+    import torch
+    from paper_2512_03825_b300 import api
+    st = torch.cuda.Stream()
+    probs = _problems()[:3]
+    gs = [api.PTProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed, stream=st) for p in probs]
+    ref = [api.PTProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed, stream=st) for p in probs]
+    assert _batch(lib, lib.lib.pt_sweep_batch_static, gs, [2, 2, 2], [1, 1, 1]) == 0
+    assert _batch(lib, lib.lib.pt_sweep_batch, ref, [2, 2, 2], [1, 1, 1]) == 0
+    torch.cuda.synchronize()
+    x = torch.zeros(16, device="cuda")
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=st):
+        x.add_(1.0)  # something to capture besides the refused call
+        rc = _batch(lib, lib.lib.pt_sweep_batch_static, gs, [3, 3, 3], [1, 1, 1])
+        msg = lib.lib.pt_last_error().decode()
+    assert rc == lib.PT_EINVAL, (rc, msg)
+    assert "captured" in msg
+    graph.replay()
+    torch.cuda.synchronize()
+    for g in gs:
+        assert g.counters() == (2, 2)  # nothing was queued
+    # the problems go on exactly as the allocating path's twins
+    assert _batch(lib, lib.lib.pt_sweep_batch_static, gs, [3, 3, 3], [1, 1, 1]) == 0
+    assert _batch(lib, lib.lib.pt_sweep_batch, ref, [3, 3, 3], [1, 1, 1]) == 0
+    for k, (ga, gb) in enumerate(zip(gs, ref)):
+        for a, b in zip(_state(ga), _state(gb)):
+            np.testing.assert_array_equal(a, b, err_msg="problem %d" % k)
