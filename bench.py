@@ -32,6 +32,12 @@ METRIC = "spin-flip attempts/sec (all replicas, 1 B300) batched vs plain; serve 
 UNIT = "attempts/s"
 MUL_PER_ATTEMPT = 5.0  # Philox4x32-10: 20 32x32->64 products per block of 4 draws
 IMUL_WIDE_PER_CLK_SM = 32.0  # 32x32->64 integer products per clock per SM (4 SMSPs x 8)
+# The issue bound of the roofline: about 25 integer operations per attempt (a quarter of a
+# Philox4x32-10 block of ~78 operations, plus ~5 for the update: class masks, threshold
+# compare, flip insert and a share of the bit-sliced neighbour count), against 4 schedulers x
+# 32 lanes issuing one operation per clock on every SM.
+OPS_PER_ATTEMPT = 25.0
+LANE_OPS_PER_CLK_SM = 128.0
 
 # DRAM traffic of one k_flat_half launch (colour 0) on the batched-256 workload, from an ncu
 # capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum; cold caches: one read
@@ -58,14 +64,17 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["batched", "single", "serve", "flip"],
+    ap.add_argument("--workload", choices=["batched", "single", "serve", "flip", "converge"],
                     default="batched")
+    ap.add_argument("--sizes", type=str, default="16,32,64,128,256",
+                    help="lattice sizes of --workload converge")
+    ap.add_argument("--seeds", type=int, default=8, help="seeds per size of --workload converge")
     ap.add_argument("--iterations", type=int, default=300_000,
                     help="single-spin-flip iterations per replica per step (--workload flip)")
     ap.add_argument("--sweeps", type=int, default=2000, help="sweeps per problem per step")
     ap.add_argument("--problems", type=int, default=256)
-    ap.add_argument("--serve-requests", type=int, default=300,
-                    help="requests in the short serving run of the default line")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the serving leg of the default line")
     ap.add_argument("--requests", type=int, default=2000,
                     help="requests of --workload serve")
     ap.add_argument("--sweep-strategy", choices=["auto", "launches", "persistent"],
@@ -227,6 +236,8 @@ def run_ours(args, rank, world, local):
         return run_single(args, rank, world, stream, sms)
     if args.workload == "flip":
         return run_flip(args, rank, world, stream)
+    if args.workload == "converge":
+        return run_converge(args, rank, world, stream)
     if args.workload == "serve":
         from paper_2512_03825_b300 import serve
         res = serve.bench_serve(args, rank, world, stream)
@@ -289,6 +300,7 @@ def run_ours(args, rank, world, local):
     peaks = measured_peaks()
     clock_mhz = float(peaks.get("sm_max_mhz", 2032.0))
     peak_mul = sms * IMUL_WIDE_PER_CLK_SM * clock_mhz * 1e6
+    peak_ops = sms * LANE_OPS_PER_CLK_SM * clock_mhz * 1e6
     flat = tuning.get("strategy", 0) in (0, 3)  # lock-step: dealt or queued tiles
     if flat:
         # the dominant kernel on its own: a batch without exchanges is nothing but
@@ -306,31 +318,40 @@ def run_ours(args, rank, world, local):
                 torch.cuda.synchronize()
                 took.append(a.elapsed_time(b) / 1e3)
         launch_s = (took[1] - took[0]) / (2 * (lens[1] - lens[0]))
-        per_launch_mul = MUL_PER_ATTEMPT * per_step / args.sweeps / 2
-        achieved_mul = per_launch_mul / launch_s
-        how = ("k_flat_half: algorithmic products of one half sweep of all %d problems (5 per "
-               "attempt) / its average launch duration, (t(%d sweeps) - t(%d sweeps)) / %d "
-               "launches (CUDA events)" % (len(probs), lens[1], lens[0],
+        att_per_s = per_step / args.sweeps / 2 / launch_s
+        how = ("k_flat_half: attempts of one half sweep of all %d problems / its average "
+               "launch duration, (t(%d sweeps) - t(%d sweeps)) / %d launches (CUDA events on "
+               "the problems' stream)" % (len(probs), lens[1], lens[0],
                                           2 * (lens[1] - lens[0])))
         traffic = _flat_traffic()
     else:
-        achieved_mul = MUL_PER_ATTEMPT * per_step / (statistics.mean(kernel_ms) / 1e3)
-        how = "k_batch: products of one batch / its duration"
+        att_per_s = per_step / (statistics.mean(kernel_ms) / 1e3)
+        how = "k_batch: attempts of one batch / its duration"
         traffic = None
+    step_att_per_s = value / world
     out["roofline"] = {
         "bound": "alu",
         "kernel": "k_flat_half" if flat else "k_batch",
-        "achieved": achieved_mul / 1e12, "peak": peak_mul / 1e12, "unit": "T int-mul/s",
-        "frac": achieved_mul / peak_mul,
+        "achieved": OPS_PER_ATTEMPT * att_per_s / 1e12, "peak": peak_ops / 1e12,
+        "unit": "T int-ops/s", "frac": OPS_PER_ATTEMPT * att_per_s / peak_ops,
         "traffic": traffic,
-        "note": "32x32->64 integer multiplies (Philox4x32-10, 5 per attempt) against %d SMs x "
-                "%d per clock x %.0f MHz (max clock; of measured SM count); %s; traffic = DRAM "
-                "bytes per launch from ncu (cold caches)" % (sms, IMUL_WIDE_PER_CLK_SM,
-                                                              clock_mhz, how),
+        "step_frac": OPS_PER_ATTEMPT * step_att_per_s / peak_ops,
+        "mul_pipe": {"achieved": MUL_PER_ATTEMPT * att_per_s / 1e12,
+                     "peak": peak_mul / 1e12, "unit": "T int-mul/s",
+                     "frac": MUL_PER_ATTEMPT * att_per_s / peak_mul,
+                     "step_frac": MUL_PER_ATTEMPT * step_att_per_s / peak_mul},
+        "note": "issue bound: %d integer operations per attempt (analytic: a quarter Philox4x32-10 "
+                "block plus the update) against %d SMs x %d lane-operations per clock x %.0f MHz "
+                "(max clock; measured SM count); %s; step_frac = the whole timed step (both half "
+                "sweeps, the bond count and the exchange launch) on the same bound; mul_pipe = "
+                "the same attempts as 32x32->64 products (5 per attempt) against %d per clock "
+                "per SM, the higher of the two ceilings; traffic = DRAM bytes per launch from ncu "
+                "(cold caches)" % (OPS_PER_ATTEMPT, sms, LANE_OPS_PER_CLK_SM, clock_mhz, how,
+                                   IMUL_WIDE_PER_CLK_SM),
     }
     if not args.quick and rank == 0:
         out["serve"] = bench_serve_short(stream, args.serve_requests)
-        out["plain"] = bench_plain_sample(probs, stream)
+        out["plain"] = bench_plain(probs, args.sweeps, stream)
         out["batched_vs_plain"] = value / world / out["plain"]["value"]
         out["single_L1024_R64"] = bench_single(stream, sms, clock_mhz)
         out["single_L128_R32"] = bench_single(stream, sms, clock_mhz, "L128_R32", 2000)
@@ -339,10 +360,10 @@ def run_ours(args, rank, world, local):
         out["paper_L300_R1500"] = bench_single(stream, sms, clock_mhz, sweeps=300,
                                                prob=W.paper_problem())
         out["paper_single_flip_full_run"] = bench_paper_flip(stream)
-        out["e2e"] = bench_e2e(probs, args.sweeps, stream, world)
-        out["cpu_baseline"] = cpu_baseline_sample(probs)
+        out["e2e"] = bench_e2e(probs, args.sweeps, stream, world, args.steps)
+        out["cpu_baseline"] = cpu_baseline_plan(probs)
     elif not args.quick:
-        bench_e2e(probs, args.sweeps, stream, world)
+        bench_e2e(probs, args.sweeps, stream, world, args.steps)
     for h in handles:
         h.close()
     return out
@@ -362,7 +383,8 @@ def launches_per_batch(probs, sweeps, tuning):
 
 
 def bench_serve_short(stream, nreq):
-    """A shorter run of the serving workload (the full one is --workload serve)."""
+    """The serving workload: `nreq` Poisson requests (default 2000, the whole stream) at 80%
+    of the measured batched rate, an 80 GB budget."""
     from paper_2512_03825_b300 import serve
 
     class A:
@@ -372,35 +394,39 @@ def bench_serve_short(stream, nreq):
     return out
 
 
-def bench_plain_sample(probs, stream, n_problems=32, sweeps=200):
-    """The plain path -- one problem at a time through pt_sweep -- on a sample of the same
-    problem mix, in both of its strategies: one persistent launch per call (the default)
-    and one launch per half sweep plus the exchange launches."""
+def _plain_run(sample, sweeps, strategy, stream):
     import torch
     from paper_2512_03825_b300 import api
-    sample = probs[:: max(1, len(probs) // n_problems)][:n_problems]
-    att = _attempts(sample, sweeps)
-    out = {}
-    for name, strategy in (("persistent", 2), ("launches", 1)):
-        hs = [api.PTProblem(p.L, p.betas, seed=p.seed, stream=stream) for p in sample]
-        for h in hs:
-            h.set_sweep_tuning(strategy)
-            h.sweep(5, 1)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for h in hs:
-            h.sweep(sweeps, 1)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b)
-        for h in hs:
-            h.close()
-        out[name] = {"value": att / (ms / 1e3),
-                     "launches": len(sample) * (1 if strategy == 2 else sweeps * 4)}
-    return {"value": out["persistent"]["value"], "unit": UNIT, "problems": len(sample),
-            "sweeps": sweeps, "launches": out["persistent"]["launches"],
-            "launches_strategy": out["launches"]}
+    hs = [api.PTProblem(p.L, p.betas, seed=p.seed, stream=stream) for p in sample]
+    for h in hs:
+        h.set_sweep_tuning(strategy)
+        h.sweep(5, 1)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for h in hs:
+        h.sweep(sweeps, 1)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    for h in hs:
+        h.close()
+    return _attempts(sample, sweeps) / (ms / 1e3)
+
+
+def bench_plain(probs, sweeps, stream, n_sample=32, sample_sweeps=200):
+    """The plain path -- one problem at a time through pt_sweep -- on the same workload: every
+    problem for the same number of sweeps with its default strategy (one persistent launch
+    per call); the other strategy (one launch per half sweep plus the exchange launches),
+    about 2.5x slower, on a sample of the same mix (every 8th problem, 200 sweeps)."""
+    full = _plain_run(probs, sweeps, 2, stream)
+    sample = probs[:: max(1, len(probs) // n_sample)][:n_sample]
+    launches = _plain_run(sample, sample_sweeps, 1, stream)
+    return {"value": full, "unit": UNIT, "problems": len(probs), "sweeps": sweeps,
+            "launches": len(probs), "strategy": "persistent (one launch per problem)",
+            "launches_strategy": {"value": launches, "problems": len(sample),
+                                  "sweeps": sample_sweeps,
+                                  "launches": len(sample) * sample_sweeps * 4}}
 
 
 def bench_single(stream, sms, clock_mhz, name="L1024_R64", sweeps=200, prob=None):
@@ -452,11 +478,11 @@ def bench_paper_flip(stream, iterations=300_000, every=100):
             "note": "the paper reports this run under 1 s on an A100 (CUDA version)"}
 
 
-def bench_e2e(probs, sweeps, stream, world):
+def bench_e2e(probs, sweeps, stream, world, steps=1):
     """The same step through the C ABI from host buffers: create every problem from host
     betas (tables copied to the device), run the batch, read energies, magnetisations,
     temperature maps and swap counters of every problem back in one transfer
-    (pt_read_batch), destroy."""
+    (pt_read_batch), destroy. One untimed step, then `steps` timed ones."""
     import torch
     from paper_2512_03825_b300 import api
 
@@ -475,33 +501,63 @@ def bench_e2e(probs, sweeps, stream, world):
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
-    h2d, d2h = step()
+    for _ in range(steps):
+        h2d, d2h = step()
     torch.cuda.synchronize()
     barrier(world)
-    dt = max_over_ranks(time.perf_counter() - t0, world)
+    dt = max_over_ranks(time.perf_counter() - t0, world) / steps
     return {"value": _attempts(probs, sweeps) * world / dt, "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "s_per_step": dt}
+            "s_per_step": dt, "steps": steps}
 
 
-def cpu_baseline_sample(probs, n_problems=32, sweeps=100):
-    """The oracle, as it stands, on a bounded sample of the same workload: 32 of the 256
-    problems (every 8th, so the sample keeps the mix of L and R), 100 sweeps each, about
-    10 s of work on 16 host cores."""
+def _oracle_rate(probs, sweeps_of, every_of, threads):
+    """Attempts per second of the oracle, as it stands, on `threads` host threads over the
+    given problems (each from creation for sweeps_of(p) sweeps)."""
     import oracle
-    threads = os.cpu_count() or 1
     oracle.set_threads(threads)
-    sample = probs[:: max(1, len(probs) // n_problems)][:n_problems]
+    att = 0.0
     t0 = time.perf_counter()
-    for p in sample:
+    for p in probs:
         o = oracle.OracleProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed)
-        o.sweep(sweeps, 1)
+        o.sweep(sweeps_of(p), every_of(p))
+        att += float(p.L * p.L * p.R) * sweeps_of(p)
     dt = time.perf_counter() - t0
-    return {"value": _attempts(sample, sweeps) / dt, "unit": UNIT, "cores": threads,
-            "kind": "oracle",
-            "sample": "%d of the batched problems (every %d-th), %d sweeps each, exchange every "
-                      "sweep, %.1f s" % (len(sample), max(1, len(probs) // n_problems), sweeps,
-                                         dt)}
+    return att / dt, dt, att
+
+
+def cpu_baseline_plan(probs):
+    """The oracle, as it stands, on the machine's host cores: the headline figure on a bounded
+    sample of the batched workload (every 8th of the 256 problems, 100 sweeps each), and
+    beside it the single-problem workloads (L = 16 and L = 128 in full, L = 1024 on its first
+    10 sweeps), one core on a sample of L = 128, and the served stream on a 5% sample
+    (every 20th request, at most 10 sweeps each; the whole stream's time extrapolated from
+    its attempts)."""
+    from paper_2512_03825_b300 import workloads as W
+    threads = os.cpu_count() or 1
+    sample = probs[:: max(1, len(probs) // 32)][:32]
+    v, dt, _ = _oracle_rate(sample, lambda p: 100, lambda p: 1, threads)
+    out = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": "%d of the batched problems (every %d-th), 100 sweeps each, exchange "
+                     "every sweep, %.1f s" % (len(sample), max(1, len(probs) // 32), dt)}
+    plan = {}
+    for name, sweeps in (("L16_R8", None), ("L128_R32", None), ("L1024_R64", 10)):
+        p = W.SINGLE[name]
+        sw = (lambda q: q.sweeps) if sweeps is None else (lambda q, k=sweeps: k)
+        v1, dt1, _ = _oracle_rate([p], sw, lambda q: q.every, threads)
+        plan[name] = {"value": v1, "sweeps": sw(p), "seconds": dt1,
+                      "full_run": sweeps is None}
+    p = W.SINGLE["L128_R32"]
+    v1, dt1, _ = _oracle_rate([p], lambda q: 100, lambda q: q.every, 1)
+    plan["L128_R32_one_core"] = {"value": v1, "sweeps": 100, "seconds": dt1, "cores": 1}
+    reqs = W.serving_requests(n=2000, rate_per_s=1.0)
+    samp = [r.problem for r in reqs[::20]]
+    v1, dt1, att = _oracle_rate(samp, lambda q: min(10, q.sweeps), lambda q: q.every, threads)
+    total = float(sum(r.problem.attempts for r in reqs))
+    plan["serve_2000"] = {"value": v1, "requests": len(samp), "sweeps_each": "min(10, asked)",
+                          "seconds": dt1, "extrapolated_total_s": total / v1}
+    out["plan"] = plan
+    return out
 
 
 def run_single(args, rank, world, stream, sms):
@@ -574,6 +630,38 @@ def run_flip(args, rank, world, stream):
                                    "T_i = 1 + 3i/1500, %d iterations, swap every 100"
                                    % args.iterations},
             "clocks": clk, "gpu_launches": args.steps}
+
+
+def run_converge(args, rank, world, stream):
+    """Sweeps to convergence against L (Sec. 4.1, Fig. 3b), by the two-start reading of
+    converge.py: the paper's ladder T_i = 1 + 3i/32 (32 temperatures), J = 1, B = 0, a swap
+    iteration after every sweep, `--seeds` seeds per size; every hot/cold pair of runs
+    advances in one batch until all its temperatures have converged (or its cap)."""
+    import torch
+    from paper_2512_03825_b300 import api
+    from paper_2512_03825_b300 import converge as CV
+    Ls = [int(x) for x in args.sizes.split(",")]
+    seeds = [0x5EED4000 + rank * RANK_SEED_STRIDE + j for j in range(args.seeds)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    barrier(world)
+    clocks.start()
+    t0 = time.perf_counter()
+    res = CV.measure(api, Ls, seeds, R=32, every=1, stream=stream)
+    torch.cuda.synchronize()
+    wall = max_over_ranks(time.perf_counter() - t0, world)
+    clk = clocks.stop()
+    summ = CV.summarise(res, CV.default_caps(Ls))
+    return {"metric": "sweeps to converge against L (Fig. 3b): fitted exponent of the median",
+            "value": summ.get("exponent_sweeps"), "unit": "exponent (t* ~ L^value sweeps)",
+            "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * wall,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (random and ordered starts from the seed)",
+            "config": {"workload": "convergence: L in %s, the paper's ladder with 32 "
+                                   "temperatures, J=1, B=0, swap every sweep, %d seeds"
+                                   % (args.sizes, args.seeds),
+                       "criterion": "per temperature: first sweep with E(random start) <= "
+                                    "E(ordered start), same seed; t* = last temperature"},
+            "convergence": summ, "clocks": clk}
 
 
 # ---------------------------------------------------------------------------------------

@@ -23,14 +23,24 @@ struct Philox4 {
   uint32_t x, y, z, w;
 };
 
+// hi:lo = a * b, the full 64-bit product of two 32-bit words, as one wide multiply. Written
+// as __umulhi(a, b) and a * b, the two halves were formed by separate multiplies: measured
+// on batched-256, 122.2 -> 115.7 us per sweep without swaps with the single wide product,
+// L = 1024, R = 64 56.7 -> 55.4 us.
+__device__ __forceinline__ void mul_wide(uint32_t a, uint32_t b, uint32_t& hi, uint32_t& lo) {
+  uint64_t p;
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(b));
+  lo = (uint32_t)p;
+  hi = (uint32_t)(p >> 32);
+}
+
 __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
                                                   uint32_t c3, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(kPhiloxM0, c0);
-    const uint32_t lo0 = kPhiloxM0 * c0;
-    const uint32_t hi1 = __umulhi(kPhiloxM1, c2);
-    const uint32_t lo1 = kPhiloxM1 * c2;
+    uint32_t hi0, lo0, hi1, lo1;
+    mul_wide(kPhiloxM0, c0, hi0, lo0);
+    mul_wide(kPhiloxM1, c2, hi1, lo1);
     const uint32_t rk0 = k0 + (uint32_t)r * kPhiloxW0;
     const uint32_t rk1 = k1 + (uint32_t)r * kPhiloxW1;
     c0 = hi1 ^ c1 ^ rk0;
@@ -52,10 +62,9 @@ __device__ __forceinline__ Philox4 philox4x32_10_rk(uint32_t c0, uint32_t c1, ui
                                                      uint32_t c3, const RoundKeys& rk) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(kPhiloxM0, c0);
-    const uint32_t lo0 = kPhiloxM0 * c0;
-    const uint32_t hi1 = __umulhi(kPhiloxM1, c2);
-    const uint32_t lo1 = kPhiloxM1 * c2;
+    uint32_t hi0, lo0, hi1, lo1;
+    mul_wide(kPhiloxM0, c0, hi0, lo0);
+    mul_wide(kPhiloxM1, c2, hi1, lo1);
     c0 = hi1 ^ c1 ^ rk.k0[r];
     c1 = lo1;
     c2 = hi0 ^ c3 ^ rk.k1[r];
@@ -101,9 +110,10 @@ __device__ __forceinline__ void block_terms(uint32_t blk0, uint32_t t_lo, const 
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const uint32_t c2 = blk0 + (uint32_t)j;
-    const uint32_t h1 = __umulhi(kPhiloxM1, c2), l1 = kPhiloxM1 * c2;  // round 1, word 2
-    const uint32_t c0 = h1 ^ t_lo ^ rk.k0[0];                           // round-1 output 0
-    const uint32_t hA = __umulhi(kPhiloxM0, c0), lA = kPhiloxM0 * c0;   // round 2, word 0
+    uint32_t h1, l1, hA, lA;
+    mul_wide(kPhiloxM1, c2, h1, l1);             // round 1, word 2
+    const uint32_t c0 = h1 ^ t_lo ^ rk.k0[0];    // round-1 output 0
+    mul_wide(kPhiloxM0, c0, hA, lA);             // round 2, word 0
     bt.X[j] = l1 ^ rk.k0[1];
     bt.Y[j] = hA ^ rk.k1[1];
     bt.Z[j] = lA;
@@ -112,25 +122,21 @@ __device__ __forceinline__ void block_terms(uint32_t blk0, uint32_t t_lo, const 
 
 __device__ __forceinline__ SiteTerms site_terms(uint32_t site, uint32_t c3, const RoundKeys& rk) {
   SiteTerms st;
-  const uint32_t h0 = __umulhi(kPhiloxM0, site);  // round 1, word 0
-  st.L0 = kPhiloxM0 * site;
-  const uint32_t c2 = h0 ^ c3 ^ rk.k1[0];         // round-1 output 2
-  st.H = __umulhi(kPhiloxM1, c2);                 // round 2, word 2
-  st.Hlo = kPhiloxM1 * c2;
+  uint32_t h0;
+  mul_wide(kPhiloxM0, site, h0, st.L0);      // round 1, word 0
+  const uint32_t c2 = h0 ^ c3 ^ rk.k1[0];    // round-1 output 2
+  mul_wide(kPhiloxM1, c2, st.H, st.Hlo);     // round 2, word 2
   return st;
 }
 
-// Philox4x32-10 block j of the site: the round-2 state from the shared terms, then rounds
-// 3-10.
-__device__ __forceinline__ Philox4 philox_site_block(const SiteTerms& st, const BlockTerms& bt,
-                                                     int j, const RoundKeys& rk) {
-  uint32_t c0 = st.H ^ bt.X[j], c1 = st.Hlo, c2 = bt.Y[j] ^ st.L0, c3 = bt.Z[j];
+// Rounds 3-10 of Philox4x32-10 from the round-2 state (c0, c1, c2, c3).
+__device__ __forceinline__ Philox4 philox_rounds_3_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                      uint32_t c3, const RoundKeys& rk) {
 #pragma unroll
   for (int r = 2; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(kPhiloxM0, c0);
-    const uint32_t lo0 = kPhiloxM0 * c0;
-    const uint32_t hi1 = __umulhi(kPhiloxM1, c2);
-    const uint32_t lo1 = kPhiloxM1 * c2;
+    uint32_t hi0, lo0, hi1, lo1;
+    mul_wide(kPhiloxM0, c0, hi0, lo0);
+    mul_wide(kPhiloxM1, c2, hi1, lo1);
     c0 = hi1 ^ c1 ^ rk.k0[r];
     c1 = lo1;
     c2 = hi0 ^ c3 ^ rk.k1[r];
@@ -138,6 +144,14 @@ __device__ __forceinline__ Philox4 philox_site_block(const SiteTerms& st, const 
   }
   return Philox4{c0, c1, c2, c3};
 }
+
+// Philox4x32-10 block j of the site: the round-2 state from the shared terms, then rounds
+// 3-10.
+__device__ __forceinline__ Philox4 philox_site_block(const SiteTerms& st, const BlockTerms& bt,
+                                                     int j, const RoundKeys& rk) {
+  return philox_rounds_3_10(st.H ^ bt.X[j], st.Hlo, bt.Y[j] ^ st.L0, bt.Z[j], rk);
+}
+
 
 // Counter words shared by every spin-update draw of one sweep.
 struct SweepCtr {

@@ -193,10 +193,10 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
     const uint32_t alw0 = pl->alw0, alw1 = pl->alw1, used = pl->used;
     BitCounter<13, 8> Uf;
     if (COUNT) Uf.zero();
-    // one loop per block count: the count-free kernel gets the word update with NB blocks
-    // fixed at compile time (measured: 131.5 -> 122.9 us per batched-256 sweep without
-    // swaps); the counting kernel keeps the count at run time (NB = 0), because with it
-    // fixed the extra live registers of the count made it slower
+    // one loop per block count: the word update runs with NB blocks fixed at compile time
+    // (measured: 131.5 -> 122.9 us per batched-256 sweep without swaps; with the wide
+    // multiplies the counting kernel gains from it too, 135.3 -> 134.0 us per sweep with a
+    // swap iteration, where before it cost registers and time)
     const auto word_loop = [&](auto nbc) {
       constexpr int NB = decltype(nbc)::value;
       for (int q = q_start; q < tl.q1; q += 32) {
@@ -229,10 +229,7 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
         }
       }
     };
-    if (COUNT)
-      word_loop(BlockCount<0>{});  // the block count at run time
-    else
-      with_block_count(nblk, word_loop);
+    with_block_count(nblk, word_loop);
     if (COUNT && count) {
       const uint32_t u = Uf.warp_total_for_lane();
       if (u) atomicAdd(&p.cnt[w * 32 + lane], u);
