@@ -166,6 +166,37 @@ int pt_set_wait_limit(pt_problem* p, double seconds);
  * described above. Applies to one launch. */
 int pt_debug_stall_barrier(pt_problem* p, int arrivals);
 
+/* The debug build of the library (libpt_debug.so, compiled with PT_DEBUG) stands in for a
+ * memory and race checker on small cases; the paper has no counterpart. In it every
+ * spin-word index a kernel reads or writes is checked against the word range of its plane and
+ * colour before the access, and so is every count-buffer index and trace row; every store of
+ * a half sweep tags its word with the number of that half sweep, so a word stored twice in
+ * one half sweep (two threads owning one site) is caught. A failed check never traps: it is
+ * recorded, the access is redirected to the start of its array or skipped, and the
+ * problem's status makes its next synchronising call return PT_EINTERNAL. The release library
+ * compiles none of these checks; its kernels are unchanged by them.
+ *
+ * pt_debug_build: 1 in the debug build, 0 in the release library. */
+int pt_debug_build(void);
+
+/* The problem's record of failed checks (debug build): how many (*violations), the kind of
+ * the first (*first_kind: 1 a spin-word load, 2 a spin-word store outside its plane and
+ * colour, 3 a spin word stored twice in one half sweep, 4 a count-buffer index, 5 a trace
+ * row, 6 a single-flip word outside its plane; 0 none) and the index it was given; and
+ * *unwritten, the spin words that the problem's last sweep did not store in their own half
+ * sweep (0 when no sweep has run since pt_create or pt_load). Any pointer may be NULL.
+ * Synchronises the stream and does not poison the problem. PT_EINVAL in the release
+ * library. */
+int pt_debug_report(pt_problem* p, uint64_t* violations, int32_t* first_kind,
+                    uint64_t* first_index, uint64_t* unwritten);
+
+/* Test support of the debug build: the next launch of the one-launch-per-half-sweep kernel
+ * (PT_SWEEP_LAUNCHES) of this problem plants one mistake in its first thread, which the
+ * checks must catch: kind 1 stores that thread's first word a second time, unchanged (a double
+ * write), kind 2 asks for a neighbour word one past its colour's range (the check redirects
+ * the load into the range). 0 clears. PT_EINVAL in the release library or for another kind. */
+int pt_debug_inject(pt_problem* p, int kind);
+
 /* The single-spin-flip variant: the paper's "iteration" (Sec. 2.1, the MH step whose trial
  * state flips one spin) read as one Metropolis trial at one uniformly chosen site of every
  * replica. n >= 0 iterations of every replica; after every iteration that leaves the

@@ -10,7 +10,10 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpt.so")
+# PT_LIBRARY=debug selects the debug build (libpt_debug.so: bounds and write-set checks in
+# every kernel); the default is the release library.
+LIB_PATH = os.path.join(HERE, "libpt_debug.so" if os.environ.get("PT_LIBRARY") == "debug"
+                        else "libpt.so")
 
 PT_OK = 0
 PT_EINVAL = -1
@@ -58,6 +61,10 @@ SIGNATURES = [
     ("pt_get_sweep_tuning", C.c_int, [P, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                       C.POINTER(C.c_int)]),
     ("pt_set_wait_limit", C.c_int, [P, C.c_double]),
+    ("pt_debug_build", C.c_int, []),
+    ("pt_debug_report", C.c_int, [P, C.POINTER(C.c_uint64), C.POINTER(C.c_int32),
+                                  C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
+    ("pt_debug_inject", C.c_int, [P, C.c_int]),
     ("pt_debug_stall_barrier", C.c_int, [P, C.c_int]),
     ("pt_sweep_batch", C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.c_int64),
                                  C.POINTER(C.c_int)]),
@@ -118,9 +125,8 @@ class PTError(RuntimeError):
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError("libpt.so is not built (%s); run "
-                          "`python -m paper_2512_03825_b300.build` or __graft_entry__.build()"
-                          % LIB_PATH)
+        raise ImportError("%s is not built; run `python -m paper_2512_03825_b300.build` or "
+                          "__graft_entry__.build()" % LIB_PATH)
     lib = C.CDLL(LIB_PATH)
     for name, res, args in SIGNATURES:
         fn = getattr(lib, name)

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "pt_batch.h"
+#include "pt_debug.cuh"
 #include "pt_device.cuh"
 #include "pt_internal.h"
 #include "pt_launch.h"
@@ -137,52 +138,61 @@ __device__ __forceinline__ uint32_t ld_row(const uint32_t* p, bool own) {
   return own ? *p : __ldcg(p);
 }
 
-__device__ __forceinline__ Nb5 load_nb(const uint32_t* own, const uint32_t* oth, int L, int half,
-                                       int y, int i, int colour, int y0, int y1) {
+__device__ __forceinline__ Nb5 load_nb(const DevProblem& p, const uint32_t* own,
+                                       const uint32_t* oth, int L, int half, int y, int i,
+                                       int colour, int y0, int y1) {
   const int par = (y + colour) & 1;
   const int ym = (y == 0) ? L - 1 : y - 1;
   const int yp = (y == L - 1) ? 0 : y + 1;
   const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
   const size_t idx = (size_t)y * half + i;
+  const int nw = L * half;  // words of one colour (the debug checks' range)
+  (void)p;
+  (void)nw;
   Nb5 v;
-  v.s = own[idx];
-  v.n0 = ld_row(oth + (size_t)ym * half + i, ym >= y0 && ym < y1);
-  v.n1 = ld_row(oth + (size_t)yp * half + i, yp >= y0 && yp < y1);
-  v.n2 = oth[idx];
-  v.n3 = oth[(size_t)y * half + ih];
+  v.s = own[PT_DBG_IDX(p, idx, nw, kDbgSpinLoad)];
+  v.n0 = ld_row(oth + PT_DBG_IDX(p, (size_t)ym * half + i, nw, kDbgSpinLoad), ym >= y0 && ym < y1);
+  v.n1 = ld_row(oth + PT_DBG_IDX(p, (size_t)yp * half + i, nw, kDbgSpinLoad), yp >= y0 && yp < y1);
+  v.n2 = oth[PT_DBG_IDX(p, idx, nw, kDbgSpinLoad)];
+  v.n3 = oth[PT_DBG_IDX(p, (size_t)y * half + ih, nw, kDbgSpinLoad)];
   return v;
 }
 
 template <int MODE>
 __device__ __forceinline__ void half_sweep_plane(const DevProblem& p, int w, int colour,
-                                                 const SweepCtr& cx, int y0, int y1, int nwords,
+                                                 uint64_t t, const SweepCtr& cx, int y0, int y1,
+                                                 int nwords,
                                                  const PlaneDeal& deal, const FerroRegs& th,
                                                  const PlaneGeneric* gen_smem) {
   const int L = p.L, half = L >> 1;
   const int lane = threadIdx.x & 31;
   const int nblk = (plane_slots(p.R, w) + 3) >> 2;
-  uint32_t* own = p.spins + word_index(L, w, colour, 0, 0);
+  const size_t own_base = word_index(L, w, colour, 0, 0);
+  uint32_t* own = p.spins + own_base;
   const uint32_t* oth = p.spins + word_index(L, w, colour ^ 1, 0, 0);
+  (void)own_base;
+  PT_DBG_CHECK(p, w, p.W, kDbgSpinLoad);
   WordWalk ww(deal.rank * 32 + lane, deal.nranks * 32, half);
   if (ww.q >= nwords) return;
   // software pipeline: the next word's loads are in flight while this word is updated
-  Nb5 cur = load_nb(own, oth, L, half, y0 + ww.yy, ww.i, colour, y0, y1);
+  Nb5 cur = load_nb(p, own, oth, L, half, y0 + ww.yy, ww.i, colour, y0, y1);
   for (;;) {
     const int y = y0 + ww.yy, i = ww.i;
     WordWalk nx = ww;
     nx.next();
     Nb5 nxt = cur;
-    if (nx.q < nwords) nxt = load_nb(own, oth, L, half, y0 + nx.yy, nx.i, colour, y0, y1);
+    if (nx.q < nwords) nxt = load_nb(p, own, oth, L, half, y0 + nx.yy, nx.i, colour, y0, y1);
     const int par = (y + colour) & 1;
     const uint32_t site = (uint32_t)(y * L + 2 * i + par);
     const size_t idx = (size_t)y * half + i;
+    uint32_t ns;
     if (MODE == kModeFerro)
-      own[idx] = update_word_ferro(cur.s, cur.n0, cur.n1, cur.n2, cur.n3, site,
-                                   (uint32_t)(8 * w), nblk, th.T0, th.T1, th.alw0, th.alw1,
-                                   th.used, cx);
+      ns = update_word_ferro(cur.s, cur.n0, cur.n1, cur.n2, cur.n3, site, (uint32_t)(8 * w),
+                             nblk, th.T0, th.T1, th.alw0, th.alw1, th.used, cx);
     else
-      own[idx] = update_word_generic(cur.s, cur.n0, cur.n1, cur.n2, cur.n3, site,
-                                     (uint32_t)(8 * w), nblk, gen_smem[w], cx);
+      ns = update_word_generic(cur.s, cur.n0, cur.n1, cur.n2, cur.n3, site, (uint32_t)(8 * w),
+                               nblk, gen_smem[w], cx);
+    if (PT_DBG_STORE(p, idx, L * half, own_base, t, colour)) own[idx] = ns;
     if (nx.q >= nwords) break;
     ww = nx;
     cur = nxt;
@@ -199,7 +209,7 @@ __device__ void half_sweep_rows(const DevProblem& p, int colour, uint64_t t, int
   const int nwords = (y1 - y0) * (p.L >> 1);
   for (int w = deal.w_first; w < p.W; w += deal.w_step) {
     if (MODE == kModeFerro && !th_loaded) th.load(reinterpret_cast<const PlaneFerro*>(p.planes) + w);
-    half_sweep_plane<MODE>(p, w, colour, cx, y0, y1, nwords, deal, th, gen_smem);
+    half_sweep_plane<MODE>(p, w, colour, t, cx, y0, y1, nwords, deal, th, gen_smem);
   }
 }
 
@@ -222,11 +232,14 @@ __device__ void count_rows(const DevProblem& p, int y0, int y1, uint32_t* acc_sm
       const int yp = (y == L - 1) ? 0 : y + 1;
       const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
       const size_t idx = (size_t)y * half + i;
-      const uint32_t s = c0[idx];
-      const uint32_t o = c1[idx];
-      const NbCount k = count4(s ^ ld_row(c1 + (size_t)ym * half + i, ym >= y0 && ym < y1),
-                               s ^ ld_row(c1 + (size_t)yp * half + i, yp >= y0 && yp < y1),
-                               s ^ o, s ^ c1[(size_t)y * half + ih]);
+      const int nw = L * half;
+      (void)nw;
+      const uint32_t s = c0[PT_DBG_IDX(p, idx, nw, kDbgSpinLoad)];
+      const uint32_t o = c1[PT_DBG_IDX(p, idx, nw, kDbgSpinLoad)];
+      const NbCount k = count4(
+          s ^ ld_row(c1 + PT_DBG_IDX(p, (size_t)ym * half + i, nw, kDbgSpinLoad), ym >= y0 && ym < y1),
+          s ^ ld_row(c1 + PT_DBG_IDX(p, (size_t)yp * half + i, nw, kDbgSpinLoad), yp >= y0 && yp < y1),
+          s ^ o, s ^ c1[PT_DBG_IDX(p, (size_t)y * half + ih, nw, kDbgSpinLoad)]);
       U.add3(k.b0, k.b1, k.b2);
       N.add2(s ^ o, s & o);
     }
@@ -343,7 +356,7 @@ __device__ void run_item(const BatchItem& it, const Gang<JOINT>& gang, uint32_t*
       count_rows(p, y0, y1, acc);
       __syncthreads();
       for (int q = threadIdx.x; q < 2 * p.W * 32; q += blockDim.x)
-        if (acc[q]) atomicAdd(&p.cnt[q], acc[q]);
+        if (acc[q]) atomicAdd(&p.cnt[PT_DBG_IDX(p, q, 2 * p.W * 32, kDbgCount)], acc[q]);
       gang.sync();
       if (gang.rank == 0) exchange_step(p, e);
       e += 1;

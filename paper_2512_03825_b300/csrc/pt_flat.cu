@@ -195,8 +195,9 @@ __global__ void __launch_bounds__(kFlatThreads) k_flat_exchange(const FlatProble
       const int64_t row = (int64_t)((t - p.trace_t0) % (uint64_t)p.trace_cap);
       for (int r = threadIdx.x; r < R; r += blockDim.x) {
         const int k = tos[r];
-        p.trace_E[row * R + k] = E_s[r];
-        p.trace_M[row * R + k] = M_s[r];
+        const int64_t at = PT_DBG_IDX(p, row * R + k, p.trace_cap * R, kDbgTrace);
+        p.trace_E[at] = E_s[r];
+        p.trace_M[at] = M_s[r];
       }
     }
   }

@@ -8,6 +8,7 @@
 
 #include <vector>
 
+#include "pt_debug.cuh"
 #include "pt_device.cuh"
 #include "pt_internal.h"
 
@@ -175,8 +176,11 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
   }
   BlockTerms bt;
   block_terms((uint32_t)(8 * w), (uint32_t)t, rk, bt);
-  uint32_t* own = p.spins + word_index(L, w, colour, 0, 0);
+  const size_t own_base = word_index(L, w, colour, 0, 0);
+  uint32_t* own = p.spins + own_base;
   const uint32_t* oth = p.spins + word_index(L, w, colour ^ 1, 0, 0);
+  const int nwords = L * half;  // words of one colour of a plane (the debug checks' range)
+  (void)nwords;
   const int q_start = tl.q0 + lane;
   int y = q_start / half, i = q_start - y * half;
   const int dy = 32 / half, di = 32 - dy * half;
@@ -204,17 +208,17 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
         const int ym = (y == 0) ? L - 1 : y - 1;
         const int yp = (y == L - 1) ? 0 : y + 1;
         const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
-        const uint32_t s = own[q];  // written by this lane only
-        const uint32_t n0 = ld_nb<NB_L2>(oth + ym * half + i);
-        const uint32_t n1 = ld_nb<NB_L2>(oth + yp * half + i);
-        const uint32_t n2 = ld_nb<NB_L2>(oth + q);
-        const uint32_t n3 = ld_nb<NB_L2>(oth + y * half + ih);
+        const uint32_t s = own[PT_DBG_IDX(p, q, nwords, kDbgSpinLoad)];  // this lane's word
+        const uint32_t n0 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, ym * half + i, nwords, kDbgSpinLoad));
+        const uint32_t n1 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, yp * half + i, nwords, kDbgSpinLoad));
+        const uint32_t n2 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, q, nwords, kDbgSpinLoad));
+        const uint32_t n3 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, y * half + ih, nwords, kDbgSpinLoad));
         const uint32_t site = (uint32_t)(y * L + 2 * i + par);
         const SiteTerms st = site_terms(site, c3, rk);
         const auto draw = [&](int jb) { return philox_site_block(st, bt, jb, rk); };
         const uint32_t ns =
             update_word_ferro_smem<NB>(s, n0, n1, n2, n3, nblk, thr, alw0, alw1, used, draw);
-        own[q] = ns;
+        if (PT_DBG_STORE(p, q, nwords, own_base, t, colour)) own[q] = ns;
         if (COUNT && count) {
           // with h = 0 the exchange needs only the bonds: U of the new state, all four bonds
           // of this colour-1 site (the colour-0 neighbours are final for this sweep)
@@ -232,7 +236,7 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
     with_block_count(nblk, word_loop);
     if (COUNT && count) {
       const uint32_t u = Uf.warp_total_for_lane();
-      if (u) atomicAdd(&p.cnt[w * 32 + lane], u);
+      if (u) atomicAdd(&p.cnt[PT_DBG_IDX(p, w * 32 + lane, 2 * p.W * 32, kDbgCount)], u);
       if (p.trace_E != nullptr) {
         // a trace row needs M too: the up spins of this lane's colour-1 words and of the
         // colour-0 words one row up, in a second pass
@@ -241,8 +245,8 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
         int yc = q_start / half, ic = q_start - yc * half;
         for (int q = q_start; q < tl.q1; q += 32) {
           const int ym = (yc == 0) ? L - 1 : yc - 1;
-          const uint32_t ns = own[q];
-          const uint32_t n0 = ld_nb<NB_L2>(oth + ym * half + ic);
+          const uint32_t ns = own[PT_DBG_IDX(p, q, nwords, kDbgSpinLoad)];
+          const uint32_t n0 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, ym * half + ic, nwords, kDbgSpinLoad));
           N.add2(ns ^ n0, ns & n0);
           ic += di;
           yc += dy;
@@ -252,7 +256,8 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
           }
         }
         const uint32_t nn = N.warp_total_for_lane();
-        if (nn) atomicAdd(&p.cnt[p.W * 32 + w * 32 + lane], nn);
+        if (nn)
+          atomicAdd(&p.cnt[PT_DBG_IDX(p, p.W * 32 + w * 32 + lane, 2 * p.W * 32, kDbgCount)], nn);
       }
     }
   } else {
@@ -275,16 +280,17 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
         const int ym = (y == 0) ? L - 1 : y - 1;
         const int yp = (y == L - 1) ? 0 : y + 1;
         const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
-        const uint32_t s = own[q];
-        const uint32_t n0 = ld_nb<NB_L2>(oth + ym * half + i);
-        const uint32_t n1 = ld_nb<NB_L2>(oth + yp * half + i);
-        const uint32_t n2 = ld_nb<NB_L2>(oth + q);
-        const uint32_t n3 = ld_nb<NB_L2>(oth + y * half + ih);
+        const uint32_t s = own[PT_DBG_IDX(p, q, nwords, kDbgSpinLoad)];
+        const uint32_t n0 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, ym * half + i, nwords, kDbgSpinLoad));
+        const uint32_t n1 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, yp * half + i, nwords, kDbgSpinLoad));
+        const uint32_t n2 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, q, nwords, kDbgSpinLoad));
+        const uint32_t n3 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, y * half + ih, nwords, kDbgSpinLoad));
         const uint32_t site = (uint32_t)(y * L + 2 * i + par);
         const SiteTerms st = site_terms(site, c3, rk);
-        own[q] = update(s, n0, n1, n2, n3, [&](int jb) {
+        const uint32_t ns = update(s, n0, n1, n2, n3, [&](int jb) {
           return philox_site_block(st, bt, jb, rk);
         });
+        if (PT_DBG_STORE(p, q, nwords, own_base, t, colour)) own[q] = ns;
         i += di;
         y += dy;
         if (i >= half) {
@@ -324,11 +330,12 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
         const int ym = (yc == 0) ? L - 1 : yc - 1;
         const int yp = (yc == L - 1) ? 0 : yc + 1;
         const int ih = par ? ((ic + 1 == half) ? 0 : ic + 1) : ((ic == 0) ? half - 1 : ic - 1);
-        const uint32_t ns = own[q];
-        const uint32_t n0 = ld_nb<NB_L2>(oth + ym * half + ic);
-        const NbCount k = count4(ns ^ n0, ns ^ ld_nb<NB_L2>(oth + yp * half + ic),
-                                 ns ^ ld_nb<NB_L2>(oth + q),
-                                 ns ^ ld_nb<NB_L2>(oth + yc * half + ih));
+        const uint32_t ns = own[PT_DBG_IDX(p, q, nwords, kDbgSpinLoad)];
+        const uint32_t n0 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, ym * half + ic, nwords, kDbgSpinLoad));
+        const NbCount k = count4(
+            ns ^ n0, ns ^ ld_nb<NB_L2>(oth + PT_DBG_IDX(p, yp * half + ic, nwords, kDbgSpinLoad)),
+            ns ^ ld_nb<NB_L2>(oth + PT_DBG_IDX(p, q, nwords, kDbgSpinLoad)),
+            ns ^ ld_nb<NB_L2>(oth + PT_DBG_IDX(p, yc * half + ih, nwords, kDbgSpinLoad)));
         U.add3(k.b0, k.b1, k.b2);
         N.add2(ns ^ n0, ns & n0);
         ic += di;
@@ -340,8 +347,9 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
       }
       const uint32_t u = U.warp_total_for_lane();
       const uint32_t nn = N.warp_total_for_lane();
-      if (u) atomicAdd(&p.cnt[w * 32 + lane], u);
-      if (nn) atomicAdd(&p.cnt[p.W * 32 + w * 32 + lane], nn);
+      if (u) atomicAdd(&p.cnt[PT_DBG_IDX(p, w * 32 + lane, 2 * p.W * 32, kDbgCount)], u);
+      if (nn)
+        atomicAdd(&p.cnt[PT_DBG_IDX(p, p.W * 32 + w * 32 + lane, 2 * p.W * 32, kDbgCount)], nn);
     }
   }
 }

@@ -21,6 +21,7 @@
 #include <stdint.h>
 
 #include "pt.h"
+#include "pt_debug.cuh"
 #include "pt_device.cuh"
 #include "pt_flip.h"
 #include "pt_grid.cuh"
@@ -174,13 +175,16 @@ __global__ void __launch_bounds__(kFlipThreads) k_flip(const __grid_constant__ F
       const int c = (x + y) & 1;
       const int xm = x == 0 ? L - 1 : x - 1, xp = x == L - 1 ? 0 : x + 1;
       const int ym = y == 0 ? L - 1 : y - 1, yp = y == L - 1 ? 0 : y + 1;
-      uint32_t* const sw = plane + ((size_t)c * L + y) * half + (x >> 1);
-      const uint32_t* const oth = plane + (size_t)(c ^ 1) * L * half;
+      const int pw = L * L;  // words of one plane, both colours (the debug checks' range)
+      (void)pw;
+      uint32_t* const sw = plane + PT_DBG_IDX(p, ((size_t)c * L + y) * half + (x >> 1), pw, kDbgFlip);
+      const size_t ob = (size_t)(c ^ 1) * L * half;  // the other colour's first word
       const uint32_t s0 = __ldcg(sw) & bit;
-      const int k = (((__ldcg(oth + (size_t)y * half + (xm >> 1)) & bit) ^ s0) != 0) +
-                    (((__ldcg(oth + (size_t)y * half + (xp >> 1)) & bit) ^ s0) != 0) +
-                    (((__ldcg(oth + (size_t)ym * half + (x >> 1)) & bit) ^ s0) != 0) +
-                    (((__ldcg(oth + (size_t)yp * half + (x >> 1)) & bit) ^ s0) != 0);
+      const int k =
+          (((__ldcg(plane + PT_DBG_IDX(p, ob + (size_t)y * half + (xm >> 1), pw, kDbgFlip)) & bit) ^ s0) != 0) +
+          (((__ldcg(plane + PT_DBG_IDX(p, ob + (size_t)y * half + (xp >> 1), pw, kDbgFlip)) & bit) ^ s0) != 0) +
+          (((__ldcg(plane + PT_DBG_IDX(p, ob + (size_t)ym * half + (x >> 1), pw, kDbgFlip)) & bit) ^ s0) != 0) +
+          (((__ldcg(plane + PT_DBG_IDX(p, ob + (size_t)yp * half + (x >> 1), pw, kDbgFlip)) & bit) ^ s0) != 0);
       const int up = s0 != 0;
       const uint64_t T = p.T_temp[(size_t)tos[r] * kClasses + 2 * k + up];
       if ((uint64_t)u.y < T) {
@@ -282,7 +286,8 @@ __global__ void __launch_bounds__(kFlipSmemThreads) k_flip_smem(const __grid_con
   const int nsites = L * L;
   auto word_of = [&](int site) {
     const int y = site / L, x = site - y * L;
-    return plane + ((size_t)((x + y) & 1) * L + y) * half + (x >> 1);
+    return plane + PT_DBG_IDX(p, ((size_t)((x + y) & 1) * L + y) * half + (x >> 1), L * L,
+                              kDbgFlip);
   };
   // bit-array word w of every replica: 32 sites, one plane word each
   for (int w = tid; w < words_per_rep; w += blockDim.x) {

@@ -20,6 +20,7 @@
 
 #include "pt.h"
 #include "pt_batch.h"
+#include "pt_debug.cuh"
 #include "pt_internal.h"
 #include "pt_launch.h"
 #include "pt_flip.h"
@@ -912,6 +913,29 @@ int pt_create_ex(int L, const double* betas, int R, double J, double h, uint64_t
   d.pairs = (const SwapPair*)(base + lay.pairs);
   d.swap_table = (const uint32_t*)(base + lay.table);
   d.status = (int32_t*)(base + lay.status);
+#ifdef PT_DEBUG
+  // the debug build's write tags (one per spin word) and check record, zeroed
+  {
+    const size_t tag_bytes = align256((size_t)p->W * L * L * 4);
+    Allocator dused;
+    void* dm = dev_alloc(tag_bytes + sizeof(DebugRecord), p->stream, &dused);
+    if (!dm) {
+      dev_free(mem, p->stream, used);
+      return fail(PT_ENOMEM, "debug build: allocation of the write tags failed");
+    }
+    p->dbg_mem = dm;
+    p->dbg_free = dused.free;
+    p->dbg_ctx = dused.ctx;
+    d.dbg_tag = (uint32_t*)dm;
+    d.dbg = (DebugRecord*)((uint8_t*)dm + tag_bytes);
+    if (cudaMemsetAsync(dm, 0, tag_bytes + sizeof(DebugRecord), p->stream) != cudaSuccess) {
+      cudaGetLastError();
+      dev_free(dm, p->stream, dused);
+      dev_free(mem, p->stream, used);
+      return fail(PT_ECUDA, "debug build: clearing the write tags failed");
+    }
+  }
+#endif
 
   // one copy of the image (asynchronous from page-locked memory; from pageable memory the
   // call returns once the bytes are staged), the initial spins and the plane thresholds
@@ -925,6 +949,12 @@ int pt_create_ex(int L, const double* betas, int R, double J, double h, uint64_t
     cudaStreamSynchronize(p->stream);
     cudaGetLastError();
     dev_free(mem, p->stream, used);
+    if (p->dbg_mem) {
+      Allocator da;
+      da.free = p->dbg_free;
+      da.ctx = p->dbg_ctx;
+      dev_free(p->dbg_mem, p->stream, da);
+    }
     return fail(PT_ECUDA, "initialising problem: %s", cudaGetErrorString(err));
   }
   if (img->locked) p->image = img;
@@ -947,6 +977,10 @@ void pt_destroy(pt_problem* p) {
   ta.free = p->trace_free;
   ta.ctx = p->trace_ctx;
   dev_free(p->trace_mem, p->stream, ta);
+  Allocator da;
+  da.free = p->dbg_free;
+  da.ctx = p->dbg_ctx;
+  dev_free(p->dbg_mem, p->stream, da);
   if (cur >= 0 && cur != p->dev_info.device) cudaSetDevice(cur);
   delete p;
 }
@@ -1002,6 +1036,7 @@ int pt_sweep(pt_problem* p, int64_t n, int exchange_every) {
   }
   for (int64_t j = 0; j < n; ++j) {
     cudaError_t err = launch_half_sweep(p->dev, p->dev_info, 0, p->t, p->stream);
+    p->dev.dbg_inject = 0;  // the debug build's test hook applies to one launch
     if (err == cudaSuccess) err = launch_half_sweep(p->dev, p->dev_info, 1, p->t, p->stream);
     if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "sweep launch", err);
     const bool ex = exchange_every > 0 && (p->t + 1) % (uint64_t)exchange_every == 0;
@@ -1122,8 +1157,53 @@ int pt_synchronize(pt_problem* p) {
   if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "reading status", err);
   if (status != 0) {
     p->poisoned = status == PT_ETIMEOUT ? PT_ETIMEOUT : PT_EINTERNAL;
-    return fail(p->poisoned, "device reported status %d", status);
+    return fail(p->poisoned, "device reported status %d%s", status,
+                status == kStatusDebug ? " (a check of the debug build failed)" : "");
   }
+  return PT_OK;
+}
+
+int pt_debug_build(void) { return PT_DBG_ON; }
+
+int pt_debug_report(pt_problem* p, uint64_t* violations, int32_t* first_kind,
+                    uint64_t* first_index, uint64_t* unwritten) {
+  if (!p) return fail(PT_EINVAL, "problem is NULL");
+  if (!PT_DBG_ON || !p->dbg_mem)
+    return fail(PT_EINVAL, "pt_debug_report needs the debug build of the library");
+  int rc = problem_device_guard(p);
+  if (rc) return rc;
+  cudaError_t err = cudaStreamSynchronize(p->stream);
+  DebugRecord rec{};
+  if (err == cudaSuccess)
+    err = cudaMemcpy(&rec, p->dev.dbg, sizeof(DebugRecord), cudaMemcpyDeviceToHost);
+  // the last sweep must have stored every word of colour c in half sweep 2 (t - 1) + c
+  uint64_t missing = 0;
+  if (err == cudaSuccess && p->t > p->dbg_t0) {
+    const size_t n = (size_t)p->W * p->L * p->L;
+    std::vector<uint32_t> tag(n);
+    err = cudaMemcpy(tag.data(), p->dev.dbg_tag, n * 4, cudaMemcpyDeviceToHost);
+    const size_t nc = (size_t)p->L * (p->L / 2);
+    for (size_t g = 0; err == cudaSuccess && g < n; ++g) {
+      const uint64_t c = (g / nc) & 1;
+      const uint32_t want = (uint32_t)((2 * (p->t - 1) + c) % 0x7fffffffull) + 1u;
+      missing += tag[g] != want;
+    }
+  }
+  if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "reading the debug record", err);
+  if (violations) *violations = rec.violations;
+  if (first_kind) *first_kind = (int32_t)rec.first_kind;
+  if (first_index) *first_index = rec.first_index;
+  if (unwritten) *unwritten = missing;
+  return PT_OK;
+}
+
+int pt_debug_inject(pt_problem* p, int kind) {
+  int rc = problem_check(p);
+  if (rc) return rc;
+  if (!PT_DBG_ON || !p->dbg_mem)
+    return fail(PT_EINVAL, "pt_debug_inject needs the debug build of the library");
+  if (kind < 0 || kind > 2) return fail(PT_EINVAL, "unknown planted mistake %d", kind);
+  p->dev.dbg_inject = kind;
   return PT_OK;
 }
 
@@ -1232,7 +1312,8 @@ int pt_read_batch(pt_problem* const* ps, int count, int64_t* const* E_int, int64
     for (int w = 0; w < d.W; ++w)
       for (int first = 0; first < nwords; first += kEnergyChunkWords)
         chunks.push_back(EnergyChunk{d.spins, d.cnt, d.L, d.W, w, first,
-                                     std::min(kEnergyChunkWords, nwords - first)});
+                                     std::min(kEnergyChunkWords, nwords - first), d.dbg,
+                                     d.status});
   }
   if (chunks.size() > (size_t)INT32_MAX) return fail(PT_EINVAL, "batched read too large");
   const int nitems = (int)items.size();
@@ -1456,6 +1537,7 @@ int pt_load(const void* buf, size_t bytes, pt_problem** out) {
   p->t = t;
   p->e = e;
   p->it = it;
+  p->dbg_t0 = t;  // the debug build's tags start with the next sweep
   *out = p;
   return PT_OK;
 }

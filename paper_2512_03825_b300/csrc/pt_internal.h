@@ -34,6 +34,10 @@ struct pt_problem {
   ptb::PersistPlan plan{};
   uint64_t wait_limit_ns = 1000000000ull;
   int stall = 0;            // pt_debug_stall_barrier, one launch
+  void* dbg_mem = nullptr;    // debug build: write tags and the check record, own allocation
+  pt_free_fn dbg_free = nullptr;
+  void* dbg_ctx = nullptr;
+  uint64_t dbg_t0 = 0;        // debug build: sweeps done when the tags were last cleared
   void* trace_mem = nullptr;  // observable trace ring (dev.trace_E / trace_M), own allocation
   size_t trace_bytes = 0;
   pt_free_fn trace_free = nullptr;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "pt_debug.cuh"
 #include "pt_device.cuh"
 #include "pt_launch.h"
 
@@ -50,6 +51,7 @@ __global__ void __launch_bounds__(kThreads) k_init(DevProblem p) {
   const uint32_t used = used_mask(nslots);
   uint32_t* out = p.spins + word_index(L, w, c, 0, 0);
   const int nwords = L * half;
+  PT_DBG_CHECK(p, w, p.W, kDbgSpinStore);
   const int start = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
   if (start >= nwords) return;
@@ -66,7 +68,7 @@ __global__ void __launch_bounds__(kThreads) k_init(DevProblem p) {
                 ((r.z >> 31) << (4 * j + 2)) | ((r.w >> 31) << (4 * j + 3));
       }
     }
-    out[idx] = word & used;
+    out[PT_DBG_IDX(p, idx, nwords, kDbgSpinStore)] = word & used;
   }
 }
 
@@ -81,11 +83,16 @@ __global__ void __launch_bounds__(kThreads) k_half_sweep(DevProblem p, int colou
   const int nslots = nslots_of_plane(p.R, w);
   const int nblk = (nslots + 3) >> 2;
   const SweepCtr cx = make_sweep_ctr(t, p.key0, p.key1);
-  uint32_t* own = p.spins + word_index(L, w, colour, 0, 0);
+  const size_t own_base = word_index(L, w, colour, 0, 0);
+  uint32_t* own = p.spins + own_base;
   const uint32_t* oth = p.spins + word_index(L, w, colour ^ 1, 0, 0);
   const int nwords = L * half;
   const int start = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
+  // test hook of the debug build: one planted mistake in this launch (thread 0 only), which
+  // the checks must catch: 1 stores its first word a second time (unchanged), 2 asks for a
+  // neighbour one past the colour's words
+  const int inject = (PT_DBG_ON && start == 0) ? p.dbg_inject : 0;
 
   if (MODE == kModeFerro) {
     const PlaneFerro* pl = reinterpret_cast<const PlaneFerro*>(p.planes) + w;
@@ -104,14 +111,18 @@ __global__ void __launch_bounds__(kThreads) k_half_sweep(DevProblem p, int colou
       const int ym = (y == 0) ? L - 1 : y - 1;
       const int yp = (y == L - 1) ? 0 : y + 1;
       const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
-      const uint32_t s = own[idx];
-      const uint32_t n0 = oth[ym * half + i];
-      const uint32_t n1 = oth[yp * half + i];
-      const uint32_t n2 = oth[y * half + i];
-      const uint32_t n3 = oth[y * half + ih];
+      const uint32_t s = own[PT_DBG_IDX(p, idx, nwords, kDbgSpinLoad)];
+      const uint32_t n0 = oth[PT_DBG_IDX(p, ym * half + i, nwords, kDbgSpinLoad)];
+      const uint32_t n1 = oth[PT_DBG_IDX(p, yp * half + i, nwords, kDbgSpinLoad)];
+      const uint32_t n2 = oth[PT_DBG_IDX(p, y * half + i, nwords, kDbgSpinLoad)];
+      const uint32_t n3 = oth[PT_DBG_IDX(p, (inject == 2 ? nwords : y * half + ih), nwords,
+                                         kDbgSpinLoad)];
       const uint32_t site = (uint32_t)(y * L + 2 * i + par);
-      own[idx] = update_word_ferro(s, n0, n1, n2, n3, site, (uint32_t)(8 * w), nblk, T0, T1,
-                                   alw0, alw1, used, cx);
+      const uint32_t ns = update_word_ferro(s, n0, n1, n2, n3, site, (uint32_t)(8 * w), nblk,
+                                            T0, T1, alw0, alw1, used, cx);
+      if (PT_DBG_STORE(p, idx, nwords, own_base, t, colour)) own[idx] = ns;
+      if (inject == 1 && idx == start && PT_DBG_STORE(p, idx, nwords, own_base, t, colour))
+        own[idx] = ns;
     }
   } else {
     __shared__ PlaneGeneric pl;
@@ -128,13 +139,15 @@ __global__ void __launch_bounds__(kThreads) k_half_sweep(DevProblem p, int colou
       const int ym = (y == 0) ? L - 1 : y - 1;
       const int yp = (y == L - 1) ? 0 : y + 1;
       const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
-      const uint32_t s = own[idx];
-      const uint32_t n0 = oth[ym * half + i];
-      const uint32_t n1 = oth[yp * half + i];
-      const uint32_t n2 = oth[y * half + i];
-      const uint32_t n3 = oth[y * half + ih];
+      const uint32_t s = own[PT_DBG_IDX(p, idx, nwords, kDbgSpinLoad)];
+      const uint32_t n0 = oth[PT_DBG_IDX(p, ym * half + i, nwords, kDbgSpinLoad)];
+      const uint32_t n1 = oth[PT_DBG_IDX(p, yp * half + i, nwords, kDbgSpinLoad)];
+      const uint32_t n2 = oth[PT_DBG_IDX(p, y * half + i, nwords, kDbgSpinLoad)];
+      const uint32_t n3 = oth[PT_DBG_IDX(p, y * half + ih, nwords, kDbgSpinLoad)];
       const uint32_t site = (uint32_t)(y * L + 2 * i + par);
-      own[idx] = update_word_generic(s, n0, n1, n2, n3, site, (uint32_t)(8 * w), nblk, pl, cx);
+      const uint32_t ns =
+          update_word_generic(s, n0, n1, n2, n3, site, (uint32_t)(8 * w), nblk, pl, cx);
+      if (PT_DBG_STORE(p, idx, nwords, own_base, t, colour)) own[idx] = ns;
     }
   }
 }
@@ -150,8 +163,14 @@ constexpr int kMaxWordsPerThread = 4000;  // 4 * 4000 < 2^14 (per-thread counter
 // The counts of colour-0 words start, start + stride, ... below end of plane w, added to
 // cnt (one call per block).
 __device__ __forceinline__ void energy_count(const uint32_t* spins, uint32_t* cnt, int L, int W,
-                                             int w, int start, int stride, int end) {
+                                             int w, int start, int stride, int end,
+                                             DbgSink dbg) {
+  (void)dbg;
   const int half = L >> 1;
+  const int nwords = L * half;
+  (void)nwords;
+  PT_DBG_CHECK(dbg, w, W, kDbgSpinLoad);
+  PT_DBG_CHECK(dbg, end - 1, nwords, kDbgSpinLoad);
   const uint32_t* c0 = spins + word_index(L, w, 0, 0, 0);
   const uint32_t* c1 = spins + word_index(L, w, 1, 0, 0);
   BitCounter<20, 14> U, N;
@@ -165,10 +184,12 @@ __device__ __forceinline__ void energy_count(const uint32_t* spins, uint32_t* cn
       const int ym = (y == 0) ? L - 1 : y - 1;
       const int yp = (y == L - 1) ? 0 : y + 1;
       const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
-      const uint32_t s = c0[idx];
-      const uint32_t o = c1[idx];
-      const NbCount k = count4(s ^ c1[ym * half + i], s ^ c1[yp * half + i], s ^ o,
-                               s ^ c1[y * half + ih]);
+      const uint32_t s = c0[PT_DBG_IDX(dbg, idx, nwords, kDbgSpinLoad)];
+      const uint32_t o = c1[PT_DBG_IDX(dbg, idx, nwords, kDbgSpinLoad)];
+      const NbCount k = count4(s ^ c1[PT_DBG_IDX(dbg, ym * half + i, nwords, kDbgSpinLoad)],
+                               s ^ c1[PT_DBG_IDX(dbg, yp * half + i, nwords, kDbgSpinLoad)],
+                               s ^ o,
+                               s ^ c1[PT_DBG_IDX(dbg, y * half + ih, nwords, kDbgSpinLoad)]);
       U.add3(k.b0, k.b1, k.b2);
       N.add2(s ^ o, s & o);
     }
@@ -183,21 +204,25 @@ __device__ __forceinline__ void energy_count(const uint32_t* spins, uint32_t* cn
   atomicAdd(&acc[1][lane], n);
   __syncthreads();
   if (threadIdx.x < 32) {
-    if (acc[0][threadIdx.x]) atomicAdd(&cnt[w * 32 + threadIdx.x], acc[0][threadIdx.x]);
-    if (acc[1][threadIdx.x]) atomicAdd(&cnt[W * 32 + w * 32 + threadIdx.x], acc[1][threadIdx.x]);
+    if (acc[0][threadIdx.x])
+      atomicAdd(&cnt[PT_DBG_IDX(dbg, w * 32 + threadIdx.x, 2 * W * 32, kDbgCount)],
+                acc[0][threadIdx.x]);
+    if (acc[1][threadIdx.x])
+      atomicAdd(&cnt[PT_DBG_IDX(dbg, W * 32 + w * 32 + threadIdx.x, 2 * W * 32, kDbgCount)],
+                acc[1][threadIdx.x]);
   }
 }
 
 __global__ void __launch_bounds__(kThreads) k_energy(DevProblem p) {
   energy_count(p.spins, p.cnt, p.L, p.W, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x,
-               gridDim.x * blockDim.x, p.L * (p.L >> 1));
+               gridDim.x * blockDim.x, p.L * (p.L >> 1), DbgSink{p.dbg, p.status});
 }
 
 // One chunk per block: kEnergyChunkWords / kThreads = 8 words per thread.
 __global__ void __launch_bounds__(kThreads) k_energy_batch(const EnergyChunk* __restrict__ chunks) {
   const EnergyChunk c = chunks[blockIdx.x];
   energy_count(c.spins, c.cnt, c.L, c.W, c.w, c.first + (int)threadIdx.x, blockDim.x,
-               c.first + c.count);
+               c.first + c.count, DbgSink{c.dbg, c.status});
 }
 
 // ---------------------------------------------------------------------------------------
@@ -294,8 +319,9 @@ __global__ void __launch_bounds__(kThreads) k_exchange(DevProblem p, uint64_t e,
     const int64_t row = (int64_t)((t - p.trace_t0) % (uint64_t)p.trace_cap);
     for (int r = threadIdx.x; r < R; r += blockDim.x) {
       const int k = p.temp_of_slot[r];
-      p.trace_E[row * R + k] = p.E_slot[r];
-      p.trace_M[row * R + k] = p.M_slot[r];
+      const int64_t at = PT_DBG_IDX(p, row * R + k, p.trace_cap * R, kDbgTrace);
+      p.trace_E[at] = p.E_slot[r];
+      p.trace_M[at] = p.M_slot[r];
     }
   }
 }

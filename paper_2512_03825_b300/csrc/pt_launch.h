@@ -55,6 +55,8 @@ struct EnergyChunk {
   const uint32_t* spins;
   uint32_t* cnt;
   int L, W, w, first, count;
+  DebugRecord* dbg;  // the debug build's record and status word of the problem (else unused)
+  int32_t* status;
 };
 constexpr int kEnergyChunkWords = 2048;
 // Counts unsatisfied bonds and up spins of every chunk into its problem's cnt (one block

@@ -38,6 +38,7 @@
 #include <stdint.h>
 
 #include "pt.h"
+#include "pt_debug.cuh"
 #include "pt_device.cuh"
 #include "pt_grid.cuh"
 #include "pt_persist.h"
@@ -156,6 +157,8 @@ __device__ __forceinline__ void half_pass(const DevProblem& p, uint32_t* plane, 
   const int nblk = (min(32, p.R - 32 * w) + 3) >> 2;
   uint32_t* own = plane + (size_t)colour * nwords;
   const uint32_t* oth = plane + (size_t)(colour ^ 1) * nwords;
+  const size_t own_base = word_index(L, w, colour, 0, 0);  // own's first word in p.spins
+  (void)own_base;
   const auto nb = [&](const uint32_t* q) { return LOCAL ? *q : __ldcg(q); };
   int y = y0, i = i0;
   for (int q = q0; q < nwords; q += step) {
@@ -163,11 +166,11 @@ __device__ __forceinline__ void half_pass(const DevProblem& p, uint32_t* plane, 
     const int ym = (y == 0) ? L - 1 : y - 1;
     const int yp = (y == L - 1) ? 0 : y + 1;
     const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
-    const uint32_t s = own[q];
-    const uint32_t n0 = nb(oth + ym * half + i);
-    const uint32_t n1 = nb(oth + yp * half + i);
-    const uint32_t n2 = nb(oth + q);
-    const uint32_t n3 = nb(oth + y * half + ih);
+    const uint32_t s = own[PT_DBG_IDX(p, q, nwords, kDbgSpinLoad)];
+    const uint32_t n0 = nb(oth + PT_DBG_IDX(p, ym * half + i, nwords, kDbgSpinLoad));
+    const uint32_t n1 = nb(oth + PT_DBG_IDX(p, yp * half + i, nwords, kDbgSpinLoad));
+    const uint32_t n2 = nb(oth + PT_DBG_IDX(p, q, nwords, kDbgSpinLoad));
+    const uint32_t n3 = nb(oth + PT_DBG_IDX(p, y * half + ih, nwords, kDbgSpinLoad));
     const uint32_t site = (uint32_t)(y * L + 2 * i + par);
     const SiteTerms st = site_terms(site, c3, rk);
     const auto draw = [&](int j) { return philox_site_block(st, bt, j, rk); };
@@ -178,7 +181,7 @@ __device__ __forceinline__ void half_pass(const DevProblem& p, uint32_t* plane, 
       ns = update_word_generic_cmp<5>(s, n0, n1, n2, n3, nblk, gen, cls5, draw);
     else
       ns = update_word_generic_with(s, n0, n1, n2, n3, nblk, gen, draw);
-    own[q] = ns;
+    if (PT_DBG_STORE(p, q, nwords, own_base, t, colour)) own[q] = ns;
     if (COUNT) {
       const NbCount k = count4(ns ^ n0, ns ^ n1, ns ^ n2, ns ^ n3);
       U.add3(k.b0, k.b1, k.b2);
@@ -224,6 +227,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
   uint32_t* const plane_s = reinterpret_cast<uint32_t*>(
       reinterpret_cast<unsigned char*>(map_s) + ((maps_bytes + 15) & ~size_t(15)));
   uint32_t* const plane = LOCAL ? plane_s : plane_g;
+  PT_DBG_CHECK(p, w, W, kDbgSpinLoad);
   if (LOCAL) {
     for (int q = threadIdx.x; q < plane_words; q += blockDim.x) plane_s[q] = plane_g[q];
     __syncthreads();
@@ -325,8 +329,12 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
     if (nn) atomicAdd(&acc[1][lane], nn);
     __syncthreads();
     if (threadIdx.x < 32) {
-      if (acc[0][threadIdx.x]) atomicAdd(&cb[w * 32 + threadIdx.x], acc[0][threadIdx.x]);
-      if (acc[1][threadIdx.x]) atomicAdd(&cb[W * 32 + w * 32 + threadIdx.x], acc[1][threadIdx.x]);
+      if (acc[0][threadIdx.x])
+        atomicAdd(&cb[PT_DBG_IDX(p, w * 32 + threadIdx.x, 2 * W * 32, kDbgCount)],
+                  acc[0][threadIdx.x]);
+      if (acc[1][threadIdx.x])
+        atomicAdd(&cb[PT_DBG_IDX(p, W * 32 + w * 32 + threadIdx.x, 2 * W * 32, kDbgCount)],
+                  acc[1][threadIdx.x]);
     }
     if (!sync_all(0)) return flush();
     if (ex) exchange_local(p, e, cb, sot, tos, blockIdx.x == 0);
@@ -337,8 +345,9 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
         const int64_t row = (int64_t)((t - p.trace_t0) % (uint64_t)p.trace_cap);
         for (int r = threadIdx.x; r < R; r += blockDim.x) {
           const int64_t U_r = __ldcg(cb + r), ones = __ldcg(cb + W * 32 + r);
-          p.trace_E[row * R + tos[r]] = slot_energy(p, L2, U_r, ones);
-          p.trace_M[row * R + tos[r]] = 2 * ones - L2;
+          const int64_t at = PT_DBG_IDX(p, row * R + tos[r], p.trace_cap * R, kDbgTrace);
+          p.trace_E[at] = slot_energy(p, L2, U_r, ones);
+          p.trace_M[at] = 2 * ones - L2;
         }
       }
       // the other buffer was last read after the previous counted sweep, before this

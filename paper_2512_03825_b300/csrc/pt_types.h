@@ -53,6 +53,14 @@ struct SwapPair {
   int64_t offset;
 };
 
+// The debug build's record of failed checks (PT_DEBUG; see pt_debug.cuh).
+struct DebugRecord {
+  unsigned long long violations;   // checks that failed
+  unsigned long long first_index;  // the index the first failed check was given
+  unsigned int first_kind;         // DebugKind of the first failed check (0: none)
+  unsigned int pad;
+};
+
 // Device-side view of one problem (all pointers are device memory).
 struct DevProblem {
   uint32_t* spins;         // [W][2][L][L/2]
@@ -80,6 +88,15 @@ struct DevProblem {
   int64_t* trace_M;
   int64_t trace_cap;
   uint64_t trace_t0;
+  // debug build only (null / 0 otherwise): per spin word, the number of the half sweep that
+  // last wrote it (2 t + colour, mod 2^31 - 1, plus 1); the record of failed checks; a test
+  // hook that makes the next launch of the plain half-sweep kernel perform one planted
+  // mistake that its checks must catch (1: a second store of an unchanged word, 2: a
+  // neighbour index one past its colour)
+  uint32_t* dbg_tag;
+  DebugRecord* dbg;
+  int32_t dbg_inject;
+  int32_t dbg_pad;
 };
 
 }  // namespace ptb

@@ -248,3 +248,11 @@ def test_getters_reject_a_null_problem(pt):
     assert pt.lib.pt_temperature_map(None, out32) == pt.PT_EINVAL
     assert pt.lib.pt_energies(None, outd) == pt.PT_EINVAL
     assert pt.lib.pt_energies_int(None, out64, None, None) == pt.PT_EINVAL
+
+
+def test_release_library_has_no_debug_checks(pt):
+    # the release library compiles none of the debug build's checks, and its debug entry points
+    # refuse (a NULL problem is refused before anything else)
+    assert pt.lib.pt_debug_build() == 0
+    assert pt.lib.pt_debug_report(None, None, None, None, None) == pt.PT_EINVAL
+    assert pt.lib.pt_debug_inject(None, 1) != 0
