@@ -646,11 +646,13 @@ def run_converge(args, rank, world, stream):
     barrier(world)
     clocks.start()
     t0 = time.perf_counter()
-    res = CV.measure(api, Ls, seeds, R=32, every=1, stream=stream)
+    details = {}
+    res = CV.measure(api, Ls, seeds, R=32, every=1, stream=stream, details=details)
     torch.cuda.synchronize()
     wall = max_over_ranks(time.perf_counter() - t0, world)
     clk = clocks.stop()
     summ = CV.summarise(res, CV.default_caps(Ls))
+    summ["slowest_temperature_index"] = CV.slowest_temperatures(details)
     return {"metric": "sweeps to converge against L (Fig. 3b): fitted exponent of the median",
             "value": summ.get("exponent_sweeps"), "unit": "exponent (t* ~ L^value sweeps)",
             "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * wall,

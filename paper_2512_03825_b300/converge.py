@@ -22,7 +22,6 @@ runs in the CUDA library; this module only schedules runs and reads their traces
 from __future__ import annotations
 
 import dataclasses
-import math
 from typing import Dict, List, Optional, Sequence
 
 import numpy as np
@@ -94,12 +93,14 @@ class Run:
 
 def measure(api, Ls: Sequence[int], seeds: Sequence[int], R: int = 32, every: int = 1,
             cap_factor: float = 8.0, cap_min: int = 2000, stream=None,
-            chunk_factor: float = 0.25, chunk_min: int = 200) -> Dict[int, List[int]]:
+            chunk_factor: float = 0.25, chunk_min: int = 200,
+            details: Optional[dict] = None) -> Dict[int, List[int]]:
     """Sweeps to convergence t* for every L and seed, on the GPU. Every (L, seed) runs as a
     hot/cold pair; all pairs advance together through pt_sweep_batch in chunks of
     max(chunk_min, chunk_factor L^2) sweeps of their own size class, and a pair leaves the
     batch once every temperature has converged, or after max(cap_min, cap_factor L^2) sweeps
-    (then its t* is NOT_YET: censored). Returns {L: [t* per seed]}."""
+    (then its t* is NOT_YET: censored). Returns {L: [t* per seed]}; with `details`, also
+    fills details[(L, seed)] with the per-temperature convergence sweeps."""
     runs: List[Run] = []
     cap = {L: int(max(cap_min, cap_factor * L * L)) for L in Ls}
     chunk = {L: int(max(chunk_min, chunk_factor * L * L)) for L in Ls}
@@ -136,6 +137,8 @@ def measure(api, Ls: Sequence[int], seeds: Sequence[int], R: int = 32, every: in
     out: Dict[int, List[int]] = {L: [] for L in Ls}
     for r in runs:
         out[r.L].append(r.t_star)
+        if details is not None:
+            details[(r.L, r.seed)] = r.per_temperature.tolist()
         r.hot.close()
         r.cold.close()
     return out
@@ -163,12 +166,24 @@ def summarise(result: Dict[int, List[int]], caps: Optional[Dict[int, int]] = Non
         e = fit_exponent(Ls, med)
         out["exponent_sweeps"] = e
         out["exponent_iterations"] = e + 2.0
+    if len(Ls) >= 3 and all(m > 0 for m in med):
+        out["exponent_sweeps_without_largest"] = fit_exponent(Ls[:-1], med[:-1])
+    return out
+
+
+def slowest_temperatures(details: dict) -> dict:
+    """Per L: how often each temperature index was the last to converge, as
+    {L: {index: runs}} (a run that has not converged at every temperature is left out)."""
+    out: Dict[str, Dict[str, int]] = {}
+    for (L, _), per_k in sorted(details.items()):
+        per_k = np.asarray(per_k)
+        if (per_k == NOT_YET).any():
+            continue
+        k = int(per_k.argmax())
+        row = out.setdefault(str(L), {})
+        row[str(k)] = row.get(str(k), 0) + 1
     return out
 
 
 def default_caps(Ls: Sequence[int], cap_factor: float = 8.0, cap_min: int = 2000) -> dict:
     return {L: int(max(cap_min, cap_factor * L * L)) for L in Ls}
-
-
-def log2_sizes(lo: int, hi: int) -> List[int]:
-    return [1 << k for k in range(int(math.log2(lo)), int(math.log2(hi)) + 1)]

@@ -201,36 +201,54 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
     // (measured: 131.5 -> 122.9 us per batched-256 sweep without swaps; with the wide
     // multiplies the counting kernel gains from it too, 135.3 -> 134.0 us per sweep with a
     // swap iteration, where before it cost registers and time)
+    // the inputs of one word: the lane's word, its four neighbours (other colour) and site
+    struct WordIn {
+      uint32_t s, n0, n1, n2, n3, site;
+    };
+    const auto load_word = [&](int q, int yy, int ii) {
+      const int par = (yy + colour) & 1;
+      const int ym = (yy == 0) ? L - 1 : yy - 1;
+      const int yp = (yy == L - 1) ? 0 : yy + 1;
+      const int ih = par ? ((ii + 1 == half) ? 0 : ii + 1) : ((ii == 0) ? half - 1 : ii - 1);
+      WordIn a;
+      a.s = own[PT_DBG_IDX(p, q, nwords, kDbgSpinLoad)];  // this lane's word
+      a.n0 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, ym * half + ii, nwords, kDbgSpinLoad));
+      a.n1 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, yp * half + ii, nwords, kDbgSpinLoad));
+      a.n2 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, q, nwords, kDbgSpinLoad));
+      a.n3 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, yy * half + ih, nwords, kDbgSpinLoad));
+      a.site = (uint32_t)(yy * L + 2 * ii + par);
+      return a;
+    };
+    const auto step = [&]() {
+      i += di;
+      y += dy;
+      if (i >= half) {
+        i -= half;
+        y += 1;
+      }
+    };
+    const auto finish_word = [&](int q, const WordIn& a, uint32_t ns) {
+      if (PT_DBG_STORE(p, q, nwords, own_base, t, colour)) own[q] = ns;
+      if (COUNT && count) {
+        // with h = 0 the exchange needs only the bonds: U of the new state, all four bonds
+        // of this colour-1 site (the colour-0 neighbours are final for this sweep)
+        const NbCount k = count4(ns ^ a.n0, ns ^ a.n1, ns ^ a.n2, ns ^ a.n3);
+        Uf.add3(k.b0, k.b1, k.b2);
+      }
+    };
     const auto word_loop = [&](auto nbc) {
       constexpr int NB = decltype(nbc)::value;
-      for (int q = q_start; q < tl.q1; q += 32) {
-        const int par = (y + colour) & 1;
-        const int ym = (y == 0) ? L - 1 : y - 1;
-        const int yp = (y == L - 1) ? 0 : y + 1;
-        const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
-        const uint32_t s = own[PT_DBG_IDX(p, q, nwords, kDbgSpinLoad)];  // this lane's word
-        const uint32_t n0 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, ym * half + i, nwords, kDbgSpinLoad));
-        const uint32_t n1 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, yp * half + i, nwords, kDbgSpinLoad));
-        const uint32_t n2 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, q, nwords, kDbgSpinLoad));
-        const uint32_t n3 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, y * half + ih, nwords, kDbgSpinLoad));
-        const uint32_t site = (uint32_t)(y * L + 2 * i + par);
-        const SiteTerms st = site_terms(site, c3, rk);
+      const auto update = [&](const WordIn& a) {
+        const SiteTerms st = site_terms(a.site, c3, rk);
         const auto draw = [&](int jb) { return philox_site_block(st, bt, jb, rk); };
-        const uint32_t ns =
-            update_word_ferro_smem<NB>(s, n0, n1, n2, n3, nblk, thr, alw0, alw1, used, draw);
-        if (PT_DBG_STORE(p, q, nwords, own_base, t, colour)) own[q] = ns;
-        if (COUNT && count) {
-          // with h = 0 the exchange needs only the bonds: U of the new state, all four bonds
-          // of this colour-1 site (the colour-0 neighbours are final for this sweep)
-          const NbCount k = count4(ns ^ n0, ns ^ n1, ns ^ n2, ns ^ n3);
-          Uf.add3(k.b0, k.b1, k.b2);
-        }
-        i += di;
-        y += dy;
-        if (i >= half) {
-          i -= half;
-          y += 1;
-        }
+        return update_word_ferro_smem<NB>(a.s, a.n0, a.n1, a.n2, a.n3, nblk, thr, alw0, alw1,
+                                          used, draw);
+      };
+      int q = q_start;
+      for (; q < tl.q1; q += 32) {
+        const WordIn a = load_word(q, y, i);
+        finish_word(q, a, update(a));
+        step();
       }
     };
     with_block_count(nblk, word_loop);
@@ -272,7 +290,8 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
       __syncwarp();
     }
     // the generic kernel keeps the block count at run time: with it fixed (one loop per
-    // count) a batch with a field ran 17% slower
+    // count) a batch with a field ran 17% slower (with the wide multiplies: 31% slower); its
+    // bond count stays a second pass (counting in the word loop measured no faster)
     const PlaneGeneric& pl = *gen;
     const auto gen_loop = [&](const auto& update) {
       for (int q = q_start; q < tl.q1; q += 32) {

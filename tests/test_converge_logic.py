@@ -73,3 +73,8 @@ def test_oracle_runs_converge_on_a_small_lattice():
     assert (per_k != CV.NOT_YET).all()
     assert per_k[-1] <= 20
     assert CV.converged_at(per_k) == per_k.max()
+
+
+def test_slowest_temperature_counts():
+    det = {(16, 1): [3, 9, 4], (16, 2): [8, 2, 1], (32, 1): [5, 6, CV.NOT_YET]}
+    assert CV.slowest_temperatures(det) == {"16": {"1": 1, "0": 1}}
