@@ -205,18 +205,22 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
     struct WordIn {
       uint32_t s, n0, n1, n2, n3, site;
     };
+    // the neighbours as offsets from the lane's own word q = yy * half + ii (rows yy - 1 and
+    // yy + 1 at the same ii, row yy at ii -+ 1 by the row parity, all mod L): no multiplies
+    // (measured: 2% fewer instructions than row * half + column addressing)
+    const int wrap = nwords - half;  // (L - 1) * half
     const auto load_word = [&](int q, int yy, int ii) {
       const int par = (yy + colour) & 1;
-      const int ym = (yy == 0) ? L - 1 : yy - 1;
-      const int yp = (yy == L - 1) ? 0 : yy + 1;
-      const int ih = par ? ((ii + 1 == half) ? 0 : ii + 1) : ((ii == 0) ? half - 1 : ii - 1);
+      const int o0 = (yy == 0) ? wrap : -half;
+      const int o1 = (yy == L - 1) ? -wrap : half;
+      const int o3 = par ? ((ii + 1 == half) ? -ii : 1) : ((ii == 0) ? half - 1 : -1);
       WordIn a;
       a.s = own[PT_DBG_IDX(p, q, nwords, kDbgSpinLoad)];  // this lane's word
-      a.n0 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, ym * half + ii, nwords, kDbgSpinLoad));
-      a.n1 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, yp * half + ii, nwords, kDbgSpinLoad));
+      a.n0 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, q + o0, nwords, kDbgSpinLoad));
+      a.n1 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, q + o1, nwords, kDbgSpinLoad));
       a.n2 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, q, nwords, kDbgSpinLoad));
-      a.n3 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, yy * half + ih, nwords, kDbgSpinLoad));
-      a.site = (uint32_t)(yy * L + 2 * ii + par);
+      a.n3 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, q + o3, nwords, kDbgSpinLoad));
+      a.site = (uint32_t)(2 * q + par);  // y L + x with x = 2 ii + par
       return a;
     };
     const auto step = [&]() {
