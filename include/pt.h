@@ -141,12 +141,23 @@ int pt_sweep(pt_problem* p, int64_t n, int exchange_every);
  *                          plane gets at least one CTA of one resident wave and no thread
  *                          owns more than 255 words of a colour; pt_sweep returns PT_EINVAL
  *                          otherwise.
+ *   PT_SWEEP_BANDS      -- the persistent kernel with each CTA owning a band of whole rows
+ *                          of a plane, kept in shared memory with one halo row on either
+ *                          side: colour 0 is updated on the band and again, from the same
+ *                          inputs, on its two halo rows, so colour 1 needs no grid barrier
+ *                          before it and a sweep takes one grid barrier instead of two (for
+ *                          small lattices, where the barriers dominate). It fits when the
+ *                          persistent kernel fits with at least two bands per plane and a
+ *                          band's copies fit 48 KB of shared memory; pt_sweep returns
+ *                          PT_EINVAL otherwise. PT_SWEEP_PERSISTENT never uses the bands;
+ *                          PT_SWEEP_AUTO uses them where they measured faster.
  * words_per_thread (1..255, 0 = the default 1) sets how many words of each colour a thread
  * of the persistent kernel aims to own: the CTA count is the one that gives that many,
  * capped at one resident wave. PT_EINVAL for an unknown strategy or a count out of range. */
 #define PT_SWEEP_AUTO 0
 #define PT_SWEEP_LAUNCHES 1
 #define PT_SWEEP_PERSISTENT 2
+#define PT_SWEEP_BANDS 3
 int pt_set_sweep_tuning(pt_problem* p, int strategy, int words_per_thread);
 
 /* The problem's sweep strategy, words-per-thread setting and the CTA count the persistent

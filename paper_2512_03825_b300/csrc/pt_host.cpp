@@ -981,6 +981,10 @@ void pt_destroy(pt_problem* p) {
   da.free = p->dbg_free;
   da.ctx = p->dbg_ctx;
   dev_free(p->dbg_mem, p->stream, da);
+  Allocator ba;
+  ba.free = p->band_free;
+  ba.ctx = p->band_ctx;
+  dev_free(p->band_mem, p->stream, ba);
   if (cur >= 0 && cur != p->dev_info.device) cudaSetDevice(cur);
   delete p;
 }
@@ -998,7 +1002,24 @@ int pt_set_stream(pt_problem* p, void* cuda_stream) {
 namespace {
 
 // pt_sweep as cooperative launches of at most kPersistChunk sweeps each.
+// The band form of the persistent kernel per sweep strategy: chosen where it measured
+// faster (AUTO), never (PERSISTENT: the strided form), always (BANDS).
+int band_choice(int strategy) {
+  return strategy == PT_SWEEP_BANDS ? kBandForce
+                                    : (strategy == PT_SWEEP_AUTO ? kBandAuto : kBandNever);
+}
+
 int sweep_persistent(pt_problem* p, int64_t n, int m) {
+  if (p->plan.band && !p->band_mem) {
+    // the band form's second copy of colour 1 (W L L/2 words), allocated once per problem
+    Allocator used;
+    void* mem = dev_alloc((size_t)p->W * p->L * (p->L / 2) * 4, p->stream, &used);
+    if (!mem) return fail(PT_ENOMEM, "allocation of the band form's colour-1 copy failed");
+    p->band_mem = mem;
+    p->band_free = used.free;
+    p->band_ctx = used.ctx;
+    p->dev.band_c1 = (uint32_t*)mem;
+  }
   while (n > 0) {
     const int c = (int)std::min<int64_t>(n, kPersistChunk);
     const cudaError_t err = launch_persist(p->dev, p->plan, p->t, p->e, c, m, p->stall,
@@ -1025,14 +1046,19 @@ int pt_sweep(pt_problem* p, int64_t n, int exchange_every) {
   if (n == 0) return PT_OK;
   if (p->sweep_strategy != PT_SWEEP_LAUNCHES) {
     if (!p->plan_valid) {
-      const cudaError_t err = persist_plan(p->dev, p->dev_info, p->words_per_thread, &p->plan);
+      const cudaError_t err = persist_plan(p->dev, p->dev_info, p->words_per_thread,
+                                           band_choice(p->sweep_strategy), &p->plan);
       if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "persistent occupancy", err);
       p->plan_valid = true;
     }
     if (p->plan.grid > 0) return sweep_persistent(p, n, exchange_every);
-    if (p->sweep_strategy == PT_SWEEP_PERSISTENT)
+    if (p->sweep_strategy == PT_SWEEP_PERSISTENT || p->sweep_strategy == PT_SWEEP_BANDS)
       return fail(PT_EINVAL, "L = %d, R = %d does not fit one resident wave of the persistent "
-                  "kernel with <= %d words per thread", p->L, p->R, kPersistMaxWordsPerThread);
+                  "kernel with <= %d words per thread%s", p->L, p->R, kPersistMaxWordsPerThread,
+                  p->sweep_strategy == PT_SWEEP_BANDS
+                      ? " in bands of rows (at least two per plane, their copies within the "
+                        "shared-memory limit)"
+                      : "");
   }
   for (int64_t j = 0; j < n; ++j) {
     cudaError_t err = launch_half_sweep(p->dev, p->dev_info, 0, p->t, p->stream);
@@ -1103,7 +1129,7 @@ int pt_iterations(pt_problem* p, uint64_t* iterations_done) {
 int pt_set_sweep_tuning(pt_problem* p, int strategy, int words_per_thread) {
   int rc = problem_check(p);
   if (rc) return rc;
-  if (strategy < PT_SWEEP_AUTO || strategy > PT_SWEEP_PERSISTENT)
+  if (strategy < PT_SWEEP_AUTO || strategy > PT_SWEEP_BANDS)
     return fail(PT_EINVAL, "unknown sweep strategy %d", strategy);
   if (words_per_thread < 0 || words_per_thread > kPersistMaxWordsPerThread)
     return fail(PT_EINVAL, "words_per_thread = %d outside 0..%d", words_per_thread,
@@ -1119,7 +1145,8 @@ int pt_get_sweep_tuning(pt_problem* p, int* strategy, int* words_per_thread, int
   if (rc) return rc;
   if ((rc = problem_device_guard(p))) return rc;
   if (!p->plan_valid) {
-    const cudaError_t err = persist_plan(p->dev, p->dev_info, p->words_per_thread, &p->plan);
+    const cudaError_t err = persist_plan(p->dev, p->dev_info, p->words_per_thread,
+                                         band_choice(p->sweep_strategy), &p->plan);
     if (err != cudaSuccess) return problem_fail(p, PT_ECUDA, "persistent occupancy", err);
     p->plan_valid = true;
   }

@@ -38,6 +38,9 @@ struct pt_problem {
   pt_free_fn dbg_free = nullptr;
   void* dbg_ctx = nullptr;
   uint64_t dbg_t0 = 0;        // debug build: sweeps done when the tags were last cleared
+  void* band_mem = nullptr;   // the band form's second copy of colour 1 (dev.band_c1)
+  pt_free_fn band_free = nullptr;
+  void* band_ctx = nullptr;
   void* trace_mem = nullptr;  // observable trace ring (dev.trace_E / trace_M), own allocation
   size_t trace_bytes = 0;
   pt_free_fn trace_free = nullptr;

@@ -33,6 +33,7 @@
 // launch, every half sweep reads and writes it there, and it is copied back at the end. The
 // half sweeps then meet at the block barrier alone; only the swap iterations, which need
 // every plane's counts, still meet at the grid barrier.
+#include <algorithm>
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -196,10 +197,108 @@ __device__ __forceinline__ void half_pass(const DevProblem& p, uint32_t* plane, 
   }
 }
 
-template <int MODE, bool CLUSTER, bool LOCAL>
+// The band form of the persistent sweep (FORM == kFormBand). CTA b of a plane's G CTAs owns
+// the rows [y0, y0 + H) of the plane, y0 = b L / G, and keeps them in shared memory: C0
+// holds colour 0 of rows y0 - 1 .. y0 + H (its band and one halo row on either side), C1
+// colour 1 of its band. Colour 0 is updated on all H + 2 rows of C0: the band's own rows are
+// also stored to global memory, the two halo rows belong to the neighbouring bands and are
+// computed here a second time from the same inputs (the same colour-1 neighbours, the same
+// Philox draws), so they equal the owners' words bit for bit and stay in shared memory. Colour
+// 1 of the band then reads all its colour-0 neighbours from C0, after a block barrier only:
+// a sweep needs one grid barrier (before the next sweep's colour 0 reads the neighbouring
+// bands' colour-1 rows) instead of two.
+// With no grid barrier between the colours, a band may store its new colour 1 while a slower
+// neighbour still reads the old one for its halo rows. So colour 1 lives in two global copies,
+// the spin array and p.band_c1, and the sweeps of a launch alternate: sweep j stores colour 1
+// in one copy (c1_dst) while colour 0 reads the other bands' colour 1 of sweep j - 1 from the
+// other (c1_src). A copy is stored again only in sweep j + 2, after the grid barrier that
+// ends sweep j + 1, when every band has finished reading it. The launch leaves colour 1 in
+// the spin array (c1_to_spins: c1_dst is the spin array).
+template <int MODE, int COLOUR, bool COUNT>
+__device__ __forceinline__ void band_pass(const DevProblem& p, int w, uint64_t t,
+                                          const RoundKeys& rk, const BlockTerms& bt, int y0,
+                                          int H, uint32_t* C0, uint32_t* C1,
+                                          const uint32_t* c1_src, uint32_t* c1_dst,
+                                          bool c1_to_spins, const uint4* thr,
+                                          uint32_t alw0, uint32_t alw1, uint32_t used,
+                                          const PlaneGeneric& gen, bool five,
+                                          const int (&cls5)[5], bool ones,
+                                          BitCounter<15, 10>& U, BitCounter<15, 10>& N) {
+  const uint32_t c3 = kTagSpin | ((uint32_t)(t >> 32) << 8);
+  const int L = p.L, half = L >> 1;
+  const int nwords = L * half;
+  const int nblk = (min(32, p.R - 32 * w) + 3) >> 2;
+  const size_t own_base = word_index(L, w, COLOUR, 0, 0);
+  uint32_t* const g_own = COLOUR == 0 ? p.spins + own_base : c1_dst;
+  (void)nwords;
+  (void)c1_to_spins;
+  // a colour-1 word as a neighbour of colour 0: the band's rows from C1, the others from
+  // the copy the last sweep stored (before the last grid barrier; read through L2)
+  const auto c1_word = [&](int yy, int ii) -> uint32_t {
+    int d = yy - y0;
+    if (d < 0) d += L;
+    return d < H ? C1[d * half + ii]
+                 : __ldcg(c1_src + PT_DBG_IDX(p, yy * half + ii, nwords, kDbgSpinLoad));
+  };
+  const int n = (COLOUR == 0 ? H + 2 : H) * half;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int r = k / half, i = k - r * half;
+    int y = COLOUR == 0 ? y0 - 1 + r : y0 + r;
+    if (y < 0) y += L;
+    if (y >= L) y -= L;
+    const int par = (y + COLOUR) & 1;
+    const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
+    uint32_t s, n0, n1, n2, n3;
+    if (COLOUR == 0) {
+      const int ym = (y == 0) ? L - 1 : y - 1;
+      const int yp = (y == L - 1) ? 0 : y + 1;
+      s = C0[k];
+      n0 = c1_word(ym, i);
+      n1 = c1_word(yp, i);
+      n2 = c1_word(y, i);
+      n3 = c1_word(y, ih);
+    } else {
+      s = C1[k];
+      n0 = C0[r * half + i];        // row y - 1
+      n1 = C0[(r + 2) * half + i];  // row y + 1
+      n2 = C0[(r + 1) * half + i];  // row y
+      n3 = C0[(r + 1) * half + ih];
+    }
+    const uint32_t site = (uint32_t)(y * L + 2 * i + par);
+    const SiteTerms st = site_terms(site, c3, rk);
+    const auto draw = [&](int j) { return philox_site_block(st, bt, j, rk); };
+    uint32_t ns;
+    if (MODE == kModeFerro)
+      ns = update_word_ferro_smem(s, n0, n1, n2, n3, nblk, thr, alw0, alw1, used, draw);
+    else if (five)
+      ns = update_word_generic_cmp<5>(s, n0, n1, n2, n3, nblk, gen, cls5, draw);
+    else
+      ns = update_word_generic_with(s, n0, n1, n2, n3, nblk, gen, draw);
+    const int q = y * half + i;
+    if (COLOUR == 0) {
+      C0[k] = ns;
+      if (r >= 1 && r <= H && PT_DBG_STORE(p, q, nwords, own_base, t, COLOUR)) g_own[q] = ns;
+    } else {
+      C1[k] = ns;
+      if (c1_to_spins ? PT_DBG_STORE(p, q, nwords, own_base, t, COLOUR)
+                      : (PT_DBG_CHECK(p, q, nwords, kDbgSpinStore), true))
+        g_own[q] = ns;
+    }
+    if (COUNT) {
+      const NbCount kk = count4(ns ^ n0, ns ^ n1, ns ^ n2, ns ^ n3);
+      U.add3(kk.b0, kk.b1, kk.b2);
+      if (MODE != kModeFerro || ones) N.add2(ns ^ n0, ns & n0);
+    }
+  }
+}
+
+template <int MODE, bool CLUSTER, int FORM>
 __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_constant__ PersistArgs a) {
+  constexpr bool LOCAL = FORM == kFormLocal;
+  constexpr bool BAND = FORM == kFormBand;
   // [R] ferro thresholds (k = 0, k = 1) by temperature, then [R] slot_of_temp and [R]
-  // temp_of_slot; persist_smem(R, mode) bytes; then (LOCAL) the plane's L * L words
+  // temp_of_slot; persist_smem(R, mode) bytes; then (LOCAL) the plane's L * L words or
+  // (BAND) the band's C0 and C1 words
   extern __shared__ __align__(16) int32_t map_s[];
   __shared__ PlaneFerro fer;
   __shared__ uint4 thr[16];  // ferro thresholds, interleaved for 16-byte broadcast loads
@@ -232,16 +331,49 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
     for (int q = threadIdx.x; q < plane_words; q += blockDim.x) plane_s[q] = plane_g[q];
     __syncthreads();
   }
-  // LOCAL: the plane goes back to global memory at every exit of the kernel
+  const int q0 = (blockIdx.x / W) * kPersistThreads + threadIdx.x;
+  const int step = (gridDim.x / W) * kPersistThreads;
+  const int half = p.L >> 1;
+  // BAND: this CTA's rows [by0, by0 + bH) of the plane and their shared copies
+  const int nbands = gridDim.x / W, band = blockIdx.x / W;
+  const int by0 = (int)((int64_t)band * p.L / nbands);
+  const int bH = (int)((int64_t)(band + 1) * p.L / nbands) - by0;
+  const int bHmax = (p.L + nbands - 1) / nbands;
+  uint32_t* const C0 = plane_s;                          // [(bHmax + 2) * half]
+  uint32_t* const C1 = plane_s + (size_t)(bHmax + 2) * half;  // [bHmax * half]
+  if (BAND) {
+    const uint32_t* g0 = plane_g;
+    const uint32_t* g1 = plane_g + (size_t)p.L * half;
+    for (int k = threadIdx.x; k < (bH + 2) * half; k += blockDim.x) {
+      const int r = k / half, i = k - r * half;
+      int y = by0 - 1 + r;
+      if (y < 0) y += p.L;
+      if (y >= p.L) y -= p.L;
+      C0[k] = g0[PT_DBG_IDX(p, y * half + i, p.L * half, kDbgSpinLoad)];
+    }
+    for (int k = threadIdx.x; k < bH * half; k += blockDim.x)
+      C1[k] = g1[PT_DBG_IDX(p, by0 * half + k, p.L * half, kDbgSpinLoad)];
+    __syncthreads();
+  }
+  // BAND: the sweep (within this launch) whose colour 1 was stored last
+  int band_last = -1;
+  // LOCAL: the plane goes back to global memory at every exit of the kernel; BAND: colour 1
+  // of the band goes to the spin array if the last sweep stored it in the other copy
   const auto flush = [&]() {
     if (LOCAL) {
       __syncthreads();
       for (int q = threadIdx.x; q < plane_words; q += blockDim.x) plane_g[q] = plane_s[q];
     }
+    if (BAND && band_last >= 0 && (band_last & 1) == 0) {
+      uint32_t* const a1 = plane_g + (size_t)p.L * half;
+      const uint64_t tl = a.t0 + (uint64_t)band_last;
+      (void)tl;
+      __syncthreads();
+      for (int k = threadIdx.x; k < bH * half; k += blockDim.x)
+        if (PT_DBG_STORE(p, by0 * half + k, p.L * half, word_index(p.L, w, 1, 0, 0), tl, 1))
+          a1[by0 * half + k] = C1[k];
+    }
   };
-  const int q0 = (blockIdx.x / W) * kPersistThreads + threadIdx.x;
-  const int step = (gridDim.x / W) * kPersistThreads;
-  const int half = p.L >> 1;
   const int y0 = q0 / half, i0 = q0 - y0 * half;
   const int dy = step / half, di = step - dy * half;
   uint32_t* const cnt_base = p.cnt + 2 * W * 32;  // two buffers of [2][W * 32]
@@ -297,20 +429,42 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
     }
     return sync_all(extra);
   };
+  uint32_t* const band_a1 = plane_g + (size_t)p.L * half;  // colour 1 in the spin array
+  uint32_t* const band_b1 = BAND ? p.band_c1 + (size_t)w * p.L * half : nullptr;
   for (int j = 0; j < a.n; ++j) {
     const uint64_t t = a.t0 + (uint64_t)j;
+    // BAND: sweep j stores colour 1 in the spin array when j is odd, in the other copy when
+    // j is even, and reads the other bands' colour 1 of sweep j - 1 from the other one
+    uint32_t* const c1_dst = (j & 1) ? band_a1 : band_b1;
+    const uint32_t* const c1_src = (j & 1) ? band_b1 : band_a1;
     BlockTerms bt;
     block_terms((uint32_t)(8 * w), (uint32_t)t, a.rk, bt);
     BitCounter<15, 10> U, N;
-    half_pass<MODE, false, LOCAL>(p, plane, w, 0, t, a.rk, bt, q0, step, y0, i0, dy, di, thr,
-                                  alw0, alw1, used, gen, five, cls5, false, U, N);
-    if (!sync_half(j == 0 ? (unsigned)a.stall : 0u)) return flush();
+    // the stall test hook applies to the launch's first grid barrier: after colour 0, or in
+    // the band form (no grid barrier between the colours) after colour 1
+    const unsigned stall0 = j == 0 ? (unsigned)a.stall : 0u;
+    if (BAND) {
+      band_pass<MODE, 0, false>(p, w, t, a.rk, bt, by0, bH, C0, C1, c1_src, c1_dst, (j & 1) != 0,
+                                thr, alw0, alw1, used, gen,
+                                five, cls5, false, U, N);
+      __syncthreads();
+    } else {
+      half_pass<MODE, false, LOCAL>(p, plane, w, 0, t, a.rk, bt, q0, step, y0, i0, dy, di, thr,
+                                    alw0, alw1, used, gen, five, cls5, false, U, N);
+      if (!sync_half(stall0)) return flush();
+    }
     const bool ex = a.m > 0 && (t + 1) % (uint64_t)a.m == 0;
     if (!ex && !trace) {
-      half_pass<MODE, false, LOCAL>(p, plane, w, 1, t, a.rk, bt, q0, step, y0, i0, dy, di, thr,
-                                    alw0, alw1, used, gen, five, cls5, false, U, N);
+      if (BAND)
+        band_pass<MODE, 1, false>(p, w, t, a.rk, bt, by0, bH, C0, C1, c1_src, c1_dst,
+                                  (j & 1) != 0, thr, alw0, alw1, used,
+                                  gen, five, cls5, false, U, N);
+      else
+        half_pass<MODE, false, LOCAL>(p, plane, w, 1, t, a.rk, bt, q0, step, y0, i0, dy, di,
+                                      thr, alw0, alw1, used, gen, five, cls5, false, U, N);
+      band_last = j;
       if (j + 1 == a.n) break;  // the kernel's end orders this half sweep before what follows
-      if (!sync_half(0)) return flush();
+      if (!sync_half(BAND ? stall0 : 0u)) return flush();
       continue;
     }
     // a swap iteration or a trace row follows: count this sweep into buffer `counted & 1`
@@ -318,8 +472,14 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
     uint32_t* const cb = cnt_base + (counted & 1) * 2 * W * 32;
     U.zero();
     N.zero();
-    half_pass<MODE, true, LOCAL>(p, plane, w, 1, t, a.rk, bt, q0, step, y0, i0, dy, di, thr,
-                                 alw0, alw1, used, gen, five, cls5, trace, U, N);
+    if (BAND)
+      band_pass<MODE, 1, true>(p, w, t, a.rk, bt, by0, bH, C0, C1, c1_src, c1_dst, (j & 1) != 0,
+                               thr, alw0, alw1, used, gen,
+                               five, cls5, trace, U, N);
+    else
+      half_pass<MODE, true, LOCAL>(p, plane, w, 1, t, a.rk, bt, q0, step, y0, i0, dy, di, thr,
+                                   alw0, alw1, used, gen, five, cls5, trace, U, N);
+    band_last = j;
     const uint32_t u = U.warp_total_for_lane();
     const uint32_t nn = (MODE == kModeFerro && !trace) ? 0u : N.warp_total_for_lane();
     if (threadIdx.x < 64) (&acc[0][0])[threadIdx.x] = 0;
@@ -336,7 +496,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
         atomicAdd(&cb[PT_DBG_IDX(p, W * 32 + w * 32 + threadIdx.x, 2 * W * 32, kDbgCount)],
                   acc[1][threadIdx.x]);
     }
-    if (!sync_all(0)) return flush();
+    if (!sync_all(BAND ? stall0 : 0u)) return flush();
     if (ex) exchange_local(p, e, cb, sot, tos, blockIdx.x == 0);
     if (blockIdx.x == 0) {
       if (trace) {
@@ -386,15 +546,23 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
   }
 }
 
-const void* persist_fn(int mode, bool cluster = false, bool local = false) {
-  if (cluster)
-    return mode == kModeFerro ? (const void*)k_persist<kModeFerro, true, false>
-                              : (const void*)k_persist<kModeGeneric, true, false>;
-  if (local)
-    return mode == kModeFerro ? (const void*)k_persist<kModeFerro, false, true>
-                              : (const void*)k_persist<kModeGeneric, false, true>;
-  return mode == kModeFerro ? (const void*)k_persist<kModeFerro, false, false>
-                            : (const void*)k_persist<kModeGeneric, false, false>;
+const void* persist_fn(int mode, bool cluster = false, int form = kFormStrided) {
+  const bool f = mode == kModeFerro;
+  if (cluster) {
+    if (form == kFormBand)
+      return f ? (const void*)k_persist<kModeFerro, true, kFormBand>
+               : (const void*)k_persist<kModeGeneric, true, kFormBand>;
+    return f ? (const void*)k_persist<kModeFerro, true, kFormStrided>
+             : (const void*)k_persist<kModeGeneric, true, kFormStrided>;
+  }
+  if (form == kFormLocal)
+    return f ? (const void*)k_persist<kModeFerro, false, kFormLocal>
+             : (const void*)k_persist<kModeGeneric, false, kFormLocal>;
+  if (form == kFormBand)
+    return f ? (const void*)k_persist<kModeFerro, false, kFormBand>
+             : (const void*)k_persist<kModeGeneric, false, kFormBand>;
+  return f ? (const void*)k_persist<kModeFerro, false, kFormStrided>
+           : (const void*)k_persist<kModeGeneric, false, kFormStrided>;
 }
 
 }  // namespace
@@ -403,17 +571,28 @@ size_t persist_smem(int R, int mode) {
   return (size_t)2 * R * sizeof(int32_t) + (mode == kModeFerro ? (size_t)R * 16 : 0);
 }
 
-size_t persist_launch_smem(int L, int R, int mode, bool local) {
+// Shared words of a band-form CTA: C0 (its rows and two halo rows of colour 0) and C1 (its
+// rows of colour 1), for the largest band of `bands` bands of L rows.
+static size_t band_bytes(int L, int bands) {
+  const size_t hmax = (size_t)((L + bands - 1) / bands);
+  return (2 * hmax + 2) * (size_t)(L / 2) * sizeof(uint32_t);
+}
+
+size_t persist_launch_smem(int L, int R, int mode, int form, int bands) {
   const size_t base = persist_smem(R, mode);
-  return local ? ((base + 15) & ~size_t(15)) + (size_t)L * L * sizeof(uint32_t) : base;
+  const size_t at = (base + 15) & ~size_t(15);
+  if (form == kFormLocal) return at + (size_t)L * L * sizeof(uint32_t);
+  if (form == kFormBand) return at + band_bytes(L, bands);
+  return base;
 }
 
 cudaError_t persist_plan(const DevProblem& p, const DeviceInfo& dev, int words_per_thread,
-                         PersistPlan* plan) {
+                         int band, PersistPlan* plan) {
   plan->grid = 0;
   plan->words_per_thread = 0;
   plan->cluster = false;
   plan->local = false;
+  plan->band = false;
   int per_sm = 0;
   // the maps and (ferro) the thresholds by temperature can pass the default 48 KB per block.
   // The limit belongs to the kernel, not to a problem: it is set to what the largest
@@ -424,10 +603,18 @@ cudaError_t persist_plan(const DevProblem& p, const DeviceInfo& dev, int words_p
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)persist_smem(PT_MAX_R, p.mode));
   if (err == cudaSuccess)
-    err = cudaFuncSetAttribute(persist_fn(p.mode, false, true),
+    err = cudaFuncSetAttribute(persist_fn(p.mode, false, kFormLocal),
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(((persist_smem(PT_MAX_R, p.mode) + 15) & ~size_t(15)) +
                                      kPersistMaxLocalBytes));
+  for (int c = 0; c < 2 && err == cudaSuccess; ++c)
+    err = cudaFuncSetAttribute(persist_fn(p.mode, c == 1, kFormBand),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(((persist_smem(PT_MAX_R, p.mode) + 15) & ~size_t(15)) +
+                                     kPersistMaxBandBytes));
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(persist_fn(p.mode, true, kFormBand),
+                               cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(persist_fn(p.mode, true),
                                cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -447,12 +634,49 @@ cudaError_t persist_plan(const DevProblem& p, const DeviceInfo& dev, int words_p
   if (wpt > kPersistMaxWordsPerThread) return cudaSuccess;
   plan->grid = (int)(g * p.W);
   plan->words_per_thread = (int)wpt;
-  if (g == 1 && (int64_t)p.L * p.L * 4 <= kPersistMaxLocalBytes) {
+  if (band != kBandNever) {
+    // the band form: gb bands of rows per plane. A band of H rows updates H + 2 rows of
+    // colour 0 and H of colour 1; with the default of one word per thread, H is the largest
+    // height whose colour-0 rows a CTA takes in one pass (at least one row), so that a sweep
+    // is one pass of each colour and one grid barrier. gb >= 2 (a band and its two halo rows
+    // never wrap onto themselves when L >= 4); the shared copies must fit and every CTA stay
+    // resident.
+    const int64_t half_w = p.L / 2;
+    int64_t H = words_per_thread <= 1
+                    ? std::max<int64_t>(1, kPersistThreads / half_w - 2)
+                    : std::max<int64_t>(1, (int64_t)words_per_thread * kPersistThreads / half_w);
+    int64_t gb = std::max<int64_t>(2, (p.L + H - 1) / H);
+    if (gb > planes_fit) {  // taller bands, so that every CTA stays resident
+      H = (p.L + planes_fit - 1) / planes_fit;
+      gb = (p.L + H - 1) / H;
+    }
+    int per_sm_band = 0;
+    bool fits = gb >= 2 && gb <= planes_fit;
+    if (fits) fits = band_bytes(p.L, (int)gb) <= (size_t)kPersistMaxBandBytes;
+    if (fits) {
+      err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &per_sm_band, persist_fn(p.mode, false, kFormBand), kPersistThreads,
+          persist_launch_smem(p.L, p.R, p.mode, kFormBand, (int)gb));
+      if (err != cudaSuccess) return err;
+      fits = (int64_t)per_sm_band * dev.sms >= gb * p.W;
+    }
+    const bool coop = g * p.W > kPersistMaxCluster;  // the strided form's grid
+    plan->band = fits && (band == kBandForce ||
+                          (coop && words_per_thread <= 1 && half_w <= kBandAutoMaxHalf));
+    if (plan->band) {
+      plan->grid = (int)(gb * p.W);
+      plan->words_per_thread = (int)(((H + 2) * half_w + kPersistThreads - 1) / kPersistThreads);
+    } else if (band == kBandForce) {
+      plan->grid = 0;
+      return cudaSuccess;
+    }
+  }
+  if (!plan->band && g == 1 && (int64_t)p.L * p.L * 4 <= kPersistMaxLocalBytes) {
     // one CTA per plane: its plane in shared memory, if every plane's CTA stays resident
     int per_sm_local = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm_local, persist_fn(p.mode, false, true), kPersistThreads,
-        persist_launch_smem(p.L, p.R, p.mode, true));
+        &per_sm_local, persist_fn(p.mode, false, kFormLocal), kPersistThreads,
+        persist_launch_smem(p.L, p.R, p.mode, kFormLocal, 1));
     if (err != cudaSuccess) return err;
     if ((int64_t)per_sm_local * dev.sms >= plan->grid) {
       plan->local = true;
@@ -468,13 +692,14 @@ cudaError_t persist_plan(const DevProblem& p, const DeviceInfo& dev, int words_p
     attr[0].val.clusterDim.x = (unsigned)plan->grid;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    const int form = plan->band ? kFormBand : kFormStrided;
     cfg.gridDim = dim3((unsigned)plan->grid);
     cfg.blockDim = dim3(kPersistThreads);
-    cfg.dynamicSmemBytes = persist_smem(p.R, p.mode);
+    cfg.dynamicSmemBytes = persist_launch_smem(p.L, p.R, p.mode, form, plan->grid / p.W);
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int clusters = 0;
-    err = cudaOccupancyMaxActiveClusters(&clusters, persist_fn(p.mode, true), &cfg);
+    err = cudaOccupancyMaxActiveClusters(&clusters, persist_fn(p.mode, true, form), &cfg);
     if (err != cudaSuccess) {
       cudaGetLastError();  // not placeable: keep the cooperative launch
       return cudaSuccess;
@@ -503,6 +728,7 @@ cudaError_t launch_persist(const DevProblem& p, const PersistPlan& plan, uint64_
     a.rk.k1[r] = p.key1 + (uint32_t)r * kPhiloxW1;
   }
   void* args[] = {&a};
+  const int form = plan.band ? kFormBand : (plan.local ? kFormLocal : kFormStrided);
   if (plan.cluster && stall == 0) {
     // the test hook (stall) needs the counting barrier: it waits for a CTA that never comes
     cudaLaunchConfig_t cfg = {};
@@ -513,15 +739,16 @@ cudaError_t launch_persist(const DevProblem& p, const PersistPlan& plan, uint64_
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3((unsigned)plan.grid);
     cfg.blockDim = dim3(kPersistThreads);
-    cfg.dynamicSmemBytes = persist_smem(p.R, p.mode);
+    cfg.dynamicSmemBytes = persist_launch_smem(p.L, p.R, p.mode, form, plan.grid / p.W);
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelExC(&cfg, persist_fn(p.mode, true), args);
+    return cudaLaunchKernelExC(&cfg, persist_fn(p.mode, true, form), args);
   }
-  return cudaLaunchCooperativeKernel(persist_fn(p.mode, false, plan.local), dim3(plan.grid),
+  return cudaLaunchCooperativeKernel(persist_fn(p.mode, false, form), dim3(plan.grid),
                                      dim3(kPersistThreads), args,
-                                     persist_launch_smem(p.L, p.R, p.mode, plan.local), st);
+                                     persist_launch_smem(p.L, p.R, p.mode, form,
+                                                         plan.grid / p.W), st);
 }
 
 }  // namespace ptb

@@ -21,11 +21,34 @@ constexpr int kPersistMaxCluster = 16;
 // The largest plane (both colours) that a CTA owning a whole plane keeps in shared memory.
 constexpr int kPersistMaxLocalBytes = 64 * 1024;
 
+// The largest band (both colours' shared copies) that a CTA of the band form keeps in shared
+// memory.
+constexpr int kPersistMaxBandBytes = 48 * 1024;
+
+// How the persistent kernel lays out a plane's words over its CTAs (a template parameter).
+enum PersistForm : int {
+  kFormStrided = 0,  // each thread takes every (CTAs x threads)-th word of a colour
+  kFormLocal = 1,    // one CTA per plane, the whole plane in shared memory
+  kFormBand = 2,     // each CTA owns a band of rows, shared copies, one grid barrier a sweep
+};
+
+// Whether a plan may or must use the band form.
+enum BandChoice : int { kBandNever = 0, kBandAuto = 1, kBandForce = 2 };
+// kBandAuto takes the band form where it measured faster: where the strided form would need
+// a cooperative grid (more CTAs than one cluster takes) at one word per thread and the rows
+// are at most this many words (L <= 128), so that bands of at least two rows plus their halo
+// rows make one pass of a CTA. L = 128, R = 32: 7.23 -> 5.77 us per sweep with a swap
+// iteration every sweep, 5.44 -> 4.11 without. The cluster grids of smaller lattices
+// (L = 32, 64: 4.95 -> 5.17 and 5.08 -> 5.31 us) and the larger lattices (L = 256: 7.45 ->
+// 8.99 us; L = 512 and 1024 lose 17-23%) keep the strided form.
+constexpr int kBandAutoMaxHalf = 64;
+
 struct PersistPlan {
   int grid;              // CTAs (a multiple of W), 0 when the problem does not fit one wave
   int words_per_thread;  // words of each colour per thread
   bool cluster;          // the grid can run as one cluster (hardware cluster barrier)
   bool local;            // one CTA per plane, its plane in shared memory
+  bool band;             // the band form: a band of rows per CTA (grid / W bands per plane)
 };
 
 // The device count buffer holds, in 32-bit words: [2][W * 32] for the per-launch kernels,
@@ -34,10 +57,13 @@ inline size_t count_words(int W) { return (size_t)6 * W * 32 + 16; }
 inline size_t persist_clear_bytes(int W) { return ((size_t)4 * W * 32 + 1) * 4; }
 
 size_t persist_smem(int R, int mode);
-// Dynamic shared memory of a launch: persist_smem, then (local) the plane's L*L words.
-size_t persist_launch_smem(int L, int R, int mode, bool local);
+// Dynamic shared memory of a launch: persist_smem, then (kFormLocal) the plane's L*L words
+// or (kFormBand, `bands` bands per plane) the band's shared copies.
+size_t persist_launch_smem(int L, int R, int mode, int form, int bands);
+// The launch shape for this problem; `band`: whether the band form may (kBandAuto: where it
+// is the measured better form) or must be used (kBandForce: plan->grid = 0 if it cannot).
 cudaError_t persist_plan(const DevProblem& p, const DeviceInfo& dev, int words_per_thread,
-                         PersistPlan* plan);
+                         int band, PersistPlan* plan);
 cudaError_t launch_persist(const DevProblem& p, const PersistPlan& plan, uint64_t t0,
                            uint64_t e0, int n, int m, int stall, uint64_t limit_ns,
                            cudaStream_t st);

@@ -97,6 +97,10 @@ struct DevProblem {
   DebugRecord* dbg;
   int32_t dbg_inject;
   int32_t dbg_pad;
+  // the band form of the persistent kernel (null until a band plan allocated it): a second
+  // copy of colour 1, [W][L][L/2], so that the sweeps of a launch alternate between the two
+  // copies (see k_persist)
+  uint32_t* band_c1;
 };
 
 }  // namespace ptb

@@ -22,7 +22,7 @@ import oracle  # noqa: E402
 from paper_2512_03825_b300 import _lib, api, autotune  # noqa: E402
 from paper_2512_03825_b300 import workloads as W  # noqa: E402
 
-LAUNCHES, PERSISTENT = 1, 2
+LAUNCHES, PERSISTENT, BANDS = 1, 2, 3
 FLAT, CLUSTER, FLOW, QUEUE = 0, 1, 2, 3
 
 
@@ -72,7 +72,9 @@ def main():
              ("persistent generic L20 R6", P(L=20, betas=W.linear_ladder(0.3, 0.6, 6), h=0.1, seed=14), PERSISTENT),
              ("launches generic L24 R37", P(L=24, betas=W.linear_ladder(0.2, 0.7, 37), h=0.1, seed=15), LAUNCHES),
              ("launches ferro L16 R8", P(L=16, betas=W.geometric_ladder(0.2, 0.6, 8), seed=16), LAUNCHES),
-             ("launches antiferro L12 R3", P(L=12, betas=W.linear_ladder(0.3, 0.5, 3), J=-1.0, h=0.25, seed=17), LAUNCHES)]
+             ("launches antiferro L12 R3", P(L=12, betas=W.linear_ladder(0.3, 0.5, 3), J=-1.0, h=0.25, seed=17), LAUNCHES),
+             ("bands L128 R32", P(L=128, betas=W.linear_ladder(0.3, 0.55, 32), seed=22), BANDS),
+             ("bands generic uneven L90 R40", P(L=90, betas=W.linear_ladder(0.3, 0.6, 40), h=0.1, seed=23), BANDS)]
     for name, p, strategy in plain:
         g = api.PTProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed)
         g.set_sweep_tuning(strategy)
@@ -81,13 +83,13 @@ def main():
         check(res, name, g, p, [("sweep", 7, 2), ("sweep", 6, 3)])
     # traced plain run (every sweep counted, trace rows written)
     p = P(L=24, betas=W.linear_ladder(0.3, 0.6, 9), seed=18)
-    for strategy in (LAUNCHES, PERSISTENT):
+    for strategy in (LAUNCHES, PERSISTENT, BANDS):
         g = api.PTProblem(p.L, p.betas, seed=p.seed)
         g.set_sweep_tuning(strategy)
         g.trace_start(5)
         g.sweep(9, 2)
-        check(res, "traced %s" % ("launches" if strategy == LAUNCHES else "persistent"), g, p,
-              [("sweep", 9, 2)])
+        check(res, "traced %s" % {LAUNCHES: "launches", PERSISTENT: "persistent",
+                                  BANDS: "bands"}[strategy], g, p, [("sweep", 9, 2)])
     # batches: every strategy, ferro and generic problems mixed, uneven n and m
     rng = np.random.Generator(np.random.PCG64(5150))
     probs = []

@@ -6,7 +6,7 @@ for a memory and race checker on small cases.
 
 The cases run in a child process that loads the debug build (PT_LIBRARY=debug): the plain
 path (persistent with a cooperative grid, with a cluster grid, with the plane in shared
-memory; one launch per half sweep; ferro, field and antiferromagnetic modes; traced), every
+memory, with a band of rows per CTA; one launch per half sweep; ferro, field and antiferromagnetic modes; traced), every
 batch strategy (dealt, queued, dataflow, cluster) and the allocation-free batch entry point on
 a mix of problems, a traced problem in a batch with the batched read, single-spin flips with
 both kernels, and a checkpoint round trip. Each must end with no failed check, with every spin
@@ -45,7 +45,8 @@ def test_every_path_passes_the_checks_and_equals_the_oracle(outcome):
                    "persistent shared-memory plane L16 R8", "launches generic L24 R37",
                    "batch dealt", "batch queued", "batch dataflow", "batch cluster",
                    "batch static", "flip shared + sweeps", "flip global + sweeps",
-                   "checkpoint load + sweeps"):
+                   "checkpoint load + sweeps", "bands L128 R32", "bands generic uneven L90 R40",
+                   "traced bands"):
         assert expect in names
 
 

@@ -1,7 +1,8 @@
-"""The two ways pt_sweep runs one problem -- one launch per half sweep, or one persistent
-cooperative launch whose CTAs meet at grid barriers -- against the CPU oracle, bit for bit,
-on grids of one CTA, several CTAs per plane, several planes with a ragged last plane, and
-ragged word shares; switching between them (and the batched path) mid-run; more sweeps than
+"""The ways pt_sweep runs one problem -- one launch per half sweep, or one persistent
+cooperative launch whose CTAs meet at grid barriers, in its strided form or with a band of
+rows per CTA (one grid barrier per sweep) -- against the CPU oracle, bit for bit, on grids of
+one CTA, several CTAs per plane, several planes with a ragged last plane, ragged word shares
+and uneven bands; switching between them (and the batched path) mid-run; more sweeps than
 one persistent launch takes; and the bounded barrier wait, made to run out on purpose by
 waiting for CTAs that do not exist."""
 from __future__ import annotations
@@ -14,7 +15,7 @@ from paper_2512_03825_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-AUTO, LAUNCHES, PERSISTENT = 0, 1, 2
+AUTO, LAUNCHES, PERSISTENT, BANDS = 0, 1, 2, 3
 
 
 @pytest.fixture(scope="module")
@@ -81,6 +82,70 @@ def test_strategy_matches_oracle(api, strategy, L, R, J, h, wpt, n, m):
     assert_same(g, o, "L%d R%d strategy %d" % (L, R, strategy))
 
 
+BAND_CASES = [
+    # (L, R, J, h, words per thread, sweeps, exchange_every); the band height is the largest
+    # whose colour-0 rows (band + 2 halo rows) a CTA of 256 threads updates in one pass
+    (24, 8, 1.0, 0.0, 1, 30, 1),       # 2 bands of 12 rows: the halo rows are the other band's
+    (30, 5, -1.0, 0.25, 1, 30, 2),     # generic, L/2 odd, 2 bands of 15 rows
+    (32, 40, 1.0, 0.0, 1, 24, 1),      # two planes, 3 uneven bands each, one cluster
+    (64, 33, 1.0, 0.0, 1, 20, 3),      # 11 uneven bands per plane, the second plane one slot
+    (90, 9, 1.0, 0.1, 1, 16, 1),       # 30 bands of 3 rows, generic
+    (128, 32, 1.0, 0.0, 1, 20, 1),     # 64 bands of 2 rows, cooperative grid
+    (128, 70, 1.0, 0.1, 1, 10, 2),     # three planes, 192 CTAs, generic
+    (130, 40, 0.5, 0.0, 1, 12, 5),     # s = 2, bands of one row, two planes
+    (256, 32, 1.0, 0.0, 1, 10, 0),     # 256 bands of one row, no exchanges
+    (512, 40, 1.0, 0.0, 1, 6, 1),      # taller bands so that the grid stays resident
+    (128, 32, 1.0, 0.0, 2, 12, 1),     # 16 bands of 8 rows: one cluster
+]
+
+
+@pytest.mark.parametrize("L,R,J,h,wpt,n,m", BAND_CASES)
+def test_bands_match_oracle(api, L, R, J, h, wpt, n, m):
+    prob = W.Problem(L=L, betas=W.linear_ladder(0.2, 0.7, R), J=J, h=h,
+                     seed=0xBA00 + 7 * L + R)
+    g, o = make(api, prob, BANDS, wpt)
+    s, w, grid = g.sweep_tuning()
+    assert s == BANDS and grid >= 2 * ((R + 31) // 32)
+    for k in (1, n - 1):                # two launches: the bands are reloaded by the second
+        g.sweep(k, m)
+        o.sweep(k, m)
+    assert_same(g, o, "bands L%d R%d" % (L, R))
+
+
+def test_bands_traced_and_switched(api):
+    """The band form with a trace (every sweep counted), then the strided form and the band
+    form again on the same problem: every trace row and the final state equal the oracle."""
+    prob = W.Problem(L=48, betas=W.linear_ladder(0.3, 0.6, 12), J=1.0, h=0.1, seed=0xBA77)
+    g, o = make(api, prob, BANDS, 1)
+    g.trace_start(20)
+    g.sweep(8, 3)
+    g.set_sweep_tuning(PERSISTENT, 1)
+    g.sweep(5, 3)
+    g.set_sweep_tuning(BANDS, 1)
+    g.sweep(7, 3)
+    E, M = o.trace(20, 3)
+    first, Eg, Mg = g.trace()
+    assert first == 1
+    np.testing.assert_array_equal(Eg, E)
+    np.testing.assert_array_equal(Mg, M)
+    assert_same(g, o, "bands traced")
+
+
+def test_bands_refused_where_they_do_not_fit(api):
+    from paper_2512_03825_b300 import _lib
+    # L = 4096: a band of every resident CTA's share of rows (14 rows and 2 halo rows of 2048
+    # words each) does not fit the 48 KB of shared copies
+    g = api.PTProblem(4096, [0.3])
+    g.set_sweep_tuning(BANDS)
+    assert g.sweep_tuning()[2] == 0
+    with pytest.raises(_lib.PTError) as ei:
+        g.sweep(1, 1)
+    assert ei.value.code == _lib.PT_EINVAL
+    g.set_sweep_tuning(AUTO)
+    g.sweep(1, 1)
+    g.synchronize()
+
+
 def test_grid_follows_words_per_thread(api):
     prob = W.Problem(L=256, betas=W.linear_ladder(0.3, 0.6, 64), seed=5)
     g = api.PTProblem(prob.L, prob.betas, seed=prob.seed)
@@ -145,7 +210,7 @@ def test_persistent_equals_launches_at_L512(api):
 def test_tuning_arguments_checked(api):
     from paper_2512_03825_b300 import _lib
     g = api.PTProblem(8, [0.3])
-    for call in (lambda: g.set_sweep_tuning(3), lambda: g.set_sweep_tuning(PERSISTENT, 256),
+    for call in (lambda: g.set_sweep_tuning(4), lambda: g.set_sweep_tuning(PERSISTENT, 256),
                  lambda: g.set_sweep_tuning(PERSISTENT, -1), lambda: g.set_wait_limit(0.0),
                  lambda: g.set_wait_limit(61.0), lambda: g.debug_stall_barrier(-1)):
         with pytest.raises(_lib.PTError) as ei:
@@ -155,14 +220,15 @@ def test_tuning_arguments_checked(api):
     g.synchronize()
 
 
-def test_barrier_wait_runs_out_and_context_survives(api):
+@pytest.mark.parametrize("strategy", [PERSISTENT, BANDS])
+def test_barrier_wait_runs_out_and_context_survives(api, strategy):
     """The first grid barrier waits for one CTA more than the launch has: every wait gives
     up after the 50 ms limit, the problem reports PT_ETIMEOUT and stays poisoned, and a new
     problem on the same context still matches the oracle."""
     from paper_2512_03825_b300 import _lib
     prob = W.Problem(L=64, betas=W.linear_ladder(0.3, 0.5, 40), seed=9)
     g = api.PTProblem(prob.L, prob.betas, seed=prob.seed)
-    g.set_sweep_tuning(PERSISTENT, 1)
+    g.set_sweep_tuning(strategy, 1)
     g.set_wait_limit(0.05)
     g.debug_stall_barrier(1)
     g.sweep(3, 1)
@@ -173,7 +239,7 @@ def test_barrier_wait_runs_out_and_context_survives(api):
         g.sweep(1, 1)
     assert ei.value.code in (_lib.PT_ETIMEOUT, _lib.PT_ESTATE)
     g.close()
-    h, o = make(api, prob, PERSISTENT, 1)
+    h, o = make(api, prob, strategy, 1)
     h.sweep(12, 1)
     o.sweep(12, 1)
     assert_same(h, o, "after a timed-out launch")
