@@ -320,9 +320,11 @@ def run_ours(args, rank, world, local):
         launch_s = (took[1] - took[0]) / (2 * (lens[1] - lens[0]))
         att_per_s = per_step / args.sweeps / 2 / launch_s
         how = ("k_flat_half: attempts of one half sweep of all %d problems / its average "
-               "launch duration, (t(%d sweeps) - t(%d sweeps)) / %d launches (CUDA events on "
-               "the problems' stream)" % (len(probs), lens[1], lens[0],
-                                          2 * (lens[1] - lens[0])))
+               "duration, (t(%d sweeps) - t(%d sweeps)) / %d half sweeps (CUDA events on "
+               "the problems' stream; with the batch in %d parts on their own streams, the "
+               "parts' launches of one half sweep overlap)"
+               % (len(probs), lens[1], lens[0], 2 * (lens[1] - lens[0]),
+                  tuning.get("streams", 1)))
         traffic = _flat_traffic()
     else:
         att_per_s = per_step / (statistics.mean(kernel_ms) / 1e3)
@@ -371,12 +373,13 @@ def run_ours(args, rank, world, local):
 
 def launches_per_batch(probs, sweeps, tuning):
     """Kernel launches of one pt_sweep_batch call: the lock-step strategies (dealt or queued
-    tiles) launch two half sweeps per sweep plus one exchange launch after every sweep with
-    an exchange (one mode here: h = 0); the dataflow strategy is one cooperative launch per
-    mode; the cluster strategy is one persistent launch plus a helper."""
+    tiles) launch, for each part of the batch (one per stream), two half sweeps per sweep
+    plus one exchange launch after every sweep with an exchange (one mode here: h = 0); the
+    dataflow strategy is one cooperative launch per mode; the cluster strategy is one
+    persistent launch plus a helper."""
     strategy = tuning.get("strategy", 0)
-    if strategy in (0, 3):
-        return sweeps * 3
+    if strategy in (0, 3):  # per sweep and part of the batch (one part per stream)
+        return sweeps * 3 * max(1, min(tuning.get("streams", 1), len(probs)))
     if strategy == 2:
         return len({p.h == 0.0 and p.J > 0 for p in probs})
     return 2

@@ -306,6 +306,21 @@ int pt_get_batch_tuning(int* strategy, int* cluster, int* joint_min_L);
 int pt_set_batch_tile_words(int tile_words);
 int pt_get_batch_tile_words(int* tile_words);
 
+/* Streams of PT_BATCH_FLAT and PT_BATCH_QUEUE (1..PT_BATCH_STREAMS_MAX, default 1; set by the
+ * autotuner): pt_sweep_batch splits the batch into that many parts of about equal work (L*L
+ * times planes times sweeps, heaviest problem first onto the lightest part) and advances each
+ * part on its own CUDA stream -- the first on the problems' stream, the others on side streams
+ * that the library owns per device, which wait for everything queued on the problems' stream
+ * before the call and which the problems' stream waits for at its end, so the call is ordered
+ * on the problems' stream as before. Sweep j of one part runs beside sweep j of the others:
+ * one part's exchange launch, launch gaps and last tiles overlap the others' half sweeps.
+ * Results never depend on it. Calls that use the side streams are serialised on the host per
+ * device. pt_sweep_batch_static always runs one part. PT_EINVAL outside the range. Applies to
+ * later batches of every problem. */
+#define PT_BATCH_STREAMS_MAX 4
+int pt_set_batch_streams(int streams);
+int pt_get_batch_streams(int* streams);
+
 /* Energies E = E_int / s of the configurations at each temperature index, out[R]. */
 int pt_energies(pt_problem* p, double* out);
 

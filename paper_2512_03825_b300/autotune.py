@@ -2,7 +2,8 @@
 
 Knobs: the batched strategy (lock-step tiles dealt by the host or handed out by a device
 queue, the same tiles in one dataflow launch, or one persistent cluster kernel); for the tile strategies the words per warp tile (the words
-each lane updates per tile: tile_words / 32); for the cluster kernel the CTAs per
+each lane updates per tile: tile_words / 32) and, for the lock-step ones, the number of
+streams the batch is split over (parts of equal work whose launches overlap); for the cluster kernel the CTAs per
 thread-block cluster and the lattice size from which a problem is spread over a whole
 cluster instead of one CTA. They change only how work is
 distributed, never a result: `tune` checks that every candidate leaves every problem in the
@@ -23,29 +24,35 @@ from ._lib import check, lib
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "autotune_cache.json")
 FLAT, CLUSTER, FLOW, QUEUE = 0, 1, 2, 3
-DEFAULT = {"strategy": FLAT, "cluster": 4, "joint_min_L": 128, "tile_words": 512}
-# (strategy, cluster, joint_min_L, tile_words)
-CANDIDATES: Tuple[Tuple[int, int, int, int], ...] = (
-    (FLAT, 1, 128, 256), (FLAT, 1, 128, 512), (FLAT, 1, 128, 1024),
-    (QUEUE, 1, 128, 256), (QUEUE, 1, 128, 512), (QUEUE, 1, 128, 1024),
-    (FLOW, 1, 128, 256), (FLOW, 1, 128, 512),
-    (CLUSTER, 1, 1 << 20, 512), (CLUSTER, 2, 128, 512), (CLUSTER, 3, 128, 512),
-    (CLUSTER, 4, 256, 512), (CLUSTER, 4, 128, 512), (CLUSTER, 4, 96, 512),
-    (CLUSTER, 6, 128, 512), (CLUSTER, 8, 128, 512))
+DEFAULT = {"strategy": FLAT, "cluster": 4, "joint_min_L": 128, "tile_words": 512, "streams": 1}
+# (strategy, cluster, joint_min_L, tile_words, streams)
+CANDIDATES: Tuple[Tuple[int, int, int, int, int], ...] = (
+    (FLAT, 1, 128, 256, 1), (FLAT, 1, 128, 512, 1), (FLAT, 1, 128, 1024, 1),
+    (QUEUE, 1, 128, 256, 1), (QUEUE, 1, 128, 512, 1), (QUEUE, 1, 128, 1024, 1),
+    (FLAT, 1, 128, 512, 2), (FLAT, 1, 128, 512, 3), (FLAT, 1, 128, 512, 4),
+    (FLAT, 1, 128, 256, 4), (FLAT, 1, 128, 1024, 4),
+    (QUEUE, 1, 128, 512, 2), (QUEUE, 1, 128, 512, 4), (QUEUE, 1, 128, 1024, 4),
+    (FLOW, 1, 128, 256, 1), (FLOW, 1, 128, 512, 1),
+    (CLUSTER, 1, 1 << 20, 512, 1), (CLUSTER, 2, 128, 512, 1), (CLUSTER, 3, 128, 512, 1),
+    (CLUSTER, 4, 256, 512, 1), (CLUSTER, 4, 128, 512, 1), (CLUSTER, 4, 96, 512, 1),
+    (CLUSTER, 6, 128, 512, 1), (CLUSTER, 8, 128, 512, 1))
 
 
-def set_tuning(strategy: int, cluster: int, joint_min_L: int, tile_words: int = 512) -> None:
+def set_tuning(strategy: int, cluster: int, joint_min_L: int, tile_words: int = 512,
+               streams: int = 1) -> None:
     check(lib.pt_set_batch_tuning(int(strategy), int(cluster), int(joint_min_L)),
           "pt_set_batch_tuning")
     check(lib.pt_set_batch_tile_words(int(tile_words)), "pt_set_batch_tile_words")
+    check(lib.pt_set_batch_streams(int(streams)), "pt_set_batch_streams")
 
 
 def get_tuning() -> Dict[str, int]:
-    s, c, j, w = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    s, c, j, w, n = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
     check(lib.pt_get_batch_tuning(C.byref(s), C.byref(c), C.byref(j)), "pt_get_batch_tuning")
     check(lib.pt_get_batch_tile_words(C.byref(w)), "pt_get_batch_tile_words")
+    check(lib.pt_get_batch_streams(C.byref(n)), "pt_get_batch_streams")
     return {"strategy": s.value, "cluster": c.value, "joint_min_L": j.value,
-            "tile_words": w.value}
+            "tile_words": w.value, "streams": n.value}
 
 
 def _device_key() -> str:
@@ -68,7 +75,7 @@ def apply_cached_or_default(workload: str = "batched") -> Dict[str, int]:
     """Apply the cached choice for this device (or the default) and return it."""
     entry = _load_cache().get(_device_key(), {}).get(workload, DEFAULT)
     set_tuning(entry.get("strategy", FLAT), entry["cluster"], entry["joint_min_L"],
-               entry.get("tile_words", DEFAULT["tile_words"]))
+               entry.get("tile_words", DEFAULT["tile_words"]), entry.get("streams", 1))
     return get_tuning()
 
 
@@ -81,7 +88,7 @@ def _snapshot(handles):
 
 
 def tune(problems: Sequence, sweeps: int = 200, every: int = 1,
-         candidates: Sequence[Tuple[int, int, int, int]] = CANDIDATES, workload: str = "batched",
+         candidates: Sequence[Tuple[int, ...]] = CANDIDATES, workload: str = "batched",
          repeats: int = 2, save: bool = True, log=None) -> Dict[str, object]:
     """Time every candidate launch shape on `problems` (workload Problems); keep the fastest.
     Raises if two candidates disagree on any problem's final state."""
@@ -89,7 +96,7 @@ def tune(problems: Sequence, sweeps: int = 200, every: int = 1,
 
     from .api import PTProblem, sweep_batch
 
-    results: List[Tuple[float, Tuple[int, int, int]]] = []
+    results: List[Tuple[float, Tuple[int, ...]]] = []
     reference = None
     for cand in candidates:
         set_tuning(*cand)
@@ -111,12 +118,14 @@ def tune(problems: Sequence, sweeps: int = 200, every: int = 1,
                 h.close()
         results.append((best, cand))
         if log:
-            log("strategy=%d cluster=%d joint_min_L=%d tile_words=%d: %.4f s"
-                % (tuple(cand) + (best,)))
-    results.sort()
-    best_t, (st, cl, jm, tw) = results[0]
-    choice = {"strategy": st, "cluster": cl, "joint_min_L": jm, "tile_words": tw}
-    set_tuning(st, cl, jm, tw)
+            full = tuple(cand) + (1,) * (5 - len(cand))
+            log("strategy=%d cluster=%d joint_min_L=%d tile_words=%d streams=%d: %.4f s"
+                % (full + (best,)))
+    results.sort(key=lambda r: r[0])
+    best_t, cand = results[0]
+    st, cl, jm, tw, ns = tuple(cand) + (1,) * (5 - len(cand))
+    choice = {"strategy": st, "cluster": cl, "joint_min_L": jm, "tile_words": tw, "streams": ns}
+    set_tuning(st, cl, jm, tw, ns)
     if save:
         cache = _load_cache()
         cache.setdefault(_device_key(), {})[workload] = dict(choice, seconds=best_t,

@@ -20,6 +20,7 @@ struct BatchTuning {
   int cluster = 4;
   int joint_min_L = 128;
   int tile_words = 512;
+  int streams = 1;  // PT_BATCH_FLAT / PT_BATCH_QUEUE: parts of the batch on their own streams
 };
 extern BatchTuning g_batch_tuning;  // written and read under the library lock only
 // A copy of the batch tuning, read under the library lock (the setters take it too).
@@ -28,8 +29,11 @@ BatchTuning batch_tuning();
 struct DeviceInfo;
 // The lock-step path (pt_flat.cu); problems are already checked.
 // queued: tiles handed out by the device queue (PT_BATCH_QUEUE) instead of dealt by the host.
+// streams: the batch is split into that many parts of about equal work, each advanced on its
+// own stream (the first on st, the others on side streams forked from st and joined to it).
 int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const int* every,
-                     cudaStream_t st, const DeviceInfo& di, int tile_words, bool queued);
+                     cudaStream_t st, const DeviceInfo& di, int tile_words, bool queued,
+                     int streams = 1);
 
 // The dataflow path (pt_flow.cu); problems are already checked.
 int sweep_batch_flow(pt_problem* const* ps, int count, const int64_t* n, const int* every,

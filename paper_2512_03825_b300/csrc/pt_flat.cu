@@ -414,13 +414,46 @@ int64_t build_flat_lists(pt_problem* const* ps, int count, const int64_t* n, con
   return n_max;
 }
 
-int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const int* every,
-                     cudaStream_t st, const DeviceInfo& di, int tile_words, bool queued) {
+// One lock-step batch on one stream, in three steps: prepare (work lists built, uploaded to
+// stream-ordered scratch), the launches of one sweep at a time, and finish (scratch freed).
+struct FlatRun {
+  cudaStream_t st = 0;
   std::vector<FlatProblem> probs;
   std::vector<Tile> tiles[2];  // by mode
-  const int64_t n_max = build_flat_lists(ps, count, n, every, tile_words, queued, &probs, tiles);
+  std::vector<int> first[2];   // dealt: per-warp offsets
+  std::vector<char> counted;   // per sweep: a swap iteration or trace row follows for some problem
+  ModeTiles mt[2];
+  const FlatProblem* d_probs = nullptr;
+  void* scratch = nullptr;
+  int np = 0;
+  int64_t n_max = 0;
+  size_t xsmem = 0;
+  int sms = 0;
+
+  int prepare(pt_problem* const* ps, int count, const int64_t* n, const int* every,
+              cudaStream_t stream, const DeviceInfo& di, int tile_words, bool queued);
+  cudaError_t launch_sweep(int64_t j) {
+    if (j >= n_max) return cudaSuccess;
+    return launch_flat_sweep(mt, d_probs, np, j, counted[(size_t)j] != 0, xsmem, sms, st);
+  }
+  cudaError_t finish() {
+    if (!scratch) return cudaSuccess;
+    const cudaError_t err = cudaFreeAsync(scratch, st);
+    scratch = nullptr;
+    return err;
+  }
+};
+
+int FlatRun::prepare(pt_problem* const* ps, int count, const int64_t* n, const int* every,
+                     cudaStream_t stream, const DeviceInfo& di, int tile_words, bool queued) {
+  st = stream;
+  sms = di.sms;
+  n_max = build_flat_lists(ps, count, n, every, tile_words, queued, &probs, tiles);
   if (n_max < 0) return fail(PT_EINTERNAL, "batch work tiles outside their planes");
-  if (probs.empty()) return PT_OK;
+  if (probs.empty()) {
+    n_max = 0;
+    return PT_OK;
+  }
   // one wave per launch: as many CTAs as are resident at once, their warps taking the
   // tiles from the mode's queue
   int per_sm[2] = {1, 1};
@@ -431,8 +464,6 @@ int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const i
         &per_sm[1], k_flat_half<kModeGeneric, true, false>, kFlatThreads, 0);
   if (err != cudaSuccess) return fail(PT_ECUDA, "occupancy: %s", cudaGetErrorString(err));
   const int wpb = kFlatThreads / 32;
-  ModeTiles mt[2];
-  std::vector<int> first[2];  // dealt: per-warp offsets
   for (int md = 0; md < 2; ++md) {
     if (tiles[md].empty()) continue;
     const int blocks = std::max(1, per_sm[md]) * di.sms;
@@ -453,11 +484,13 @@ int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const i
   const size_t fb[2] = {first[0].size() * sizeof(int), first[1].size() * sizeof(int)};
   const size_t qb = 2 * sizeof(unsigned long long);  // the two modes' queue counters
   const size_t total = al(pb) + al(tb[0]) + al(tb[1]) + al(fb[0]) + al(fb[1]) + al(qb) + 256;
-  void* scratch = nullptr;
   err = cudaMallocAsync(&scratch, total, st);
-  if (err != cudaSuccess) return fail(PT_ENOMEM, "batch scratch: %s", cudaGetErrorString(err));
+  if (err != cudaSuccess) {
+    scratch = nullptr;
+    return fail(PT_ENOMEM, "batch scratch: %s", cudaGetErrorString(err));
+  }
   char* cur = (char*)scratch;
-  FlatProblem* d_probs = (FlatProblem*)cur;
+  d_probs = (const FlatProblem*)cur;
   cur += al(pb);
   for (int md = 0; md < 2; ++md) {
     mt[md].tiles = (const Tile*)cur;
@@ -470,7 +503,7 @@ int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const i
   unsigned long long* d_ctr = (unsigned long long*)cur;
   mt[0].ctr = d_ctr;
   mt[1].ctr = d_ctr + 1;
-  err = cudaMemcpyAsync(d_probs, probs.data(), pb, cudaMemcpyHostToDevice, st);
+  err = cudaMemcpyAsync((void*)d_probs, probs.data(), pb, cudaMemcpyHostToDevice, st);
   for (int md = 0; md < 2 && err == cudaSuccess; ++md) {
     if (!tb[md]) continue;
     err = cudaMemcpyAsync((void*)mt[md].tiles, tiles[md].data(), tb[md], cudaMemcpyHostToDevice,
@@ -481,28 +514,120 @@ int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const i
   }
   if (err == cudaSuccess) err = cudaMemsetAsync(d_ctr, 0, qb, st);
   // which sweeps are counted for at least one problem (a swap iteration or a trace row)
-  std::vector<char> any_exchange((size_t)n_max, 0);
+  counted.assign((size_t)n_max, 0);
   for (const FlatProblem& fp : probs)
     for (int64_t j = 0; j < fp.n; ++j)
       if (fp.p.trace_E != nullptr ||
           (fp.m > 0 && (fp.t0 + (uint64_t)j + 1) % (uint64_t)fp.m == 0))
-        any_exchange[(size_t)j] = 1;
-  const int np = (int)probs.size();
-  size_t xsmem = 0;
+        counted[(size_t)j] = 1;
+  np = (int)probs.size();
   for (const FlatProblem& fp : probs)
     xsmem = std::max(xsmem, flat_exchange_smem(fp.p.R, fp.p.mode));
   if (err == cudaSuccess) err = flat_exchange_prepare(xsmem);
-  for (int64_t j = 0; j < n_max && err == cudaSuccess; ++j)
-    err = launch_flat_sweep(mt, d_probs, np, j, any_exchange[(size_t)j] != 0, xsmem, di.sms, st);
-  const cudaError_t err2 = cudaFreeAsync(scratch, st);
-  if (err == cudaSuccess) err = err2;
-  if (err != cudaSuccess) {
-    for (int j = 0; j < count; ++j) ps[j]->poisoned = PT_ECUDA;
-    return fail(PT_ECUDA, "flat batch launch: %s", cudaGetErrorString(err));
-  }
+  if (err != cudaSuccess) return fail(PT_ECUDA, "flat batch set-up: %s", cudaGetErrorString(err));
   return PT_OK;
 }
 
+// Side streams per device for the multi-stream lock-step batch (fork / join through
+// events); the mutex keeps two host threads from using one set of streams and events at once.
+constexpr int kMaxBatchStreams = PT_BATCH_STREAMS_MAX;
+struct SideStreams {
+  bool ok = false;
+  cudaStream_t stream[kMaxBatchStreams - 1] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kMaxBatchStreams - 1] = {};
+  std::mutex mu;
+};
+
+SideStreams& side_streams(int device) {
+  static std::mutex mu;
+  static SideStreams streams[64];
+  std::lock_guard<std::mutex> lk(mu);
+  SideStreams& s = streams[device & 63];
+  if (!s.ok) {
+    bool ok = cudaEventCreateWithFlags(&s.fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; ok && k < kMaxBatchStreams - 1; ++k)
+      ok = cudaStreamCreateWithFlags(&s.stream[k], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&s.join[k], cudaEventDisableTiming) == cudaSuccess;
+    s.ok = ok;
+  }
+  return s;
+}
+
+// The lock-step batch as `parts` parts of about equal work (L^2 W n each, heaviest first onto
+// the lightest part), each on its own stream: sweep j of one part runs beside sweep j of the
+// others, so one part's exchange launch, launch gaps and last tiles overlap the others' half
+// sweeps. Part 0 runs on the problems' stream, the others on side streams that start after
+// everything queued on it so far and that it waits for at the end.
+int sweep_batch_flat_parts(pt_problem* const* ps, int count, const int64_t* n, const int* every,
+                           cudaStream_t st, const DeviceInfo& di, int tile_words, bool queued,
+                           int parts) {
+  std::vector<int> order;
+  for (int j = 0; j < count; ++j)
+    if (n[j] > 0) order.push_back(j);
+  auto work = [&](int j) { return (double)ps[j]->L * ps[j]->L * ps[j]->W * (double)n[j]; };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+  parts = std::max(1, std::min(parts, std::min(kMaxBatchStreams, (int)order.size())));
+  std::vector<pt_problem*> gp[kMaxBatchStreams];
+  std::vector<int64_t> gn[kMaxBatchStreams];
+  std::vector<int> ge[kMaxBatchStreams];
+  double load[kMaxBatchStreams] = {};
+  for (int j : order) {
+    int g = 0;
+    for (int k = 1; k < parts; ++k)
+      if (load[k] < load[g]) g = k;
+    gp[g].push_back(ps[j]);
+    gn[g].push_back(n[j]);
+    ge[g].push_back(every[j]);
+    load[g] += work(j);
+  }
+  SideStreams* ss = parts > 1 ? &side_streams(di.device) : nullptr;
+  std::unique_lock<std::mutex> lk;
+  if (ss) {
+    lk = std::unique_lock<std::mutex>(ss->mu);
+    if (!ss->ok) return fail(PT_ECUDA, "batch side streams could not be created");
+  }
+  cudaError_t err = cudaSuccess;
+  if (parts > 1) {
+    err = cudaEventRecord(ss->fork, st);
+    for (int k = 0; k + 1 < parts && err == cudaSuccess; ++k)
+      err = cudaStreamWaitEvent(ss->stream[k], ss->fork, 0);
+    if (err != cudaSuccess) return fail(PT_ECUDA, "batch fork: %s", cudaGetErrorString(err));
+  }
+  FlatRun run[kMaxBatchStreams];
+  int rc = PT_OK;
+  int64_t n_max = 0;
+  for (int g = 0; g < parts && !rc; ++g) {
+    rc = run[g].prepare(gp[g].data(), (int)gp[g].size(), gn[g].data(), ge[g].data(),
+                        g == 0 ? st : ss->stream[g - 1], di, tile_words, queued);
+    n_max = std::max(n_max, run[g].n_max);
+  }
+  err = rc ? cudaErrorUnknown : cudaSuccess;
+  for (int64_t j = 0; j < n_max && err == cudaSuccess; ++j)
+    for (int g = 0; g < parts && err == cudaSuccess; ++g) err = run[g].launch_sweep(j);
+  cudaError_t err2 = cudaSuccess;
+  for (int g = 0; g < parts; ++g) {
+    const cudaError_t e = run[g].finish();
+    if (err2 == cudaSuccess) err2 = e;
+  }
+  // the problems' stream waits for the side streams' work
+  for (int k = 0; k + 1 < parts; ++k) {
+    if (err2 == cudaSuccess) err2 = cudaEventRecord(ss->join[k], ss->stream[k]);
+    if (err2 == cudaSuccess) err2 = cudaStreamWaitEvent(st, ss->join[k], 0);
+  }
+  if (rc == PT_ECUDA || (!rc && (err != cudaSuccess || err2 != cudaSuccess)))
+    for (int j = 0; j < count; ++j) ps[j]->poisoned = PT_ECUDA;
+  if (rc) return rc;
+  if (err == cudaSuccess) err = err2;
+  if (err != cudaSuccess) return fail(PT_ECUDA, "flat batch launch: %s", cudaGetErrorString(err));
+  return PT_OK;
+}
+
+int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const int* every,
+                     cudaStream_t st, const DeviceInfo& di, int tile_words, bool queued,
+                     int streams) {
+  return sweep_batch_flat_parts(ps, count, n, every, st, di, tile_words, queued, streams);
+}
 
 // =======================================================================================
 // Allocation-free variant of the lock-step batch.

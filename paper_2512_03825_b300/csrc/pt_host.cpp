@@ -1717,6 +1717,21 @@ int pt_set_batch_tile_words(int tile_words) {
   return PT_OK;
 }
 
+int pt_set_batch_streams(int streams) {
+  if (streams < 1 || streams > PT_BATCH_STREAMS_MAX)
+    return fail(PT_EINVAL, "streams = %d outside 1..%d", streams, PT_BATCH_STREAMS_MAX);
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_batch_tuning.streams = streams;
+  return PT_OK;
+}
+
+int pt_get_batch_streams(int* streams) {
+  if (!streams) return fail(PT_EINVAL, "null output");
+  std::lock_guard<std::mutex> lk(g_mu);
+  *streams = g_batch_tuning.streams;
+  return PT_OK;
+}
+
 int pt_get_batch_tile_words(int* tile_words) {
   if (!tile_words) return fail(PT_EINVAL, "null output");
   std::lock_guard<std::mutex> lk(g_mu);

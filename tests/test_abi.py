@@ -256,3 +256,16 @@ def test_release_library_has_no_debug_checks(pt):
     assert pt.lib.pt_debug_build() == 0
     assert pt.lib.pt_debug_report(None, None, None, None, None) == pt.PT_EINVAL
     assert pt.lib.pt_debug_inject(None, 1) != 0
+
+
+def test_batch_streams_validated(pt):
+    import ctypes as C
+    n = C.c_int()
+    assert pt.lib.pt_get_batch_streams(C.byref(n)) == 0
+    before = n.value
+    for bad in (0, -1, 5):
+        assert pt.lib.pt_set_batch_streams(bad) == pt.PT_EINVAL
+    assert pt.lib.pt_set_batch_streams(3) == 0
+    assert pt.lib.pt_get_batch_streams(C.byref(n)) == 0 and n.value == 3
+    assert pt.lib.pt_get_batch_streams(None) == pt.PT_EINVAL
+    assert pt.lib.pt_set_batch_streams(before) == 0

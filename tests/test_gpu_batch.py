@@ -206,12 +206,47 @@ def test_flow_wait_runs_out_and_context_survives(api, tuning):
         np.testing.assert_array_equal(h.chain_map(), o.chain_map())
 
 
+@pytest.mark.parametrize("strategy", [0, 3])
+@pytest.mark.parametrize("streams", [2, 3, 4])
+def test_batch_over_several_streams(api, strategy, streams):
+    """The lock-step batch split into parts on their own streams: every problem ends exactly
+    as when advanced alone, and the problems' stream is ordered after every part -- a plain
+    sweep queued right after the batch, on the same stream, sees the batch's result (checked
+    against the oracle)."""
+    import torch
+    from paper_2512_03825_b300 import autotune
+    before = autotune.get_tuning()
+    probs = mixed_problems(n=20, seed=23 + streams)
+    try:
+        autotune.set_tuning(strategy, 1, 128, 128, streams)
+        st = torch.cuda.Stream()
+        batch = [api.PTProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed, stream=st)
+                 for p in probs]
+        api.sweep_batch(batch, [p.sweeps for p in probs], [p.every for p in probs])
+        for b in batch[:5]:
+            b.sweep(3, 2)   # on the problems' stream, right behind the batch's parts
+        api.sweep_batch(batch[5:], 2, 1)
+    finally:
+        autotune.set_tuning(**before)
+    oracle.set_threads(8)
+    for j, (pr, b) in enumerate(zip(probs, batch)):
+        o = oracle.OracleProblem(pr.L, pr.betas, J=pr.J, h=pr.h, seed=pr.seed)
+        o.sweep(pr.sweeps, pr.every)
+        o.sweep(3, 2) if j < 5 else o.sweep(2, 1)
+        np.testing.assert_array_equal(b.spins(), o.spins(), err_msg="problem %d" % j)
+        np.testing.assert_array_equal(b.energies_int(), o.energies_int(), err_msg=str(j))
+        np.testing.assert_array_equal(b.chain_map(), o.chain_map(), err_msg=str(j))
+        for x, y in zip(b.swap_stats(), o.swap_stats()):
+            np.testing.assert_array_equal(x, y, err_msg=str(j))
+
+
 def test_autotuner_compares_equal_results(api, tuning):
     """The autotuner times a few candidates (tile sizes, strategies), checks that they all
     leave the problems in the same state, and applies the fastest without saving it."""
     from paper_2512_03825_b300 import autotune
     probs = W.batched_problems(n=10)
-    cands = [(0, 1, 128, 128), (3, 1, 128, 1024), (2, 1, 128, 256), (1, 2, 64, 512)]
+    cands = [(0, 1, 128, 128, 1), (3, 1, 128, 1024, 1), (2, 1, 128, 256, 1), (1, 2, 64, 512, 1),
+             (0, 1, 128, 512, 3), (3, 1, 128, 512, 2)]
     out = autotune.tune(probs, sweeps=4, every=1, candidates=cands, repeats=1, save=False)
     assert tuple(out["choice"].values()) in cands
     assert len(out["timings"]) == len(cands)
