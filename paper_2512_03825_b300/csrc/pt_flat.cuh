@@ -324,7 +324,24 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
     };
     // few classes with dE > 0 (five for J > 0, 0 < |h| < 2 J): compare with all of them
     const uint32_t cm = (uint32_t)p.cmp_classes;
-    if (__popc(cm) == 5) {
+    // J > 0 and 0 < h < 2 J (the served mix's field problems): the classes with dE > 0 are
+    // 0..4 (k = 0, 1 with either spin, k = 2 against the field); h < 0 mirrors it (0..3, 5).
+    // With the class set known at compile time the threshold rows are read at fixed offsets:
+    // 181.3 / 160.7 -> 174.3 / 154.5 us per batched-256 sweep at h = 0.1 (with / without a
+    // swap iteration every sweep)
+    if (cm == 0x1Fu) {
+      constexpr int cls_pos[5] = {0, 1, 2, 3, 4};
+      gen_loop([&](uint32_t s, uint32_t n0, uint32_t n1, uint32_t n2, uint32_t n3,
+                   const auto& draw) {
+        return update_word_generic_cmp<5>(s, n0, n1, n2, n3, nblk, pl, cls_pos, draw);
+      });
+    } else if (cm == 0x2Fu) {
+      constexpr int cls_neg[5] = {0, 1, 2, 3, 5};
+      gen_loop([&](uint32_t s, uint32_t n0, uint32_t n1, uint32_t n2, uint32_t n3,
+                   const auto& draw) {
+        return update_word_generic_cmp<5>(s, n0, n1, n2, n3, nblk, pl, cls_neg, draw);
+      });
+    } else if (__popc(cm) == 5) {
       int cls[5];
       uint32_t rest = cm;
 #pragma unroll

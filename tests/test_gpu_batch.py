@@ -240,6 +240,32 @@ def test_batch_over_several_streams(api, strategy, streams):
             np.testing.assert_array_equal(x, y, err_msg=str(j))
 
 
+@pytest.mark.parametrize("strategy", [0, 3])
+def test_field_signs_and_class_sets_match_oracle(api, strategy):
+    """Batched problems whose trials compare with five class thresholds (J > 0, 0 < |h| < 2J,
+    either sign of the field: the class sets the kernel knows at compile time) and with other
+    class counts (|h| >= 2J, J < 0) all equal the oracle."""
+    from paper_2512_03825_b300 import autotune
+    before = autotune.get_tuning()
+    cases = [(1.0, 0.1), (1.0, -0.1), (1.0, 0.7), (1.0, -1.3), (1.0, 2.5), (-1.0, 0.25),
+             (0.5, -0.2), (2.0, 0.0)]
+    probs = [W.Problem(L=24 + 8 * (j % 3), betas=W.linear_ladder(0.2, 0.7, 5 + 9 * j), J=J,
+                       h=h, seed=7700 + j) for j, (J, h) in enumerate(cases)]
+    try:
+        autotune.set_tuning(strategy, 1, 128, 128, 1)
+        gs = [api.PTProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed) for p in probs]
+        api.sweep_batch(gs, 9, 2)
+    finally:
+        autotune.set_tuning(**before)
+    oracle.set_threads(8)
+    for p, g in zip(probs, gs):
+        o = oracle.OracleProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed)
+        o.sweep(9, 2)
+        np.testing.assert_array_equal(g.spins(), o.spins(), err_msg="J %g h %g" % (p.J, p.h))
+        np.testing.assert_array_equal(g.energies_int(), o.energies_int())
+        np.testing.assert_array_equal(g.chain_map(), o.chain_map())
+
+
 def test_autotuner_compares_equal_results(api, tuning):
     """The autotuner times a few candidates (tile sizes, strategies), checks that they all
     leave the problems in the same state, and applies the fastest without saving it."""
