@@ -327,13 +327,15 @@ __device__ __forceinline__ uint32_t update_word_generic_with(uint32_t s, uint32_
 // cls[0..NC-1]; every other class has dE <= 0, so its threshold is 2^32 and its slots are in
 // the always-masks): each trial is compared with the thresholds of all NC classes (read four
 // slots at a time), and bit-sliced class masks pick the result of the slot's own class,
-// instead of a class extracted and looked up per slot. Same decisions, bit for bit.
-template <int NC, class Draw>
+// instead of a class extracted and looked up per slot. Same decisions, bit for bit. NBC > 0
+// fixes the block count at compile time (nblk_rt is then ignored).
+template <int NC, int NBC = 0, class Draw>
 __device__ __forceinline__ uint32_t update_word_generic_cmp(uint32_t s, uint32_t n0, uint32_t n1,
-                                                            uint32_t n2, uint32_t n3, int nblk,
+                                                            uint32_t n2, uint32_t n3, int nblk_rt,
                                                             const PlaneGeneric& pl,
                                                             const int (&cls)[NC],
                                                             const Draw& draw) {
+  const int nblk = NBC > 0 ? NBC : nblk_rt;
   const NbCount k = count4(s ^ n0, s ^ n1, s ^ n2, s ^ n3);
   const uint32_t z[5] = {~(k.b0 | k.b1 | k.b2), k.b0 & ~k.b1 & ~k.b2, ~k.b0 & k.b1 & ~k.b2,
                          k.b0 & k.b1, k.b2};

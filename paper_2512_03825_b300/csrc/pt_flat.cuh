@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
 #include <vector>
 
 #include "pt_debug.cuh"
@@ -184,6 +185,36 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
   const int q_start = tl.q0 + lane;
   int y = q_start / half, i = q_start - y * half;
   const int dy = 32 / half, di = 32 - dy * half;
+  // the inputs of one word: the lane's word, its four neighbours (other colour) and site
+  struct WordIn {
+    uint32_t s, n0, n1, n2, n3, site;
+  };
+  // the neighbours as offsets from the lane's own word q = yy * half + ii (rows yy - 1 and
+  // yy + 1 at the same ii, row yy at ii -+ 1 by the row parity, all mod L): no multiplies
+  // (measured: 2% fewer instructions than row * half + column addressing)
+  const int wrap = nwords - half;  // (L - 1) * half
+  const auto load_word = [&](int q, int yy, int ii) {
+    const int par = (yy + colour) & 1;
+    const int o0 = (yy == 0) ? wrap : -half;
+    const int o1 = (yy == L - 1) ? -wrap : half;
+    const int o3 = par ? ((ii + 1 == half) ? -ii : 1) : ((ii == 0) ? half - 1 : -1);
+    WordIn a;
+    a.s = own[PT_DBG_IDX(p, q, nwords, kDbgSpinLoad)];  // this lane's word
+    a.n0 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, q + o0, nwords, kDbgSpinLoad));
+    a.n1 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, q + o1, nwords, kDbgSpinLoad));
+    a.n2 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, q, nwords, kDbgSpinLoad));
+    a.n3 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, q + o3, nwords, kDbgSpinLoad));
+    a.site = (uint32_t)(2 * q + par);  // y L + x with x = 2 ii + par
+    return a;
+  };
+  const auto step = [&]() {
+    i += di;
+    y += dy;
+    if (i >= half) {
+      i -= half;
+      y += 1;
+    }
+  };
   if (MODE == kModeFerro) {
     // the tile's thresholds in the warp's shared slot, interleaved for 16-byte broadcast
     // loads (the previous tile's readers are done at the warp barrier)
@@ -201,36 +232,6 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
     // (measured: 131.5 -> 122.9 us per batched-256 sweep without swaps; with the wide
     // multiplies the counting kernel gains from it too, 135.3 -> 134.0 us per sweep with a
     // swap iteration, where before it cost registers and time)
-    // the inputs of one word: the lane's word, its four neighbours (other colour) and site
-    struct WordIn {
-      uint32_t s, n0, n1, n2, n3, site;
-    };
-    // the neighbours as offsets from the lane's own word q = yy * half + ii (rows yy - 1 and
-    // yy + 1 at the same ii, row yy at ii -+ 1 by the row parity, all mod L): no multiplies
-    // (measured: 2% fewer instructions than row * half + column addressing)
-    const int wrap = nwords - half;  // (L - 1) * half
-    const auto load_word = [&](int q, int yy, int ii) {
-      const int par = (yy + colour) & 1;
-      const int o0 = (yy == 0) ? wrap : -half;
-      const int o1 = (yy == L - 1) ? -wrap : half;
-      const int o3 = par ? ((ii + 1 == half) ? -ii : 1) : ((ii == 0) ? half - 1 : -1);
-      WordIn a;
-      a.s = own[PT_DBG_IDX(p, q, nwords, kDbgSpinLoad)];  // this lane's word
-      a.n0 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, q + o0, nwords, kDbgSpinLoad));
-      a.n1 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, q + o1, nwords, kDbgSpinLoad));
-      a.n2 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, q, nwords, kDbgSpinLoad));
-      a.n3 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, q + o3, nwords, kDbgSpinLoad));
-      a.site = (uint32_t)(2 * q + par);  // y L + x with x = 2 ii + par
-      return a;
-    };
-    const auto step = [&]() {
-      i += di;
-      y += dy;
-      if (i >= half) {
-        i -= half;
-        y += 1;
-      }
-    };
     const auto finish_word = [&](int q, const WordIn& a, uint32_t ns) {
       if (PT_DBG_STORE(p, q, nwords, own_base, t, colour)) own[q] = ns;
       if (COUNT && count) {
@@ -293,53 +294,58 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
         dst[q] = src[q];
       __syncwarp();
     }
-    // the generic kernel keeps the block count at run time: with it fixed (one loop per
-    // count) a batch with a field ran 17% slower (with the wide multiplies: 31% slower); its
-    // bond count stays a second pass (counting in the word loop measured no faster)
     const PlaneGeneric& pl = *gen;
-    const auto gen_loop = [&](const auto& update) {
+    // few classes with dE > 0 (five for J > 0, 0 < |h| < 2 J): compare with all of them
+    const uint32_t cm = (uint32_t)p.cmp_classes;
+    // the five-class paths count the bonds and up spins of the words they write in the word
+    // loop (158.7 -> 155.5 us per batched-256 sweep at h = 0.1 with a swap iteration every
+    // sweep); the lookup path counts them in a second pass
+    BitCounter<13, 8> Ug, Ng;
+    if (COUNT) {
+      Ug.zero();
+      Ng.zero();
+    }
+    const auto gen_loop = [&](auto in_loop, const auto& update) {
+      constexpr bool CNT_IN_LOOP = decltype(in_loop)::value;
       for (int q = q_start; q < tl.q1; q += 32) {
-        const int par = (y + colour) & 1;
-        const int ym = (y == 0) ? L - 1 : y - 1;
-        const int yp = (y == L - 1) ? 0 : y + 1;
-        const int ih = par ? ((i + 1 == half) ? 0 : i + 1) : ((i == 0) ? half - 1 : i - 1);
-        const uint32_t s = own[PT_DBG_IDX(p, q, nwords, kDbgSpinLoad)];
-        const uint32_t n0 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, ym * half + i, nwords, kDbgSpinLoad));
-        const uint32_t n1 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, yp * half + i, nwords, kDbgSpinLoad));
-        const uint32_t n2 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, q, nwords, kDbgSpinLoad));
-        const uint32_t n3 = ld_nb<NB_L2>(oth + PT_DBG_IDX(p, y * half + ih, nwords, kDbgSpinLoad));
-        const uint32_t site = (uint32_t)(y * L + 2 * i + par);
-        const SiteTerms st = site_terms(site, c3, rk);
-        const uint32_t ns = update(s, n0, n1, n2, n3, [&](int jb) {
+        const WordIn a = load_word(q, y, i);
+        const SiteTerms st = site_terms(a.site, c3, rk);
+        const uint32_t ns = update(a.s, a.n0, a.n1, a.n2, a.n3, [&](int jb) {
           return philox_site_block(st, bt, jb, rk);
         });
         if (PT_DBG_STORE(p, q, nwords, own_base, t, colour)) own[q] = ns;
-        i += di;
-        y += dy;
-        if (i >= half) {
-          i -= half;
-          y += 1;
+        if (COUNT && CNT_IN_LOOP && count) {
+          const NbCount k = count4(ns ^ a.n0, ns ^ a.n1, ns ^ a.n2, ns ^ a.n3);
+          Ug.add3(k.b0, k.b1, k.b2);
+          Ng.add2(ns ^ a.n0, ns & a.n0);
         }
+        step();
       }
     };
-    // few classes with dE > 0 (five for J > 0, 0 < |h| < 2 J): compare with all of them
-    const uint32_t cm = (uint32_t)p.cmp_classes;
     // J > 0 and 0 < h < 2 J (the served mix's field problems): the classes with dE > 0 are
     // 0..4 (k = 0, 1 with either spin, k = 2 against the field); h < 0 mirrors it (0..3, 5).
-    // With the class set known at compile time the threshold rows are read at fixed offsets:
-    // 181.3 / 160.7 -> 174.3 / 154.5 us per batched-256 sweep at h = 0.1 (with / without a
-    // swap iteration every sweep)
+    // With the class set known at compile time the threshold rows are read at fixed offsets
+    // (181.3 / 160.7 -> 174.3 / 154.5 us per batched-256 sweep at h = 0.1, with / without a
+    // swap iteration every sweep), and with the Philox block count fixed too, one loop per
+    // count: 158.3 / 138.6 us. The other class sets keep the per-slot lookup and the block
+    // count at run time (with the lookup, a fixed count measured 17% slower).
     if (cm == 0x1Fu) {
       constexpr int cls_pos[5] = {0, 1, 2, 3, 4};
-      gen_loop([&](uint32_t s, uint32_t n0, uint32_t n1, uint32_t n2, uint32_t n3,
-                   const auto& draw) {
-        return update_word_generic_cmp<5>(s, n0, n1, n2, n3, nblk, pl, cls_pos, draw);
+      with_block_count(nblk, [&](auto nbc) {
+        constexpr int NB = decltype(nbc)::value;
+        gen_loop(std::true_type{}, [&](uint32_t s, uint32_t n0, uint32_t n1, uint32_t n2,
+                                       uint32_t n3, const auto& draw) {
+          return update_word_generic_cmp<5, NB>(s, n0, n1, n2, n3, nblk, pl, cls_pos, draw);
+        });
       });
     } else if (cm == 0x2Fu) {
       constexpr int cls_neg[5] = {0, 1, 2, 3, 5};
-      gen_loop([&](uint32_t s, uint32_t n0, uint32_t n1, uint32_t n2, uint32_t n3,
-                   const auto& draw) {
-        return update_word_generic_cmp<5>(s, n0, n1, n2, n3, nblk, pl, cls_neg, draw);
+      with_block_count(nblk, [&](auto nbc) {
+        constexpr int NB = decltype(nbc)::value;
+        gen_loop(std::true_type{}, [&](uint32_t s, uint32_t n0, uint32_t n1, uint32_t n2,
+                                       uint32_t n3, const auto& draw) {
+          return update_word_generic_cmp<5, NB>(s, n0, n1, n2, n3, nblk, pl, cls_neg, draw);
+        });
       });
     } else if (__popc(cm) == 5) {
       int cls[5];
@@ -349,17 +355,23 @@ __device__ __forceinline__ void tile_half(const FlatProblem& fp, const Tile& tl,
         cls[c] = __ffs(rest) - 1;
         rest &= rest - 1;
       }
-      gen_loop([&](uint32_t s, uint32_t n0, uint32_t n1, uint32_t n2, uint32_t n3,
-                   const auto& draw) {
+      gen_loop(std::false_type{}, [&](uint32_t s, uint32_t n0, uint32_t n1, uint32_t n2,
+                                      uint32_t n3, const auto& draw) {
         return update_word_generic_cmp<5>(s, n0, n1, n2, n3, nblk, pl, cls, draw);
       });
     } else {
-      gen_loop([&](uint32_t s, uint32_t n0, uint32_t n1, uint32_t n2, uint32_t n3,
-                   const auto& draw) {
+      gen_loop(std::false_type{}, [&](uint32_t s, uint32_t n0, uint32_t n1, uint32_t n2,
+                                      uint32_t n3, const auto& draw) {
         return update_word_generic_with(s, n0, n1, n2, n3, nblk, pl, draw);
       });
     }
-    if (COUNT && count) {
+    if (COUNT && count && (cm == 0x1Fu || cm == 0x2Fu)) {
+      const uint32_t u = Ug.warp_total_for_lane();
+      const uint32_t nn = Ng.warp_total_for_lane();
+      if (u) atomicAdd(&p.cnt[PT_DBG_IDX(p, w * 32 + lane, 2 * p.W * 32, kDbgCount)], u);
+      if (nn)
+        atomicAdd(&p.cnt[PT_DBG_IDX(p, p.W * 32 + w * 32 + lane, 2 * p.W * 32, kDbgCount)], nn);
+    } else if (COUNT && count) {
       // second pass over the words this lane just wrote and their colour-0 neighbours
       BitCounter<13, 8> U, N;
       U.zero();
