@@ -46,7 +46,7 @@ FLAT_TRAFFIC_BYTES = 25.977344e6 + 0.0
 FLAT_TRAFFIC_SOURCES = ("paper_2512_03825_b300/csrc/pt_device.cuh",
                         "paper_2512_03825_b300/csrc/pt_flat.cuh",
                         "paper_2512_03825_b300/csrc/pt_flat.cu")
-FLAT_TRAFFIC_SOURCE_HASH = "68f5fe60b3c28e17"
+FLAT_TRAFFIC_SOURCE_HASH = "f93b2dae4d7a4b04"
 
 
 def _flat_traffic():
@@ -73,6 +73,9 @@ def parse_args(argv=None):
                     help="single-spin-flip iterations per replica per step (--workload flip)")
     ap.add_argument("--sweeps", type=int, default=2000, help="sweeps per problem per step")
     ap.add_argument("--problems", type=int, default=256)
+    ap.add_argument("--field", type=float, default=0.0,
+                    help="field h of the batched workload's problems (J = 1; h != 0 runs the "
+                         "generic update)")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving leg of the default line")
     ap.add_argument("--requests", type=int, default=2000,
@@ -130,13 +133,14 @@ def sum_over_ranks(x, world):
 RANK_SEED_STRIDE = 0x10000
 
 
-def rank_problems(rank, n, sweeps, every=1):
+def rank_problems(rank, n, sweeps, every=1, h=0.0):
     """This rank's share of the work: its own copy of the batched workload with seeds offset
-    by rank, so every rank advances different (independent) problems of the same shape."""
+    by rank, so every rank advances different (independent) problems of the same shape; h is
+    the problems' field."""
     from paper_2512_03825_b300 import workloads as W
     import dataclasses
     probs = W.batched_problems(n=n, sweeps=sweeps, every=every)
-    return [dataclasses.replace(p, seed=p.seed + rank * RANK_SEED_STRIDE) for p in probs]
+    return [dataclasses.replace(p, seed=p.seed + rank * RANK_SEED_STRIDE, h=h) for p in probs]
 
 
 def job_throughput(attempts_this_rank, seconds_this_rank, world):
@@ -255,7 +259,7 @@ def run_ours(args, rank, world, local):
                                        % args.requests},
                 "serve": res}
 
-    probs = rank_problems(rank, args.problems, args.sweeps, 1)
+    probs = rank_problems(rank, args.problems, args.sweeps, 1, args.field)
     handles = [api.PTProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed, stream=stream)
                for p in probs]
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
@@ -291,8 +295,8 @@ def run_ours(args, rank, world, local):
         "data": "synthetic (seeded problem mix; random +-1 initial spins)",
         "config": {
             "workload": "batched-256: %d PT problems, L in {32,48,64,96,128,256}, R 8-48, "
-                        "betas 0.30-0.60, J=1, h=0, %d sweeps, exchange every sweep"
-                        % (args.problems, args.sweeps),
+                        "betas 0.30-0.60, J=1, h=%g, %d sweeps, exchange every sweep"
+                        % (args.problems, args.field, args.sweeps),
             "problems": args.problems, "sweeps_per_step": args.sweeps, "exchange_every": 1,
             "attempts_per_step": per_step, "parallelism": "independent problems per GPU",
             "l2": "flushed (256 MiB write) between timed steps",
@@ -338,7 +342,7 @@ def run_ours(args, rank, world, local):
                "stream) / its average launch duration, (t(%d sweeps) - t(%d sweeps)) / %d "
                "launches (CUDA events on the problems' stream)"
                % (len(probs), lens[1], lens[0], 2 * (lens[1] - lens[0])))
-        traffic = _flat_traffic()
+        traffic = _flat_traffic() if args.field == 0.0 else None
         if tuning.get("streams", 1) > 1:
             ov = per_step / args.sweeps / 2 / half_sweep_s(tuning["streams"])
             overlapped = {"streams": tuning["streams"],
@@ -376,6 +380,8 @@ def run_ours(args, rank, world, local):
     }
     if not args.quick and rank == 0:
         out["serve"] = bench_serve_short(stream, args.serve_requests)
+        if args.field == 0.0:
+            out["batched_h0.1"] = bench_batched_field(stream, args.problems, args.sweeps, 0.1)
         out["plain"] = bench_plain(probs, args.sweeps, stream)
         out["batched_vs_plain"] = value / world / out["plain"]["value"]
         out["single_L1024_R64"] = bench_single(stream, sms, clock_mhz)
@@ -438,6 +444,33 @@ def _plain_run(sample, sweeps, strategy, stream):
     for h in hs:
         h.close()
     return _attempts(sample, sweeps) / (ms / 1e3)
+
+
+def bench_batched_field(stream, n, sweeps, h, steps=2):
+    """The default step's problems with a field h (J = 1): the generic update (five threshold
+    classes with dE > 0 for 0 < h < 2), the same batch call, `steps` timed batches of `sweeps`
+    sweeps with an exchange after every sweep, L2 flushed between them."""
+    import torch
+    from paper_2512_03825_b300 import api
+    probs = rank_problems(0, n, sweeps, 1, h)
+    hs = [api.PTProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed, stream=stream) for p in probs]
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    took = []
+    with torch.cuda.stream(stream):
+        api.sweep_batch(hs, 200, 1)
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            api.sweep_batch(hs, sweeps, 1)
+            b.record(stream)
+            torch.cuda.synchronize()
+            took.append(a.elapsed_time(b) / 1e3)
+    for g in hs:
+        g.close()
+    t = statistics.mean(took)
+    return {"value": _attempts(probs, sweeps) / t, "unit": UNIT, "h": h, "problems": n,
+            "sweeps": sweeps, "every": 1, "steps": steps, "us_per_sweep": 1e6 * t / sweeps}
 
 
 def bench_plain(probs, sweeps, stream, n_sample=32, sample_sweeps=200):
