@@ -489,12 +489,14 @@ def bench_plain(probs, sweeps, stream, n_sample=32, sample_sweeps=200):
 
 
 def bench_single(stream, sms, clock_mhz, name="L1024_R64", sweeps=200, prob=None):
-    """One single-problem config on the plain path (pt_sweep, default strategy)."""
+    """One single-problem config on the plain path (pt_sweep), in the shape the plain-path
+    autotuner cached for it on this device, else the library's default strategy."""
     import torch
-    from paper_2512_03825_b300 import api
+    from paper_2512_03825_b300 import api, autotune
     from paper_2512_03825_b300 import workloads as W
     p = prob if prob is not None else W.SINGLE[name]
     h = api.PTProblem(p.L, p.betas, seed=p.seed, stream=stream)
+    tuned = autotune.apply_single(h, p.L, p.R, p.J, p.h)
     h.sweep(10, p.every)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -503,14 +505,17 @@ def bench_single(stream, sms, clock_mhz, name="L1024_R64", sweeps=200, prob=None
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
-    strategy, _, grid = h.sweep_tuning()
+    strategy, wpt, grid = h.sweep_tuning()
     h.close()
     att = float(p.L * p.L * p.R * sweeps)
     v = att / (ms / 1e3)
     peak_att = sms * IMUL_WIDE_PER_CLK_SM * clock_mhz * 1e6 / MUL_PER_ATTEMPT
+    peak_issue = sms * LANE_OPS_PER_CLK_SM * clock_mhz * 1e6 / OPS_PER_ATTEMPT
     return {"value": v, "unit": UNIT, "sweeps": sweeps, "every": p.every,
+            "frac_of_issue_roofline": v / peak_issue,
             "frac_of_mul_roofline": v / peak_att, "us_per_sweep": 1e3 * ms / sweeps,
-            "persistent_grid": grid}
+            "sweep_strategy": strategy, "words_per_thread": wpt, "persistent_grid": grid,
+            "tuned": tuned is not None}
 
 
 def bench_paper_flip(stream, iterations=300_000, every=100):

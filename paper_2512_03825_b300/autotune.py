@@ -1,4 +1,4 @@
-"""Autotuner for the batched kernel's launch shape.
+"""Autotuners for the launch shapes of the batched path and of the plain (one problem) path.
 
 Knobs: the batched strategy (lock-step tiles dealt by the host or handed out by a device
 queue, the same tiles in one dataflow launch, or one persistent cluster kernel); for the tile strategies the words per warp tile (the words
@@ -8,6 +8,12 @@ thread-block cluster and the lattice size from which a problem is spread over a 
 cluster instead of one CTA. They change only how work is
 distributed, never a result: `tune` checks that every candidate leaves every problem in the
 same state (spins, temperature map, swap counters) before it compares times.
+
+For the plain path (`tune_single`) the knobs are the halo scheme of the persistent sweep
+(each CTA owning strided words of a plane, with a grid barrier between the colours, or a
+band of whole rows in shared memory whose halo rows it recomputes, with one grid barrier a
+sweep), the words of each colour a thread owns, and one launch per half sweep instead of a
+persistent launch; the choice is kept per problem shape (L, R, J, h).
 
 Choices are cached per device name in ``autotune_cache.json`` next to this module.
 """
@@ -133,3 +139,136 @@ def tune(problems: Sequence, sweeps: int = 200, every: int = 1,
         with open(CACHE, "w") as f:
             json.dump(cache, f, indent=1, sort_keys=True)
     return {"choice": choice, "timings": [(c, t) for t, c in results]}
+
+
+# ---------------------------------------------------------------------------------------
+# plain path: one problem per pt_sweep call
+# ---------------------------------------------------------------------------------------
+SWEEP_AUTO, SWEEP_LAUNCHES, SWEEP_PERSISTENT, SWEEP_BANDS = 0, 1, 2, 3
+# (strategy, words_per_thread)
+SINGLE_CANDIDATES: Tuple[Tuple[int, int], ...] = (
+    (SWEEP_PERSISTENT, 1), (SWEEP_PERSISTENT, 2), (SWEEP_PERSISTENT, 4), (SWEEP_PERSISTENT, 8),
+    (SWEEP_BANDS, 1), (SWEEP_BANDS, 2), (SWEEP_BANDS, 4), (SWEEP_LAUNCHES, 1))
+
+
+def shape_key(L: int, R: int, J: float, h: float) -> str:
+    return "L%d_R%d_J%g_h%g" % (L, R, J, h)
+
+
+def _single_snapshot(h):
+    att, acc = h.swap_stats()
+    return (h.spins().tobytes(), h.chain_map().tobytes(), att.tobytes(), acc.tobytes(),
+            h.energies_int().tobytes())
+
+
+def tune_single(problem, sweeps: int = 200, every: int = 1,
+                candidates: Sequence[Tuple[int, int]] = SINGLE_CANDIDATES, repeats: int = 2,
+                save: bool = True, log=None) -> Dict[str, object]:
+    """Time every plain-path shape on `problem` (a workload Problem), each on a fresh copy
+    from the same seed, with CUDA events on the copy's stream; keep the fastest. A shape the
+    problem does not fit (pt_sweep answers PT_EINVAL) is skipped. Raises if two shapes
+    disagree on the final state (spins, energies, temperature map, swap counters)."""
+    import torch
+
+    from ._lib import PTError
+    from .api import PTProblem
+
+    stream = torch.cuda.Stream()
+    results: List[Tuple[float, Tuple[int, int]]] = []
+    reference = None
+    for cand in candidates:
+        best = float("inf")
+        try:
+            for rep in range(repeats):
+                h = PTProblem(problem.L, problem.betas, J=problem.J, h=problem.h,
+                              seed=problem.seed, stream=stream)
+                try:
+                    h.set_sweep_tuning(*cand)
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    h.sweep(sweeps, every)
+                    b.record(stream)
+                    h.synchronize()
+                    best = min(best, a.elapsed_time(b) / 1e3)
+                    if rep == 0:
+                        snap = _single_snapshot(h)
+                        if reference is None:
+                            reference = snap
+                        elif snap != reference:
+                            raise RuntimeError("sweep shape %r changed a result" % (cand,))
+                finally:
+                    h.close()
+        except PTError as e:
+            if log:
+                log("strategy=%d words_per_thread=%d: does not fit (%s)" % (cand + (e,)))
+            continue
+        results.append((best, tuple(cand)))
+        if log:
+            log("strategy=%d words_per_thread=%d: %.6f s" % (tuple(cand) + (best,)))
+    if not results:
+        raise RuntimeError("no plain-path shape fits this problem")
+    results.sort(key=lambda r: r[0])
+    best_t, (st, wpt) = results[0]
+    choice = {"strategy": st, "words_per_thread": wpt}
+    if save:
+        cache = _load_cache()
+        key = shape_key(problem.L, len(problem.betas), problem.J, problem.h)
+        cache.setdefault(_device_key(), {}).setdefault("single", {})[key] = dict(
+            choice, seconds=best_t, sweeps=sweeps, every=every, when=time.strftime("%Y-%m-%d"))
+        with open(CACHE, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+    return {"choice": choice, "timings": [(c, t) for t, c in results]}
+
+
+def apply_single(handle, L: int, R: int, J: float, h: float) -> Optional[Dict[str, int]]:
+    """Give `handle` (an api.PTProblem) the cached plain-path shape of its problem shape on
+    this device; None (and the library's default, PT_SWEEP_AUTO) when there is none."""
+    entry = _load_cache().get(_device_key(), {}).get("single", {}).get(shape_key(L, R, J, h))
+    if entry is None:
+        return None
+    handle.set_sweep_tuning(entry["strategy"], entry["words_per_thread"])
+    return {"strategy": entry["strategy"], "words_per_thread": entry["words_per_thread"]}
+
+
+def main(argv=None) -> int:
+    """python -m paper_2512_03825_b300.autotune {batched,serve,single} [--out PATH]: tune on
+    this device's GPU and update the cache (and copy it to PATH)."""
+    import argparse
+    import shutil
+
+    import torch
+
+    from . import workloads as W
+
+    ap = argparse.ArgumentParser(prog="python -m paper_2512_03825_b300.autotune")
+    ap.add_argument("workload", choices=["batched", "serve", "single"])
+    ap.add_argument("--out", default=None, help="also copy the updated cache here")
+    args = ap.parse_args(argv)
+    torch.cuda.set_device(0)
+
+    def log(s):
+        print(s, flush=True)
+
+    tiles = [c for c in CANDIDATES if c[0] in (FLAT, FLOW, QUEUE)]
+    if args.workload == "batched":
+        r = tune(W.batched_problems(), sweeps=200, every=1, candidates=tiles,
+                 workload="batched", repeats=3, log=log)
+        log("batched: %r" % (r["choice"],))
+    elif args.workload == "serve":
+        reqs = W.serving_requests(n=96, rate_per_s=1.0, draw_seed=4242)
+        r = tune([q.problem for q in reqs], sweeps=100, every=1, candidates=tiles,
+                 workload="serve", repeats=3, log=log)
+        log("serve: %r" % (r["choice"],))
+    else:
+        for name, p in list(W.SINGLE.items()) + [("paper", W.paper_problem())]:
+            sweeps = 2000 if p.L <= 128 else 200
+            r = tune_single(p, sweeps=sweeps, every=p.every, log=log)
+            log("single %s: %r" % (name, r["choice"]))
+    if args.out:
+        shutil.copy(CACHE, args.out)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -267,3 +267,26 @@ def test_kernel_smem_limits_survive_smaller_problems(api):
     o.flip(80, 10)
     np.testing.assert_array_equal(a.energies_int(), o.energies_int())
     np.testing.assert_array_equal(a.chain_map(), o.chain_map())
+
+
+def test_plain_path_tuner_compares_equal_results(api, tmp_path, monkeypatch):
+    """The plain-path autotuner times the halo schemes (strided words, bands of rows) and
+    words-per-thread settings on fresh copies of one problem, skips the shapes the problem
+    does not fit, checks that all of them end in the same state (the oracle's), and the
+    choice it caches is the one apply_single gives a new handle."""
+    from paper_2512_03825_b300 import autotune
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "cache.json"))
+    p = W.Problem(L=64, betas=W.linear_ladder(0.3, 0.6, 40), seed=515, every=2)
+    r = autotune.tune_single(p, sweeps=30, every=2, save=True)
+    shapes = [c for c, _ in r["timings"]]
+    assert (PERSISTENT, 1) in shapes and (LAUNCHES, 1) in shapes and (BANDS, 1) in shapes
+    assert tuple(r["choice"].values()) in shapes
+    g = api.PTProblem(p.L, p.betas, seed=p.seed)
+    got = autotune.apply_single(g, p.L, p.R, p.J, p.h)
+    assert got == r["choice"]
+    assert g.sweep_tuning()[:2] == (got["strategy"], got["words_per_thread"])
+    g.sweep(30, 2)
+    o = oracle.OracleProblem(p.L, p.betas, seed=p.seed)
+    o.sweep(30, 2)
+    assert_same(g, o, "tuned shape")
+    assert autotune.apply_single(g, 48, p.R, p.J, p.h) is None
