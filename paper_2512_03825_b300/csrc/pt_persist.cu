@@ -111,7 +111,9 @@ __device__ __forceinline__ int64_t slot_energy(const DevProblem& p, int64_t L2, 
 }
 
 // Swap iteration e on this CTA's copy of the maps (every CTA draws the same numbers and so
-// reaches the same maps); `owner` also counts attempts and acceptances.
+// reaches the same maps); `owner` also counts attempts and acceptances. cb: the counts, in
+// global memory (read through L2) or, with SHARED_COUNTS, in this CTA's shared memory.
+template <bool SHARED_COUNTS>
 __device__ void exchange_local(const DevProblem& p, uint64_t e, const uint32_t* cb,
                                int32_t* sot, int32_t* tos, bool owner) {
   const int R = p.R, W = p.W;
@@ -120,8 +122,9 @@ __device__ void exchange_local(const DevProblem& p, uint64_t e, const uint32_t* 
   const uint32_t c3 = kTagExch | ((uint32_t)(e >> 32) << 8);
   for (int k = parity + 2 * (int)threadIdx.x; k + 1 < R; k += 2 * (int)blockDim.x) {
     const int a = sot[k], b = sot[k + 1];
-    const int64_t Ea = slot_energy(p, L2, __ldcg(cb + a), __ldcg(cb + W * 32 + a));
-    const int64_t Eb = slot_energy(p, L2, __ldcg(cb + b), __ldcg(cb + W * 32 + b));
+    const auto count = [&](int i) { return SHARED_COUNTS ? cb[i] : __ldcg(cb + i); };
+    const int64_t Ea = slot_energy(p, L2, count(a), count(W * 32 + a));
+    const int64_t Eb = slot_energy(p, L2, count(b), count(W * 32 + b));
     const int64_t n = Ea - Eb;
     const SwapPair sp = p.pairs[k];
     const uint64_t S = pair_threshold(sp, p.swap_table, p.table_shift, n);
@@ -408,6 +411,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
   load_plane();
 
   const bool trace = p.trace_E != nullptr;
+  const bool solo = gridDim.x == 1;  // then W == 1: one CTA holds every count
   unsigned counted = 0;  // sweeps counted so far in this launch
   unsigned target = 0;
   uint64_t e = a.e0;
@@ -488,7 +492,9 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
     if (u) atomicAdd(&acc[0][lane], u);
     if (nn) atomicAdd(&acc[1][lane], nn);
     __syncthreads();
-    if (threadIdx.x < 32) {
+    // a grid of one CTA (one plane) keeps its counts in shared memory: acc has the layout
+    // of a count buffer with W = 1, and no other CTA needs them
+    if (!solo && threadIdx.x < 32) {
       if (acc[0][threadIdx.x])
         atomicAdd(&cb[PT_DBG_IDX(p, w * 32 + threadIdx.x, 2 * W * 32, kDbgCount)],
                   acc[0][threadIdx.x]);
@@ -497,14 +503,20 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
                   acc[1][threadIdx.x]);
     }
     if (!sync_all(BAND ? stall0 : 0u)) return flush();
-    if (ex) exchange_local(p, e, cb, sot, tos, blockIdx.x == 0);
+    if (ex) {
+      if (solo)
+        exchange_local<true>(p, e, &acc[0][0], sot, tos, true);
+      else
+        exchange_local<false>(p, e, cb, sot, tos, blockIdx.x == 0);
+    }
     if (blockIdx.x == 0) {
       if (trace) {
         // the trace row of sweep t, by temperature index after its swap iteration
         const int64_t L2 = (int64_t)p.L * p.L;
         const int64_t row = (int64_t)((t - p.trace_t0) % (uint64_t)p.trace_cap);
         for (int r = threadIdx.x; r < R; r += blockDim.x) {
-          const int64_t U_r = __ldcg(cb + r), ones = __ldcg(cb + W * 32 + r);
+          const int64_t U_r = solo ? acc[0][r] : __ldcg(cb + r);
+          const int64_t ones = solo ? acc[1][r] : __ldcg(cb + W * 32 + r);
           const int64_t at = PT_DBG_IDX(p, row * R + tos[r], p.trace_cap * R, kDbgTrace);
           p.trace_E[at] = slot_energy(p, L2, U_r, ones);
           p.trace_M[at] = 2 * ones - L2;
@@ -512,8 +524,10 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
       }
       // the other buffer was last read after the previous counted sweep, before this
       // sweep's first barrier; it is next written after the next sweep's first barrier
-      uint32_t* const nb = cnt_base + ((counted + 1) & 1) * 2 * W * 32;
-      for (int q = threadIdx.x; q < 2 * W * 32; q += blockDim.x) nb[q] = 0;
+      if (!solo) {
+        uint32_t* const nb = cnt_base + ((counted + 1) & 1) * 2 * W * 32;
+        for (int q = threadIdx.x; q < 2 * W * 32; q += blockDim.x) nb[q] = 0;
+      }
     }
     ++counted;
     if (ex) {
