@@ -381,7 +381,9 @@ def run_ours(args, rank, world, local):
     if not args.quick and rank == 0:
         out["serve"] = bench_serve_short(stream, args.serve_requests)
         if args.field == 0.0:
-            out["batched_h0.1"] = bench_batched_field(stream, args.problems, args.sweeps, 0.1)
+            out["batched_h0.1"] = bench_batched_variant(stream, args.problems, args.sweeps, 0.1)
+            # sixteen times the problems: the spin words alone (about 360 MB) exceed the L2
+            out["batched_4096"] = bench_batched_variant(stream, 16 * args.problems, 100, 0.0)
         out["plain"] = bench_plain(probs, args.sweeps, stream)
         out["batched_vs_plain"] = value / world / out["plain"]["value"]
         out["single_L1024_R64"] = bench_single(stream, sms, clock_mhz)
@@ -446,10 +448,11 @@ def _plain_run(sample, sweeps, strategy, stream):
     return _attempts(sample, sweeps) / (ms / 1e3)
 
 
-def bench_batched_field(stream, n, sweeps, h, steps=2):
-    """The default step's problems with a field h (J = 1): the generic update (five threshold
-    classes with dE > 0 for 0 < h < 2), the same batch call, `steps` timed batches of `sweeps`
-    sweeps with an exchange after every sweep, L2 flushed between them."""
+def bench_batched_variant(stream, n, sweeps, h, steps=2):
+    """The default step's problem mix, n problems with a field h (J = 1; h != 0 runs the
+    generic update: five threshold classes with dE > 0 for 0 < h < 2), the same batch call,
+    `steps` timed batches of `sweeps` sweeps with an exchange after every sweep, L2 flushed
+    between them."""
     import torch
     from paper_2512_03825_b300 import api
     probs = rank_problems(0, n, sweeps, 1, h)
@@ -469,8 +472,10 @@ def bench_batched_field(stream, n, sweeps, h, steps=2):
     for g in hs:
         g.close()
     t = statistics.mean(took)
+    spin_bytes = sum(p.L * p.L * ((p.R + 31) // 32) * 4 for p in probs)
     return {"value": _attempts(probs, sweeps) / t, "unit": UNIT, "h": h, "problems": n,
-            "sweeps": sweeps, "every": 1, "steps": steps, "us_per_sweep": 1e6 * t / sweeps}
+            "sweeps": sweeps, "every": 1, "steps": steps, "us_per_sweep": 1e6 * t / sweeps,
+            "spin_state_mb": spin_bytes / 1e6}
 
 
 def bench_plain(probs, sweeps, stream, n_sample=32, sample_sweeps=200):
