@@ -8,7 +8,8 @@ Default workload (one step): 256 independent PT problems, L uniform over
 2000 sweeps each with an exchange after every sweep, advanced by one pt_sweep_batch call.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload batched|single|serve]
+                    [--workload batched|single|serve|flip|converge] [--field H]
+                    [--streams S] [--quick]
 
 Prints one JSON line (rank 0). With N > 1 (torchrun) every rank runs its own copy of the
 workload on its own GPU (independent problems, no collective on the data path).
