@@ -96,7 +96,7 @@ def main():
     for j in range(10):
         L = int(rng.choice([8, 16, 24, 32, 48]))
         R = int(rng.integers(1, 70))
-        J, h = [(1.0, 0.0), (1.0, 0.1), (-1.0, 0.25)][j % 3]
+        J, h = [(1.0, 0.0), (1.0, 0.1), (-1.0, 0.25), (1.0, -0.1)][j % 4]
         probs.append(P(L=L, betas=W.linear_ladder(0.2, 0.8, R), J=J, h=h, seed=2000 + j))
     ns = [int(x) for x in rng.integers(1, 9, size=len(probs))]
     ms = [int(x) for x in rng.integers(0, 3, size=len(probs))]

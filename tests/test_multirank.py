@@ -59,3 +59,18 @@ def test_two_gloo_ranks(tmp_path):
         assert r["total"] == 300.0 and r["slowest"] == 2.0 and r["value"] == 150.0
     assert res[0]["ref"] is not None and res[0]["ref"]["impl"] == "reference"
     assert res[1]["ref"] is None                                 # only rank 0 reports
+
+
+def test_field_workload_keeps_the_shapes():
+    """--field H gives the batched workload's problems the field H and nothing else: the
+    same lattices, ladders and seeds as the h = 0 workload."""
+    sys.path.insert(0, ROOT)
+    import bench
+    args = bench.parse_args(["--field", "0.1", "--streams", "2", "--quick"])
+    assert args.field == 0.1 and args.streams == 2 and args.quick
+    assert bench.parse_args([]).field == 0.0
+    plain = bench.rank_problems(1, 24, 10)
+    field = bench.rank_problems(1, 24, 10, 1, args.field)
+    assert [(p.L, p.betas, p.J, p.seed) for p in plain] == [(p.L, p.betas, p.J, p.seed)
+                                                           for p in field]
+    assert all(p.h == 0.0 for p in plain) and all(p.h == 0.1 for p in field)
