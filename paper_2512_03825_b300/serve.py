@@ -68,6 +68,10 @@ class Engine:
     def read(self, handle) -> dict:
         raise NotImplementedError
 
+    def read_many(self, handles: Sequence) -> List[dict]:
+        """read() of several problems; an engine may do it in one transfer."""
+        return [self.read(h) for h in handles]
+
     def destroy(self, handle) -> None:
         raise NotImplementedError
 
@@ -103,6 +107,13 @@ class LibEngine(Engine):
         att, acc = h.swap_stats()
         return dict(E_int=E, M=M, scale=h.scale, slot_of_temp=h.chain_map(), attempted=att,
                     accepted=acc)
+
+    def read_many(self, handles) -> List[dict]:
+        # one energy-count launch, one gather and one copy for all of them (pt_read_batch)
+        recs = self.api.read_batch(list(handles))
+        return [dict(E_int=r["E_int"], M=r["M"], scale=h.scale, slot_of_temp=r["chain_map"],
+                     attempted=r["attempted"], accepted=r["accepted"])
+                for h, r in zip(handles, recs)]
 
     def destroy(self, h) -> None:
         h.close()
@@ -213,9 +224,10 @@ class Server:
         if not finished:
             return 0
         self.active = [a for a in self.active if a.done < a.req.problem.sweeps]
-        for a in finished:
-            data = self.engine.read(a.handle)  # synchronises the problem's stream
-            now = self._now()
+        # the finished requests' results in one read (it synchronises the problems' stream)
+        datas = self.engine.read_many([a.handle for a in finished])
+        now = self._now()
+        for a, data in zip(finished, datas):
             self.results[a.req.rid] = Result(rid=a.req.rid, problem=a.req.problem,
                                              arrival=a.req.arrival, admitted=a.admitted,
                                              finished=now, **data)
@@ -294,6 +306,9 @@ def _bench_serve(args, stream):
     # the service rate: batched throughput on a sample of the same request mix
     probe = W.serving_requests(n=64, rate_per_s=1.0, draw_seed=4242)
     hs = [eng.create(r.problem) for r in probe]
+    # one short untimed call first: the first batch call of a process also sets up the
+    # library's side streams and the launch attributes
+    eng.advance(hs, [1] * len(hs), [1] * len(hs))
     torch.cuda.synchronize()
     n = [min(200, r.problem.sweeps) for r in probe]
     t0 = time.perf_counter()
