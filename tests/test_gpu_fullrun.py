@@ -114,12 +114,21 @@ class _KeepSpins:
     def __getattr__(self, name):
         return getattr(self.base, name)
 
-    def read(self, h):
-        data = self.base.read(h)
+    def _keep(self, h):
         if h.seed in self.seeds:
             self.spins[h.seed] = h.spins()
             self.counters[h.seed] = h.counters()
+
+    def read(self, h):
+        data = self.base.read(h)
+        self._keep(h)
         return data
+
+    def read_many(self, hs):
+        datas = self.base.read_many(hs)
+        for h in hs:
+            self._keep(h)
+        return datas
 
 
 def test_served_stream_2000_requests_sample_from_creation(api):
