@@ -81,8 +81,12 @@ def parse_args(argv=None):
                     help="requests of the serving leg of the default line")
     ap.add_argument("--requests", type=int, default=2000,
                     help="requests of --workload serve")
-    ap.add_argument("--sweep-strategy", choices=["auto", "launches", "persistent"],
-                    default="auto", help="plain-path strategy of --workload single")
+    ap.add_argument("--sweep-strategy", choices=["auto", "launches", "persistent", "bands"],
+                    default="auto", help="plain-path strategy of --workload single (auto: the "
+                                         "tuned shape of the problem, else the library's "
+                                         "default)")
+    ap.add_argument("--single", choices=["L16_R8", "L128_R32", "L1024_R64"],
+                    default="L1024_R64", help="the problem of --workload single")
     ap.add_argument("--streams", type=int, default=None,
                     help="streams of the lock-step batch (default: the tuned choice)")
     ap.add_argument("--quick", action="store_true",
@@ -632,12 +636,16 @@ def cpu_baseline_plan(probs):
 
 def run_single(args, rank, world, stream, sms):
     import torch
-    from paper_2512_03825_b300 import api
+    from paper_2512_03825_b300 import api, autotune
     from paper_2512_03825_b300 import workloads as W
-    p = W.SINGLE["L1024_R64"]
+    p = W.SINGLE[args.single]
     h = api.PTProblem(p.L, p.betas, seed=p.seed, stream=stream)
-    strategy = {"auto": 0, "launches": 1, "persistent": 2}[args.sweep_strategy]
-    h.set_sweep_tuning(strategy)
+    if args.sweep_strategy == "auto":
+        if autotune.apply_single(h, p.L, p.R, p.J, p.h) is None:
+            h.set_sweep_tuning(0)
+    else:
+        h.set_sweep_tuning({"launches": 1, "persistent": 2, "bands": 3}[args.sweep_strategy])
+    shape = h.sweep_tuning()
     for _ in range(args.warmup):
         h.sweep(p.sweeps // 10, p.every)
     torch.cuda.synchronize()
@@ -661,9 +669,12 @@ def run_single(args, rank, world, stream, sms):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * s / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "single L=1024 R=64 betas 0.35-0.50, 1000 sweeps, "
-                                   "exchange every 5, plain path",
-                       "sweep_strategy": args.sweep_strategy},
+            "config": {"workload": "single L=%d R=%d betas %.2f-%.2f, %d sweeps, exchange "
+                                   "every %d, plain path" % (p.L, p.R, min(p.betas),
+                                                             max(p.betas), p.sweeps, p.every),
+                       "sweep_strategy": args.sweep_strategy,
+                       "shape": {"strategy": shape[0], "words_per_thread": shape[1],
+                                 "persistent_grid": shape[2]}},
             "clocks": clk, "gpu_launches": launches}
 
 
