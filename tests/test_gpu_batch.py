@@ -302,3 +302,52 @@ def test_read_batch_equals_single_getters(api):
         np.testing.assert_array_equal(r["attempted"], att, err_msg=str(j))
         np.testing.assert_array_equal(r["accepted"], acc, err_msg=str(j))
     assert api.read_batch([]) == []
+
+
+# the plain path's edge cases (test_gpu_parity), here in one batch: beta = 0 and frozen
+# temperatures (every threshold saturated either way), one replica, a plane with one slot,
+# L / 2 odd, the field and antiferromagnetic modes, no coupling, and exchange tables strided
+# by 2^k in n
+EDGE_BATCH = [
+    W.Problem(L=4, betas=(0.2, 0.44, 0.6), seed=1),
+    W.Problem(L=6, betas=W.linear_ladder(0.2, 0.7, 5), seed=2),
+    W.Problem(L=10, betas=W.linear_ladder(0.1, 0.9, 33), seed=3),
+    W.Problem(L=30, betas=W.linear_ladder(0.3, 0.6, 63), seed=4),
+    W.Problem(L=8, betas=(0.4,), seed=5),
+    W.Problem(L=12, betas=(0.0, 0.0, 0.3, 10.0), seed=6),
+    W.Problem(L=12, betas=(0.0, 0.0, 0.3, 10.0), h=0.1, seed=16),
+    W.Problem(L=16, betas=W.linear_ladder(0.2, 0.7, 7), h=0.1, seed=7),
+    W.Problem(L=14, betas=W.linear_ladder(0.2, 0.7, 9), J=-1.0, h=0.25, seed=8),
+    W.Problem(L=20, betas=W.linear_ladder(0.3, 0.5, 40), J=0.5, h=-0.3, seed=9),
+    W.Problem(L=10, betas=W.linear_ladder(0.1, 0.8, 12), J=0.0, h=0.5, seed=13),
+    W.Problem(L=12, betas=W.linear_ladder(0.1, 0.4, 12), J=2.0, seed=14),
+    W.Problem(L=8, betas=W.linear_ladder(0.05, 0.3, 10), J=3.0, h=1.0, seed=15),
+]
+
+
+@pytest.mark.parametrize("strategy,streams", [(0, 1), (0, 4), (3, 3), (2, 1), (1, 1)])
+def test_edge_cases_in_one_batch(api, strategy, streams):
+    """Every edge case of the plain path, advanced together by one batch call under each
+    batch strategy (dealt and queued tiles on one or several streams, dataflow, cluster),
+    with exchange intervals 0, 1 and 3 mixed: each problem equals the oracle."""
+    from paper_2512_03825_b300 import autotune
+    before = autotune.get_tuning()
+    every = [(0, 1, 3)[j % 3] for j in range(len(EDGE_BATCH))]
+    try:
+        autotune.set_tuning(strategy, 2, 16, 64, streams)
+        gs = [api.PTProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed) for p in EDGE_BATCH]
+        api.sweep_batch(gs, 7, every)
+        api.sweep_batch(gs, 6, every)
+    finally:
+        autotune.set_tuning(**before)
+    oracle.set_threads(8)
+    for j, (p, g) in enumerate(zip(EDGE_BATCH, gs)):
+        o = oracle.OracleProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed)
+        o.sweep(13, every[j])
+        where = "L%d R%d J%g h%g every %d" % (p.L, p.R, p.J, p.h, every[j])
+        np.testing.assert_array_equal(g.spins(), o.spins(), err_msg=where)
+        np.testing.assert_array_equal(g.energies_int(), o.energies_int(), err_msg=where)
+        np.testing.assert_array_equal(g.magnetisations(), o.magnetisations(), err_msg=where)
+        np.testing.assert_array_equal(g.chain_map(), o.chain_map(), err_msg=where)
+        for x, y in zip(g.swap_stats(), o.swap_stats()):
+            np.testing.assert_array_equal(x, y, err_msg=where)
