@@ -38,6 +38,10 @@ CASES = [
     W.Problem(L=16, betas=W.linear_ladder(0.25, 0.65, 70), seed=202),             # 3 planes
     W.Problem(L=12, betas=W.linear_ladder(0.3, 0.6, 6), J=1.0, h=0.1, seed=203),  # field
     W.Problem(L=10, betas=(0.44,), J=-1.0, seed=204),                             # one slot
+    W.Problem(L=12, betas=(0.0, 0.0, 0.3, 10.0), seed=205),       # beta 0 and frozen: saturated
+    W.Problem(L=12, betas=(0.0, 0.3, 10.0), h=0.2, seed=206),     # the same with a field
+    W.Problem(L=10, betas=W.linear_ladder(0.1, 0.8, 12), J=0.0, h=0.5, seed=207),  # no coupling
+    W.Problem(L=6, betas=W.linear_ladder(0.05, 0.3, 10), J=3.0, h=1.0, seed=208),  # L / 2 odd
 ]
 
 
