@@ -229,9 +229,14 @@ int pt_set_flip_tuning(pt_problem* p, int shared_memory);
 /* Single-spin-flip iterations done since pt_create. */
 int pt_iterations(pt_problem* p, uint64_t* iterations_done);
 
-/* Advance `count` problems together in one persistent kernel: problem j runs n[j] >= 0
- * sweeps with exchange_every[j] (same meaning as pt_sweep). All problems must be on the
- * same stream. Results are bit-identical to calling pt_sweep on each problem alone. */
+/* Advance `count` problems together (Sec. 3's execution phase for many independent
+ * problems): problem j runs n[j] >= 0 sweeps with exchange_every[j] (same meaning as
+ * pt_sweep). The batched strategy is pt_set_batch_tuning's: by default one launch per half
+ * sweep over warp tiles of every problem plus one exchange launch per sweep that ends with a
+ * swap iteration (PT_BATCH_FLAT, or PT_BATCH_QUEUE), in the parts of pt_set_batch_streams;
+ * PT_BATCH_FLOW and PT_BATCH_CLUSTER make one persistent launch per call. All problems must be on the same stream and device,
+ * none listed twice. Results are bit-identical to calling pt_sweep on each problem alone.
+ * count = 0 does nothing and returns PT_OK; count < 0, or missing arrays, PT_EINVAL. */
 int pt_sweep_batch(pt_problem* const* problems, int count, const int64_t* n,
                    const int* exchange_every);
 

@@ -269,3 +269,17 @@ def test_batch_streams_validated(pt):
     assert pt.lib.pt_get_batch_streams(C.byref(n)) == 0 and n.value == 3
     assert pt.lib.pt_get_batch_streams(None) == pt.PT_EINVAL
     assert pt.lib.pt_set_batch_streams(before) == 0
+
+
+def test_empty_batches_are_no_ops(pt):
+    """A batch of no problems is a no-op that succeeds before any device is touched (so it
+    does here, without a GPU); a negative count, or a positive one without its arrays, is
+    PT_EINVAL."""
+    lib = pt.lib
+    for fn in (lib.pt_sweep_batch, lib.pt_sweep_batch_static):
+        assert fn(None, 0, None, None) == 0
+        assert fn(None, -1, None, None) == pt.PT_EINVAL
+        assert fn(None, 2, None, None) == pt.PT_EINVAL
+    assert lib.pt_read_batch(None, 0, None, None, None, None, None) == 0
+    assert lib.pt_read_batch(None, -1, None, None, None, None, None) == pt.PT_EINVAL
+    assert lib.pt_read_batch(None, 3, None, None, None, None, None) == pt.PT_EINVAL
