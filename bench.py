@@ -224,6 +224,18 @@ def measured_peaks():
 # ---------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------
+def batched_config(args, per_step):
+    """The `config` of the batched workload's line: the same dict in both arms."""
+    return {
+        "workload": "batched-256: %d PT problems, L in {32,48,64,96,128,256}, R 8-48, "
+                    "betas 0.30-0.60, J=1, h=%g, %d sweeps, exchange every sweep"
+                    % (args.problems, args.field, args.sweeps),
+        "problems": args.problems, "sweeps_per_step": args.sweeps, "exchange_every": 1,
+        "attempts_per_step": per_step, "parallelism": "independent problems per GPU",
+        "l2": "flushed (256 MiB write) between timed steps",
+    }
+
+
 def _attempts(probs, sweeps):
     return float(sum(p.L * p.L * p.R for p in probs)) * sweeps
 
@@ -298,15 +310,8 @@ def run_ours(args, rank, world, local):
         "ms_per_step": 1e3 * total_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded problem mix; random +-1 initial spins)",
-        "config": {
-            "workload": "batched-256: %d PT problems, L in {32,48,64,96,128,256}, R 8-48, "
-                        "betas 0.30-0.60, J=1, h=%g, %d sweeps, exchange every sweep"
-                        % (args.problems, args.field, args.sweeps),
-            "problems": args.problems, "sweeps_per_step": args.sweeps, "exchange_every": 1,
-            "attempts_per_step": per_step, "parallelism": "independent problems per GPU",
-            "l2": "flushed (256 MiB write) between timed steps",
-            "batch_tuning": tuning,
-        },
+        "config": batched_config(args, per_step),
+        "batch_tuning": tuning,
         "clocks": clk,
         "gpu_launches": args.steps * launches_per_batch(probs, args.sweeps, tuning),
         "wall_s": wall,
@@ -757,7 +762,7 @@ def run_reference(args, rank, world):
     from paper_2512_03825_b300 import workloads as W
     threads = os.cpu_count() or 1
     oracle.set_threads(threads)
-    probs = W.batched_problems(n=args.problems, sweeps=args.sweeps, every=1)
+    probs = rank_problems(0, args.problems, args.sweeps, 1, args.field)
     sample = probs[::16][:16]
     sweeps = 20
     for _ in range(max(0, min(args.warmup, 1))):
@@ -777,10 +782,11 @@ def run_reference(args, rank, world):
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int8",
             "data": "synthetic (same seeded problem mix)",
-            "config": {"workload": "batched-256 (bounded sample: 16 problems x %d sweeps per "
-                                   "step)" % sweeps},
+            "config": batched_config(args, _attempts(probs, args.sweeps)),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": "16 of the 256 batched problems, %d sweeps each" % sweeps},
+                             "sample": "each step: 16 of the %d batched problems (every 16th), "
+                                       "%d sweeps each, exchange every sweep"
+                                       % (len(probs), sweeps)},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
