@@ -9,6 +9,8 @@ energies of the GPU's final configurations equal the GPU's, attempt counts follo
 form, and each temperature map is a permutation."""
 from __future__ import annotations
 
+import os
+
 import numpy as np
 import pytest
 
@@ -129,3 +131,29 @@ def test_batched_256_full_run(api, bench_tuning):
         assert g.counters() == (n, n)
     for j in order[::32]:
         check_properties(gs[j], probs[j], n)
+
+
+def test_4096_problem_batch_sample(api, bench_tuning):
+    """The bench's beyond-L2 leg: 4096 problems of the default mix (about 360 MB of spin
+    words, more than the L2) in the tuned launch shape, 12 sweeps with an exchange after each.
+    Every 512th problem, from creation, equals the oracle in every output; every problem keeps
+    a permutation for its map and the closed-form attempt counts."""
+    import torch
+    probs = W.batched_problems(n=4096, sweeps=12)
+    st = torch.cuda.Stream()
+    gs = [api.PTProblem(p.L, p.betas, seed=p.seed, stream=st) for p in probs]
+    api.sweep_batch(gs, 12, 1)
+    torch.cuda.synchronize()
+    oracle.set_threads(os.cpu_count() or 1)
+    for j in range(0, len(probs), 512):
+        p = probs[j]
+        o = oracle.OracleProblem(p.L, p.betas, seed=p.seed)
+        o.sweep(12, 1)
+        assert_same(gs[j], o, "problem %d of 4096" % j)
+    for j in range(0, len(probs), 97):
+        g, p = gs[j], probs[j]
+        assert sorted(g.chain_map().tolist()) == list(range(p.R)), j
+        np.testing.assert_array_equal(g.swap_stats()[0], closed_form_attempts(p.R, 12, 1),
+                                      err_msg=str(j))
+    for g in gs:
+        g.close()
