@@ -47,7 +47,7 @@ FLAT_TRAFFIC_BYTES = 25.977344e6 + 0.0
 FLAT_TRAFFIC_SOURCES = ("paper_2512_03825_b300/csrc/pt_device.cuh",
                         "paper_2512_03825_b300/csrc/pt_flat.cuh",
                         "paper_2512_03825_b300/csrc/pt_flat.cu")
-FLAT_TRAFFIC_SOURCE_HASH = "f93b2dae4d7a4b04"
+FLAT_TRAFFIC_SOURCE_HASH = "0b1708e3cb5d833b"
 
 
 def _flat_traffic():

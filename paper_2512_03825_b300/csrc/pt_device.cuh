@@ -447,17 +447,11 @@ struct BitCounter {
 };
 
 // ---------------------------------------------------------------------------------------
-// Waiting inside persistent kernels: an acquire load of a counter and the global nanosecond
-// timer that bounds every wait.
+// Waiting inside persistent kernels: relaxed polls of a counter, release/acquire ordering
+// and the global nanosecond timer that bounds every wait.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Polling a counter with a relaxed load leaves the SM's L1 alone; the one acquire (load or
-// fence) after the wait is what orders the reads that follow it.
+// Polling a counter with a relaxed load leaves the SM's L1 alone; the one acquire fence
+// after the wait is what orders the reads that follow it.
 __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
