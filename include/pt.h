@@ -326,6 +326,23 @@ int pt_get_batch_tile_words(int* tile_words);
 int pt_set_batch_streams(int streams);
 int pt_get_batch_streams(int* streams);
 
+/* Graph replay of PT_BATCH_FLAT and PT_BATCH_QUEUE batches (0 = off, the default; 1 = on; set
+ * by the autotuner): the launches of a batch call depend only on its shape -- per problem, in
+ * call order, L, R, the mode, n, exchange_every, the phase of its exchange schedule and
+ * whether a trace is on -- and on the tile size, schedule, streams and stream. With replay on,
+ * the first call of a shape builds its work lists in device memory of their own and captures
+ * its launches into a CUDA graph; a later call of the same shape copies the problems'
+ * descriptors (counters and device arrays) and launches that graph: one launch instead of
+ * about three per part and sweep, which frees the host on long calls and on batches of small
+ * problems, where issuing the launches can take longer than running them. The first call of
+ * a shape is slower (lists built in blocking copies, capture, instantiation); the library
+ * keeps four shapes per device (least recently used dropped; dropping one waits for the
+ * device). A call on the legacy default stream, or made while the problems' stream is being
+ * captured, launches as without replay. Results never depend on it. PT_EINVAL for other
+ * values. */
+int pt_set_batch_graphs(int on);
+int pt_get_batch_graphs(int* on);
+
 /* Energies E = E_int / s of the configurations at each temperature index, out[R]. */
 int pt_energies(pt_problem* p, double* out);
 

@@ -76,6 +76,8 @@ SIGNATURES = [
     ("pt_set_batch_tile_words", C.c_int, [C.c_int]),
     ("pt_set_batch_streams", C.c_int, [C.c_int]),
     ("pt_get_batch_streams", C.c_int, [C.POINTER(C.c_int)]),
+    ("pt_set_batch_graphs", C.c_int, [C.c_int]),
+    ("pt_get_batch_graphs", C.c_int, [C.POINTER(C.c_int)]),
     ("pt_read_batch", C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.POINTER(C.c_int64)),
                                 C.POINTER(C.POINTER(C.c_int64)), C.POINTER(C.POINTER(C.c_int32)),
                                 C.POINTER(C.POINTER(C.c_uint64)),

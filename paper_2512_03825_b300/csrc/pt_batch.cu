@@ -549,7 +549,8 @@ int sweep_batch(pt_problem* const* ps, int count, const int64_t* n, const int* e
     rc = tune.strategy == PT_BATCH_FLOW
              ? sweep_batch_flow(ps, count, n, every, st, di, tune.tile_words)
              : sweep_batch_flat(ps, count, n, every, st, di, tune.tile_words,
-                                tune.strategy == PT_BATCH_QUEUE, tune.streams);
+                                tune.strategy == PT_BATCH_QUEUE, tune.streams,
+                                tune.graphs != 0);
     if (rc) return rc;
     advance_counters(ps, count, n, every);
     return PT_OK;

@@ -21,6 +21,7 @@ struct BatchTuning {
   int joint_min_L = 128;
   int tile_words = 512;
   int streams = 1;  // PT_BATCH_FLAT / PT_BATCH_QUEUE: parts of the batch on their own streams
+  int graphs = 0;   // PT_BATCH_FLAT / PT_BATCH_QUEUE: replay repeated batch shapes from graphs
 };
 extern BatchTuning g_batch_tuning;  // written and read under the library lock only
 // A copy of the batch tuning, read under the library lock (the setters take it too).
@@ -33,7 +34,7 @@ struct DeviceInfo;
 // own stream (the first on st, the others on side streams forked from st and joined to it).
 int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const int* every,
                      cudaStream_t st, const DeviceInfo& di, int tile_words, bool queued,
-                     int streams = 1);
+                     int streams = 1, bool graphs = false);
 
 // The dataflow path (pt_flow.cu); problems are already checked.
 int sweep_batch_flow(pt_problem* const* ps, int count, const int64_t* n, const int* every,

@@ -376,6 +376,21 @@ void sort_tiles(std::vector<Tile>* tiles, const std::vector<FlatProblem>& probs)
   });
 }
 
+// The descriptor of problem p in a batch that runs it n sweeps with exchange interval m.
+FlatProblem flat_problem(pt_problem* p, int64_t n, int m, int tile_words) {
+  FlatProblem fp{};
+  fp.p = p->dev;
+  fp.t0 = p->t;
+  fp.e0 = p->e;
+  fp.n = n;
+  fp.m = m;
+  fp.wait_ns = p->wait_limit_ns;
+  fp.stall = p->stall;
+  const int words = p->L * (p->L / 2);
+  fp.ntiles = std::max(1, (words + tile_words / 2) / tile_words) * p->W;
+  return fp;
+}
+
 int64_t build_flat_lists(pt_problem* const* ps, int count, const int64_t* n, const int* every,
                          int tile_words, bool refine, std::vector<FlatProblem>* probs,
                          std::vector<Tile> tiles[2]) {
@@ -383,18 +398,10 @@ int64_t build_flat_lists(pt_problem* const* ps, int count, const int64_t* n, con
   for (int j = 0; j < count; ++j) {
     if (n[j] <= 0) continue;
     pt_problem* p = ps[j];
-    FlatProblem fp{};
-    fp.p = p->dev;
-    fp.t0 = p->t;
-    fp.e0 = p->e;
-    fp.n = n[j];
-    fp.m = every[j];
-    fp.wait_ns = p->wait_limit_ns;
-    fp.stall = p->stall;
+    const FlatProblem fp = flat_problem(p, n[j], every[j], tile_words);
     const int pi = (int)probs->size();
     const int words = p->L * (p->L / 2);
     const int ntile = std::max(1, (words + tile_words / 2) / tile_words);
-    fp.ntiles = ntile * p->W;
     probs->push_back(fp);
     n_max = std::max(n_max, n[j]);
     for (int w = 0; w < p->W; ++w)
@@ -429,6 +436,10 @@ struct FlatRun {
   int64_t n_max = 0;
   size_t xsmem = 0;
   int sms = 0;
+  // persistent: the lists live in memory the caller owns after prepare (a replayed graph's),
+  // allocated with cudaMalloc and filled with blocking copies; finish() leaves them alone
+  bool persistent = false;
+  unsigned long long* d_ctr = nullptr;
 
   int prepare(pt_problem* const* ps, int count, const int64_t* n, const int* every,
               cudaStream_t stream, const DeviceInfo& di, int tile_words, bool queued);
@@ -437,7 +448,7 @@ struct FlatRun {
     return launch_flat_sweep(mt, d_probs, np, j, counted[(size_t)j] != 0, xsmem, sms, st);
   }
   cudaError_t finish() {
-    if (!scratch) return cudaSuccess;
+    if (!scratch || persistent) return cudaSuccess;
     const cudaError_t err = cudaFreeAsync(scratch, st);
     scratch = nullptr;
     return err;
@@ -484,7 +495,7 @@ int FlatRun::prepare(pt_problem* const* ps, int count, const int64_t* n, const i
   const size_t fb[2] = {first[0].size() * sizeof(int), first[1].size() * sizeof(int)};
   const size_t qb = 2 * sizeof(unsigned long long);  // the two modes' queue counters
   const size_t total = al(pb) + al(tb[0]) + al(tb[1]) + al(fb[0]) + al(fb[1]) + al(qb) + 256;
-  err = cudaMallocAsync(&scratch, total, st);
+  err = persistent ? cudaMalloc(&scratch, total) : cudaMallocAsync(&scratch, total, st);
   if (err != cudaSuccess) {
     scratch = nullptr;
     return fail(PT_ENOMEM, "batch scratch: %s", cudaGetErrorString(err));
@@ -500,19 +511,22 @@ int FlatRun::prepare(pt_problem* const* ps, int count, const int64_t* n, const i
     if (fb[md]) mt[md].first = (const int*)cur;
     cur += al(fb[md]);
   }
-  unsigned long long* d_ctr = (unsigned long long*)cur;
+  d_ctr = (unsigned long long*)cur;
   mt[0].ctr = d_ctr;
   mt[1].ctr = d_ctr + 1;
-  err = cudaMemcpyAsync((void*)d_probs, probs.data(), pb, cudaMemcpyHostToDevice, st);
+  // (persistent: the memory is new and used by no queued work, so blocking copies are safe)
+  const auto copy = [&](void* dst, const void* src, size_t bytes) {
+    return persistent ? cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice)
+                      : cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+  };
+  err = copy((void*)d_probs, probs.data(), pb);
   for (int md = 0; md < 2 && err == cudaSuccess; ++md) {
     if (!tb[md]) continue;
-    err = cudaMemcpyAsync((void*)mt[md].tiles, tiles[md].data(), tb[md], cudaMemcpyHostToDevice,
-                          st);
-    if (err == cudaSuccess && fb[md])
-      err = cudaMemcpyAsync((void*)mt[md].first, first[md].data(), fb[md],
-                            cudaMemcpyHostToDevice, st);
+    err = copy((void*)mt[md].tiles, tiles[md].data(), tb[md]);
+    if (err == cudaSuccess && fb[md]) err = copy((void*)mt[md].first, first[md].data(), fb[md]);
   }
-  if (err == cudaSuccess) err = cudaMemsetAsync(d_ctr, 0, qb, st);
+  if (err == cudaSuccess)
+    err = persistent ? cudaMemset(d_ctr, 0, qb) : cudaMemsetAsync(d_ctr, 0, qb, st);
   // which sweeps are counted for at least one problem (a swap iteration or a trace row)
   counted.assign((size_t)n_max, 0);
   for (const FlatProblem& fp : probs)
@@ -554,6 +568,141 @@ SideStreams& side_streams(int device) {
   return s;
 }
 
+// ---------------------------------------------------------------------------------------
+// Replay of repeated batches from captured CUDA graphs (pt_set_batch_graphs). The launches
+// of a lock-step batch call depend only on the batch's shape: per problem, in call order,
+// L, R, the mode, the sweeps n and interval m, the phase of its exchange schedule (t mod m)
+// and whether a trace is on, plus the tile size, the schedule, the parts and the stream.
+// Everything else a kernel reads -- the sweep and swap counters, the problem's device arrays
+// -- comes from the problem descriptors, which every call copies to the device before its
+// launches. So a call whose shape was seen before copies its descriptors, clears its queue
+// counters and launches the graph captured the first time: one graph launch instead of about
+// three launches per part and sweep. The first call of a shape builds the work lists in
+// memory of their own, captures the launches (forks and joins of the parts included) and
+// instantiates the graph. A few shapes are kept per device, the least recently used dropped.
+// ---------------------------------------------------------------------------------------
+struct GraphEntry {
+  std::vector<int64_t> key;
+  cudaGraphExec_t exec = nullptr;
+  FlatRun run[kMaxBatchStreams];  // each part's lists, in the entry's own device memory
+  int parts = 0;
+  uint64_t used = 0;
+};
+constexpr size_t kGraphCacheEntries = 4;
+std::mutex g_graph_mu;
+std::vector<GraphEntry*> g_graph_cache[64];  // per device
+uint64_t g_graph_clock = 0;
+
+void free_graph_entry(GraphEntry* e) {
+  if (e->exec) cudaGraphExecDestroy(e->exec);
+  for (int g = 0; g < e->parts; ++g)
+    if (e->run[g].scratch) cudaFree(e->run[g].scratch);  // waits for work that reads it
+  delete e;
+}
+
+std::vector<int64_t> graph_key(std::vector<pt_problem*> gp[], std::vector<int64_t> gn[],
+                               std::vector<int> ge[], int parts, cudaStream_t st,
+                               int tile_words, bool queued) {
+  std::vector<int64_t> key = {(int64_t)(intptr_t)st, queued ? 1 : 0, tile_words, parts};
+  for (int g = 0; g < parts; ++g) {
+    key.push_back(-1 - g);
+    for (size_t i = 0; i < gp[g].size(); ++i) {
+      const pt_problem* p = gp[g][i];
+      const int m = ge[g][i];
+      key.insert(key.end(), {(int64_t)p->L, (int64_t)p->R, (int64_t)p->mode, gn[g][i],
+                             (int64_t)m, m > 0 ? (int64_t)(p->t % (uint64_t)m) : 0,
+                             p->dev.trace_E != nullptr ? 1 : 0});
+    }
+  }
+  return key;
+}
+
+// The batch through a cached or newly captured graph. Returns 1 (nothing done) when the
+// problems' stream cannot be captured (the legacy default stream) or is being captured by
+// the caller: the caller then launches as usual.
+int sweep_batch_graph(std::vector<pt_problem*> gp[], std::vector<int64_t> gn[],
+                      std::vector<int> ge[], int parts, cudaStream_t st, const DeviceInfo& di,
+                      int tile_words, bool queued, SideStreams* ss) {
+  // the legacy default stream cannot be captured: launch as without replay
+  if (st == nullptr || st == cudaStreamLegacy) return 1;
+  std::lock_guard<std::mutex> glk(g_graph_mu);
+  std::vector<GraphEntry*>& cache = g_graph_cache[di.device & 63];
+  const std::vector<int64_t> key = graph_key(gp, gn, ge, parts, st, tile_words, queued);
+  GraphEntry* e = nullptr;
+  for (GraphEntry* c : cache)
+    if (c->key == key) e = c;
+  cudaError_t err = cudaSuccess;
+  if (!e) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    err = cudaStreamIsCapturing(st, &cs);
+    if (err != cudaSuccess) return fail(PT_ECUDA, "batch graph: %s", cudaGetErrorString(err));
+    if (cs != cudaStreamCaptureStatusNone) return 1;
+    e = new GraphEntry;
+    e->key = key;
+    e->parts = parts;
+    int64_t n_max = 0;
+    int rc = PT_OK;
+    for (int g = 0; g < parts && !rc; ++g) {
+      e->run[g].persistent = true;
+      rc = e->run[g].prepare(gp[g].data(), (int)gp[g].size(), gn[g].data(), ge[g].data(),
+                             g == 0 ? st : ss->stream[g - 1], di, tile_words, queued);
+      n_max = std::max(n_max, e->run[g].n_max);
+    }
+    if (rc) {
+      free_graph_entry(e);
+      return rc;
+    }
+    // relaxed: a kernel's first launch in the process may load its code during the capture
+    err = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+    if (err == cudaSuccess) {
+      cudaError_t cap = cudaSuccess;
+      if (parts > 1) {
+        cap = cudaEventRecord(ss->fork, st);
+        for (int k = 0; k + 1 < parts && cap == cudaSuccess; ++k)
+          cap = cudaStreamWaitEvent(ss->stream[k], ss->fork, 0);
+      }
+      for (int64_t j = 0; j < n_max && cap == cudaSuccess; ++j)
+        for (int g = 0; g < parts && cap == cudaSuccess; ++g) cap = e->run[g].launch_sweep(j);
+      for (int k = 0; k + 1 < parts && cap == cudaSuccess; ++k) {
+        cap = cudaEventRecord(ss->join[k], ss->stream[k]);
+        if (cap == cudaSuccess) cap = cudaStreamWaitEvent(st, ss->join[k], 0);
+      }
+      cudaGraph_t graph = nullptr;
+      err = cudaStreamEndCapture(st, &graph);  // always ends the capture, also after an error
+      if (err == cudaSuccess) err = cap;
+      if (err == cudaSuccess) err = cudaGraphInstantiate(&e->exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+    }
+    if (err != cudaSuccess) {
+      free_graph_entry(e);
+      return fail(PT_ECUDA, "batch graph capture: %s", cudaGetErrorString(err));
+    }
+    if (cache.size() >= kGraphCacheEntries) {
+      auto lru = std::min_element(cache.begin(), cache.end(), [](GraphEntry* a, GraphEntry* b) {
+        return a->used < b->used;
+      });
+      free_graph_entry(*lru);
+      cache.erase(lru);
+    }
+    cache.push_back(e);
+  }
+  e->used = ++g_graph_clock;
+  // this call's descriptors (counters, device arrays) and clear queue counters, then the graph
+  for (int g = 0; g < parts && err == cudaSuccess; ++g) {
+    std::vector<FlatProblem> probs;
+    for (size_t i = 0; i < gp[g].size(); ++i)
+      if (gn[g][i] > 0) probs.push_back(flat_problem(gp[g][i], gn[g][i], ge[g][i], tile_words));
+    if (probs.empty()) continue;
+    err = cudaMemcpyAsync((void*)e->run[g].d_probs, probs.data(), probs.size() * sizeof(FlatProblem),
+                          cudaMemcpyHostToDevice, st);
+    if (err == cudaSuccess && queued)
+      err = cudaMemsetAsync(e->run[g].d_ctr, 0, 2 * sizeof(unsigned long long), st);
+  }
+  if (err == cudaSuccess) err = cudaGraphLaunch(e->exec, st);
+  if (err != cudaSuccess) return fail(PT_ECUDA, "batch graph launch: %s", cudaGetErrorString(err));
+  return PT_OK;
+}
+
 // The lock-step batch as `parts` parts of about equal work (L^2 W n each, heaviest first onto
 // the lightest part), each on its own stream: sweep j of one part runs beside sweep j of the
 // others, so one part's exchange launch, launch gaps and last tiles overlap the others' half
@@ -561,7 +710,7 @@ SideStreams& side_streams(int device) {
 // everything queued on it so far and that it waits for at the end.
 int sweep_batch_flat_parts(pt_problem* const* ps, int count, const int64_t* n, const int* every,
                            cudaStream_t st, const DeviceInfo& di, int tile_words, bool queued,
-                           int parts) {
+                           int parts, bool graphs) {
   std::vector<int> order;
   for (int j = 0; j < count; ++j)
     if (n[j] > 0) order.push_back(j);
@@ -586,6 +735,14 @@ int sweep_batch_flat_parts(pt_problem* const* ps, int count, const int64_t* n, c
   if (ss) {
     lk = std::unique_lock<std::mutex>(ss->mu);
     if (!ss->ok) return fail(PT_ECUDA, "batch side streams could not be created");
+  }
+  if (graphs && !order.empty()) {
+    const int grc = sweep_batch_graph(gp, gn, ge, parts, st, di, tile_words, queued, ss);
+    if (grc <= 0) {
+      if (grc == PT_ECUDA)
+        for (int j = 0; j < count; ++j) ps[j]->poisoned = PT_ECUDA;
+      return grc;
+    }
   }
   cudaError_t err = cudaSuccess;
   if (parts > 1) {
@@ -625,8 +782,9 @@ int sweep_batch_flat_parts(pt_problem* const* ps, int count, const int64_t* n, c
 
 int sweep_batch_flat(pt_problem* const* ps, int count, const int64_t* n, const int* every,
                      cudaStream_t st, const DeviceInfo& di, int tile_words, bool queued,
-                     int streams) {
-  return sweep_batch_flat_parts(ps, count, n, every, st, di, tile_words, queued, streams);
+                     int streams, bool graphs) {
+  return sweep_batch_flat_parts(ps, count, n, every, st, di, tile_words, queued, streams,
+                                graphs);
 }
 
 // =======================================================================================

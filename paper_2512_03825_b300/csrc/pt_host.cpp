@@ -1732,6 +1732,20 @@ int pt_get_batch_streams(int* streams) {
   return PT_OK;
 }
 
+int pt_set_batch_graphs(int on) {
+  if (on != 0 && on != 1) return fail(PT_EINVAL, "graphs = %d: 0 or 1", on);
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_batch_tuning.graphs = on;
+  return PT_OK;
+}
+
+int pt_get_batch_graphs(int* on) {
+  if (!on) return fail(PT_EINVAL, "null output");
+  std::lock_guard<std::mutex> lk(g_mu);
+  *on = g_batch_tuning.graphs;
+  return PT_OK;
+}
+
 int pt_get_batch_tile_words(int* tile_words) {
   if (!tile_words) return fail(PT_EINVAL, "null output");
   std::lock_guard<std::mutex> lk(g_mu);

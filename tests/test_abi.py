@@ -283,3 +283,16 @@ def test_empty_batches_are_no_ops(pt):
     assert lib.pt_read_batch(None, 0, None, None, None, None, None) == 0
     assert lib.pt_read_batch(None, -1, None, None, None, None, None) == pt.PT_EINVAL
     assert lib.pt_read_batch(None, 3, None, None, None, None, None) == pt.PT_EINVAL
+
+
+def test_batch_graphs_validated(pt):
+    import ctypes as C
+    g = C.c_int()
+    assert pt.lib.pt_get_batch_graphs(C.byref(g)) == 0
+    before = g.value
+    for bad in (-1, 2, 7):
+        assert pt.lib.pt_set_batch_graphs(bad) == pt.PT_EINVAL
+    assert pt.lib.pt_set_batch_graphs(1) == 0
+    assert pt.lib.pt_get_batch_graphs(C.byref(g)) == 0 and g.value == 1
+    assert pt.lib.pt_get_batch_graphs(None) == pt.PT_EINVAL
+    assert pt.lib.pt_set_batch_graphs(before) == 0

@@ -271,9 +271,10 @@ def test_autotuner_compares_equal_results(api, tuning):
     leave the problems in the same state, and applies the fastest without saving it."""
     from paper_2512_03825_b300 import autotune
     probs = W.batched_problems(n=10)
-    cands = [(0, 1, 128, 128, 1), (3, 1, 128, 1024, 1), (2, 1, 128, 256, 1), (1, 2, 64, 512, 1),
-             (0, 1, 128, 512, 3), (3, 1, 128, 512, 2)]
-    out = autotune.tune(probs, sweeps=4, every=1, candidates=cands, repeats=1, save=False)
+    cands = [(0, 1, 128, 128, 1, 0), (3, 1, 128, 1024, 1, 0), (2, 1, 128, 256, 1, 0),
+             (1, 2, 64, 512, 1, 0), (0, 1, 128, 512, 3, 0), (3, 1, 128, 512, 2, 0),
+             (0, 1, 128, 512, 2, 1), (3, 1, 128, 256, 1, 1)]
+    out = autotune.tune(probs, sweeps=4, every=1, candidates=cands, repeats=2, save=False)
     assert tuple(out["choice"].values()) in cands
     assert len(out["timings"]) == len(cands)
     assert autotune.get_tuning() == out["choice"]
@@ -351,3 +352,59 @@ def test_edge_cases_in_one_batch(api, strategy, streams):
         np.testing.assert_array_equal(g.chain_map(), o.chain_map(), err_msg=where)
         for x, y in zip(g.swap_stats(), o.swap_stats()):
             np.testing.assert_array_equal(x, y, err_msg=where)
+
+
+
+@pytest.mark.parametrize("strategy,streams", [(0, 1), (0, 3), (3, 2)])
+def test_graph_replay_matches_oracle(api, strategy, streams):
+    """Batches replayed from captured graphs (pt_set_batch_graphs): a mixed batch (both
+    modes, uneven sweeps, exchange intervals and schedule phases, a traced problem) runs
+    three calls of one shape -- the first captures, the next two replay with the problems'
+    advanced counters -- then calls of other shapes until the least recently used graph is
+    dropped, then the first shape again (captured anew). Every problem equals the oracle, the
+    trace rows included, and results equal those of launches without replay."""
+    from paper_2512_03825_b300 import autotune
+    before = autotune.get_tuning()
+    probs = mixed_problems(n=18, seed=71 + streams)
+    ns = [p.sweeps for p in probs]
+    ms = [p.every for p in probs]
+    plan = [(ns, ms), (ns, ms), (ns, ms)]
+    plan += [([k + 1] * len(probs), ms) for k in range(5)]   # five more shapes: evictions
+    plan += [(ns, ms)]
+    import torch
+    st = torch.cuda.Stream()  # replay needs a stream other than the legacy default one
+    try:
+        autotune.set_tuning(strategy, 1, 128, 128, streams, 1)
+        gs = [api.PTProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed, stream=st) for p in probs]
+        gs[2].trace_start(64)
+        for n, m in plan:
+            api.sweep_batch(gs, n, m)
+        autotune.set_tuning(strategy, 1, 128, 128, streams, 0)
+        hs = [api.PTProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed) for p in probs[:6]]
+        for n, m in plan:
+            api.sweep_batch(hs, n[:6], m[:6])
+    finally:
+        autotune.set_tuning(**before)
+    oracle.set_threads(8)
+    for j, (p, g) in enumerate(zip(probs, gs)):
+        o = oracle.OracleProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed)
+        for n, m in plan:
+            o.sweep(n[j], m[j])
+        where = "problem %d" % j
+        np.testing.assert_array_equal(g.spins(), o.spins(), err_msg=where)
+        np.testing.assert_array_equal(g.energies_int(), o.energies_int(), err_msg=where)
+        np.testing.assert_array_equal(g.chain_map(), o.chain_map(), err_msg=where)
+        for x, y in zip(g.swap_stats(), o.swap_stats()):
+            np.testing.assert_array_equal(x, y, err_msg=where)
+        if j < 6:
+            np.testing.assert_array_equal(g.spins(), hs[j].spins(), err_msg=where)
+    # the traced problem's rows, sweep by sweep across all calls (the ring keeps the last 64)
+    first, Eg, Mg = gs[2].trace()
+    o = oracle.OracleProblem(probs[2].L, probs[2].betas, J=probs[2].J, h=probs[2].h,
+                             seed=probs[2].seed)
+    rows = [o.trace(n[2], m[2]) for n, m in plan]
+    E = np.concatenate([r[0] for r in rows])
+    M = np.concatenate([r[1] for r in rows])
+    assert first >= 1 and len(Eg) == min(64, len(E))
+    np.testing.assert_array_equal(Eg, E[first - 1:first - 1 + len(Eg)])
+    np.testing.assert_array_equal(Mg, M[first - 1:first - 1 + len(Mg)])
