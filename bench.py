@@ -47,7 +47,7 @@ FLAT_TRAFFIC_BYTES = 25.978624e6 + 0.0
 FLAT_TRAFFIC_SOURCES = ("paper_2512_03825_b300/csrc/pt_device.cuh",
                         "paper_2512_03825_b300/csrc/pt_flat.cuh",
                         "paper_2512_03825_b300/csrc/pt_flat.cu")
-FLAT_TRAFFIC_SOURCE_HASH = "4e03d8d171bd67c8"
+FLAT_TRAFFIC_SOURCE_HASH = "6070d95436772318"
 
 
 def _flat_traffic():

@@ -587,6 +587,17 @@ struct GraphEntry {
   FlatRun run[kMaxBatchStreams];  // each part's lists, in the entry's own device memory
   int parts = 0;
   uint64_t used = 0;
+  // the descriptors of a call go up from page-locked host memory, two buffers used in turn;
+  // copied[b] marks when the copy that read buffer b is done (before b is written again).
+  // `launched` follows the entry's last graph launch: the next call's copies wait for it, so
+  // a call on another stream cannot overwrite descriptors a running replay still reads.
+  FlatProblem* host[2] = {nullptr, nullptr};
+  size_t host_count = 0;
+  cudaEvent_t copied[2] = {nullptr, nullptr};
+  cudaEvent_t launched = nullptr;
+  bool pending[2] = {false, false};
+  bool ever_launched = false;
+  int next = 0;
 };
 constexpr size_t kGraphCacheEntries = 4;
 std::mutex g_graph_mu;
@@ -597,6 +608,11 @@ void free_graph_entry(GraphEntry* e) {
   if (e->exec) cudaGraphExecDestroy(e->exec);
   for (int g = 0; g < e->parts; ++g)
     if (e->run[g].scratch) cudaFree(e->run[g].scratch);  // waits for work that reads it
+  for (int b = 0; b < 2; ++b) {
+    if (e->host[b]) cudaFreeHost(e->host[b]);
+    if (e->copied[b]) cudaEventDestroy(e->copied[b]);
+  }
+  if (e->launched) cudaEventDestroy(e->launched);
   delete e;
 }
 
@@ -652,6 +668,16 @@ int sweep_batch_graph(std::vector<pt_problem*> gp[], std::vector<int64_t> gn[],
       free_graph_entry(e);
       return rc;
     }
+    for (int g = 0; g < parts; ++g) e->host_count += e->run[g].probs.size();
+    for (int b = 0; b < 2 && err == cudaSuccess; ++b) {
+      err = cudaMallocHost(&e->host[b], std::max<size_t>(1, e->host_count) * sizeof(FlatProblem));
+      if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->copied[b], cudaEventDisableTiming);
+    }
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->launched, cudaEventDisableTiming);
+    if (err != cudaSuccess) {
+      free_graph_entry(e);
+      return fail(PT_ECUDA, "batch graph buffers: %s", cudaGetErrorString(err));
+    }
     // relaxed: a kernel's first launch in the process may load its code during the capture
     err = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
     if (err == cudaSuccess) {
@@ -687,18 +713,32 @@ int sweep_batch_graph(std::vector<pt_problem*> gp[], std::vector<int64_t> gn[],
     cache.push_back(e);
   }
   e->used = ++g_graph_clock;
-  // this call's descriptors (counters, device arrays) and clear queue counters, then the graph
-  for (int g = 0; g < parts && err == cudaSuccess; ++g) {
-    std::vector<FlatProblem> probs;
+  // this call's descriptors (counters, device arrays) into the next host buffer, up to the
+  // device after the entry's last replay, queue counters cleared, then the graph
+  const int b = e->next;
+  e->next ^= 1;
+  if (e->pending[b]) err = cudaEventSynchronize(e->copied[b]);  // its last copy is done
+  size_t at = 0;
+  for (int g = 0; g < parts; ++g)
     for (size_t i = 0; i < gp[g].size(); ++i)
-      if (gn[g][i] > 0) probs.push_back(flat_problem(gp[g][i], gn[g][i], ge[g][i], tile_words));
-    if (probs.empty()) continue;
-    err = cudaMemcpyAsync((void*)e->run[g].d_probs, probs.data(), probs.size() * sizeof(FlatProblem),
+      if (gn[g][i] > 0)
+        e->host[b][at++] = flat_problem(gp[g][i], gn[g][i], ge[g][i], tile_words);
+  if (err == cudaSuccess && e->ever_launched) err = cudaStreamWaitEvent(st, e->launched, 0);
+  at = 0;
+  for (int g = 0; g < parts && err == cudaSuccess; ++g) {
+    const size_t k = e->run[g].probs.size();
+    if (k == 0) continue;
+    err = cudaMemcpyAsync((void*)e->run[g].d_probs, e->host[b] + at, k * sizeof(FlatProblem),
                           cudaMemcpyHostToDevice, st);
+    at += k;
     if (err == cudaSuccess && queued)
       err = cudaMemsetAsync(e->run[g].d_ctr, 0, 2 * sizeof(unsigned long long), st);
   }
+  if (err == cudaSuccess) err = cudaEventRecord(e->copied[b], st);
+  if (err == cudaSuccess) e->pending[b] = true;
   if (err == cudaSuccess) err = cudaGraphLaunch(e->exec, st);
+  if (err == cudaSuccess) err = cudaEventRecord(e->launched, st);
+  if (err == cudaSuccess) e->ever_launched = true;
   if (err != cudaSuccess) return fail(PT_ECUDA, "batch graph launch: %s", cudaGetErrorString(err));
   return PT_OK;
 }
