@@ -109,6 +109,17 @@ def main():
         api.sweep_batch(gs, [3] * len(gs), ms)
         for q, g, n, m in zip(probs, gs, ns, ms):
             check(res, name, g, q, [("sweep", n, m), ("sweep", 3, m)])
+    # graph replay (needs a stream of its own): one capture, then replays of the same shape
+    import torch
+    st = torch.cuda.Stream()
+    for strategy, name in ((FLAT, "batch dealt, graph replay"), (QUEUE, "batch queued, graph replay")):
+        autotune.set_tuning(strategy=strategy, cluster=2, joint_min_L=24, tile_words=64,
+                            streams=2, graphs=1)
+        gs = [api.PTProblem(q.L, q.betas, J=q.J, h=q.h, seed=q.seed, stream=st) for q in probs]
+        for _ in range(3):
+            api.sweep_batch(gs, [3] * len(gs), ms)
+        for q, g, m in zip(probs, gs, ms):
+            check(res, name, g, q, [("sweep", 3, m)] * 3)
     autotune.set_tuning(strategy=QUEUE, cluster=2, joint_min_L=24, tile_words=64)
     gs = [api.PTProblem(q.L, q.betas, J=q.J, h=q.h, seed=q.seed) for q in probs]
     api.sweep_batch_static(gs, ns, ms)
