@@ -408,3 +408,40 @@ def test_graph_replay_matches_oracle(api, strategy, streams):
     assert first >= 1 and len(Eg) == min(64, len(E))
     np.testing.assert_array_equal(Eg, E[first - 1:first - 1 + len(Eg)])
     np.testing.assert_array_equal(Mg, M[first - 1:first - 1 + len(Mg)])
+
+
+def test_graph_replay_with_new_problems_and_streams(api):
+    """A replayed graph serves any problems of its shape: each call here creates fresh
+    problems (new device arrays, the same shapes), alternating between two streams, and the
+    problems of every call equal the oracle -- the descriptors, not the graph, carry the
+    problems."""
+    import torch
+    from paper_2512_03825_b300 import autotune
+    before = autotune.get_tuning()
+    probs = mixed_problems(n=10, seed=404)
+    ns = [max(1, p.sweeps) for p in probs]
+    ms = [p.every for p in probs]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    finals = []
+    try:
+        autotune.set_tuning(0, 1, 128, 128, 2, 1)
+        for k in range(4):
+            st = streams[k % 2]
+            gs = [api.PTProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed + 100 * k, stream=st)
+                  for p in probs]
+            api.sweep_batch(gs, ns, ms)
+            finals.append([(g.spins(), g.energies_int(), g.chain_map()) for g in gs])
+            for g in gs:
+                g.close()
+    finally:
+        autotune.set_tuning(**before)
+    oracle.set_threads(8)
+    for k in range(4):
+        for j, p in enumerate(probs):
+            o = oracle.OracleProblem(p.L, p.betas, J=p.J, h=p.h, seed=p.seed + 100 * k)
+            o.sweep(ns[j], ms[j])
+            s, e, c = finals[k][j]
+            where = "call %d problem %d" % (k, j)
+            np.testing.assert_array_equal(s, o.spins(), err_msg=where)
+            np.testing.assert_array_equal(e, o.energies_int(), err_msg=where)
+            np.testing.assert_array_equal(c, o.chain_map(), err_msg=where)
