@@ -16,10 +16,11 @@
 // shared-memory copy of the temperature map, and rebuilds its plane's thresholds. Only block 0
 // writes the swap statistics; the maps and the plane tables go back to global memory at the
 // end of the launch. When an observable trace is on, every sweep counts, and block 0 writes
-// the sweep's row. Two count buffers alternate between counted sweeps: block 0 clears the
-// other one while the current one is being read.
+// the sweep's row. Three count buffers take turns between counted sweeps: after the barrier
+// of one, block 0 clears the buffer of the counted sweep after next, which every CTA has
+// finished reading and none writes before another grid barrier.
 //
-// The barrier counter and both count buffers are cleared by the host before each launch.
+// The barrier counter and the count buffers are cleared by the host before each launch.
 // A barrier wait that exceeds its time limit stores PT_ETIMEOUT in the status word; every
 // waiting CTA that sees a non-zero status (or runs out of time itself) leaves the kernel.
 //
@@ -379,8 +380,8 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
   };
   const int y0 = q0 / half, i0 = q0 - y0 * half;
   const int dy = step / half, di = step - dy * half;
-  uint32_t* const cnt_base = p.cnt + 2 * W * 32;  // two buffers of [2][W * 32]
-  unsigned* const bar = p.cnt + 6 * W * 32;
+  uint32_t* const cnt_base = p.cnt + 2 * W * 32;  // three buffers of [2][W * 32]
+  unsigned* const bar = p.cnt + 8 * W * 32;
 
   uint32_t alw0 = 0, alw1 = 0, used = 0;
   // generic: the classes with dE > 0, when there are exactly five of them (each trial is
@@ -433,6 +434,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
     }
     return sync_all(extra);
   };
+  bool tail_met = false;  // the CTAs met at a grid barrier after the last sweep done
   uint32_t* const band_a1 = plane_g + (size_t)p.L * half;  // colour 1 in the spin array
   uint32_t* const band_b1 = BAND ? p.band_c1 + (size_t)w * p.L * half : nullptr;
   for (int j = 0; j < a.n; ++j) {
@@ -467,13 +469,14 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
         half_pass<MODE, false, LOCAL>(p, plane, w, 1, t, a.rk, bt, q0, step, y0, i0, dy, di,
                                       thr, alw0, alw1, used, gen, five, cls5, false, U, N);
       band_last = j;
+      tail_met = false;
       if (j + 1 == a.n) break;  // the kernel's end orders this half sweep before what follows
       if (!sync_half(BAND ? stall0 : 0u)) return flush();
       continue;
     }
-    // a swap iteration or a trace row follows: count this sweep into buffer `counted & 1`
-    // (the buffers alternate between counted sweeps)
-    uint32_t* const cb = cnt_base + (counted & 1) * 2 * W * 32;
+    // a swap iteration or a trace row follows: count this sweep into buffer `counted % 3`
+    // (the three buffers take turns between counted sweeps)
+    uint32_t* const cb = cnt_base + (counted % 3) * 2 * W * 32;
     U.zero();
     N.zero();
     if (BAND)
@@ -503,6 +506,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
                   acc[1][threadIdx.x]);
     }
     if (!sync_all(BAND ? stall0 : 0u)) return flush();
+    tail_met = true;  // every CTA is done with sweep j
     if (ex) {
       if (solo)
         exchange_local<true>(p, e, &acc[0][0], sot, tos, true);
@@ -522,10 +526,13 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
           p.trace_M[at] = 2 * ones - L2;
         }
       }
-      // the other buffer was last read after the previous counted sweep, before this
-      // sweep's first barrier; it is next written after the next sweep's first barrier
+      // buffer (counted + 2) % 3 was last read after counted sweep counted - 1, which every
+      // CTA finished before it arrived at this sweep's barrier, and is next written in
+      // counted sweep counted + 2, after at least one more grid barrier. (With two buffers
+      // the band form, whose only barrier ends the sweep, could count the next sweep into
+      // the buffer before block 0 cleared it.)
       if (!solo) {
-        uint32_t* const nb = cnt_base + ((counted + 1) & 1) * 2 * W * 32;
+        uint32_t* const nb = cnt_base + ((counted + 2) % 3) * 2 * W * 32;
         for (int q = threadIdx.x; q < 2 * W * 32; q += blockDim.x) nb[q] = 0;
       }
     }
@@ -537,6 +544,14 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
     }
   }
 
+  // BAND: when the last sweep's index is even, it stored colour 1 in the other copy, and the
+  // spin array still holds the colour 1 that the other bands read for their halo rows in that
+  // sweep (its c1_src). Only after every CTA is done with the sweep may a band copy its new
+  // colour 1 back into the spin array. (A launch whose last sweep ends with a swap iteration
+  // or a trace row has met at that sweep's barrier already; one that ends without must meet
+  // here.)
+  if (BAND && band_last >= 0 && (band_last & 1) == 0 && !tail_met)
+    if (!sync_all(0u)) return flush();
   flush();
   if (exchanged) {
     if (blockIdx.x == 0)

@@ -52,9 +52,9 @@ struct PersistPlan {
 };
 
 // The device count buffer holds, in 32-bit words: [2][W * 32] for the per-launch kernels,
-// then two [2][W * 32] buffers for the persistent kernel and its barrier counter.
-inline size_t count_words(int W) { return (size_t)6 * W * 32 + 16; }
-inline size_t persist_clear_bytes(int W) { return ((size_t)4 * W * 32 + 1) * 4; }
+// then three [2][W * 32] buffers for the persistent kernel and its barrier counter.
+inline size_t count_words(int W) { return (size_t)8 * W * 32 + 16; }
+inline size_t persist_clear_bytes(int W) { return ((size_t)6 * W * 32 + 1) * 4; }
 
 size_t persist_smem(int R, int mode);
 // Dynamic shared memory of a launch: persist_smem, then (kFormLocal) the plane's L*L words

@@ -290,3 +290,18 @@ def test_plain_path_tuner_compares_equal_results(api, tmp_path, monkeypatch):
     o.sweep(30, 2)
     assert_same(g, o, "tuned shape")
     assert autotune.apply_single(g, 48, p.R, p.J, p.h) is None
+
+
+@pytest.mark.parametrize("L,R,m", [(128, 32, 3), (128, 32, 0), (64, 33, 3), (96, 40, 2)])
+def test_bands_launch_ends_and_count_buffers(api, L, R, m):
+    """Band-form launches of many lengths, ending on even and odd sweep indices, with and
+    without a swap iteration on their last sweep: a band copies its last colour 1 back into
+    the spin array only after every band is done reading it, and the three count buffers
+    take turns without one being counted into before it is cleared."""
+    prob = W.Problem(L=L, betas=W.linear_ladder(0.2, 0.7, R), seed=0xBE00 + L + R)
+    g, o = make(api, prob, BANDS, 1)
+    for k in (1, 19, 2, 4, 7, 6, 3, 10):
+        g.sweep(k, m)
+        o.sweep(k, m)
+        np.testing.assert_array_equal(g.spins(), o.spins(), err_msg="after %d more" % k)
+    assert_same(g, o, "bands L%d R%d m%d" % (L, R, m))
