@@ -427,15 +427,22 @@ struct BitCounter {
   // sum over the warp (every lane ends with the total), then lane b returns the count of
   // slot bit b. Counts must fit NB bits after the sum.
   __device__ __forceinline__ uint32_t warp_total_for_lane() {
+    // before round r (r = 0..4) a lane's counts are below 2^(NT + r): levels NT + r and up
+    // are zero on both sides, so level NT + r takes the carry and the rest stay zero
 #pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
+    for (int r = 0; r < 5; ++r) {
+      const int off = 16 >> r;
       uint32_t carry = 0;
 #pragma unroll
       for (int l = 0; l < NB; ++l) {
-        const uint32_t o = __shfl_xor_sync(0xffffffffu, c[l], off);
-        const uint32_t sum = c[l] ^ o ^ carry;
-        carry = maj3(c[l], o, carry);
-        c[l] = sum;
+        if (l < NT + r) {
+          const uint32_t o = __shfl_xor_sync(0xffffffffu, c[l], off);
+          const uint32_t sum = c[l] ^ o ^ carry;
+          carry = maj3(c[l], o, carry);
+          c[l] = sum;
+        } else if (l == NT + r) {
+          c[l] = carry;
+        }
       }
     }
     const uint32_t lane = threadIdx.x & 31u;
