@@ -437,6 +437,10 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
   bool tail_met = false;  // the CTAs met at a grid barrier after the last sweep done
   uint32_t* const band_a1 = plane_g + (size_t)p.L * half;  // colour 1 in the spin array
   uint32_t* const band_b1 = BAND ? p.band_c1 + (size_t)w * p.L * half : nullptr;
+  // sweeps left before the next one that a swap iteration follows (0: this one): one 64-bit
+  // remainder per launch instead of one per sweep (measured: L = 16, R = 8 1.41 -> 1.27 us
+  // per sweep, L = 128, R = 32 5.90 -> 5.75 us)
+  int until_ex = a.m > 0 ? (int)((uint64_t)(a.m - 1) - a.t0 % (uint64_t)a.m) : -1;
   for (int j = 0; j < a.n; ++j) {
     const uint64_t t = a.t0 + (uint64_t)j;
     // BAND: sweep j stores colour 1 in the spin array when j is odd, in the other copy when
@@ -459,7 +463,8 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(const __grid_con
                                     alw0, alw1, used, gen, five, cls5, false, U, N);
       if (!sync_half(stall0)) return flush();
     }
-    const bool ex = a.m > 0 && (t + 1) % (uint64_t)a.m == 0;
+    const bool ex = until_ex == 0;  // (t + 1) % m == 0
+    if (a.m > 0) until_ex = ex ? a.m - 1 : until_ex - 1;
     if (!ex && !trace) {
       if (BAND)
         band_pass<MODE, 1, false>(p, w, t, a.rk, bt, by0, bH, C0, C1, c1_src, c1_dst,
