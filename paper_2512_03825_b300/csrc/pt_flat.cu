@@ -208,11 +208,15 @@ size_t flat_exchange_smem(int R, int mode) {
                       (mode == kModeFerro ? 2 : kClasses) * sizeof(uint64_t));
 }
 
+// Threads of an exchange block: one per slot of the batch's widest problem (whole warps, at
+// most kFlatThreads), so that the block barriers of small ladders span few warps.
+int flat_exchange_threads(int W) { return std::min(kFlatThreads, 32 * std::max(1, W)); }
+
 // The exchange launch of sweep j with `smem` bytes of shared memory (the largest problem's
-// need, flat_exchange_smem).
+// need, flat_exchange_smem) and `threads` threads per block (flat_exchange_threads).
 cudaError_t launch_flat_exchange(const FlatProblem* d_probs, int np, int64_t j, size_t smem,
-                                 int sms, cudaStream_t st) {
-  k_flat_exchange<<<std::min(np, sms * 8), kFlatThreads, smem, st>>>(d_probs, np, j);
+                                 int threads, int sms, cudaStream_t st) {
+  k_flat_exchange<<<std::min(np, sms * 8), threads, smem, st>>>(d_probs, np, j);
   return cudaGetLastError();
 }
 
@@ -246,13 +250,14 @@ cudaError_t launch_flat_half(ModeTiles& mt, const FlatProblem* d_probs, int colo
 // The launches of sweep j: half sweep 0, half sweep 1 (counting when `counted`: some
 // problem's swap iteration or trace row follows), then the exchange step when counted.
 cudaError_t launch_flat_sweep(ModeTiles mt[2], const FlatProblem* d_probs, int np, int64_t j,
-                              bool counted, size_t xsmem, int sms, cudaStream_t st) {
+                              bool counted, size_t xsmem, int xthreads, int sms,
+                              cudaStream_t st) {
   cudaError_t err = launch_flat_half<kModeFerro, false>(mt[0], d_probs, 0, j, st);
   if (err == cudaSuccess) err = launch_flat_half<kModeGeneric, false>(mt[1], d_probs, 0, j, st);
   if (counted) {
     if (err == cudaSuccess) err = launch_flat_half<kModeFerro, true>(mt[0], d_probs, 1, j, st);
     if (err == cudaSuccess) err = launch_flat_half<kModeGeneric, true>(mt[1], d_probs, 1, j, st);
-    if (err == cudaSuccess) err = launch_flat_exchange(d_probs, np, j, xsmem, sms, st);
+    if (err == cudaSuccess) err = launch_flat_exchange(d_probs, np, j, xsmem, xthreads, sms, st);
   } else {
     if (err == cudaSuccess) err = launch_flat_half<kModeFerro, false>(mt[0], d_probs, 1, j, st);
     if (err == cudaSuccess) err = launch_flat_half<kModeGeneric, false>(mt[1], d_probs, 1, j, st);
@@ -435,6 +440,7 @@ struct FlatRun {
   int np = 0;
   int64_t n_max = 0;
   size_t xsmem = 0;
+  int xthreads = 32;
   int sms = 0;
   // persistent: the lists live in memory the caller owns after prepare (a replayed graph's),
   // allocated with cudaMalloc and filled with blocking copies; finish() leaves them alone
@@ -445,7 +451,8 @@ struct FlatRun {
               cudaStream_t stream, const DeviceInfo& di, int tile_words, bool queued);
   cudaError_t launch_sweep(int64_t j) {
     if (j >= n_max) return cudaSuccess;
-    return launch_flat_sweep(mt, d_probs, np, j, counted[(size_t)j] != 0, xsmem, sms, st);
+    return launch_flat_sweep(mt, d_probs, np, j, counted[(size_t)j] != 0, xsmem, xthreads, sms,
+                             st);
   }
   cudaError_t finish() {
     if (!scratch || persistent) return cudaSuccess;
@@ -535,8 +542,10 @@ int FlatRun::prepare(pt_problem* const* ps, int count, const int64_t* n, const i
           (fp.m > 0 && (fp.t0 + (uint64_t)j + 1) % (uint64_t)fp.m == 0))
         counted[(size_t)j] = 1;
   np = (int)probs.size();
-  for (const FlatProblem& fp : probs)
+  for (const FlatProblem& fp : probs) {
     xsmem = std::max(xsmem, flat_exchange_smem(fp.p.R, fp.p.mode));
+    xthreads = std::max(xthreads, flat_exchange_threads(fp.p.W));
+  }
   if (err == cudaSuccess) err = flat_exchange_prepare(xsmem);
   if (err != cudaSuccess) return fail(PT_ECUDA, "flat batch set-up: %s", cudaGetErrorString(err));
   return PT_OK;
@@ -1106,8 +1115,11 @@ int sweep_batch_static(pt_problem* const* ps, int count, const int64_t* n, const
   if (err == cudaSuccess) err = cudaStreamSynchronize(st);
   const FlatProblem* d_probs = (const FlatProblem*)base;
   size_t xsmem = 0;
-  for (int k = 0; k < np; ++k)
+  int xthreads = 32;
+  for (int k = 0; k < np; ++k) {
     xsmem = std::max(xsmem, flat_exchange_smem(g_sp_probs[k].p.R, g_sp_probs[k].p.mode));
+    xthreads = std::max(xthreads, flat_exchange_threads(g_sp_probs[k].p.W));
+  }
   if (err == cudaSuccess) err = flat_exchange_prepare(xsmem);
   for (int64_t j = 0; j < n_max && err == cudaSuccess; ++j) {
     bool ex = false;  // counted for at least one problem (a swap iteration or a trace row)
@@ -1116,7 +1128,7 @@ int sweep_batch_static(pt_problem* const* ps, int count, const int64_t* n, const
       ex = j < fp.n && (fp.p.trace_E != nullptr ||
                         (fp.m > 0 && (fp.t0 + (uint64_t)j + 1) % (uint64_t)fp.m == 0));
     }
-    err = launch_flat_sweep(mt, d_probs, np, j, ex, xsmem, di.sms, st);
+    err = launch_flat_sweep(mt, d_probs, np, j, ex, xsmem, xthreads, di.sms, st);
   }
   if (err != cudaSuccess) {
     for (int j = 0; j < count; ++j) ps[j]->poisoned = PT_ECUDA;
